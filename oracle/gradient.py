@@ -1,0 +1,53 @@
+"""Workload runner and finite-difference gradient (oracle; test infrastructure).
+
+``run_candidate`` integrates one pulse candidate from |g> and from |e> with
+the low-rank oracle (Eq. S5) and returns the readout signals, populations and
+the assignment error (Sec. S3.A). Trajectory 2c is |g>, 2c+1 is |e>; the
+initial state of trajectory j uses ``init_state.initial_state(..., traj=j)``.
+
+``fd_gradient`` is the central finite difference of the assignment error with
+respect to the pulse parameters, step h_i = rel * |theta_i| (rel = 1e-4).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import init_state, lowrank, pulse, signal
+from .model import Model
+
+
+def run_candidate(wl, cand_index: int, n_steps=None, pop_every=1, theta=None,
+                  model=None):
+    cand = wl.candidates[cand_index]
+    p = cand.model
+    mdl = model if model is not None else Model.from_params(p)
+    n_steps = wl.n_steps if n_steps is None else n_steps
+    tau = wl.tau
+    th = cand.pulse.p if theta is None else tuple(theta)
+    coef = pulse.coefficient(cand.pulse.kind, th, tau)
+    res = {}
+    for lvl, tag in ((0, "g"), (1, "e")):
+        traj = 2 * cand_index + lvl
+        psi_index = mdl.basis_index((lvl,) + (0,) * (len(p.dims) - 1))
+        m0 = init_state.initial_state(mdl.N, cand.M, psi_index, wl.eps,
+                                      wl.init_seed, traj)
+        res[tag] = lowrank.integrate(m0, mdl, coef, wl.dt, n_steps, pop_every)
+    res["eps_a"] = signal.assignment_error(res["g"]["beta"], res["e"]["beta"],
+                                           wl.dt, p.kappa, p.gamma, wl.eta)
+    return res
+
+
+def fd_gradient(wl, cand_index: int, n_steps=None, rel=1e-4):
+    cand = wl.candidates[cand_index]
+    mdl = Model.from_params(cand.model)
+    theta = np.array(cand.pulse.p, dtype=float)
+    grad = np.zeros_like(theta)
+    for i in range(theta.size):
+        h = rel * abs(theta[i]) if theta[i] != 0.0 else rel
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        ep = run_candidate(wl, cand_index, n_steps, theta=tp, model=mdl)["eps_a"]
+        em = run_candidate(wl, cand_index, n_steps, theta=tm, model=mdl)["eps_a"]
+        grad[i] = (ep - em) / (2.0 * h)
+    return grad
