@@ -1,0 +1,206 @@
+/*
+ * lr.h - C ABI of the GB300 low-rank Lindblad readout library.
+ *
+ * The library time-integrates the low-rank ansatz rho = Z Z^dag (Z complex,
+ * N x M, M << N) under the non-stochastic matrix Schroedinger equation of
+ * Sec. S1.A (Eq. S5):
+ *
+ *     dZ/dt = -i H(t) Z + O[Z],
+ *     O[Z]  = 1/2 sum_k [ L_k Z (Z^+ L_k Z)^dag - L_k^dag L_k Z ],
+ *     Z^+   = (Z^dag Z)^{-1} Z^dag            (Moore-Penrose inverse),
+ *
+ * for the driven transmon-resonator(-filter) readout model of Eq. 1 / Eq. 2,
+ * in the bare-mode Duffing form without the rotating-wave approximation:
+ *
+ *     H(t) = wq b^dag b + (alpha/2) b^dag b^dag b b + wr a^dag a
+ *            + g (b + b^dag)(a + a^dag)
+ *            [ + wf f^dag f + J (a + a^dag)(f + f^dag) ]
+ *            + Omega(t) cos(w_d t + phi) (r + r^dag),
+ *     L_1 = sqrt(kappa) r,   L_2 = sqrt(gamma) b,
+ *
+ * where r, the readout mode, is the last mode (a with two modes, the filter
+ * f with three). Time stepping is classical fixed-step RK4. Observables are
+ * the readout signal beta(t) = tr(rho r) (Fig. 2), transmon level
+ * populations, the readout-mode photon number tr(rho r^dag r), tr rho, and
+ * the assignment error of Sec. S3.A (Eqs. S-SNR, S-separation_error,
+ * S-assignment_error):
+ *
+ *     SNR   = sqrt(2 eta kappa int_0^tau |beta_e - beta_g|^2 dt),
+ *     eps_a = 1/2 erfc(SNR/2) + tau gamma / 2.
+ *
+ * Units: ns, rad/ns, 1/ns.
+ *
+ * Work is organised in *candidates* (one pulse each). Every candidate c owns
+ * two trajectories: 2c starts from the transmon ground state |g,0,0> and
+ * 2c+1 from the first excited state |e,0,0> (Eq. S(initial states)).
+ *
+ * Memory ownership: the context (host) is allocated by lr_create and freed
+ * by lr_destroy. The library never allocates device memory: every device
+ * buffer lives in one caller-owned workspace (e.g. a torch tensor's storage)
+ * bound with lr_bind_workspace, which must stay alive and unmodified while
+ * the context uses it. Host buffers passed to the calls are owned by the
+ * caller and only read/written during the call.
+ *
+ * Errors: every call returns an lr_status; nothing crosses the ABI as an
+ * exception. lr_last_error() gives a human-readable message for the last
+ * failing call on a context. Device-side failures (Cholesky breakdown,
+ * non-finite values, a device wait that ran out) set an error word in the
+ * workspace; lr_observables and lr_sync read it and return the status.
+ *
+ * Streams: `stream` arguments are cudaStream_t values passed as void*
+ * (NULL = the legacy default stream). Calls marked "async" only enqueue work.
+ *
+ * Threading: a context is not thread-safe; distinct contexts are independent.
+ * Determinism: with the same inputs, seed and options, results are bitwise
+ * identical from run to run (all reductions use a fixed order).
+ */
+#ifndef LR_H
+#define LR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LR_ABI_VERSION 1
+#define LR_MAX_RANK 32      /* largest supported rank M */
+#define LR_MAX_NT 16        /* largest supported transmon truncation N_t */
+
+typedef struct lr_ctx lr_ctx;
+
+typedef enum {
+  LR_OK = 0,
+  LR_ERR_ARG = 1,         /* invalid argument: null pointer, size or value out of range */
+  LR_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+  LR_ERR_NOMEM = 3,       /* host allocation failed */
+  LR_ERR_WORKSPACE = 4,   /* no workspace bound, or it is too small or misaligned */
+  LR_ERR_NOT_PD = 5,      /* Gram matrix Z^dag Z not positive definite (Cholesky breakdown) */
+  LR_ERR_NONFINITE = 6,   /* NaN/Inf reached the state or the readout signal */
+  LR_ERR_TIMEOUT = 7,     /* a device-side wait exceeded its iteration budget */
+  LR_ERR_STATE = 8,       /* call out of order (e.g. integrate before set_pulse) */
+  LR_ERR_UNSUPPORTED = 9  /* configuration not supported by the selected engine */
+} lr_status;
+
+/* Arithmetic of the bulk state. FP64: complex128 everywhere.
+ * FP32_G64: Z, the operator apply, the projection term and the RK4 stages in
+ * complex64; the Gram matrix Z^dag Z (exact FP32 products, FP64-class
+ * double-word accumulation), its Cholesky factor, the solves and the readout
+ * signal in FP64. */
+typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1 } lr_precision;
+
+/* PLAIN: straightforward HBM-resident kernels, several launches per RK4
+ * stage (the reference GPU path). FUSED: one persistent launch per
+ * integrate call, state resident on chip. AUTO picks FUSED when supported. */
+typedef enum { LR_ENGINE_AUTO = 0, LR_ENGINE_PLAIN = 1, LR_ENGINE_FUSED = 2 } lr_engine;
+
+typedef struct {
+  int n_modes;        /* 2: transmon x resonator; 3: transmon x resonator x filter */
+  int dims[3];        /* N_t (<= LR_MAX_NT), N_r, N_f; dims[2] ignored when n_modes == 2 */
+  double wq, alpha;   /* transmon frequency and anharmonicity [rad/ns] */
+  double wr, wf;      /* resonator / filter frequency [rad/ns] (wf ignored with 2 modes) */
+  double g, J;        /* transmon-resonator / resonator-filter coupling [rad/ns] */
+  double kappa;       /* decay rate of the readout (last) mode [1/ns] */
+  double gamma;       /* transmon decay rate 1/T1 [1/ns] */
+} lr_model;
+
+/* Pulse envelope Omega(t), Sec. S2.C, logistic f(t,t0,s) = 1/(1+exp(-(t-t0)/s)):
+ *  kind 0 flat-top:    p = {A, w_d, t_r, phi};  s = t_r/5, t0 = 6 s,
+ *                      Omega = A f(t,t0,s) [1 - f(t,tau-t0,s)].
+ *  kind 1 two-segment: p = {A1, A2, t_sw, t_rise, t_fall, t_sm, w_d, phi};
+ *                      Omega = A1 f(t,6 t_rise/5,t_rise/5)
+ *                            + (A2-A1) f(t,t_sw,t_sm/5)
+ *                            - A2 f(t,tau-6 t_fall/5,t_fall/5).
+ *  The term in H is Omega(t) cos(w_d t + phi) (r + r^dag). */
+typedef struct {
+  int kind;
+  double p[8];
+} lr_pulse;
+
+typedef struct {
+  lr_precision precision;
+  lr_engine engine;
+  long max_steps;     /* capacity: largest total number of RK4 steps per pulse run */
+  int pop_every;      /* record populations, photons, trace every pop_every steps (>= 1) */
+  double eta;         /* measurement efficiency in the SNR (the paper uses 0.6) */
+} lr_options;
+
+typedef struct {
+  int n_cand, n_traj;
+  int nt_max;         /* largest N_t in the batch: pops row length */
+  long n_rec;         /* recorded points per trajectory: max_steps / pop_every + 1 */
+  long max_steps;
+  long step;          /* RK4 steps taken since lr_set_initial / lr_set_state */
+  lr_engine engine;   /* engine actually used */
+  int team_size;      /* CTAs per trajectory (FUSED) */
+} lr_info;
+
+/* Create a context for n_cand candidates (2 n_cand trajectories).
+ * models[c], ranks[c]: model and rank M (1 <= M <= min(N, LR_MAX_RANK)) of
+ * candidate c. Host arrays are copied. No device memory is touched. */
+lr_status lr_create(int n_cand, const lr_model* models, const int* ranks,
+                    const lr_options* opt, lr_ctx** out);
+
+/* Device bytes the context needs in its workspace. */
+lr_status lr_workspace_size(const lr_ctx* ctx, size_t* bytes);
+
+/* Bind caller-owned device memory (>= lr_workspace_size bytes, 256-byte
+ * aligned). The library keeps the pointer; it does not free it. */
+lr_status lr_bind_workspace(lr_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Set the pulse of every candidate (pulses[n_cand], host) and the pulse
+ * duration tau [ns] that places the falling edges. Async (copies from a
+ * context-owned staging buffer). */
+lr_status lr_set_pulse(lr_ctx* ctx, const lr_pulse* pulses, double tau, void* stream);
+
+/* Fixed-rank initial condition of Sec. S1.A on the device:
+ * Z(0) = (sqrt(1-(M-1) eps) psi, sqrt(eps) q_2, ..., sqrt(eps) q_M), with
+ * psi = |g or e, 0, 0> and q_j the Gram-Schmidt orthonormalisation of
+ * (psi, xi_2, ..., xi_M), xi_j complex Gaussian vectors drawn by SplitMix64 +
+ * Box-Muller (per-trajectory seed = SplitMix64 output number `traj` of
+ * `seed`; pair p = (j-1) N + n uses uniforms 2p and 2p+1, u = ((x>>11)+1)/2^53,
+ * xi = sqrt(-2 ln u1) exp(2 pi i u2)). Resets the step counter and the
+ * recorded observables. 0 < eps, (M-1) eps < 1. Async. */
+lr_status lr_set_initial(lr_ctx* ctx, uint64_t seed, double eps, void* stream);
+
+/* Replace the state of one trajectory with host_Z (complex, row-major
+ * [N][M] as interleaved (re, im) doubles) and set the step counter to
+ * `step` (for resuming a run; all trajectories share one counter).
+ * Synchronous. */
+lr_status lr_set_state(lr_ctx* ctx, int traj, const double* host_Z, long step, void* stream);
+
+/* Copy the current state of one trajectory to host_Z (layout as above).
+ * Synchronous. */
+lr_status lr_get_state(lr_ctx* ctx, int traj, double* host_Z, void* stream);
+
+/* Advance every trajectory by n_steps RK4 steps of size dt from the current
+ * step counter (t = step * dt), recording beta at every step and the other
+ * observables every pop_every steps, then recompute eps_a of every candidate
+ * over [0, step*dt]. dt must not change within one pulse run. Async. */
+lr_status lr_integrate(lr_ctx* ctx, double dt, long n_steps, void* stream);
+
+/* Copy recorded observables out (any pointer may be NULL to skip it; each
+ * may be host or device memory). Layouts, per trajectory j = 0..n_traj-1:
+ *   beta  [n_traj][max_steps+1][2]   (re, im) of tr(rho r) at t = n dt
+ *   pops  [n_traj][n_rec][nt_max]    transmon level populations (zero padded)
+ *   nphot [n_traj][n_rec]            tr(rho r^dag r)
+ *   trace [n_traj][n_rec]            tr(rho)
+ *   eps_a [n_cand]                   assignment error over [0, step dt]
+ * Only entries up to the current step are meaningful. Synchronises the
+ * stream and returns the device error word's status. */
+lr_status lr_observables(lr_ctx* ctx, double* beta, double* pops, double* nphot,
+                         double* trace, double* eps_a, void* stream);
+
+/* Synchronise the stream and return the device error word's status. */
+lr_status lr_sync(lr_ctx* ctx, void* stream);
+
+lr_status lr_query(const lr_ctx* ctx, lr_info* info);
+const char* lr_status_string(lr_status s);
+const char* lr_last_error(const lr_ctx* ctx);
+void lr_destroy(lr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LR_H */

@@ -1,0 +1,174 @@
+// Kernels shared by the engines: fixed-rank initial state (Sec. S1.A),
+// assignment-error epilogue (Sec. S3.A) and state precision conversion.
+#include "lr_internal.cuh"
+
+namespace lr {
+
+constexpr int IT = 512;   // threads of the initial-state kernel
+constexpr int ET = 256;   // threads of the epilogue kernel
+constexpr unsigned long long GOLDEN = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 (Steele, Lea & Flood 2014): k-th output for a seed.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long k) {
+  return mix64(seed + (k + 1ull) * GOLDEN);
+}
+__device__ __forceinline__ double uniform_open0(unsigned long long seed, unsigned long long k) {
+  return ((double)(splitmix64(seed, k) >> 11) + 1.0) * 0x1.0p-53;
+}
+
+// Fixed-order block reduction (deterministic for a fixed block size).
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < NT / 32; ++w) r += sh[w];
+    sh[32] = r;
+  }
+  __syncthreads();
+  const double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// One block per trajectory: Gaussian padding columns, modified Gram-Schmidt
+// (two passes) against psi and each other, weights 1-(M-1)eps and eps.
+// Works in FP64 in `W` (layout of the state), writes the state as T2.
+template <typename T2>
+__global__ void __launch_bounds__(IT) initial_state_kernel(const TrajDev* __restrict__ traj, double2* __restrict__ Wbase,
+                                                           T2* __restrict__ Zbase, unsigned long long seed, double eps) {
+  __shared__ double sh[33];
+  const int tj = blockIdx.x;
+  const TrajDev d = traj[tj];
+  const int N = d.N, M = d.M, ld = d.ld;
+  double2* W = Wbase + d.z_off;
+  T2* Z = Zbase + d.z_off;
+  const int psi = d.level0 * d.Nr * d.Nf;
+  const unsigned long long ts = splitmix64(seed, (unsigned long long)tj);
+  for (int n = threadIdx.x; n < N; n += IT) {
+    W[(size_t)n * ld] = mk(n == psi ? 1.0 : 0.0, 0.0);
+    for (int j = 1; j < M; ++j) {
+      const unsigned long long pidx = (unsigned long long)(j - 1) * N + n;
+      const double u1 = uniform_open0(ts, 2ull * pidx), u2 = uniform_open0(ts, 2ull * pidx + 1ull);
+      const double r = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      W[(size_t)n * ld + j] = mk(r * cs, r * sn);
+    }
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 1; j < M; ++j) {
+      for (int i = 0; i < j; ++i) {
+        double re = 0.0, im = 0.0;
+        for (int n = threadIdx.x; n < N; n += IT) {
+          const double2 a = W[(size_t)n * ld + i], b = W[(size_t)n * ld + j];   // conj(a) b
+          re += a.x * b.x + a.y * b.y;
+          im += a.x * b.y - a.y * b.x;
+        }
+        re = block_sum<IT>(re, sh);
+        im = block_sum<IT>(im, sh);
+        for (int n = threadIdx.x; n < N; n += IT) {
+          const double2 a = W[(size_t)n * ld + i], b = W[(size_t)n * ld + j];
+          W[(size_t)n * ld + j] = mk(b.x - (re * a.x - im * a.y), b.y - (re * a.y + im * a.x));
+        }
+        __syncthreads();
+      }
+      double nn = 0.0;
+      for (int n = threadIdx.x; n < N; n += IT) {
+        const double2 b = W[(size_t)n * ld + j];
+        nn += b.x * b.x + b.y * b.y;
+      }
+      nn = block_sum<IT>(nn, sh);
+      const double inv = 1.0 / sqrt(nn);
+      for (int n = threadIdx.x; n < N; n += IT) {
+        const double2 b = W[(size_t)n * ld + j];
+        W[(size_t)n * ld + j] = mk(b.x * inv, b.y * inv);
+      }
+      __syncthreads();
+    }
+  }
+  const double w0 = sqrt(1.0 - (M - 1) * eps), we = sqrt(eps);
+  for (int n = threadIdx.x; n < N; n += IT) {
+    for (int j = 0; j < ld; ++j) {
+      double2 v = mk(0.0, 0.0);
+      if (j < M) {
+        const double2 q = W[(size_t)n * ld + j];
+        const double s = j == 0 ? w0 : we;
+        v = mk(s * q.x, s * q.y);
+      }
+      if constexpr (sizeof(T2) == sizeof(double2)) {
+        Z[(size_t)n * ld + j] = v;
+      } else {
+        Z[(size_t)n * ld + j] = make_float2((float)v.x, (float)v.y);
+      }
+    }
+  }
+}
+
+cudaError_t launch_initial_state(const DevPtrs& p, const RunParams& rp, int /*max_N*/, int prec_fp32,
+                                 uint64_t seed, double eps, cudaStream_t s) {
+  double2* W = reinterpret_cast<double2*>(p.Za);
+  if (prec_fp32)
+    initial_state_kernel<float2><<<rp.n_traj, IT, 0, s>>>(p.traj, W, reinterpret_cast<float2*>(p.Zn), seed, eps);
+  else
+    initial_state_kernel<double2><<<rp.n_traj, IT, 0, s>>>(p.traj, W, reinterpret_cast<double2*>(p.Zn), seed, eps);
+  return cudaGetLastError();
+}
+
+// One block per candidate: trapezoid of |beta_e - beta_g|^2 over the step grid,
+// SNR = sqrt(2 eta kappa S), eps_a = erfc(SNR/2)/2 + tau gamma/2.
+__global__ void __launch_bounds__(ET) eps_a_kernel(DevPtrs p, RunParams rp, long step) {
+  __shared__ double sh[33];
+  const int c = blockIdx.x;
+  const TrajDev d = p.traj[2 * c];
+  const double2* bg = p.beta + (size_t)(2 * c) * (rp.max_steps + 1);
+  const double2* be = p.beta + (size_t)(2 * c + 1) * (rp.max_steps + 1);
+  double acc = 0.0;
+  for (long i = threadIdx.x; i <= step; i += ET) {
+    const double dx = be[i].x - bg[i].x, dy = be[i].y - bg[i].y;
+    const double w = (i == 0 || i == step) ? 0.5 : 1.0;
+    acc += w * (dx * dx + dy * dy);
+  }
+  acc = block_sum<ET>(acc, sh);
+  if (threadIdx.x == 0) {
+    const double S = step > 0 ? rp.dt * acc : 0.0;
+    const double snr = sqrt(2.0 * rp.eta * d.kappa * S);
+    const double tau = (double)step * rp.dt;
+    const double e = 0.5 * erfc(0.5 * snr) + 0.5 * tau * d.gamma;
+    p.eps_a[c] = e;
+    if (!isfinite(e)) set_error(p.err, DEV_NONFINITE);
+  }
+}
+
+cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long step, cudaStream_t s) {
+  eps_a_kernel<<<rp.n_cand, ET, 0, s>>>(p, rp, step);
+  return cudaGetLastError();
+}
+
+__global__ void convert_kernel(const void* __restrict__ src, void* __restrict__ dst, long long n, int to_fp32) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (to_fp32) {
+      const double2 v = reinterpret_cast<const double2*>(src)[i];
+      reinterpret_cast<float2*>(dst)[i] = make_float2((float)v.x, (float)v.y);
+    } else {
+      const float2 v = reinterpret_cast<const float2*>(src)[i];
+      reinterpret_cast<double2*>(dst)[i] = make_double2(v.x, v.y);
+    }
+  }
+}
+
+cudaError_t launch_convert(const void* src, void* dst, long long n, int to_fp32, cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  convert_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, s>>>(src, dst, n, to_fp32);
+  return cudaGetLastError();
+}
+
+}  // namespace lr

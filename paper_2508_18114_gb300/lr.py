@@ -1,0 +1,260 @@
+"""Thin ctypes binding of ``include/lr.h`` (argument marshalling only).
+
+Every computation happens in the CUDA library ``liblr.so``; this module only
+converts Python values to the C structs, owns the device workspace (a torch
+uint8 tensor) and passes torch's current CUDA stream. If the library is
+missing the import fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblr.so")
+
+LR_MAX_RANK = 32
+LR_MAX_NT = 16
+
+STATUS = {
+    0: "LR_OK", 1: "LR_ERR_ARG", 2: "LR_ERR_CUDA", 3: "LR_ERR_NOMEM",
+    4: "LR_ERR_WORKSPACE", 5: "LR_ERR_NOT_PD", 6: "LR_ERR_NONFINITE",
+    7: "LR_ERR_TIMEOUT", 8: "LR_ERR_STATE", 9: "LR_ERR_UNSUPPORTED",
+}
+PRECISION = {"fp64": 0, "fp32_g64": 1}
+ENGINE = {"auto": 0, "plain": 1, "fused": 2}
+ENGINE_NAME = {v: k for k, v in ENGINE.items()}
+
+# exported names declared in include/lr.h
+EXPORTS = (
+    "lr_create", "lr_workspace_size", "lr_bind_workspace", "lr_set_pulse",
+    "lr_set_initial", "lr_set_state", "lr_get_state", "lr_integrate",
+    "lr_observables", "lr_sync", "lr_query", "lr_status_string",
+    "lr_last_error", "lr_destroy",
+)
+
+
+class LrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class lr_model(C.Structure):
+    _fields_ = [("n_modes", C.c_int), ("dims", C.c_int * 3),
+                ("wq", C.c_double), ("alpha", C.c_double),
+                ("wr", C.c_double), ("wf", C.c_double),
+                ("g", C.c_double), ("J", C.c_double),
+                ("kappa", C.c_double), ("gamma", C.c_double)]
+
+
+class lr_pulse(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 8)]
+
+
+class lr_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("engine", C.c_int),
+                ("max_steps", C.c_long), ("pop_every", C.c_int),
+                ("eta", C.c_double)]
+
+
+class lr_info(C.Structure):
+    _fields_ = [("n_cand", C.c_int), ("n_traj", C.c_int), ("nt_max", C.c_int),
+                ("n_rec", C.c_long), ("max_steps", C.c_long), ("step", C.c_long),
+                ("engine", C.c_int), ("team_size", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load liblr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("liblr.so not found at %s: build it with "
+                          "`python -m paper_2508_18114_gb300.build`" % path)
+    lib = C.CDLL(path)
+    vp, i, l, d = C.c_void_p, C.c_int, C.c_long, C.c_double
+    lib.lr_create.argtypes = [i, C.POINTER(lr_model), C.POINTER(C.c_int), C.POINTER(lr_options), C.POINTER(vp)]
+    lib.lr_workspace_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+    lib.lr_bind_workspace.argtypes = [vp, vp, C.c_size_t]
+    lib.lr_set_pulse.argtypes = [vp, C.POINTER(lr_pulse), d, vp]
+    lib.lr_set_initial.argtypes = [vp, C.c_uint64, d, vp]
+    lib.lr_set_state.argtypes = [vp, i, vp, l, vp]
+    lib.lr_get_state.argtypes = [vp, i, vp, vp]
+    lib.lr_integrate.argtypes = [vp, d, l, vp]
+    lib.lr_observables.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.lr_sync.argtypes = [vp, vp]
+    lib.lr_query.argtypes = [vp, C.POINTER(lr_info)]
+    lib.lr_status_string.argtypes = [i]
+    lib.lr_status_string.restype = C.c_char_p
+    lib.lr_last_error.argtypes = [vp]
+    lib.lr_last_error.restype = C.c_char_p
+    lib.lr_destroy.argtypes = [vp]
+    lib.lr_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("lr_status_string", "lr_last_error", "lr_destroy"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_model(p) -> lr_model:
+    """lr_model from an object with dims, wq, alpha, wr, g, kappa, gamma[, wf, J]."""
+    m = lr_model()
+    dims = tuple(p.dims)
+    m.n_modes = len(dims)
+    for k in range(3):
+        m.dims[k] = dims[k] if k < len(dims) else 1
+    m.wq, m.alpha, m.wr = p.wq, p.alpha, p.wr
+    m.wf, m.g, m.J = getattr(p, "wf", 0.0), p.g, getattr(p, "J", 0.0)
+    m.kappa, m.gamma = p.kappa, p.gamma
+    return m
+
+
+def make_pulse(kind: int, params: Sequence[float]) -> lr_pulse:
+    q = lr_pulse()
+    q.kind = int(kind)
+    for k, v in enumerate(params):
+        q.p[k] = float(v)
+    return q
+
+
+class LowRankBatch:
+    """A batch of candidates (pulses) x {|g>, |e>} trajectories on one GPU.
+
+    models / ranks: per candidate. The device workspace is a torch tensor
+    owned by this object.
+    """
+
+    def __init__(self, models, ranks, precision="fp64", engine="auto", max_steps=1000,
+                 pop_every=1, eta=0.6, device="cuda:0"):
+        import torch
+        self._lib = load_library()
+        n = len(models)
+        if n == 0 or len(ranks) != n:
+            raise ValueError("need one rank per model")
+        arr = (lr_model * n)(*[make_model(m) for m in models])
+        rk = (C.c_int * n)(*[int(r) for r in ranks])
+        opt = lr_options(PRECISION[precision], ENGINE[engine], int(max_steps), int(pop_every), float(eta))
+        h = C.c_void_p()
+        st = self._lib.lr_create(n, arr, rk, C.byref(opt), C.byref(h))
+        if st != 0:
+            raise LrError(st, "lr_create failed")
+        self._h = h
+        self.models = list(models)
+        self.ranks = [int(r) for r in ranks]
+        self.precision = precision
+        self.device = torch.device(device)
+        sz = C.c_size_t()
+        self._check(self._lib.lr_workspace_size(h, C.byref(sz)))
+        self.workspace_bytes = int(sz.value)
+        self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._check(self._lib.lr_bind_workspace(h, C.c_void_p(self._ws_ptr), C.c_size_t(self.workspace_bytes)))
+        self.info = self.query()
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, st: int):
+        if st != 0:
+            msg = self._lib.lr_last_error(self._h)
+            raise LrError(st, msg.decode() if msg else "")
+
+    def query(self) -> lr_info:
+        info = lr_info()
+        self._check(self._lib.lr_query(self._h, C.byref(info)))
+        return info
+
+    @property
+    def engine(self) -> str:
+        return ENGINE_NAME[self.query().engine]
+
+    @property
+    def n_traj(self) -> int:
+        return 2 * len(self.models)
+
+    # ------------------------------------------------------------ calls
+    def set_pulse(self, pulses, tau: float, stream=None):
+        """pulses: sequence of (kind, params)."""
+        n = len(self.models)
+        arr = (lr_pulse * n)(*[make_pulse(k, p) for k, p in pulses])
+        self._check(self._lib.lr_set_pulse(self._h, arr, float(tau), C.c_void_p(_stream_ptr(stream))))
+
+    def set_initial(self, seed: int, eps: float = 1e-5, stream=None):
+        self._check(self._lib.lr_set_initial(self._h, C.c_uint64(seed), float(eps),
+                                             C.c_void_p(_stream_ptr(stream))))
+
+    def _NM(self, traj: int):
+        m = self.models[traj // 2]
+        N = int(np.prod(m.dims))
+        return N, self.ranks[traj // 2]
+
+    def set_state(self, traj: int, Z: np.ndarray, step: int = 0, stream=None):
+        N, M = self._NM(traj)
+        z = np.ascontiguousarray(np.asarray(Z, dtype=np.complex128).reshape(N, M))
+        self._check(self._lib.lr_set_state(self._h, int(traj), z.ctypes.data_as(C.c_void_p), int(step),
+                                           C.c_void_p(_stream_ptr(stream))))
+
+    def get_state(self, traj: int, stream=None) -> np.ndarray:
+        N, M = self._NM(traj)
+        z = np.empty((N, M), dtype=np.complex128)
+        self._check(self._lib.lr_get_state(self._h, int(traj), z.ctypes.data_as(C.c_void_p),
+                                           C.c_void_p(_stream_ptr(stream))))
+        return z
+
+    def integrate(self, dt: float, n_steps: int, stream=None):
+        self._check(self._lib.lr_integrate(self._h, float(dt), int(n_steps), C.c_void_p(_stream_ptr(stream))))
+
+    def sync(self, stream=None):
+        self._check(self._lib.lr_sync(self._h, C.c_void_p(_stream_ptr(stream))))
+
+    def observables(self, stream=None, out=None):
+        """Host copies of the recorded observables (numpy), see lr_observables."""
+        info = self.query()
+        nt, nrec, ms = info.nt_max, info.n_rec, info.max_steps
+        o = out or {}
+        beta = o.get("beta", np.empty((self.n_traj, ms + 1, 2)))
+        pops = o.get("pops", np.empty((self.n_traj, nrec, nt)))
+        nphot = o.get("nphot", np.empty((self.n_traj, nrec)))
+        trace = o.get("trace", np.empty((self.n_traj, nrec)))
+        eps = o.get("eps_a", np.empty(len(self.models)))
+        ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+        self._check(self._lib.lr_observables(self._h, ptr(beta), ptr(pops), ptr(nphot), ptr(trace), ptr(eps),
+                                             C.c_void_p(_stream_ptr(stream))))
+        step = info.step
+        return {
+            "beta": beta[..., 0] + 1j * beta[..., 1],
+            "pops": pops, "nphot": nphot, "trace": trace, "eps_a": eps, "step": step,
+        }
+
+    def observables_device(self, tensors, stream=None):
+        """Copy observables into caller device tensors (dict of torch tensors)."""
+        ptr = lambda k: C.c_void_p(tensors[k].data_ptr()) if k in tensors else None  # noqa: E731
+        self._check(self._lib.lr_observables(self._h, ptr("beta"), ptr("pops"), ptr("nphot"),
+                                             ptr("trace"), ptr("eps_a"), C.c_void_p(_stream_ptr(stream))))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
