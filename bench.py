@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the low-rank readout integrator on GB300.
+
+Metric: trajectory-steps per second (one RK4 step of one trajectory) and
+pulse evaluations per second (the |g> and |e> trajectories of one candidate
+over the full pulse, tau / dt RK4 steps each, plus the assignment error).
+
+One bench *step* integrates every trajectory of the batch for `--chunk` RK4
+steps of the same pulse run (consecutive slices: warm-up slices first, then
+the timed ones) and recomputes eps_a over the integrated interval, i.e. one
+pass of the whole hot path. Inputs are seeded synthetic workloads
+(lr_inputs) with the shapes of the paper's readout problem.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead
+(bounded samples, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP32 / FP64 CUDA-core peaks from unit counts: 152 SMs x 128 FP32 FMA/clk
+# (2 flops each) and x 2 FP64 FMA/clk, at the sampled SM clock.
+SMS = 152
+FP32_FMA_PER_CLK = 128
+FP64_FMA_PER_CLK = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--chunk", type=int, default=None, help="RK4 steps per bench step")
+    ap.add_argument("--candidates", type=int, default=None, help="limit the number of candidates")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=None, help="RK4 steps of the oracle sample")
+    return ap.parse_args()
+
+
+def load_workload(args):
+    import lr_inputs as li
+    name = args.workload
+    kw = {}
+    if args.candidates is not None and name in ("c3", "c4", "c5"):
+        kw["n_candidates"] = args.candidates
+    wl = li.workload(name, **kw)
+    return wl
+
+
+def workload_desc(wl, precision):
+    c = wl.candidates
+    Ns = sorted(set(x.model.N for x in c))
+    Ms = sorted(set(x.M for x in c))
+    dims = c[0].model.dims
+    return {
+        "workload": "%s: %d candidates x {g,e} = %d trajectories, N=%s (dims %s), M=%s, dt=%g ns, tau=%g ns, %s"
+                    % (wl.name, len(c), 2 * len(c), Ns[0] if len(Ns) == 1 else "%d-%d" % (Ns[0], Ns[-1]),
+                       "x".join(map(str, dims)) if len(Ns) == 1 else "uneven",
+                       Ms[0] if len(Ms) == 1 else "%d-%d" % (Ms[0], Ms[-1]), wl.dt, wl.tau, precision),
+        "trajectories": 2 * len(c),
+        "N": Ns if len(Ns) > 1 else Ns[0],
+        "M": Ms if len(Ms) > 1 else Ms[0],
+        "dt_ns": wl.dt,
+        "steps_per_pulse": int(round(wl.tau / wl.dt)),
+    }
+
+
+def flops_per_stage(N, M, K=2, nnz=11):
+    """Algorithmic flops of one RK4 stage of one trajectory (complex MAC = 8):
+    Gram upper triangle 4 N M^2, projections Z^dag L_k Z 8 K N M^2,
+    projection term 8 K N M^2, operator apply ~ 4 nnz N M (real coefficients),
+    RK4 update ~ 12 N M."""
+    return 4 * N * M * M + 16 * K * N * M * M + 4 * nnz * N * M + 12 * N * M
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_sample(wl, n_steps, candidates=(0,)):
+    """Oracle traj-steps/s on a bounded sample: `n_steps` RK4 steps of the
+    given candidates' g and e trajectories, one process per trajectory."""
+    from oracle import parallel
+    t0 = time.perf_counter()
+    parallel.run_workload(wl, n_steps, max(1, n_steps), candidates=list(candidates),
+                          processes=2 * len(candidates))
+    dt = time.perf_counter() - t0
+    ntraj = 2 * len(candidates)
+    return ntraj * n_steps / dt, dt, ntraj
+
+
+def default_cpu_steps(wl):
+    N = max(c.model.N for c in wl.candidates)
+    M = max(c.M for c in wl.candidates)
+    # ~1-2e-3 s per RK4 step at N=2000, M=20 on one core (numpy/scipy)
+    return int(max(20, min(4000, 3e5 / (N * M / 40.0 + 50))))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = load_workload(args)
+    prec = args.precision or getattr(wl, "precision", "fp64")
+    ns = args.cpu_steps or default_cpu_steps(wl)
+    for _ in range(args.warmup):
+        oracle_sample(wl, max(2, ns // 10))
+    vals, tt = [], 0.0
+    for _ in range(args.steps):
+        v, dt, ntraj = oracle_sample(wl, ns)
+        vals.append(v)
+        tt += dt
+    value = ntraj * ns * args.steps / tt
+    desc = workload_desc(wl, prec)
+    line = {
+        "impl": "reference", "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(desc, parallelism="cpu oracle, one process per trajectory"),
+        "pulse_evals_per_s": value / (2 * desc["steps_per_pulse"]),
+        "cpu_baseline": {"value": value, "unit": "traj*steps/s", "cores": ntraj, "kind": "oracle",
+                         "sample": "%d RK4 steps of the g and e trajectories of candidate 0 per step" % ns},
+        "e2e": {"value": value, "unit": "traj*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2508_18114_gb300 import LowRankBatch
+    from paper_2508_18114_gb300 import lr as lrmod
+
+    wl = load_workload(args)
+    prec = args.precision or getattr(wl, "precision", "fp64")
+    spp = int(round(wl.tau / wl.dt))
+    chunk = args.chunk or max(1, min(spp // 20, 4000))
+    total_steps = chunk * (args.warmup + args.steps)
+    if total_steps > spp:
+        raise SystemExit("warmup + steps slices exceed one pulse (%d steps)" % spp)
+    # weak scaling: every rank integrates the whole batch (independent replicas
+    # of the candidate population, no data-path collective)
+    cands = wl.candidates
+    b = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision=prec, engine=args.engine,
+                     max_steps=spp, pop_every=max(1, chunk), eta=wl.eta, device=dev)
+    b.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
+    b.set_initial(wl.init_seed + 7919 * rank, wl.eps)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        b.integrate(wl.dt, chunk)
+    b.sync()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between timed iterations (not timed)
+        ev[k][0].record(stream)
+        b.integrate(wl.dt, chunk)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    b.sync()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ntraj = b.n_traj
+    value_rank = ntraj * chunk * args.steps / (ms * 1e-3)
+    value = value_rank * world
+    info = b.query()
+    engine = lrmod.ENGINE_NAME[info.engine]
+
+    # algorithmic work and roofline of the integrate kernel(s)
+    fl = sum(2 * flops_per_stage(c.model.N, c.M) for c in cands) * 4 * chunk   # per bench step
+    peaks, peak_src = measured_peaks()
+    mhz = clocks.get("sm_mhz") or 2070.0
+    if prec == "fp64":
+        peak = SMS * FP64_FMA_PER_CLK * 2 * mhz * 1e6 / 1e12
+        pipe = "FP64 FMA"
+    else:
+        peak = SMS * FP32_FMA_PER_CLK * 2 * mhz * 1e6 / 1e12
+        pipe = "FP32 FMA"
+    achieved = fl / (ms * 1e-3 / args.steps) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "integrate (%s engine)" % engine,
+                "peak_source": "%s pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
+                               % (pipe, FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK, mhz),
+                "flops_per_step": fl}
+    if engine == "plain":
+        launches = (12 * chunk + 2) + 1
+    else:
+        launches = 2
+    launches *= args.steps
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        N0 = [int(np.prod(c.model.dims)) for c in cands]
+        host_Z = [np.asarray(b.get_state(j)) for j in range(ntraj)]
+        out = {"beta": np.empty((ntraj, spp + 1, 2)), "pops": np.empty((ntraj, info.n_rec, info.nt_max)),
+               "nphot": np.empty((ntraj, info.n_rec)), "trace": np.empty((ntraj, info.n_rec)),
+               "eps_a": np.empty(len(cands))}
+        h2d = sum(z.nbytes for z in host_Z)
+        d2h = sum(v.nbytes for v in out.values())
+        step0 = info.step
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 2))
+        for r in range(reps):
+            for j in range(ntraj):
+                b.set_state(j, host_Z[j], step=step0)
+            b.integrate(wl.dt, chunk)
+            b.observables(out=out)
+        te = time.perf_counter() - t0
+        e2e = {"value": world * ntraj * chunk * reps / te, "unit": "traj*steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ns = args.cpu_steps or default_cpu_steps(wl)
+        v, dt_cpu, nt = oracle_sample(wl, ns)
+        cpu = {"value": v, "unit": "traj*steps/s", "cores": nt, "kind": "oracle",
+               "sample": "%d RK4 steps of the g and e trajectories of candidate 0 (%.1f s)" % (ns, dt_cpu)}
+
+    if rank == 0:
+        desc = workload_desc(wl, prec)
+        desc.update({"parallelism": "dp%d (independent replicas)" % world, "engine": engine,
+                     "team_size": info.team_size, "chunk_rk4_steps": chunk,
+                     "l2": "flushed (256 MiB write) between timed steps"})
+        line = {
+            "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32 (f64 Gram/Cholesky/signal)",
+            "data": "synthetic (seeded pulses and initial states)", "config": desc,
+            "pulse_evals_per_s": value / (2 * spp),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "peaks_source": peak_src,
+        }
+        print(json.dumps(line))
+    b.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
