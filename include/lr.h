@@ -196,6 +196,42 @@ lr_status lr_observables(lr_ctx* ctx, double* beta, double* pops, double* nphot,
 lr_status lr_sync(lr_ctx* ctx, void* stream);
 
 lr_status lr_query(const lr_ctx* ctx, lr_info* info);
+
+/* No-allocation entry point (the paper has no counterpart; this is a
+ * deployment convenience).
+ *
+ * Some callers cannot allocate device memory at all: a plug-in running
+ * inside a host application that has already reserved the GPU's memory and
+ * forbids further cudaMalloc, code that runs while another library holds the
+ * device in a fixed memory budget, or a thin binding with no device
+ * allocator of its own. They cannot bind a workspace, so this call runs the
+ * PLAIN FP64 engine for ONE trajectory with all of its scratch (stage
+ * buffers, RK4 accumulator, partial sums, solved projections, small tables)
+ * in a file-scope static device array of about 15.8 MB that every GPU which
+ * loads the library keeps until the process exits. It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Limits: N = N_t N_r [N_f] <= 4096, M <= 32, N*M <= 65536; larger sizes
+ * return LR_ERR_UNSUPPORTED.
+ *
+ * Arguments: model and rank M as in lr_create; pulse and tau as in
+ * lr_set_pulse; Z (device, in/out): the state, complex128 row-major [N][M]
+ * as interleaved (re, im) doubles, advanced in place; beta (device, out):
+ * n_steps+1 complex values, beta[k] = tr(rho r) at step step0 + k; dt, step0
+ * (t = step * dt) and n_steps as in lr_integrate. The call is synchronous
+ * and returns the device error status (LR_ERR_NOT_PD, LR_ERR_NONFINITE).
+ * Results equal those of lr_integrate with the plain FP64 engine for the
+ * same state.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array, which keeps the
+ * previous call's contents (everything a call reads is rewritten or cleared
+ * by that call first); calls that overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. */
+lr_status lr_integrate_plain_noalloc(const lr_model* model, int M, const lr_pulse* pulse, double tau,
+                                     double* Z, double* beta, double dt, long step0, long n_steps,
+                                     void* stream);
 const char* lr_status_string(lr_status s);
 const char* lr_last_error(const lr_ctx* ctx);
 void lr_destroy(lr_ctx* ctx);

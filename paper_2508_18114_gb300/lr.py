@@ -33,7 +33,7 @@ EXPORTS = (
     "lr_create", "lr_workspace_size", "lr_bind_workspace", "lr_set_pulse",
     "lr_set_initial", "lr_set_state", "lr_get_state", "lr_integrate",
     "lr_observables", "lr_sync", "lr_query", "lr_status_string",
-    "lr_last_error", "lr_destroy",
+    "lr_last_error", "lr_destroy", "lr_integrate_plain_noalloc",
 )
 
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_last_error.restype = C.c_char_p
     lib.lr_destroy.argtypes = [vp]
     lib.lr_destroy.restype = None
+    lib.lr_integrate_plain_noalloc.argtypes = [C.POINTER(lr_model), i, C.POINTER(lr_pulse), d, vp, vp, d, l, l, vp]
     for name in EXPORTS:
         if name not in ("lr_status_string", "lr_last_error", "lr_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -132,6 +133,21 @@ def make_pulse(kind: int, params: Sequence[float]) -> lr_pulse:
     for k, v in enumerate(params):
         q.p[k] = float(v)
     return q
+
+
+def integrate_plain_noalloc(model, M, pulse, tau, Z, beta, dt, step0, n_steps, stream=None):
+    """lr_integrate_plain_noalloc on caller device tensors (no workspace).
+
+    Z: complex128 device tensor [N, M], advanced in place; beta: complex128
+    device tensor with at least n_steps + 1 entries. Returns the lr status.
+    """
+    lib = load_library()
+    m = make_model(model)
+    q = make_pulse(*pulse)
+    return lib.lr_integrate_plain_noalloc(C.byref(m), int(M), C.byref(q), float(tau),
+                                          C.c_void_p(Z.data_ptr()), C.c_void_p(beta.data_ptr()),
+                                          float(dt), int(step0), int(n_steps),
+                                          C.c_void_p(_stream_ptr(stream)))
 
 
 class LowRankBatch:
