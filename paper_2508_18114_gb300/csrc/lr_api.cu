@@ -392,7 +392,7 @@ lr_status lr_query(const lr_ctx* c, lr_info* info) {
   info->max_steps = c->opt.max_steps;
   info->step = c->step;
   info->engine = c->engine;
-  info->team_size = c->engine == LR_ENGINE_FUSED ? c->fused.team : 0;
+  info->team_size = c->engine == LR_ENGINE_FUSED ? c->fused.C : 0;
   return LR_OK;
 }
 

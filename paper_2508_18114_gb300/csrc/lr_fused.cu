@@ -1,15 +1,942 @@
+// FUSED engine: persistent cluster kernel integrating whole pulses.
+//
+// Per RK4 stage of Eq. S5, for one trajectory on a team of C CTAs:
+//   P  (local)  partial sums over the CTA's rows of the stage input Z_s:
+//               G = Z^dag Z (upper tiles), T_r = Z^dag r Z, T_b = Z^dag b Z
+//               (+ level populations and readout photons at recording steps);
+//   B1          one cluster barrier: partials and the new Z_s are visible;
+//   R  (every CTA, redundantly) reduce the C partial slots in rank order,
+//               Cholesky G = L L^dag, L^-1, G^-1 = L^-dag L^-1 (all FP64),
+//               X_k = G^-1 T_k (bulk precision), pre-scaled and conjugate-
+//               transposed: XT_r = kappa/2 X_r^dag, XT_b = gamma/2 X_b^dag;
+//   F  (local + DSMEM halo) F = -i H_eff Z_s + (rZ_s) XT_r + (bZ_s) XT_b and the
+//               RK4 stage update; the next stage input goes to the other Z_s
+//               buffer, the accumulator and Z_n are updated in L2.
+// Partial slots and Z_s buffers are double-buffered by stage parity, so the
+// single barrier per stage separates every write from the reads of it.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
 #include "lr_fused.cuh"
 
-namespace lr {
+namespace cg = cooperative_groups;
 
-bool fused_plan(const std::vector<TrajDev>&, lr_precision, FusedPlan* plan) {
-  *plan = FusedPlan{};
-  return false;
+namespace lr {
+namespace fz {
+
+constexpr int NT = 384;
+constexpr int NWARP = NT / 32;
+constexpr int TAB = 64;   // mode truncations handled by the fused engine: N_t, N_r, N_f < 64
+
+struct Args {
+  DevPtrs p;
+  RunParams rp;
+  long step0, n_steps;
+  int C, n_clusters, Mp, R, Nmax;
+  int zs_smem;
+  // byte offsets in dynamic shared memory
+  int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop;   // s_*: offsets inside one slot
+  int o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
+  const int* order;
+  void* zs_glob;      // global stage buffers, per cluster [2][Nmax*Mp]
+  void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
+};
+
+// ----------------------------------------------------------------- complex
+
+template <typename T2> struct Real;
+template <> struct Real<float2> { using t = float; };
+template <> struct Real<double2> { using t = double; };
+
+template <typename T2> __device__ __forceinline__ T2 cm(typename Real<T2>::t r, typename Real<T2>::t i) {
+  T2 v;
+  v.x = r;
+  v.y = i;
+  return v;
 }
-size_t fused_scratch_bytes(const FusedPlan&, int) { return 0; }
-cudaError_t fused_integrate(const FusedPlan&, const DevPtrs&, const RunParams&, lr_precision, long, long,
-                            cudaStream_t) {
-  return cudaErrorNotSupported;
+
+// ----------------------------------------------------------------- partition
+
+struct Part {
+  int r_lo, nr, st, R;
+};
+
+__device__ __forceinline__ Part part_of(const TrajDev& d, int C, int q) {
+  Part P;
+  const int base = d.Nr / C, rem = d.Nr % C;
+  P.r_lo = q * base + min(q, rem);
+  P.nr = base + (q < rem ? 1 : 0);
+  P.st = P.nr * d.Nf;
+  P.R = d.Nt * P.st;
+  return P;
+}
+
+// ----------------------------------------------------------------- double-word accumulation
+// Exact FP32 products (p + e = a*b via FMA) accumulated in an unevaluated
+// sum of two floats (hi + lo): ~2^-48 relative, the FP64-class Gram matrix.
+struct DW {
+  float hi, lo;
+};
+__device__ __forceinline__ void dw_add_prod(DW& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+__device__ __forceinline__ void dw_add(DW& s, const DW& o) {
+  const float t = s.hi + o.hi;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (o.hi - bp);
+  s.hi = t;
+  s.lo += err + o.lo;
+}
+__device__ __forceinline__ double dw_value(const DW& s) { return (double)s.hi + (double)s.lo; }
+
+// ----------------------------------------------------------------- the kernel
+
+template <typename T2, int GRAM_DW>
+__global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
+  using T = typename Real<T2>::t;
+  constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
+  constexpr int TR = sizeof(T) == 4 ? 2 : 1;     // phase-F rows per thread tile
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = a.C;
+  const int q = (int)cluster.block_rank();
+  const int cid = blockIdx.x / C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Mp = a.Mp;
+  const long long zs_buf = (long long)a.R * Mp;   // elements per smem Z_s buffer
+
+  double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);     // [Mp][Mp+1]  G -> L -> G^-1
+  double2* W = reinterpret_cast<double2*>(smem + a.o_w);       // [Mp][Mp+1]  L^-1
+  T2* Tred = reinterpret_cast<T2*>(smem + a.o_tred);           // [2][Mp*Mp]
+  double* trd = reinterpret_cast<double*>(smem + a.o_trd);     // [Mp] diag of T_r (FP64)
+  T2* XT = reinterpret_cast<T2*>(smem + a.o_xs);               // [2][Mp][Mp] (l, m)
+  double* misc = reinterpret_cast<double*>(smem + a.o_misc);   // coef, flags
+  T* sq = reinterpret_cast<T*>(smem + a.o_tab);                 // sqrt(k), k < TAB
+  T* dtab = sq + TAB;                                           // [3][TAB][2]: diagonal energies (hi, lo)
+  const int ldg = Mp + 1;
+
+  T2* zs_local = reinterpret_cast<T2*>(smem + a.o_zs);
+  T2* zs_glob = reinterpret_cast<T2*>(a.zs_glob) + (size_t)cid * 2 * a.Nmax * Mp;
+  T2* accg = reinterpret_cast<T2*>(a.acc_glob) + (size_t)cid * a.Nmax * Mp;
+
+  const double dt = a.rp.dt;
+  const int pe = a.rp.pop_every;
+
+  for (int it_idx = cid; it_idx < a.rp.n_traj; it_idx += a.n_clusters) {
+    const int tj = a.order[it_idx];
+    const TrajDev d = a.p.traj[tj];
+    const int M = d.M;
+    const Part P = part_of(d, C, q);
+    const Part Pm = part_of(d, C, q > 0 ? q - 1 : q);
+    const Part Pp = part_of(d, C, q < C - 1 ? q + 1 : q);
+    const int Nf = d.Nf, Nr = d.Nr, Nt = d.Nt;
+    const bool three = d.n_modes == 3;
+    const int dro = three ? Nf : Nr;
+    T2* Zn = reinterpret_cast<T2*>(a.p.Zn) + d.z_off;
+    const PulseDev pulse = a.p.pulse[d.cand];
+    // remote Z_s bases (smem mode)
+    T2* zs_m = zs_local;
+    T2* zs_p = zs_local;
+    if (a.zs_smem) {
+      zs_m = cluster.map_shared_rank(zs_local, q > 0 ? q - 1 : q);
+      zs_p = cluster.map_shared_rank(zs_local, q < C - 1 ? q + 1 : q);
+    }
+
+    // global row of local row l
+    auto grow = [&](int l) {
+      const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
+      return (it * Nr + P.r_lo + irl) * Nf + iff;
+    };
+    // pointer to the start of row (it, ir, iff) of Z_s buffer b (any owner)
+    auto zrow = [&](int b, int it2, int ir2, int iff2) -> const T2* {
+      if (!a.zs_smem) return zs_glob + ((size_t)b * a.Nmax + (size_t)((it2 * Nr + ir2) * Nf + iff2)) * Mp;
+      if (ir2 < P.r_lo) {
+        const int l = (it2 * Pm.nr + (ir2 - Pm.r_lo)) * Nf + iff2;
+        return zs_m + (size_t)b * zs_buf + (size_t)l * Mp;
+      }
+      if (ir2 >= P.r_lo + P.nr) {
+        const int l = (it2 * Pp.nr + (ir2 - Pp.r_lo)) * Nf + iff2;
+        return zs_p + (size_t)b * zs_buf + (size_t)l * Mp;
+      }
+      const int l = (it2 * P.nr + (ir2 - P.r_lo)) * Nf + iff2;
+      return zs_local + (size_t)b * zs_buf + (size_t)l * Mp;
+    };
+    // own row l of buffer b (writable)
+    auto own = [&](int b, int l) -> T2* {
+      if (!a.zs_smem) return zs_glob + ((size_t)b * a.Nmax + (size_t)grow(l)) * Mp;
+      return zs_local + (size_t)b * zs_buf + (size_t)l * Mp;
+    };
+
+    // ---- per-trajectory tables: sqrt(k) and the separable diagonal of H,
+    //      wq i_t + alpha/2 i_t(i_t-1) | wr i_r | wf i_f, each as hi + lo so that
+    //      the bulk precision does not round the mode frequencies
+    for (int k = tid; k < TAB; k += NT) {
+      sq[k] = (T)sqrt((double)k);
+      const double v[3] = {d.wq * k + 0.5 * d.alpha * k * (k - 1.0), d.wr * k, three ? d.wf * k : 0.0};
+      for (int c3 = 0; c3 < 3; ++c3) {
+        const T hi = (T)v[c3];
+        dtab[(c3 * TAB + k) * 2] = hi;
+        dtab[(c3 * TAB + k) * 2 + 1] = (T)(v[c3] - (double)hi);
+      }
+    }
+    // ---- load Z_n into Z_s buffer 0 (own rows), zero the rank padding
+    for (int e = tid; e < P.R * Mp; e += NT) {
+      const int l = e / Mp, m = e - l * Mp;
+      own(0, l)[m] = m < M ? Zn[(size_t)grow(l) * M + m] : cm<T2>(0, 0);
+    }
+    __syncthreads();
+
+    int cur = 0;
+    const long s_end = a.step0 + a.n_steps;
+    for (long step = a.step0;; ++step) {
+      const bool last = step == s_end;
+      for (int stage = 0; stage < 4; ++stage) {
+        const int par = stage & 1;
+        const bool record = stage == 0 && (step % pe) == 0;
+        unsigned char* slot = smem + a.o_slot + par * a.slot_bytes;
+        double2* gp = reinterpret_cast<double2*>(slot + a.s_gp);
+        T2* tp = reinterpret_cast<T2*>(slot + a.s_tp);
+        double* popp = reinterpret_cast<double*>(slot + a.s_pop);
+
+        // ================= P: partial sums over own rows of Z_s[cur]
+        {
+          const int nt_ = Mp / TP;
+          const int n_g = nt_ * (nt_ + 1) / 2, n_t = nt_ * nt_;
+          for (int task = warp; task < n_g + n_t; task += NWARP) {
+            if (task < n_g) {
+              // upper tile (ti <= tj) of G
+              int ti = 0, rem = task;
+              while (rem >= nt_ - ti) { rem -= nt_ - ti; ++ti; }
+              const int tj2 = ti + rem;
+              const int i0 = ti * TP, j0 = tj2 * TP;
+              if constexpr (GRAM_DW) {
+                DW acc[TP][TP][2];
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) acc[i][j][0] = acc[i][j][1] = DW{0.f, 0.f};
+                for (int l = lane; l < P.R; l += 32) {
+                  const T2* z = own(cur, l);
+                  T2 zi[TP], zj[TP];
+#pragma unroll
+                  for (int i = 0; i < TP; ++i) zi[i] = z[i0 + i];
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
+#pragma unroll
+                  for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TP; ++j) {   // conj(zi) * zj
+                      dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
+                      dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
+                      dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
+                      dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+#pragma unroll
+                      for (int o = 16; o > 0; o >>= 1) {
+                        DW t;
+                        t.hi = __shfl_xor_sync(0xffffffffu, acc[i][j][c].hi, o);
+                        t.lo = __shfl_xor_sync(0xffffffffu, acc[i][j][c].lo, o);
+                        dw_add(acc[i][j][c], t);
+                      }
+                if (lane == 0)
+#pragma unroll
+                  for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TP; ++j)
+                      gp[(i0 + i) * Mp + j0 + j] = mk(dw_value(acc[i][j][0]), dw_value(acc[i][j][1]));
+              } else {
+                T gr[TP][TP], gi[TP][TP];
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) gr[i][j] = gi[i][j] = 0;
+                for (int l = lane; l < P.R; l += 32) {
+                  const T2* z = own(cur, l);
+                  T2 zi[TP], zj[TP];
+#pragma unroll
+                  for (int i = 0; i < TP; ++i) zi[i] = z[i0 + i];
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
+#pragma unroll
+                  for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TP; ++j) {
+                      gr[i][j] = fma(zi[i].x, zj[j].x, fma(zi[i].y, zj[j].y, gr[i][j]));
+                      gi[i][j] = fma(zi[i].x, zj[j].y, fma(-zi[i].y, zj[j].x, gi[i][j]));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                      gr[i][j] += __shfl_xor_sync(0xffffffffu, gr[i][j], o);
+                      gi[i][j] += __shfl_xor_sync(0xffffffffu, gi[i][j], o);
+                    }
+                if (lane == 0)
+#pragma unroll
+                  for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TP; ++j) gp[(i0 + i) * Mp + j0 + j] = mk((double)gr[i][j], (double)gi[i][j]);
+              }
+            } else {
+              // tile of T_r and T_b
+              const int t2 = task - n_g, ti = t2 / nt_, tj2 = t2 - ti * nt_;
+              const int i0 = ti * TP, j0 = tj2 * TP;
+              T rr[TP][TP], ri[TP][TP], br[TP][TP], bi[TP][TP];
+#pragma unroll
+              for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TP; ++j) rr[i][j] = ri[i][j] = br[i][j] = bi[i][j] = 0;
+              for (int l = lane; l < P.R; l += 32) {
+                const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
+                const int iro = three ? iff : irl;     // with two modes C == 1 and r_lo == 0
+                const T sr = iro + 1 < dro ? sq[iro + 1] : (T)0;
+                const T sb = it + 1 < Nt ? sq[it + 1] : (T)0;
+                const T2* z = own(cur, l);
+                const T2* zr = own(cur, iro + 1 < dro ? l + 1 : l);
+                const T2* zb = own(cur, it + 1 < Nt ? l + P.st : l);
+                T2 wr[TP], wb[TP], yr[TP], yb[TP];
+#pragma unroll
+                for (int i = 0; i < TP; ++i) {
+                  const T2 zi = z[i0 + i];
+                  wr[i] = cm<T2>(sr * zi.x, -sr * zi.y);   // sr conj(z_i)
+                  wb[i] = cm<T2>(sb * zi.x, -sb * zi.y);
+                }
+#pragma unroll
+                for (int j = 0; j < TP; ++j) {
+                  yr[j] = zr[j0 + j];
+                  yb[j] = zb[j0 + j];
+                }
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) {
+                    rr[i][j] = fma(wr[i].x, yr[j].x, fma(-wr[i].y, yr[j].y, rr[i][j]));
+                    ri[i][j] = fma(wr[i].x, yr[j].y, fma(wr[i].y, yr[j].x, ri[i][j]));
+                    br[i][j] = fma(wb[i].x, yb[j].x, fma(-wb[i].y, yb[j].y, br[i][j]));
+                    bi[i][j] = fma(wb[i].x, yb[j].y, fma(wb[i].y, yb[j].x, bi[i][j]));
+                  }
+              }
+#pragma unroll
+              for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TP; ++j)
+#pragma unroll
+                  for (int o = 16; o > 0; o >>= 1) {
+                    rr[i][j] += __shfl_xor_sync(0xffffffffu, rr[i][j], o);
+                    ri[i][j] += __shfl_xor_sync(0xffffffffu, ri[i][j], o);
+                    br[i][j] += __shfl_xor_sync(0xffffffffu, br[i][j], o);
+                    bi[i][j] += __shfl_xor_sync(0xffffffffu, bi[i][j], o);
+                  }
+              if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) {
+                    tp[(i0 + i) * Mp + j0 + j] = cm<T2>(rr[i][j], ri[i][j]);
+                    tp[Mp * Mp + (i0 + i) * Mp + j0 + j] = cm<T2>(br[i][j], bi[i][j]);
+                  }
+            }
+          }
+          if (record) {
+            // level populations and readout photons of own rows (FP64)
+            for (int lv = warp; lv < Nt; lv += NWARP) {
+              double s = 0.0, ph = 0.0;
+              for (int r = lane; r < P.st; r += 32) {
+                const int l = lv * P.st + r;
+                const int irl = r / Nf, iff = r - irl * Nf;
+                const int iro = three ? iff : irl;
+                const T2* z = own(cur, l);
+                double w = 0.0;
+                for (int m = 0; m < M; ++m) w += (double)z[m].x * z[m].x + (double)z[m].y * z[m].y;
+                s += w;
+                ph += iro * w;
+              }
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                ph += __shfl_xor_sync(0xffffffffu, ph, o);
+              }
+              if (lane == 0) {
+                popp[lv] = s;
+                misc[8 + lv] = ph;
+              }
+            }
+            __syncthreads();
+            if (tid == 0) {
+              double ph = 0.0;
+              for (int lv = 0; lv < Nt; ++lv) ph += misc[8 + lv];
+              popp[LR_MAX_NT] = ph;
+            }
+          }
+        }
+        // ================= B1
+        cluster.sync();
+
+        // ================= R: reduce in rank order, FP64 Cholesky and inverse
+        {
+          const int MM = Mp * Mp;
+          for (int e = tid; e < 3 * MM; e += NT) {
+            const int mat = e / MM, ij = e - mat * MM, i = ij / Mp, j = ij - i * Mp;
+            if (mat == 0) {
+              if (i > j || j >= M) continue;
+              double re = 0.0, im = 0.0;
+              for (int r = 0; r < C; ++r) {
+                const double2* gpr = cluster.map_shared_rank(gp, r);
+                const double2 v = gpr[i * Mp + j];
+                re += v.x;
+                im += v.y;
+              }
+              if (i == j) {
+                Gd[i * ldg + i] = mk(re, 0.0);
+              } else {
+                Gd[i * ldg + j] = mk(re, im);
+                Gd[j * ldg + i] = mk(re, -im);
+              }
+            } else {
+              double re = 0.0, im = 0.0;
+              for (int r = 0; r < C; ++r) {
+                const T2* tpr = cluster.map_shared_rank(tp, r);
+                const T2 v = tpr[(mat - 1) * MM + ij];
+                re += (double)v.x;
+                im += (double)v.y;
+              }
+              Tred[(mat - 1) * MM + ij] = cm<T2>((T)re, (T)im);
+              if (mat == 1 && i == j) {
+                trd[i] = re;
+                misc[40 + i] = im;
+              }
+            }
+          }
+          if (record && tid < LR_MAX_NT + 1) {
+            double s = 0.0;
+            const bool use = tid < Nt || tid == LR_MAX_NT;
+            if (use)
+              for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(popp, r)[tid];
+            misc[80 + tid] = s;
+          }
+          if (tid == 0) {
+            const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
+            misc[0] = pulse_coefficient(pulse, a.rp.tau, ts);
+            misc[1] = 0.0;   // not-PD flag
+          }
+          __syncthreads();
+          if (stage == 0 && q == 0 && tid == 0) {
+            double br = 0.0, bi = 0.0;
+            for (int i = 0; i < M; ++i) {
+              br += trd[i];
+              bi += misc[40 + i];
+            }
+            a.p.beta[(size_t)tj * (a.rp.max_steps + 1) + step] = mk(br, bi);
+            if (!isfinite(br) || !isfinite(bi)) set_error(a.p.err, DEV_NONFINITE);
+            if (record) {
+              const long rec = step / pe;
+              double trace = 0.0;
+              for (int lv = 0; lv < a.rp.nt_max; ++lv) {
+                const double v = lv < Nt ? misc[80 + lv] : 0.0;
+                a.p.pops[((size_t)tj * a.rp.n_rec + rec) * a.rp.nt_max + lv] = v;
+                trace += v;
+              }
+              a.p.nphot[(size_t)tj * a.rp.n_rec + rec] = misc[80 + LR_MAX_NT];
+              a.p.trace[(size_t)tj * a.rp.n_rec + rec] = trace;
+            }
+          }
+          if (last) break;
+          // Cholesky G = L L^dag in Gd (lower)
+          for (int k = 0; k < M; ++k) {
+            if (tid == 0) {
+              double piv = Gd[k * ldg + k].x;
+              if (!(piv > 0.0) || !isfinite(piv)) {
+                misc[1] = 1.0;
+                piv = 1.0;
+              }
+              Gd[k * ldg + k] = mk(sqrt(piv), 0.0);
+            }
+            __syncthreads();
+            const double inv = 1.0 / Gd[k * ldg + k].x;
+            for (int i = k + 1 + tid; i < M; i += NT) {
+              const double2 v = Gd[i * ldg + k];
+              Gd[i * ldg + k] = mk(v.x * inv, v.y * inv);
+            }
+            __syncthreads();
+            const int w = M - k - 1;
+            for (int e = tid; e < w * w; e += NT) {
+              const int i = k + 1 + e / w, j = k + 1 + e % w;
+              if (j > i) continue;
+              const double2 x = Gd[i * ldg + k], y = Gd[j * ldg + k], g = Gd[i * ldg + j];
+              Gd[i * ldg + j] = mk(g.x - (x.x * y.x + x.y * y.y), g.y - (x.y * y.x - x.x * y.y));
+            }
+            __syncthreads();
+          }
+          if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
+          // W = L^-1 (lower): column-oriented substitution, all columns at once
+          for (int e = tid; e < M * M; e += NT) {
+            const int i = e / M, j = e - i * M;
+            W[i * ldg + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+          }
+          __syncthreads();
+          for (int k = 0; k < M; ++k) {
+            const double inv = 1.0 / Gd[k * ldg + k].x;
+            for (int j = tid; j <= k; j += NT) {
+              const double2 v = W[k * ldg + j];
+              W[k * ldg + j] = mk(v.x * inv, v.y * inv);
+            }
+            __syncthreads();
+            const int rows = M - k - 1;
+            for (int e = tid; e < rows * (k + 1); e += NT) {
+              const int i = k + 1 + e / (k + 1), j = e % (k + 1);
+              const double2 l = Gd[i * ldg + k], w = W[k * ldg + j], o = W[i * ldg + j];
+              W[i * ldg + j] = mk(o.x - (l.x * w.x - l.y * w.y), o.y - (l.x * w.y + l.y * w.x));
+            }
+            __syncthreads();
+          }
+          // G^-1 = W^dag W (Hermitian) into Gd
+          for (int e = tid; e < M * M; e += NT) {
+            const int i = e / M, j = e - i * M;
+            if (i > j) continue;
+            double re = 0.0, im = 0.0;
+            for (int k = j; k < M; ++k) {          // W[k][i], W[k][j] nonzero for k >= max(i, j) = j
+              const double2 x = W[k * ldg + i], y = W[k * ldg + j];   // conj(x) y
+              re += x.x * y.x + x.y * y.y;
+              im += x.x * y.y - x.y * y.x;
+            }
+            Gd[i * ldg + j] = mk(re, im);
+            if (i != j) Gd[j * ldg + i] = mk(re, -im);
+          }
+          __syncthreads();
+          // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
+          const double sk[2] = {0.5 * d.kappa, 0.5 * d.gamma};
+          for (int e = tid; e < 2 * MM; e += NT) {
+            const int k = e / MM, lm = e - k * MM, l = lm / Mp, m = lm - l * Mp;
+            T xr = 0, xi = 0;
+            if (l < M && m < M) {
+              const T2* Tk = Tred + k * MM;
+              for (int j = 0; j < M; ++j) {
+                const double2 g = Gd[m * ldg + j];
+                const T gr = (T)g.x, gi = (T)g.y;
+                const T2 t = Tk[j * Mp + l];
+                xr = fma(gr, t.x, fma(-gi, t.y, xr));
+                xi = fma(gr, t.y, fma(gi, t.x, xi));
+              }
+            }
+            const T s = (T)sk[k];
+            XT[k * MM + lm] = cm<T2>(s * xr, -s * xi);
+          }
+          __syncthreads();
+        }
+
+        // ================= F: right-hand side and RK4 stage update
+        {
+          const T c = (T)misc[0];
+          const int nxt = cur ^ 1;
+          const int mq = Mp / 4;
+          const int nrt = (P.R + TR - 1) / TR;
+          // split step sizes: h = hi + lo exactly (no systematic FP32 step error)
+          const double hs = stage == 2 ? dt : 0.5 * dt, h6 = dt / 6.0;
+          const T hs_hi = (T)hs, hs_lo = (T)(hs - (double)hs_hi);
+          const T h6_hi = (T)h6, h6_lo = (T)(h6 - (double)h6_hi);
+          const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
+          for (int tile = tid; tile < nrt * mq; tile += NT) {
+            const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+              const int l = rt * TR + r;
+              if (l >= P.R) break;
+              const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
+              const int ir = P.r_lo + irl;
+              const int iro = three ? iff : ir;
+              // H_eff diagonal: real part as an unevaluated sum dh + dl
+              T dh, dl;
+              {
+                const T a0 = dtab[(0 * TAB + it) * 2], a1 = dtab[(1 * TAB + ir) * 2], a2 = dtab[(2 * TAB + iff) * 2];
+                T s1 = a0 + a1;
+                T bp = s1 - a0;
+                T er = (a0 - (s1 - bp)) + (a1 - bp);
+                T s2 = s1 + a2;
+                bp = s2 - s1;
+                er += (s1 - (s2 - bp)) + (a2 - bp);
+                dh = s2;
+                dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
+              }
+              const T dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
+              const T2* z = own(cur, l) + m0;
+              T hr[4], hi[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
+                hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
+              }
+              auto add_row = [&](const T2* v, T w) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  hr[u] = fma(w, v[u].x, hr[u]);
+                  hi[u] = fma(w, v[u].y, hi[u]);
+                }
+              };
+              // g (b + b^dag)(a + a^dag)
+#pragma unroll
+              for (int sa = -1; sa <= 1; sa += 2) {
+                const int it2 = it + sa;
+                if (it2 < 0 || it2 >= Nt) continue;
+                const T ct = g * sq[max(it, it2)];
+#pragma unroll
+                for (int sb = -1; sb <= 1; sb += 2) {
+                  const int ir2 = ir + sb;
+                  if (ir2 < 0 || ir2 >= Nr) continue;
+                  add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
+                }
+              }
+              if (three) {
+                // J (a + a^dag)(f + f^dag)
+#pragma unroll
+                for (int sa = -1; sa <= 1; sa += 2) {
+                  const int ir2 = ir + sa;
+                  if (ir2 < 0 || ir2 >= Nr) continue;
+                  const T cr = J * sq[max(ir, ir2)];
+#pragma unroll
+                  for (int sb = -1; sb <= 1; sb += 2) {
+                    const int if2 = iff + sb;
+                    if (if2 < 0 || if2 >= Nf) continue;
+                    add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
+                  }
+                }
+                // drive on the filter
+#pragma unroll
+                for (int sa = -1; sa <= 1; sa += 2) {
+                  const int if2 = iff + sa;
+                  if (if2 < 0 || if2 >= Nf) continue;
+                  add_row(own(cur, l + sa) + m0, c * sq[max(iff, if2)]);
+                }
+              } else {
+                // drive on the resonator (two modes, C == 1)
+#pragma unroll
+                for (int sa = -1; sa <= 1; sa += 2) {
+                  const int ir2 = ir + sa;
+                  if (ir2 < 0 || ir2 >= Nr) continue;
+                  add_row(own(cur, l + sa) + m0, c * sq[max(ir, ir2)]);
+                }
+              }
+              // F = -i H_eff z + projection terms
+              T fr[4], fi[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                fr[u] = hi[u];
+                fi[u] = -hr[u];
+              }
+              const int MM = Mp * Mp;
+              if (iro + 1 < dro) {
+                const T s = sq[iro + 1];
+                const T2* y = own(cur, l + 1);
+                T ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+                for (int k = 0; k < M; ++k) {
+                  const T2 yk = y[k];
+                  const T2* xt = XT + k * Mp + m0;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const T2 x = xt[u];
+                    ar[u] = fma(yk.x, x.x, fma(-yk.y, x.y, ar[u]));
+                    ai[u] = fma(yk.x, x.y, fma(yk.y, x.x, ai[u]));
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  fr[u] = fma(s, ar[u], fr[u]);
+                  fi[u] = fma(s, ai[u], fi[u]);
+                }
+              }
+              if (it + 1 < Nt) {
+                const T s = sq[it + 1];
+                const T2* y = own(cur, l + P.st);
+                T ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+                for (int k = 0; k < M; ++k) {
+                  const T2 yk = y[k];
+                  const T2* xt = XT + MM + k * Mp + m0;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const T2 x = xt[u];
+                    ar[u] = fma(yk.x, x.x, fma(-yk.y, x.y, ar[u]));
+                    ai[u] = fma(yk.x, x.y, fma(yk.y, x.x, ai[u]));
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  fr[u] = fma(s, ar[u], fr[u]);
+                  fi[u] = fma(s, ai[u], fi[u]);
+                }
+              }
+              // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
+              const int n = (it * Nr + ir) * Nf + iff;
+              T2* zo = own(nxt, l) + m0;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int m = m0 + u;
+                if (m >= M) {
+                  zo[u] = cm<T2>(0, 0);
+                  continue;
+                }
+                const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
+                const T2 zn = Zn[oz];
+                if (stage == 0) {
+                  accg[oa] = cm<T2>(fr[u], fi[u]);
+                } else if (stage < 3) {
+                  const T2 ac = accg[oa];
+                  accg[oa] = cm<T2>(fma((T)2, fr[u], ac.x), fma((T)2, fi[u], ac.y));
+                }
+                if (stage < 3) {
+                  zo[u] = cm<T2>(zn.x + fma(hs_lo, fr[u], hs_hi * fr[u]), zn.y + fma(hs_lo, fi[u], hs_hi * fi[u]));
+                } else {
+                  const T2 ac = accg[oa];
+                  const T sr_ = ac.x + fr[u], si_ = ac.y + fi[u];
+                  const T2 z1 = cm<T2>(zn.x + fma(h6_lo, sr_, h6_hi * sr_), zn.y + fma(h6_lo, si_, h6_hi * si_));
+                  Zn[oz] = z1;
+                  zo[u] = z1;
+                }
+              }
+            }
+          }
+          cur = nxt;
+          __syncthreads();
+        }
+      }
+      if (last) break;
+    }
+    // every CTA is done reading its peers' shared memory before it is reused
+    cluster.sync();
+  }
+}
+
+}  // namespace fz
+
+// ----------------------------------------------------------------- host side
+
+namespace {
+
+struct SmemLayout {
+  int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop, o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab, total;
+};
+
+int al16(int x) { return (x + 15) / 16 * 16; }
+
+SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
+  SmemLayout L{};
+  int o = 0;
+  L.o_zs = o;
+  if (zs_smem) o += al16((int)(2 * (size_t)R * Mp * es));
+  L.s_gp = 0;
+  L.s_tp = al16(Mp * Mp * (int)sizeof(double2));
+  L.s_pop = L.s_tp + al16(2 * Mp * Mp * (int)es);
+  L.slot_bytes = L.s_pop + al16((LR_MAX_NT + 2) * (int)sizeof(double));
+  L.o_slot = o;
+  o += 2 * L.slot_bytes;
+  L.o_gd = o;
+  o += al16(Mp * (Mp + 1) * (int)sizeof(double2));
+  L.o_w = o;
+  o += al16(Mp * (Mp + 1) * (int)sizeof(double2));
+  L.o_tred = o;
+  o += al16(2 * Mp * Mp * (int)es);
+  L.o_trd = o;
+  o += al16(Mp * (int)sizeof(double));
+  L.o_xs = o;
+  o += al16(2 * Mp * Mp * (int)es);
+  L.o_misc = o;
+  o += al16(128 * (int)sizeof(double));
+  L.o_tab = o;
+  o += al16(fz::TAB * 7 * (int)(es / 2));
+  L.total = o;
+  return L;
+}
+
+const void* kernel_ptr(lr_precision prec) {
+  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0>;
+  return (const void*)fz::fused_kernel<float2, 1>;
+}
+
+int rows_per_cta(const TrajDev& d, int C) {
+  return d.Nt * ((d.Nr + C - 1) / C) * d.Nf;
+}
+
+}  // namespace
+
+bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* plan) {
+  *plan = FusedPlan{};
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (prop.major < 10) return false;
+  const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  int Mmax = 0, Nmax = 0, min_nr = 1 << 30;
+  bool two = false;
+  double max_work = 0.0, tot_work = 0.0;
+  for (const TrajDev& d : traj) {
+    Mmax = std::max(Mmax, d.M);
+    Nmax = std::max(Nmax, d.N);
+    if (d.n_modes == 2) two = true;
+    min_nr = std::min(min_nr, d.Nr);
+    if (d.Nt >= fz::TAB || d.Nr >= fz::TAB || d.Nf >= fz::TAB) return false;
+    const double w = (double)d.N * d.M * (d.M + 11.0);
+    max_work = std::max(max_work, w);
+    tot_work += w;
+  }
+  const int Mp = (Mmax + 3) / 4 * 4;
+  const int smem_max = (int)prop.sharedMemPerBlockOptin;
+  const void* kern = kernel_ptr(prec);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // Overrides for tuning and tests: LR_FUSED_C = cluster size,
+  // LR_FUSED_ZS = "global" keeps the stage state in L2 instead of shared memory.
+  int force_c = 0, force_global = 0;
+  if (const char* e = getenv("LR_FUSED_C")) force_c = atoi(e);
+  if (const char* e = getenv("LR_FUSED_ZS")) force_global = strcmp(e, "global") == 0;
+  double best = 1e300;
+  for (int C = 1; C <= 16; ++C) {
+    if (two && C > 1) break;
+    if (C > min_nr) break;
+    if (force_c > 0 && C != force_c) continue;
+    int R = 0;
+    for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
+    for (int zs_smem = 1; zs_smem >= 0; --zs_smem) {
+      if (force_global && zs_smem) continue;
+      const SmemLayout L = layout(R, Mp, zs_smem, es);
+      if (L.total > smem_max) continue;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(C * 32);
+      cfg.blockDim = dim3(fz::NT);
+      cfg.dynamicSmemBytes = L.total;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl <= 0) {
+        cudaGetLastError();
+        continue;
+      }
+      const int n_traj = (int)traj.size();
+      const int used = std::min(ncl, n_traj);
+      // cost model: the slowest team, with waves of trajectories per team
+      const double waves = std::ceil((double)n_traj / used);
+      const double per_team = std::max(waves * tot_work / n_traj, max_work) / C;
+      const double t = per_team * (1.0 + 0.04 * (C - 1)) * (zs_smem ? 1.0 : 1.5);
+      if (t < best) {
+        best = t;
+        plan->ok = 1;
+        plan->C = C;
+        plan->n_clusters = used;
+        plan->threads = fz::NT;
+        plan->smem = L.total;
+        plan->zs_smem = zs_smem;
+        plan->Mp = Mp;
+        plan->R = R;
+        plan->Nmax = Nmax;
+        plan->gram_mode = prec == LR_PREC_FP64 ? 0 : 1;
+      }
+      break;   // smem mode preferred when it fits
+    }
+  }
+  if (!plan->ok) return false;
+  // largest work first, round-robin over the teams
+  std::vector<std::pair<double, int>> w;
+  for (size_t j = 0; j < traj.size(); ++j)
+    w.push_back({-(double)traj[j].N * traj[j].M * (traj[j].M + 11.0), (int)j});
+  std::stable_sort(w.begin(), w.end());
+  for (auto& x : w) plan->order.push_back(x.second);
+  return true;
+}
+
+size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj) {
+  // order list, then global stage buffers (only without smem residency) and accumulators per team
+  size_t b = ((sizeof(int) * n_traj + 255) / 256) * 256;
+  const size_t es = plan.gram_mode == 0 ? sizeof(double2) : sizeof(float2);
+  if (!plan.zs_smem) b += ((2 * (size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
+  b += (((size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
+  return b;
+}
+
+cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunParams& rp, lr_precision prec,
+                            long step0, long n_steps, cudaStream_t s) {
+  const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es);
+  fz::Args a{};
+  a.p = p;
+  a.rp = rp;
+  a.step0 = step0;
+  a.n_steps = n_steps;
+  a.C = plan.C;
+  a.n_clusters = plan.n_clusters;
+  a.Mp = plan.Mp;
+  a.R = plan.R;
+  a.Nmax = plan.Nmax;
+  a.zs_smem = plan.zs_smem;
+  a.o_zs = L.o_zs;
+  a.o_slot = L.o_slot;
+  a.slot_bytes = L.slot_bytes;
+  a.s_gp = L.s_gp;
+  a.s_tp = L.s_tp;
+  a.s_pop = L.s_pop;
+  a.o_gd = L.o_gd;
+  a.o_w = L.o_w;
+  a.o_tred = L.o_tred;
+  a.o_trd = L.o_trd;
+  a.o_xs = L.o_xs;
+  a.o_misc = L.o_misc;
+  a.o_tab = L.o_tab;
+  char* sc = static_cast<char*>(p.scratch);
+  size_t off = ((sizeof(int) * rp.n_traj + 255) / 256) * 256;
+  a.order = reinterpret_cast<const int*>(sc);
+  if (!plan.zs_smem) {
+    a.zs_glob = sc + off;
+    off += ((2 * (size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
+  }
+  a.acc_glob = sc + off;
+  cudaError_t e = cudaMemcpyAsync(sc, plan.order.data(), sizeof(int) * rp.n_traj, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const void* kern = kernel_ptr(prec);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+  if (e != cudaSuccess) return e;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan.C * plan.n_clusters);
+  cfg.blockDim = dim3(fz::NT);
+  cfg.dynamicSmemBytes = L.total;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = plan.C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (prec == LR_PREC_FP64)
+    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0>, a);
+  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1>, a);
 }
 
 }  // namespace lr
