@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c4")
     ap.add_argument("--engine", default="auto")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--chunk", type=int, default=None, help="RK4 steps per bench step")
@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=None, help="RK4 steps of the oracle sample")
+    ap.add_argument("--no-plain-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=8, help="RK4 steps timed on the plain FP64 engine")
     return ap.parse_args()
 
 
@@ -305,12 +307,50 @@ def run_ours(args):
         e2e = {"value": world * ntraj * chunk * reps / te, "unit": "traj*steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # plain FP64 engine (the reference GPU path) on the same batch
+    plain = None
+    if not args.no_plain_baseline and engine != "plain":
+        bp = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision="fp64", engine="plain",
+                          max_steps=args.plain_steps + 1, pop_every=args.plain_steps, eta=wl.eta, device=dev)
+        bp.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
+        bp.set_initial(wl.init_seed, wl.eps)
+        bp.integrate(wl.dt, 1)
+        bp.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bp.integrate(wl.dt, args.plain_steps)
+        e1.record(stream)
+        bp.sync()
+        pms = e0.elapsed_time(e1)
+        pv = world * bp.n_traj * args.plain_steps / (pms * 1e-3)
+        plain = {"value": pv, "unit": "traj*steps/s", "engine": "plain", "dtype": "f64",
+                 "steps_timed": args.plain_steps, "speedup": value / pv}
+        bp.close()
+
     cpu = None
+    err = None
     if rank == 0 and not args.no_cpu_baseline:
+        from oracle import parallel
         ns = args.cpu_steps or default_cpu_steps(wl)
-        v, dt_cpu, nt = oracle_sample(wl, ns)
-        cpu = {"value": v, "unit": "traj*steps/s", "cores": nt, "kind": "oracle",
+        t0 = time.perf_counter()
+        ora = parallel.run_workload(wl, ns, max(1, ns), candidates=[0], processes=2)
+        dt_cpu = time.perf_counter() - t0
+        cpu = {"value": 2 * ns / dt_cpu, "unit": "traj*steps/s", "cores": 2, "kind": "oracle",
                "sample": "%d RK4 steps of the g and e trajectories of candidate 0 (%.1f s)" % (ns, dt_cpu)}
+        # accuracy of this path on the same sample, against the FP64 oracle
+        bq = LowRankBatch([cands[0].model], [cands[0].M], precision=prec, engine=args.engine, max_steps=ns,
+                          pop_every=ns, eta=wl.eta, device=dev)
+        bq.set_pulse([(cands[0].pulse.kind, cands[0].pulse.p)], wl.tau)
+        bq.set_initial(wl.init_seed, wl.eps)
+        bq.integrate(wl.dt, ns)
+        og = bq.observables()
+        bq.close()
+        bo = ora["beta"]
+        err = {"sample": "candidate 0, g and e, %d RK4 steps" % ns,
+               "beta_rel": float(np.abs(og["beta"] - bo).max() / np.abs(bo).max()),
+               "pops_abs": float(max(np.abs(og["pops"][j][:, :ora["pops"][j].shape[1]] - ora["pops"][j]).max()
+                                     for j in range(2))),
+               "eps_a_rel": float(abs(og["eps_a"][0] - ora["eps_a"][0]) / abs(ora["eps_a"][0]))}
 
     if rank == 0:
         desc = workload_desc(wl, prec)
@@ -326,6 +366,7 @@ def run_ours(args):
             "pulse_evals_per_s": value / (2 * spp),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "peaks_source": peak_src,
+            "plain_fp64_baseline": plain, "error_vs_oracle": err,
         }
         print(json.dumps(line))
     b.close()

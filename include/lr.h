@@ -195,6 +195,27 @@ lr_status lr_observables(lr_ctx* ctx, double* beta, double* pops, double* nphot,
 /* Synchronise the stream and return the device error word's status. */
 lr_status lr_sync(lr_ctx* ctx, void* stream);
 
+/* Gradient of the assignment errors with respect to the pulse parameters,
+ * by the discrete adjoint of the RK4 integration of Eq. S5 (reverse-mode
+ * differentiation of Eq. S5, the readout signal beta = tr(rho r) and the
+ * assignment error of Sec. S3.A). Differentiates the pulse run made since
+ * lr_set_initial (or lr_set_state at step 0): the current step counter S and
+ * dt are those of the run; tau stays fixed.
+ *
+ * d_eps_a (host, [n_cand]): cotangent dL/d eps_a of each candidate.
+ * d_theta (host, [n_cand][8], out): dL/d theta; entries past the pulse kind's
+ *   parameter count (4 for flat-top) are zero.
+ * ckpt_every: states are kept every ckpt_every steps and each segment is
+ *   recomputed; memory is (ceil(S/ckpt_every) + ckpt_every + 13) copies of all
+ *   states in complex128 plus small tables, in the caller's workspace `dev_ws`
+ *   (lr_backward_workspace_size bytes, 256-byte aligned).
+ * Arithmetic: FP64 throughout (for an FP32 context the kept initial state is
+ * widened), forward recomputation with the PLAIN engine's kernels.
+ * Synchronous; returns the device error status. */
+lr_status lr_backward_workspace_size(const lr_ctx* ctx, int ckpt_every, size_t* bytes);
+lr_status lr_backward(lr_ctx* ctx, void* dev_ws, size_t ws_bytes, const double* d_eps_a, double* d_theta,
+                      int ckpt_every, void* stream);
+
 lr_status lr_query(const lr_ctx* ctx, lr_info* info);
 
 /* No-allocation entry point (the paper has no counterpart; this is a

@@ -32,6 +32,8 @@ struct lr_ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool have_pulse = false, have_state = false;
+  bool z0_valid = false;   // the state at step 0 is kept for lr_backward
+  size_t o_z0 = 0;
   double tau = 0.0, dt = 0.0;
   long step = 0;
   std::string last_error;
@@ -195,6 +197,7 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   c->o_pulse = take(sizeof(PulseDev) * n_cand);
   c->o_err = take(sizeof(unsigned));
   c->o_zn = take(es * c->tot_elems);
+  c->o_z0 = take(es * c->tot_elems);
   c->o_za = take(sizeof(double2) * c->tot_elems);
   if (c->engine == LR_ENGINE_PLAIN) {
     c->o_zb = take(sizeof(double2) * c->tot_elems);
@@ -279,9 +282,13 @@ lr_status lr_set_initial(lr_ctx* c, uint64_t seed, double eps, void* stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "initial state kernel");
   e = cudaMemsetAsync(c->ws + c->o_err, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "clearing error word");
+  const size_t es = c->opt.precision == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  e = cudaMemcpyAsync(c->ws + c->o_z0, c->ws + c->o_zn, es * c->tot_elems, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "keeping the initial state");
   c->step = 0;
   c->dt = 0.0;
   c->have_state = true;
+  c->z0_valid = true;
   return LR_OK;
 }
 
@@ -300,9 +307,16 @@ lr_status lr_set_state(lr_ctx* c, int traj, const double* host_Z, long step, voi
     e = cudaMemcpyAsync(tmp, host_Z, sizeof(double2) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = lr::launch_convert(tmp, c->ws + c->o_zn + sizeof(float2) * d.z_off, n, 1, s);
   }
+  if (e == cudaSuccess && step == 0) {
+    const size_t es = c->opt.precision == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    e = cudaMemcpyAsync(c->ws + c->o_z0 + es * d.z_off, c->ws + c->o_zn + es * d.z_off, es * n,
+                        cudaMemcpyDeviceToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "setting state");
   if (step != c->step) c->step = step;
+  if (step != 0) c->z0_valid = false;
+  if (step == 0) c->dt = 0.0;
   c->have_state = true;
   return LR_OK;
 }
@@ -380,6 +394,38 @@ lr_status lr_sync(lr_ctx* c, void* stream) {
   if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronising");
+  return check_device_error(c);
+}
+
+lr_status lr_backward_workspace_size(const lr_ctx* c, int ckpt_every, size_t* bytes) {
+  if (!c || !bytes || ckpt_every < 1) return LR_ERR_ARG;
+  if (c->step < 1) return LR_ERR_STATE;
+  size_t part = 0;
+  for (const TrajDev& d : c->traj) part += (size_t)d.nblk * lr::plain_pstride(d.M);
+  const lr::BwdLayout L = lr::bwd_layout(c->tot_elems, c->n_traj, c->n_cand, c->nt_max, part, c->step, ckpt_every);
+  *bytes = L.total;
+  return LR_OK;
+}
+
+lr_status lr_backward(lr_ctx* c, void* dev_ws, size_t ws_bytes, const double* d_eps_a, double* d_theta,
+                      int ckpt_every, void* stream) {
+  if (!c || !d_eps_a || !d_theta || ckpt_every < 1) return LR_ERR_ARG;
+  if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
+  if (!c->have_pulse || !c->z0_valid || c->step < 1 || !(c->dt > 0.0))
+    return fail(c, LR_ERR_STATE, "lr_backward needs a pulse run integrated from step 0 of a kept initial state");
+  for (int k = 0; k < c->n_cand; ++k)
+    if (!std::isfinite(d_eps_a[k])) return fail(c, LR_ERR_ARG, "non-finite cotangent");
+  size_t part = 0;
+  for (const TrajDev& d : c->traj) part += (size_t)d.nblk * lr::plain_pstride(d.M);
+  const lr::BwdLayout L = lr::bwd_layout(c->tot_elems, c->n_traj, c->n_cand, c->nt_max, part, c->step, ckpt_every);
+  if (!dev_ws || ws_bytes < L.total) return fail(c, LR_ERR_WORKSPACE, "backward workspace missing or too small");
+  if (reinterpret_cast<uintptr_t>(dev_ws) % 256 != 0) return fail(c, LR_ERR_WORKSPACE, "backward workspace misaligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevPtrs p = dev_ptrs(c);
+  RunParams rp = run_params(c);
+  cudaError_t e = lr::backward_run(p, rp, static_cast<char*>(dev_ws), L, c->tot_elems, c->max_nblk, c->max_N, c->step,
+                                   c->ws + c->o_z0, c->opt.precision == LR_PREC_FP32_G64, d_eps_a, d_theta, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "backward");
   return check_device_error(c);
 }
 

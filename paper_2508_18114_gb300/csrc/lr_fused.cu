@@ -113,14 +113,20 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   const int cid = blockIdx.x / C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Mp = a.Mp;
-  const long long zs_buf = (long long)a.R * Mp;   // elements per smem Z_s buffer
+  // shared-memory row stride of Z_s: odd in complex elements, so lanes that
+  // read consecutive rows hit distinct banks
+  const int lds = Mp + 1;
+  const long long zs_buf = (long long)a.R * lds;  // elements per smem Z_s buffer
 
   double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);     // [Mp][Mp+1]  G -> L -> G^-1
   double2* W = reinterpret_cast<double2*>(smem + a.o_w);       // [Mp][Mp+1]  L^-1
   T2* Tred = reinterpret_cast<T2*>(smem + a.o_tred);           // [2][Mp*Mp]
   double* trd = reinterpret_cast<double*>(smem + a.o_trd);     // [Mp] diag of T_r (FP64)
   T2* XT = reinterpret_cast<T2*>(smem + a.o_xs);               // [2][Mp][Mp] (l, m)
-  double* misc = reinterpret_cast<double*>(smem + a.o_misc);   // coef, flags
+  // misc (FP64 scalars): [0] pulse coefficient, [1] not-PD flag, [8..24) photon
+  // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
+  // photons, [96..128) 1/L[k][k], [128..) bulk-precision coefficient and steps
+  double* misc = reinterpret_cast<double*>(smem + a.o_misc);
   T* sq = reinterpret_cast<T*>(smem + a.o_tab);                 // sqrt(k), k < TAB
   T* dtab = sq + TAB;                                           // [3][TAB][2]: diagonal energies (hi, lo)
   const int ldg = Mp + 1;
@@ -162,19 +168,19 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
       if (!a.zs_smem) return zs_glob + ((size_t)b * a.Nmax + (size_t)((it2 * Nr + ir2) * Nf + iff2)) * Mp;
       if (ir2 < P.r_lo) {
         const int l = (it2 * Pm.nr + (ir2 - Pm.r_lo)) * Nf + iff2;
-        return zs_m + (size_t)b * zs_buf + (size_t)l * Mp;
+        return zs_m + (size_t)b * zs_buf + (size_t)l * lds;
       }
       if (ir2 >= P.r_lo + P.nr) {
         const int l = (it2 * Pp.nr + (ir2 - Pp.r_lo)) * Nf + iff2;
-        return zs_p + (size_t)b * zs_buf + (size_t)l * Mp;
+        return zs_p + (size_t)b * zs_buf + (size_t)l * lds;
       }
       const int l = (it2 * P.nr + (ir2 - P.r_lo)) * Nf + iff2;
-      return zs_local + (size_t)b * zs_buf + (size_t)l * Mp;
+      return zs_local + (size_t)b * zs_buf + (size_t)l * lds;
     };
     // own row l of buffer b (writable)
     auto own = [&](int b, int l) -> T2* {
       if (!a.zs_smem) return zs_glob + ((size_t)b * a.Nmax + (size_t)grow(l)) * Mp;
-      return zs_local + (size_t)b * zs_buf + (size_t)l * Mp;
+      return zs_local + (size_t)b * zs_buf + (size_t)l * lds;
     };
 
     // ---- per-trajectory tables: sqrt(k) and the separable diagonal of H,
@@ -189,6 +195,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
         dtab[(c3 * TAB + k) * 2 + 1] = (T)(v[c3] - (double)hi);
       }
     }
+    if (tid == 0) *reinterpret_cast<int*>(misc + 140) = 0;
     // ---- load Z_n into Z_s buffer 0 (own rows), zero the rank padding
     for (int e = tid; e < P.R * Mp; e += NT) {
       const int l = e / Mp, m = e - l * Mp;
@@ -212,7 +219,15 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
         {
           const int nt_ = Mp / TP;
           const int n_g = nt_ * (nt_ + 1) / 2, n_t = nt_ * nt_;
-          for (int task = warp; task < n_g + n_t; task += NWARP) {
+          // warps take tasks dynamically (heavier Gram tiles first); every task's
+          // arithmetic is independent of which warp runs it, so results stay bitwise
+          // reproducible
+          int* task_ctr = reinterpret_cast<int*>(misc + 140);
+          for (;;) {
+            int task = 0;
+            if (lane == 0) task = atomicAdd(task_ctr, 1);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (task >= n_g + n_t) break;
             if (task < n_g) {
               // upper tile (ti <= tj) of G
               int ti = 0, rem = task;
@@ -413,17 +428,17 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 Gd[j * ldg + i] = mk(re, -im);
               }
             } else {
-              double re = 0.0, im = 0.0;
+              T re = 0, im = 0;
               for (int r = 0; r < C; ++r) {
                 const T2* tpr = cluster.map_shared_rank(tp, r);
                 const T2 v = tpr[(mat - 1) * MM + ij];
-                re += (double)v.x;
-                im += (double)v.y;
+                re += v.x;
+                im += v.y;
               }
-              Tred[(mat - 1) * MM + ij] = cm<T2>((T)re, (T)im);
+              Tred[(mat - 1) * MM + ij] = cm<T2>(re, im);
               if (mat == 1 && i == j) {
-                trd[i] = re;
-                misc[40 + i] = im;
+                trd[i] = (double)re;
+                misc[32 + i] = (double)im;
               }
             }
           }
@@ -432,19 +447,28 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             const bool use = tid < Nt || tid == LR_MAX_NT;
             if (use)
               for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(popp, r)[tid];
-            misc[80 + tid] = s;
+            misc[64 + tid] = s;
           }
           if (tid == 0) {
             const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
             misc[0] = pulse_coefficient(pulse, a.rp.tau, ts);
             misc[1] = 0.0;   // not-PD flag
+            *reinterpret_cast<int*>(misc + 140) = 0;   // phase-P task counter of the next stage
+            // bulk-precision copies: coefficient, step sizes split as hi + lo
+            T* tb = reinterpret_cast<T*>(misc + 128);
+            const double hs = stage == 2 ? dt : 0.5 * dt, h6 = dt / 6.0;
+            tb[0] = (T)misc[0];
+            tb[1] = (T)hs;
+            tb[2] = (T)(hs - (double)tb[1]);
+            tb[3] = (T)h6;
+            tb[4] = (T)(h6 - (double)tb[3]);
           }
           __syncthreads();
           if (stage == 0 && q == 0 && tid == 0) {
             double br = 0.0, bi = 0.0;
             for (int i = 0; i < M; ++i) {
               br += trd[i];
-              bi += misc[40 + i];
+              bi += misc[32 + i];
             }
             a.p.beta[(size_t)tj * (a.rp.max_steps + 1) + step] = mk(br, bi);
             if (!isfinite(br) || !isfinite(bi)) set_error(a.p.err, DEV_NONFINITE);
@@ -452,16 +476,19 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               const long rec = step / pe;
               double trace = 0.0;
               for (int lv = 0; lv < a.rp.nt_max; ++lv) {
-                const double v = lv < Nt ? misc[80 + lv] : 0.0;
+                const double v = lv < Nt ? misc[64 + lv] : 0.0;
                 a.p.pops[((size_t)tj * a.rp.n_rec + rec) * a.rp.nt_max + lv] = v;
                 trace += v;
               }
-              a.p.nphot[(size_t)tj * a.rp.n_rec + rec] = misc[80 + LR_MAX_NT];
+              a.p.nphot[(size_t)tj * a.rp.n_rec + rec] = misc[64 + LR_MAX_NT];
               a.p.trace[(size_t)tj * a.rp.n_rec + rec] = trace;
             }
           }
           if (last) break;
           // Cholesky G = L L^dag in Gd (lower)
+          // (FP64 runs at 2 FMA/clk/SM here: every reciprocal is formed once, by
+          //  one thread, and shared through shared memory)
+          double* rinv = misc + 96;     // [M] 1 / L[k][k]
           for (int k = 0; k < M; ++k) {
             if (tid == 0) {
               double piv = Gd[k * ldg + k].x;
@@ -469,10 +496,12 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 misc[1] = 1.0;
                 piv = 1.0;
               }
-              Gd[k * ldg + k] = mk(sqrt(piv), 0.0);
+              const double sd = sqrt(piv);
+              Gd[k * ldg + k] = mk(sd, 0.0);
+              rinv[k] = 1.0 / sd;
             }
             __syncthreads();
-            const double inv = 1.0 / Gd[k * ldg + k].x;
+            const double inv = rinv[k];
             for (int i = k + 1 + tid; i < M; i += NT) {
               const double2 v = Gd[i * ldg + k];
               Gd[i * ldg + k] = mk(v.x * inv, v.y * inv);
@@ -495,7 +524,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           }
           __syncthreads();
           for (int k = 0; k < M; ++k) {
-            const double inv = 1.0 / Gd[k * ldg + k].x;
+            const double inv = rinv[k];
             for (int j = tid; j <= k; j += NT) {
               const double2 v = W[k * ldg + j];
               W[k * ldg + j] = mk(v.x * inv, v.y * inv);
@@ -509,7 +538,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
             __syncthreads();
           }
-          // G^-1 = W^dag W (Hermitian) into Gd
+          // G^-1 = W^dag W (Hermitian), rounded once to the bulk precision
+          T2* Gi = reinterpret_cast<T2*>(Gd);   // L is no longer needed: reuse its storage
           for (int e = tid; e < M * M; e += NT) {
             const int i = e / M, j = e - i * M;
             if (i > j) continue;
@@ -519,8 +549,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               re += x.x * y.x + x.y * y.y;
               im += x.x * y.y - x.y * y.x;
             }
-            Gd[i * ldg + j] = mk(re, im);
-            if (i != j) Gd[j * ldg + i] = mk(re, -im);
+            Gi[i * Mp + j] = cm<T2>((T)re, (T)im);
+            if (i != j) Gi[j * Mp + i] = cm<T2>((T)re, (T)-im);
           }
           __syncthreads();
           // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
@@ -531,8 +561,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             if (l < M && m < M) {
               const T2* Tk = Tred + k * MM;
               for (int j = 0; j < M; ++j) {
-                const double2 g = Gd[m * ldg + j];
-                const T gr = (T)g.x, gi = (T)g.y;
+                const T2 gv = Gi[m * Mp + j];
+                const T gr = gv.x, gi = gv.y;
                 const T2 t = Tk[j * Mp + l];
                 xr = fma(gr, t.x, fma(-gi, t.y, xr));
                 xi = fma(gr, t.y, fma(gi, t.x, xi));
@@ -546,14 +576,12 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
 
         // ================= F: right-hand side and RK4 stage update
         {
-          const T c = (T)misc[0];
+          // coefficient and split step sizes h = hi + lo (no systematic FP32 step error)
+          const T* tb = reinterpret_cast<const T*>(misc + 128);
+          const T c = tb[0], hs_hi = tb[1], hs_lo = tb[2], h6_hi = tb[3], h6_lo = tb[4];
           const int nxt = cur ^ 1;
           const int mq = Mp / 4;
           const int nrt = (P.R + TR - 1) / TR;
-          // split step sizes: h = hi + lo exactly (no systematic FP32 step error)
-          const double hs = stage == 2 ? dt : 0.5 * dt, h6 = dt / 6.0;
-          const T hs_hi = (T)hs, hs_lo = (T)(hs - (double)hs_hi);
-          const T h6_hi = (T)h6, h6_lo = (T)(h6 - (double)h6_hi);
           const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
           for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
@@ -740,7 +768,7 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
   SmemLayout L{};
   int o = 0;
   L.o_zs = o;
-  if (zs_smem) o += al16((int)(2 * (size_t)R * Mp * es));
+  if (zs_smem) o += al16((int)(2 * (size_t)R * (Mp + 1) * es));
   L.s_gp = 0;
   L.s_tp = al16(Mp * Mp * (int)sizeof(double2));
   L.s_pop = L.s_tp + al16(2 * Mp * Mp * (int)es);
@@ -758,7 +786,7 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
   L.o_xs = o;
   o += al16(2 * Mp * Mp * (int)es);
   L.o_misc = o;
-  o += al16(128 * (int)sizeof(double));
+  o += al16(144 * (int)sizeof(double));
   L.o_tab = o;
   o += al16(fz::TAB * 7 * (int)(es / 2));
   L.total = o;

@@ -72,6 +72,55 @@ __device__ __forceinline__ double pulse_coefficient(const PulseDev& P, double ta
   return env * cos(wd * t + phi);
 }
 
+// d c(t) / d theta_i for the pulse parameters (kind 0: 4 entries, kind 1: 8),
+// written into dc[8]; returns c(t). With f = logistic(u), df/du = f (1 - f):
+//  flat-top   u1 = 5t/t_r - 6, u2 = 5(t - tau)/t_r + 6, Omega = A f1 (1 - f2);
+//  two-segment u_r = 5t/t_rise - 6, u_m = 5(t - t_sw)/t_sm,
+//              u_f = 5(t - tau)/t_fall + 6,
+//              Omega = A1 f_r + (A2 - A1) f_m - A2 f_f;
+//  c = Omega cos(w_d t + phi).
+__device__ __forceinline__ double pulse_coefficient_grad(const PulseDev& P, double tau, double t, double* dc) {
+  double env, wd, phi;
+  double denv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int iw, ip;
+  if (P.kind == 0) {
+    const double A = P.p[0], tr = P.p[2];
+    const double s = tr / 5.0, t0 = 6.0 * s;
+    const double f1 = logistic(t, t0, s), f2 = logistic(t, tau - t0, s);
+    env = A * f1 * (1.0 - f2);
+    const double du1 = -5.0 * t / (tr * tr), du2 = -5.0 * (t - tau) / (tr * tr);
+    denv[0] = f1 * (1.0 - f2);
+    denv[2] = A * (f1 * (1.0 - f1) * du1 * (1.0 - f2) - f1 * f2 * (1.0 - f2) * du2);
+    iw = 1;
+    ip = 3;
+  } else {
+    const double A1 = P.p[0], A2 = P.p[1], tsw = P.p[2], trs = P.p[3], tfl = P.p[4], tsm = P.p[5];
+    const double fr = logistic(t, 1.2 * trs, 0.2 * trs), fm = logistic(t, tsw, 0.2 * tsm),
+                 ff = logistic(t, tau - 1.2 * tfl, 0.2 * tfl);
+    env = A1 * fr + (A2 - A1) * fm - A2 * ff;
+    denv[0] = fr - fm;
+    denv[1] = fm - ff;
+    denv[2] = (A2 - A1) * fm * (1.0 - fm) * (-5.0 / tsm);
+    denv[3] = A1 * fr * (1.0 - fr) * (-5.0 * t / (trs * trs));
+    denv[4] = -A2 * ff * (1.0 - ff) * (-5.0 * (t - tau) / (tfl * tfl));
+    denv[5] = (A2 - A1) * fm * (1.0 - fm) * (-5.0 * (t - tsw) / (tsm * tsm));
+    iw = 6;
+    ip = 7;
+  }
+  wd = P.p[iw];
+  phi = P.p[ip];
+  double sn, cs;
+  sincos(wd * t + phi, &sn, &cs);
+  for (int i = 0; i < 8; ++i) dc[i] = denv[i] * cs;
+  dc[iw] = -env * t * sn;
+  dc[ip] = -env * sn;
+  return env * cs;
+}
+
+// Doubles per row block of the plain engine's partial sums: G, Z^dag r Z,
+// Z^dag b Z (M x M complex each) then level populations and photons.
+__host__ __device__ inline size_t plain_pstride(int M) { return (size_t)6 * M * M + LR_MAX_NT + 2; }
+
 // ------------------------------------------------------------------ stencil
 
 // Mode indices of a row.
@@ -151,5 +200,20 @@ int plain_rows_per_block();
 size_t plain_partial_doubles(int M);
 cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0,
                             long n_steps, cudaStream_t s);
+// single kernels of the plain engine (used by the adjoint's recomputation)
+void plain_gram_launch(const DevPtrs& p, const RunParams& rp, int max_nblk, const double2* zin, cudaStream_t s);
+void plain_rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const double2* zin, double2* zout, int stage,
+                      double t, cudaStream_t s);
+
+// lr_adjoint.cu
+struct BwdLayout {
+  size_t ck, seg, cur, za, zb, acc, U, Ub, lam, lamn, X, part, Xs, Gi, EP, bpart, beta, pops, nphot, trace, gcoef,
+      deps, thbar, total;
+  long n_seg, K;
+};
+BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t part_doubles, long S, int K);
+cudaError_t backward_run(const DevPtrs& main, const RunParams& rp, char* ws, const BwdLayout& L, long long tot,
+                         int max_nblk, int max_N, long S, const void* z0, int z0_fp32, const double* deps_host,
+                         double* dtheta_host, cudaStream_t s);
 
 }  // namespace lr

@@ -19,7 +19,7 @@ namespace lr {
 constexpr int PR = 16;        // rows per Gram block
 constexpr int PT = 256;       // threads per block
 
-__host__ __device__ inline size_t pstride(int M) { return (size_t)6 * M * M + LR_MAX_NT + 2; }
+__host__ __device__ inline size_t pstride(int M) { return plain_pstride(M); }
 
 int plain_rows_per_block() { return PR; }
 size_t plain_partial_doubles(int M) { return pstride(M); }
@@ -327,6 +327,16 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
       Zn[o] = mk(zn.x + h * (a.x + fr), zn.y + h * (a.y + fi));
     }
   }
+}
+
+void plain_gram_launch(const DevPtrs& p, const RunParams& rp, int max_nblk, const double2* zin, cudaStream_t s) {
+  plain_gram<<<dim3(max_nblk, rp.n_traj), PT, 0, s>>>(p.traj, zin, p.part, 0);
+}
+
+void plain_rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const double2* zin, double2* zout, int stage,
+                      double t, cudaStream_t s) {
+  const int rhs_blocks = (int)((long)max_N * LR_MAX_RANK / PT / 2 + 1);
+  plain_rhs<<<dim3(rhs_blocks, rp.n_traj), PT, 0, s>>>(p, rp, zin, zout, stage, t);
 }
 
 cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0,

@@ -34,6 +34,7 @@ EXPORTS = (
     "lr_set_initial", "lr_set_state", "lr_get_state", "lr_integrate",
     "lr_observables", "lr_sync", "lr_query", "lr_status_string",
     "lr_last_error", "lr_destroy", "lr_integrate_plain_noalloc",
+    "lr_backward_workspace_size", "lr_backward",
 )
 
 
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_destroy.argtypes = [vp]
     lib.lr_destroy.restype = None
     lib.lr_integrate_plain_noalloc.argtypes = [C.POINTER(lr_model), i, C.POINTER(lr_pulse), d, vp, vp, d, l, l, vp]
+    lib.lr_backward_workspace_size.argtypes = [vp, i, C.POINTER(C.c_size_t)]
+    lib.lr_backward.argtypes = [vp, vp, C.c_size_t, vp, vp, i, vp]
     for name in EXPORTS:
         if name not in ("lr_status_string", "lr_last_error", "lr_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -263,6 +266,22 @@ class LowRankBatch:
         ptr = lambda k: C.c_void_p(tensors[k].data_ptr()) if k in tensors else None  # noqa: E731
         self._check(self._lib.lr_observables(self._h, ptr("beta"), ptr("pops"), ptr("nphot"),
                                              ptr("trace"), ptr("eps_a"), C.c_void_p(_stream_ptr(stream))))
+
+    def backward(self, d_eps_a, ckpt_every=200, stream=None):
+        """dL/dtheta [n_cand, 8] for cotangents dL/deps_a (lr_backward)."""
+        import torch
+        n = len(self.models)
+        g = np.ascontiguousarray(np.asarray(d_eps_a, dtype=np.float64).reshape(n))
+        sz = C.c_size_t()
+        self._check(self._lib.lr_backward_workspace_size(self._h, int(ckpt_every), C.byref(sz)))
+        ws = torch.empty(int(sz.value) + 256, dtype=torch.uint8, device=self.device)
+        ptr = (ws.data_ptr() + 255) // 256 * 256
+        out = np.zeros((n, 8))
+        self._check(self._lib.lr_backward(self._h, C.c_void_p(ptr), sz, g.ctypes.data_as(C.c_void_p),
+                                          out.ctypes.data_as(C.c_void_p), int(ckpt_every),
+                                          C.c_void_p(_stream_ptr(stream))))
+        del ws
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
