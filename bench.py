@@ -218,7 +218,8 @@ def run_ours(args):
     wl = load_workload(args)
     prec = args.precision or getattr(wl, "precision", "fp64")
     spp = int(round(wl.tau / wl.dt))
-    chunk = args.chunk or max(1, min(spp // 20, 4000))
+    # default slice: ~4 s of integration per bench step on this workload
+    chunk = args.chunk or max(1, min(spp // 20, int(7e10 / sum(c.model.N * c.M * c.M for c in wl.candidates))))
     total_steps = chunk * (args.warmup + args.steps)
     if total_steps > spp:
         raise SystemExit("warmup + steps slices exceed one pulse (%d steps)" % spp)

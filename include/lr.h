@@ -84,11 +84,13 @@ typedef enum {
 } lr_status;
 
 /* Arithmetic of the bulk state. FP64: complex128 everywhere.
+ * FP32: as FP32_G64 but with the Gram matrix accumulated in FP32 (Cholesky,
+ * inverse and signal stay FP64); FUSED engine only.
  * FP32_G64: Z, the operator apply, the projection term and the RK4 stages in
  * complex64; the Gram matrix Z^dag Z (exact FP32 products, FP64-class
  * double-word accumulation), its Cholesky factor, the solves and the readout
  * signal in FP64. */
-typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1 } lr_precision;
+typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1, LR_PREC_FP32 = 2 } lr_precision;
 
 /* PLAIN: straightforward HBM-resident kernels, several launches per RK4
  * stage (the reference GPU path). FUSED: one persistent launch per

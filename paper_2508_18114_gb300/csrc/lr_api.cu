@@ -112,7 +112,8 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   *out = nullptr;
   if (n_cand <= 0 || !models || !ranks || !opt) return LR_ERR_ARG;
   if (opt->max_steps < 1 || opt->pop_every < 1 || !(opt->eta > 0.0 && opt->eta <= 1.0)) return LR_ERR_ARG;
-  if (opt->precision != LR_PREC_FP64 && opt->precision != LR_PREC_FP32_G64) return LR_ERR_ARG;
+  if (opt->precision != LR_PREC_FP64 && opt->precision != LR_PREC_FP32_G64 && opt->precision != LR_PREC_FP32)
+    return LR_ERR_ARG;
   if (opt->engine != LR_ENGINE_AUTO && opt->engine != LR_ENGINE_PLAIN && opt->engine != LR_ENGINE_FUSED)
     return LR_ERR_ARG;
   lr_ctx* c = new (std::nothrow) lr_ctx();
@@ -278,7 +279,7 @@ lr_status lr_set_initial(lr_ctx* c, uint64_t seed, double eps, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevPtrs p = dev_ptrs(c);
   RunParams rp = run_params(c);
-  cudaError_t e = lr::launch_initial_state(p, rp, c->max_N, c->opt.precision == LR_PREC_FP32_G64, seed, eps, s);
+  cudaError_t e = lr::launch_initial_state(p, rp, c->max_N, c->opt.precision != LR_PREC_FP64, seed, eps, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "initial state kernel");
   e = cudaMemsetAsync(c->ws + c->o_err, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "clearing error word");
@@ -424,7 +425,7 @@ lr_status lr_backward(lr_ctx* c, void* dev_ws, size_t ws_bytes, const double* d_
   DevPtrs p = dev_ptrs(c);
   RunParams rp = run_params(c);
   cudaError_t e = lr::backward_run(p, rp, static_cast<char*>(dev_ws), L, c->tot_elems, c->max_nblk, c->max_N, c->step,
-                                   c->ws + c->o_z0, c->opt.precision == LR_PREC_FP32_G64, d_eps_a, d_theta, s);
+                                   c->ws + c->o_z0, c->opt.precision != LR_PREC_FP64, d_eps_a, d_theta, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "backward");
   return check_device_error(c);
 }

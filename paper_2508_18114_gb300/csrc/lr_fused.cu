@@ -795,6 +795,7 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
 
 const void* kernel_ptr(lr_precision prec) {
   if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0>;
+  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0>;
   return (const void*)fz::fused_kernel<float2, 1>;
 }
 
@@ -884,7 +885,8 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
         plan->Mp = Mp;
         plan->R = R;
         plan->Nmax = Nmax;
-        plan->gram_mode = prec == LR_PREC_FP64 ? 0 : 1;
+        plan->gram_mode = prec == LR_PREC_FP32_G64 ? 1 : 0;
+        plan->es = (int)es;
       }
       break;   // smem mode preferred when it fits
     }
@@ -902,7 +904,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
 size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj) {
   // order list, then global stage buffers (only without smem residency) and accumulators per team
   size_t b = ((sizeof(int) * n_traj + 255) / 256) * 256;
-  const size_t es = plan.gram_mode == 0 ? sizeof(double2) : sizeof(float2);
+  const size_t es = plan.es;
   if (!plan.zs_smem) b += ((2 * (size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
   b += (((size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
   return b;
@@ -962,8 +964,8 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (prec == LR_PREC_FP64)
-    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0>, a);
+  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0>, a);
+  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0>, a);
   return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1>, a);
 }
 

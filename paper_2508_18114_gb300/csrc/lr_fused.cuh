@@ -27,6 +27,7 @@ struct FusedPlan {
   int R;           // largest rows per CTA
   int Nmax;        // largest N in the batch
   int gram_mode;   // 0 native (bulk type), 1 double-word FP32 (FP64-class)
+  int es;          // bytes per complex state element
   std::vector<int> order;   // trajectories, largest work first
 };
 

@@ -24,7 +24,7 @@ STATUS = {
     4: "LR_ERR_WORKSPACE", 5: "LR_ERR_NOT_PD", 6: "LR_ERR_NONFINITE",
     7: "LR_ERR_TIMEOUT", 8: "LR_ERR_STATE", 9: "LR_ERR_UNSUPPORTED",
 }
-PRECISION = {"fp64": 0, "fp32_g64": 1}
+PRECISION = {"fp64": 0, "fp32_g64": 1, "fp32": 2}
 ENGINE = {"auto": 0, "plain": 1, "fused": 2}
 ENGINE_NAME = {v: k for k, v in ENGINE.items()}
 
