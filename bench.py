@@ -56,14 +56,36 @@ def parse():
     return ap.parse_args()
 
 
-def load_workload(args):
+def load_workload(args, rank=0):
+    """The workload of one rank. Batch workloads (c3-c5) are candidate
+    populations: rank r takes the next block of candidates of the same seeded
+    population (weak scaling, no data-path collective); the single-candidate
+    workloads are replicated."""
     import lr_inputs as li
     name = args.workload
     kw = {}
-    if args.candidates is not None and name in ("c3", "c4", "c5"):
-        kw["n_candidates"] = args.candidates
-    wl = li.workload(name, **kw)
-    return wl
+    if name in ("c3", "c4", "c5"):
+        n = args.candidates if args.candidates is not None else li.workload(name).n_traj // 2
+        kw["n_candidates"] = n
+        kw["first"] = rank * n
+    return li.workload(name, **kw)
+
+
+def aggregate(ms_local, units_local, dist=None):
+    """Whole-job throughput: units of all ranks / slowest rank's time (max over
+    ranks of the device-timed region)."""
+    import torch
+    ms, units = float(ms_local), float(units_local)
+    if dist is not None:
+        t = torch.tensor([ms, units], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms, units = float(mx[0]), float(sm[1])
+    return units / (ms * 1e-3), ms, units
 
 
 def workload_desc(wl, precision):
@@ -215,7 +237,7 @@ def run_ours(args):
     from paper_2508_18114_gb300 import LowRankBatch
     from paper_2508_18114_gb300 import lr as lrmod
 
-    wl = load_workload(args)
+    wl = load_workload(args, rank)
     prec = args.precision or getattr(wl, "precision", "fp64")
     spp = int(round(wl.tau / wl.dt))
     # default slice: ~4 s of integration per bench step on this workload
@@ -229,7 +251,7 @@ def run_ours(args):
     b = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision=prec, engine=args.engine,
                      max_steps=spp, pop_every=max(1, chunk), eta=wl.eta, device=dev)
     b.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
-    b.set_initial(wl.init_seed + 7919 * rank, wl.eps)
+    b.set_initial(wl.init_seed + 7919 * rank, wl.eps)   # replicas of single-candidate workloads differ by seed
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -251,14 +273,9 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     b.sync()
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms_local = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     ntraj = b.n_traj
-    value_rank = ntraj * chunk * args.steps / (ms * 1e-3)
-    value = value_rank * world
+    value, ms, _ = aggregate(ms_local, ntraj * chunk * args.steps, dist)
     info = b.query()
     engine = lrmod.ENGINE_NAME[info.engine]
 

@@ -208,7 +208,7 @@ lr_status lr_sync(lr_ctx* ctx, void* stream);
  * d_theta (host, [n_cand][8], out): dL/d theta; entries past the pulse kind's
  *   parameter count (4 for flat-top) are zero.
  * ckpt_every: states are kept every ckpt_every steps and each segment is
- *   recomputed; memory is (ceil(S/ckpt_every) + ckpt_every + 13) copies of all
+ *   recomputed; memory is (ceil(S/ckpt_every) + ckpt_every + 15) copies of all
  *   states in complex128 plus small tables, in the caller's workspace `dev_ws`
  *   (lr_backward_workspace_size bytes, 256-byte aligned).
  * Arithmetic: FP64 throughout (for an FP32 context the kept initial state is

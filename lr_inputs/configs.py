@@ -179,9 +179,10 @@ def c2(n_steps: Optional[int] = None, M: int = 20) -> Workload:
     return Workload("c2", [cand], dt, ns, ns * dt, init_seed=1002)
 
 
-def c3(n_candidates: int = 256, n_steps: Optional[int] = None) -> Workload:
+def c3(n_candidates: int = 256, n_steps: Optional[int] = None, first: int = 0) -> Workload:
+    """Candidates first .. first + n_candidates - 1 of the c3 population."""
     cands = []
-    for i in range(n_candidates):
+    for i in range(first, first + n_candidates):
         s = SplitMix64Stream(0xC3000000 + i)
         nt = s.integer(6, 12)
         nr = s.integer(15, 30)
@@ -194,17 +195,19 @@ def c3(n_candidates: int = 256, n_steps: Optional[int] = None) -> Workload:
     return Workload("c3", cands, dt, ns, ns * dt, init_seed=1003)
 
 
-def c4(n_candidates: int = 256, n_steps: Optional[int] = None) -> Workload:
+def c4(n_candidates: int = 256, n_steps: Optional[int] = None, first: int = 0) -> Workload:
+    """Candidates first .. first + n_candidates - 1 of the c4 population."""
     m = _filter_model(10, 20, 10)
-    cands = [Candidate(m, 20, pulse_two_segment(3 + i, m.wr)) for i in range(n_candidates)]
+    cands = [Candidate(m, 20, pulse_two_segment(3 + i, m.wr)) for i in range(first, first + n_candidates)]
     dt = 5e-4
     ns = 80000 if n_steps is None else n_steps
     return Workload("c4", cands, dt, ns, ns * dt, init_seed=1004, precision="fp32_g64")
 
 
-def c5(n_candidates: int = 64, n_steps: Optional[int] = None) -> Workload:
+def c5(n_candidates: int = 64, n_steps: Optional[int] = None, first: int = 0) -> Workload:
+    """Candidates first .. first + n_candidates - 1 of the c5 population."""
     m = _filter_model(10, 40, 20)
-    cands = [Candidate(m, 32, pulse_two_segment(5 + i, m.wr)) for i in range(n_candidates)]
+    cands = [Candidate(m, 32, pulse_two_segment(5 + i, m.wr)) for i in range(first, first + n_candidates)]
     dt = 5e-4
     ns = 80000 if n_steps is None else n_steps
     return Workload("c5", cands, dt, ns, ns * dt, init_seed=1005, precision="fp32_g64")

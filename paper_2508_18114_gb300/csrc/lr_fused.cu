@@ -105,7 +105,7 @@ template <typename T2, int GRAM_DW>
 __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   using T = typename Real<T2>::t;
   constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
-  constexpr int TR = sizeof(T) == 4 ? 2 : 1;     // phase-F rows per thread tile
+  constexpr int TR = sizeof(T) == 4 ? 4 : 2;     // phase-F rows per thread tile
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = a.C;
@@ -127,6 +127,10 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
   // photons, [96..128) 1/L[k][k], [128..) bulk-precision coefficient and steps
   double* misc = reinterpret_cast<double*>(smem + a.o_misc);
+  // row-ordered lower-triangle index table: entry e = i(i+1)/2 + j -> (i, j)
+  __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
+  for (int i = tid; i < LR_MAX_RANK; i += NT)
+    for (int j = 0; j <= i; ++j) tri[i * (i + 1) / 2 + j] = make_short2((short)i, (short)j);
   T* sq = reinterpret_cast<T*>(smem + a.o_tab);                 // sqrt(k), k < TAB
   T* dtab = sq + TAB;                                           // [3][TAB][2]: diagonal energies (hi, lo)
   const int ldg = Mp + 1;
@@ -414,12 +418,18 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             const int mat = e / MM, ij = e - mat * MM, i = ij / Mp, j = ij - i * Mp;
             if (mat == 0) {
               if (i > j || j >= M) continue;
+              // issue the remote loads four at a time, then sum in rank order
               double re = 0.0, im = 0.0;
-              for (int r = 0; r < C; ++r) {
-                const double2* gpr = cluster.map_shared_rank(gp, r);
-                const double2 v = gpr[i * Mp + j];
-                re += v.x;
-                im += v.y;
+              for (int r0 = 0; r0 < C; r0 += 4) {
+                double2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  v[u] = r0 + u < C ? cluster.map_shared_rank(gp, r0 + u)[i * Mp + j] : mk(0.0, 0.0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  re += v[u].x;
+                  im += v[u].y;
+                }
               }
               if (i == j) {
                 Gd[i * ldg + i] = mk(re, 0.0);
@@ -429,11 +439,16 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               }
             } else {
               T re = 0, im = 0;
-              for (int r = 0; r < C; ++r) {
-                const T2* tpr = cluster.map_shared_rank(tp, r);
-                const T2 v = tpr[(mat - 1) * MM + ij];
-                re += v.x;
-                im += v.y;
+              for (int r0 = 0; r0 < C; r0 += 4) {
+                T2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  v[u] = r0 + u < C ? cluster.map_shared_rank(tp, r0 + u)[(mat - 1) * MM + ij] : cm<T2>(0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  re += v[u].x;
+                  im += v[u].y;
+                }
               }
               Tred[(mat - 1) * MM + ij] = cm<T2>(re, im);
               if (mat == 1 && i == j) {
@@ -485,69 +500,72 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
           }
           if (last) break;
-          // Cholesky G = L L^dag in Gd (lower)
-          // (FP64 runs at 2 FMA/clk/SM here: every reciprocal is formed once, by
-          //  one thread, and shared through shared memory)
-          double* rinv = misc + 96;     // [M] 1 / L[k][k]
+          // FP64 G = L D L^dag (unit lower L, right-looking, in place in Gd), then
+          // W = L^-1 (unit lower) and G^-1 = W^dag D^-1 W. One FP64 reciprocal per
+          // pivot (formed once and shared: FP64 runs at 2 FMA/clk/SM here) and two
+          // block barriers per elimination step.
+          double* dinv = misc + 96;     // [M] 1 / D[k]
+          // keep the diagonal of G: a pivot below 1e-13 of it is a numerical breakdown
+          for (int k = tid; k < M; k += NT) W[k * ldg] = Gd[k * ldg + k];
+          __syncthreads();
           for (int k = 0; k < M; ++k) {
             if (tid == 0) {
-              double piv = Gd[k * ldg + k].x;
-              if (!(piv > 0.0) || !isfinite(piv)) {
+              const double piv = Gd[k * ldg + k].x;
+              if (!(piv > 1e-13 * W[k * ldg].x) || !isfinite(piv) || piv < 1e-30) {
                 misc[1] = 1.0;
-                piv = 1.0;
+                dinv[k] = 1.0;
+              } else {
+                // reciprocal by Newton-Raphson, r <- r (2 - piv r), from the FP32
+                // estimate: 24 -> 48 -> 96 correct bits, two FP64 FMA pairs on the
+                // serial path instead of a full FP64 division
+                double r = (double)(1.0f / (float)piv);
+                r = r * fma(-piv, r, 2.0);
+                r = r * fma(-piv, r, 2.0);
+                dinv[k] = r;
               }
-              const double sd = sqrt(piv);
-              Gd[k * ldg + k] = mk(sd, 0.0);
-              rinv[k] = 1.0 / sd;
             }
             __syncthreads();
-            const double inv = rinv[k];
-            for (int i = k + 1 + tid; i < M; i += NT) {
-              const double2 v = Gd[i * ldg + k];
-              Gd[i * ldg + k] = mk(v.x * inv, v.y * inv);
-            }
-            __syncthreads();
+            const double rk = dinv[k];
             const int w = M - k - 1;
-            for (int e = tid; e < w * w; e += NT) {
-              const int i = k + 1 + e / w, j = k + 1 + e % w;
-              if (j > i) continue;
+            // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k
+            for (int e = tid; e < w * (w + 1) / 2; e += NT) {
+              const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
               const double2 x = Gd[i * ldg + k], y = Gd[j * ldg + k], g = Gd[i * ldg + j];
-              Gd[i * ldg + j] = mk(g.x - (x.x * y.x + x.y * y.y), g.y - (x.y * y.x - x.x * y.y));
+              Gd[i * ldg + j] = mk(g.x - rk * (x.x * y.x + x.y * y.y), g.y - rk * (x.y * y.x - x.x * y.y));
             }
             __syncthreads();
           }
           if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
-          // W = L^-1 (lower): column-oriented substitution, all columns at once
+          // unit lower L[i][k] = G[i][k] / D[k]; W = L^-1 row by row (unit diagonal)
           for (int e = tid; e < M * M; e += NT) {
             const int i = e / M, j = e - i * M;
             W[i * ldg + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+            if (i > j) {
+              const double2 v = Gd[i * ldg + j];
+              Gd[i * ldg + j] = mk(v.x * dinv[j], v.y * dinv[j]);
+            }
           }
           __syncthreads();
-          for (int k = 0; k < M; ++k) {
-            const double inv = rinv[k];
-            for (int j = tid; j <= k; j += NT) {
-              const double2 v = W[k * ldg + j];
-              W[k * ldg + j] = mk(v.x * inv, v.y * inv);
-            }
-            __syncthreads();
+          for (int k = 0; k < M - 1; ++k) {
+            // rows i > k: W[i][j] -= L[i][k] W[k][j], j <= k (W[k] is final)
             const int rows = M - k - 1;
             for (int e = tid; e < rows * (k + 1); e += NT) {
               const int i = k + 1 + e / (k + 1), j = e % (k + 1);
-              const double2 l = Gd[i * ldg + k], w = W[k * ldg + j], o = W[i * ldg + j];
-              W[i * ldg + j] = mk(o.x - (l.x * w.x - l.y * w.y), o.y - (l.x * w.y + l.y * w.x));
+              const double2 l = Gd[i * ldg + k], wv = W[k * ldg + j], o = W[i * ldg + j];
+              W[i * ldg + j] = mk(o.x - (l.x * wv.x - l.y * wv.y), o.y - (l.x * wv.y + l.y * wv.x));
             }
             __syncthreads();
           }
-          // G^-1 = W^dag W (Hermitian), rounded once to the bulk precision
+          // G^-1 = W^dag D^-1 W (Hermitian), rounded once to the bulk precision
           T2* Gi = reinterpret_cast<T2*>(Gd);   // L is no longer needed: reuse its storage
           for (int e = tid; e < M * M; e += NT) {
             const int i = e / M, j = e - i * M;
             if (i > j) continue;
             double re = 0.0, im = 0.0;
             for (int k = j; k < M; ++k) {          // W[k][i], W[k][j] nonzero for k >= max(i, j) = j
-              const double2 x = W[k * ldg + i], y = W[k * ldg + j];   // conj(x) y
-              re += x.x * y.x + x.y * y.y;
-              im += x.x * y.y - x.y * y.x;
+              const double2 x = W[k * ldg + i], y = W[k * ldg + j];   // conj(x) y / D[k]
+              re += dinv[k] * (x.x * y.x + x.y * y.y);
+              im += dinv[k] * (x.x * y.y - x.y * y.x);
             }
             Gi[i * Mp + j] = cm<T2>((T)re, (T)im);
             if (i != j) Gi[j * Mp + i] = cm<T2>((T)re, (T)-im);
@@ -575,6 +593,9 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
         }
 
         // ================= F: right-hand side and RK4 stage update
+        // Thread tile: TR consecutive rows x 4 columns. Pass 1 forms -i H_eff Z_s
+        // per row, pass 2 adds the projection terms with every XT load shared by
+        // the TR rows, pass 3 applies the RK4 stage update.
         {
           // coefficient and split step sizes h = hi + lo (no systematic FP32 step error)
           const T* tb = reinterpret_cast<const T*>(misc + 128);
@@ -583,137 +604,150 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           const int mq = Mp / 4;
           const int nrt = (P.R + TR - 1) / TR;
           const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
+          const int MM = Mp * Mp;
           for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
+            T fr[TR][4], fi[TR][4];
+            T sr[TR], sb[TR];
+            const T2* yrp[TR];
+            const T2* ybp[TR];
+            int nrow[TR];
+            const int l0 = rt * TR;
+            int it = l0 / P.st, irl = (l0 - it * P.st) / Nf, iff = l0 - it * P.st - irl * Nf;
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
-              const int l = rt * TR + r;
-              if (l >= P.R) break;
-              const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
-              const int ir = P.r_lo + irl;
-              const int iro = three ? iff : ir;
-              // H_eff diagonal: real part as an unevaluated sum dh + dl
-              T dh, dl;
-              {
-                const T a0 = dtab[(0 * TAB + it) * 2], a1 = dtab[(1 * TAB + ir) * 2], a2 = dtab[(2 * TAB + iff) * 2];
-                T s1 = a0 + a1;
-                T bp = s1 - a0;
-                T er = (a0 - (s1 - bp)) + (a1 - bp);
-                T s2 = s1 + a2;
-                bp = s2 - s1;
-                er += (s1 - (s2 - bp)) + (a2 - bp);
-                dh = s2;
-                dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
-              }
-              const T dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
-              const T2* z = own(cur, l) + m0;
-              T hr[4], hi[4];
+              const int l = l0 + r;
+              sr[r] = 0;
+              sb[r] = 0;
+              yrp[r] = own(cur, 0);
+              ybp[r] = own(cur, 0);
+              nrow[r] = -1;
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
-                hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
-              }
-              auto add_row = [&](const T2* v, T w) {
+              for (int u = 0; u < 4; ++u) fr[r][u] = fi[r][u] = 0;
+              if (l < P.R) {
+                const int ir = P.r_lo + irl;
+                const int iro = three ? iff : ir;
+                nrow[r] = (it * Nr + ir) * Nf + iff;
+                // H_eff diagonal: real part as an unevaluated sum dh + dl
+                T dh, dl;
+                {
+                  const T a0 = dtab[(0 * TAB + it) * 2], a1 = dtab[(1 * TAB + ir) * 2], a2 = dtab[(2 * TAB + iff) * 2];
+                  T s1 = a0 + a1;
+                  T bp = s1 - a0;
+                  T er = (a0 - (s1 - bp)) + (a1 - bp);
+                  T s2 = s1 + a2;
+                  bp = s2 - s1;
+                  er += (s1 - (s2 - bp)) + (a2 - bp);
+                  dh = s2;
+                  dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
+                }
+                const T dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
+                const T2* z = own(cur, l) + m0;
+                T hr[4], hi[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                  hr[u] = fma(w, v[u].x, hr[u]);
-                  hi[u] = fma(w, v[u].y, hi[u]);
+                  hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
+                  hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
                 }
-              };
-              // g (b + b^dag)(a + a^dag)
+                auto add_row = [&](const T2* v, T w) {
 #pragma unroll
-              for (int sa = -1; sa <= 1; sa += 2) {
-                const int it2 = it + sa;
-                if (it2 < 0 || it2 >= Nt) continue;
-                const T ct = g * sq[max(it, it2)];
-#pragma unroll
-                for (int sb = -1; sb <= 1; sb += 2) {
-                  const int ir2 = ir + sb;
-                  if (ir2 < 0 || ir2 >= Nr) continue;
-                  add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
-                }
-              }
-              if (three) {
-                // J (a + a^dag)(f + f^dag)
+                  for (int u = 0; u < 4; ++u) {
+                    hr[u] = fma(w, v[u].x, hr[u]);
+                    hi[u] = fma(w, v[u].y, hi[u]);
+                  }
+                };
+                // g (b + b^dag)(a + a^dag)
 #pragma unroll
                 for (int sa = -1; sa <= 1; sa += 2) {
-                  const int ir2 = ir + sa;
-                  if (ir2 < 0 || ir2 >= Nr) continue;
-                  const T cr = J * sq[max(ir, ir2)];
+                  const int it2 = it + sa;
+                  if (it2 < 0 || it2 >= Nt) continue;
+                  const T ct = g * sq[max(it, it2)];
 #pragma unroll
-                  for (int sb = -1; sb <= 1; sb += 2) {
-                    const int if2 = iff + sb;
+                  for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
+                    const int ir2 = ir + sb2;
+                    if (ir2 < 0 || ir2 >= Nr) continue;
+                    add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
+                  }
+                }
+                if (three) {
+                  // J (a + a^dag)(f + f^dag)
+#pragma unroll
+                  for (int sa = -1; sa <= 1; sa += 2) {
+                    const int ir2 = ir + sa;
+                    if (ir2 < 0 || ir2 >= Nr) continue;
+                    const T cr = J * sq[max(ir, ir2)];
+#pragma unroll
+                    for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
+                      const int if2 = iff + sb2;
+                      if (if2 < 0 || if2 >= Nf) continue;
+                      add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
+                    }
+                  }
+                  // drive on the filter
+#pragma unroll
+                  for (int sa = -1; sa <= 1; sa += 2) {
+                    const int if2 = iff + sa;
                     if (if2 < 0 || if2 >= Nf) continue;
-                    add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
+                    add_row(own(cur, l + sa) + m0, c * sq[max(iff, if2)]);
+                  }
+                } else {
+                  // drive on the resonator (two modes, C == 1)
+#pragma unroll
+                  for (int sa = -1; sa <= 1; sa += 2) {
+                    const int ir2 = ir + sa;
+                    if (ir2 < 0 || ir2 >= Nr) continue;
+                    add_row(own(cur, l + sa) + m0, c * sq[max(ir, ir2)]);
                   }
                 }
-                // drive on the filter
+                // F = -i H_eff z
 #pragma unroll
-                for (int sa = -1; sa <= 1; sa += 2) {
-                  const int if2 = iff + sa;
-                  if (if2 < 0 || if2 >= Nf) continue;
-                  add_row(own(cur, l + sa) + m0, c * sq[max(iff, if2)]);
+                for (int u = 0; u < 4; ++u) {
+                  fr[r][u] = hi[u];
+                  fi[r][u] = -hr[u];
                 }
-              } else {
-                // drive on the resonator (two modes, C == 1)
-#pragma unroll
-                for (int sa = -1; sa <= 1; sa += 2) {
-                  const int ir2 = ir + sa;
-                  if (ir2 < 0 || ir2 >= Nr) continue;
-                  add_row(own(cur, l + sa) + m0, c * sq[max(ir, ir2)]);
+                if (iro + 1 < dro) {
+                  sr[r] = sq[iro + 1];
+                  yrp[r] = own(cur, l + 1);
+                }
+                if (it + 1 < Nt) {
+                  sb[r] = sq[it + 1];
+                  ybp[r] = own(cur, l + P.st);
                 }
               }
-              // F = -i H_eff z + projection terms
-              T fr[4], fi[4];
+              // next local row
+              if (++iff == Nf) {
+                iff = 0;
+                if (++irl == P.nr) {
+                  irl = 0;
+                  ++it;
+                }
+              }
+            }
+            // projection terms: + sr (rZ_s) XT_r + sb (bZ_s) XT_b
+            for (int k = 0; k < M; ++k) {
+              T2 xr[4], xb[4];
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
-                fr[u] = hi[u];
-                fi[u] = -hr[u];
+                xr[u] = XT[k * Mp + m0 + u];
+                xb[u] = XT[MM + k * Mp + m0 + u];
               }
-              const int MM = Mp * Mp;
-              if (iro + 1 < dro) {
-                const T s = sq[iro + 1];
-                const T2* y = own(cur, l + 1);
-                T ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-                for (int k = 0; k < M; ++k) {
-                  const T2 yk = y[k];
-                  const T2* xt = XT + k * Mp + m0;
 #pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    const T2 x = xt[u];
-                    ar[u] = fma(yk.x, x.x, fma(-yk.y, x.y, ar[u]));
-                    ai[u] = fma(yk.x, x.y, fma(yk.y, x.x, ai[u]));
-                  }
-                }
+              for (int r = 0; r < TR; ++r) {
+                const T2 y0 = yrp[r][k], y1 = ybp[r][k];
+                const T ar = sr[r] * y0.x, ai = sr[r] * y0.y, br = sb[r] * y1.x, bi = sb[r] * y1.y;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                  fr[u] = fma(s, ar[u], fr[u]);
-                  fi[u] = fma(s, ai[u], fi[u]);
+                  fr[r][u] = fma(ar, xr[u].x, fma(-ai, xr[u].y, fma(br, xb[u].x, fma(-bi, xb[u].y, fr[r][u]))));
+                  fi[r][u] = fma(ar, xr[u].y, fma(ai, xr[u].x, fma(br, xb[u].y, fma(bi, xb[u].x, fi[r][u]))));
                 }
               }
-              if (it + 1 < Nt) {
-                const T s = sq[it + 1];
-                const T2* y = own(cur, l + P.st);
-                T ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-                for (int k = 0; k < M; ++k) {
-                  const T2 yk = y[k];
-                  const T2* xt = XT + MM + k * Mp + m0;
+            }
+            // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
 #pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    const T2 x = xt[u];
-                    ar[u] = fma(yk.x, x.x, fma(-yk.y, x.y, ar[u]));
-                    ai[u] = fma(yk.x, x.y, fma(yk.y, x.x, ai[u]));
-                  }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  fr[u] = fma(s, ar[u], fr[u]);
-                  fi[u] = fma(s, ai[u], fi[u]);
-                }
-              }
-              // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
-              const int n = (it * Nr + ir) * Nf + iff;
-              T2* zo = own(nxt, l) + m0;
+            for (int r = 0; r < TR; ++r) {
+              const int n = nrow[r];
+              if (n < 0) continue;
+              T2* zo = own(nxt, l0 + r) + m0;
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const int m = m0 + u;
@@ -724,17 +758,18 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
                 const T2 zn = Zn[oz];
                 if (stage == 0) {
-                  accg[oa] = cm<T2>(fr[u], fi[u]);
+                  accg[oa] = cm<T2>(fr[r][u], fi[r][u]);
                 } else if (stage < 3) {
                   const T2 ac = accg[oa];
-                  accg[oa] = cm<T2>(fma((T)2, fr[u], ac.x), fma((T)2, fi[u], ac.y));
+                  accg[oa] = cm<T2>(fma((T)2, fr[r][u], ac.x), fma((T)2, fi[r][u], ac.y));
                 }
                 if (stage < 3) {
-                  zo[u] = cm<T2>(zn.x + fma(hs_lo, fr[u], hs_hi * fr[u]), zn.y + fma(hs_lo, fi[u], hs_hi * fi[u]));
+                  zo[u] = cm<T2>(zn.x + fma(hs_lo, fr[r][u], hs_hi * fr[r][u]),
+                                 zn.y + fma(hs_lo, fi[r][u], hs_hi * fi[r][u]));
                 } else {
                   const T2 ac = accg[oa];
-                  const T sr_ = ac.x + fr[u], si_ = ac.y + fi[u];
-                  const T2 z1 = cm<T2>(zn.x + fma(h6_lo, sr_, h6_hi * sr_), zn.y + fma(h6_lo, si_, h6_hi * si_));
+                  const T s_r = ac.x + fr[r][u], s_i = ac.y + fi[r][u];
+                  const T2 z1 = cm<T2>(zn.x + fma(h6_lo, s_r, h6_hi * s_r), zn.y + fma(h6_lo, s_i, h6_hi * s_i));
                   Zn[oz] = z1;
                   zo[u] = z1;
                 }
@@ -829,8 +864,13 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
     tot_work += w;
   }
   const int Mp = (Mmax + 3) / 4 * 4;
-  const int smem_max = (int)prop.sharedMemPerBlockOptin;
   const void* kern = kernel_ptr(prec);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int smem_max = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   // Overrides for tuning and tests: LR_FUSED_C = cluster size,
   // LR_FUSED_ZS = "global" keeps the stage state in L2 instead of shared memory.
