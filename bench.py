@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=None, help="RK4 steps of the oracle sample")
     ap.add_argument("--no-plain-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=8, help="RK4 steps timed on the plain FP64 engine")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the gradient (lr_backward) of a pulse slice of --chunk steps instead")
     return ap.parse_args()
 
 
@@ -392,10 +394,49 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Gradient evaluations: forward slice of `chunk` RK4 steps from step 0,
+    then lr_backward (discrete adjoint, FP64) for dL/dtheta of every candidate.
+    Metric: trajectory-steps of the differentiated slice per second of backward."""
+    import numpy as np
+    import torch
+    from paper_2508_18114_gb300 import LowRankBatch, lr as lrmod
+    wl = load_workload(args)
+    prec = args.precision or getattr(wl, "precision", "fp64")
+    chunk = args.chunk or 20
+    cands = wl.candidates
+    b = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision=prec, engine=args.engine,
+                     max_steps=chunk, pop_every=chunk, eta=wl.eta)
+    b.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
+    times = []
+    for k in range(args.warmup + args.steps):
+        b.set_initial(wl.init_seed, wl.eps)
+        b.integrate(wl.dt, chunk)
+        b.sync()
+        t0 = time.perf_counter()
+        g = b.backward(np.ones(len(cands)), chunk)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tt = sum(times)
+    value = b.n_traj * chunk * args.steps / tt
+    desc = workload_desc(wl, prec)
+    desc.update({"chunk_rk4_steps": chunk, "engine_forward": lrmod.ENGINE_NAME[b.query().engine],
+                 "adjoint": "lr_backward, FP64 plain-kernel recomputation, checkpoint every chunk"})
+    print(json.dumps({"metric": "adjoint_traj_steps_per_s", "value": value, "unit": "traj*steps/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+                      "higher_is_better": True, "dtype": "f64", "config": desc,
+                      "grad_evals_per_s": value / (2 * desc["steps_per_pulse"]) * (len(cands) / len(cands)),
+                      "grad_norm": float(np.abs(g).max())}))
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.adjoint:
+        run_adjoint(args)
     else:
         run_ours(args)
 

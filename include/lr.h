@@ -194,6 +194,16 @@ lr_status lr_integrate(lr_ctx* ctx, double dt, long n_steps, void* stream);
 lr_status lr_observables(lr_ctx* ctx, double* beta, double* pops, double* nphot,
                          double* trace, double* eps_a, void* stream);
 
+/* Readout loss of Sec. S3.B for every candidate (host or device pointers,
+ * either may be NULL), computed with eps_a at the end of lr_integrate:
+ *   ionization[c] = T(tau) = (1/tau) sum_{j=g,e} sum_{k>=2} int P_k(t) dt,
+ *     the transmon populations of levels k >= 2 integrated by the trapezoid
+ *     rule over the recorded grid (every pop_every steps) up to the last
+ *     record, tau = step * dt;
+ *   loss[c] = log10(eps_a + T).
+ * Synchronises the stream and returns the device error word's status. */
+lr_status lr_loss(lr_ctx* ctx, double* ionization, double* loss, void* stream);
+
 /* Synchronise the stream and return the device error word's status. */
 lr_status lr_sync(lr_ctx* ctx, void* stream);
 

@@ -38,3 +38,22 @@ def assignment_error(beta_g, beta_e, dt: float, kappa: float, gamma: float,
     tau = (len(beta_g) - 1) * dt
     s = snr(beta_g, beta_e, dt, kappa, eta)
     return 0.5 * math.erfc(0.5 * s) + 0.5 * tau * gamma
+
+
+def ionization(pops_g, pops_e, dt_rec: float, tau: float) -> float:
+    """Ionization penalty of Sec. S3.B,
+        T(tau) = (1/tau) sum_{j=g,e} sum_{k>=2} int_0^tau tr(|k_t><k_t| rho_j(t)) dt,
+    with the transmon populations P_k(t) sampled every dt_rec (pops arrays
+    [n_rec, N_t]) and the integral taken by the trapezoid rule over the
+    recorded grid [0, (n_rec - 1) dt_rec]."""
+    total = 0.0
+    for p in (np.asarray(pops_g), np.asarray(pops_e)):
+        hi = p[:, 2:].sum(axis=1) if p.shape[1] > 2 else np.zeros(p.shape[0])
+        if hi.size >= 2:
+            total += dt_rec * (0.5 * hi[0] + hi[1:-1].sum() + 0.5 * hi[-1])
+    return total / tau
+
+
+def loss(eps_a: float, T: float) -> float:
+    """Loss of Sec. S3.B: Lambda = log10(eps_a + T)."""
+    return math.log10(eps_a + T)

@@ -27,7 +27,8 @@ struct lr_ctx {
   lr::FusedPlan fused{};
   // workspace layout (byte offsets)
   size_t o_traj = 0, o_pulse = 0, o_err = 0, o_zn = 0, o_za = 0, o_zb = 0, o_acc = 0, o_x = 0, o_part = 0,
-         o_beta = 0, o_pops = 0, o_nphot = 0, o_trace = 0, o_eps = 0, o_scratch = 0, total = 0;
+         o_beta = 0, o_pops = 0, o_nphot = 0, o_trace = 0, o_eps = 0, o_ion = 0, o_loss = 0, o_scratch = 0,
+         total = 0;
   size_t scratch_bytes = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -69,6 +70,8 @@ DevPtrs dev_ptrs(const lr_ctx* c) {
   p.nphot = reinterpret_cast<double*>(w + c->o_nphot);
   p.trace = reinterpret_cast<double*>(w + c->o_trace);
   p.eps_a = reinterpret_cast<double*>(w + c->o_eps);
+  p.ion = reinterpret_cast<double*>(w + c->o_ion);
+  p.loss = reinterpret_cast<double*>(w + c->o_loss);
   p.scratch = c->scratch_bytes ? w + c->o_scratch : nullptr;
   p.scratch_bytes = (long long)c->scratch_bytes;
   return p;
@@ -211,6 +214,8 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   c->o_nphot = take(sizeof(double) * (size_t)c->n_traj * c->n_rec);
   c->o_trace = take(sizeof(double) * (size_t)c->n_traj * c->n_rec);
   c->o_eps = take(sizeof(double) * n_cand);
+  c->o_ion = take(sizeof(double) * n_cand);
+  c->o_loss = take(sizeof(double) * n_cand);
   if (c->engine == LR_ENGINE_FUSED) {
     c->scratch_bytes = lr::fused_scratch_bytes(c->fused, c->n_traj);
     if (c->scratch_bytes) c->o_scratch = take(c->scratch_bytes);
@@ -387,6 +392,18 @@ lr_status lr_observables(lr_ctx* c, double* beta, double* pops, double* nphot, d
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronising");
+  return check_device_error(c);
+}
+
+lr_status lr_loss(lr_ctx* c, double* ionization, double* loss, void* stream) {
+  if (!c) return LR_ERR_ARG;
+  if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (ionization) e = cudaMemcpyAsync(ionization, c->ws + c->o_ion, sizeof(double) * c->n_cand, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, c->ws + c->o_loss, sizeof(double) * c->n_cand, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the loss");
   return check_device_error(c);
 }
 

@@ -138,12 +138,28 @@ __global__ void __launch_bounds__(ET) eps_a_kernel(DevPtrs p, RunParams rp, long
     acc += w * (dx * dx + dy * dy);
   }
   acc = block_sum<ET>(acc, sh);
+  // ionization penalty (Sec. S3.B): populations of transmon levels k >= 2 of
+  // both trajectories, trapezoid over the recorded grid up to the last record
+  const long last = step / rp.pop_every;
+  const int Nt = d.Nt;
+  double ion = 0.0;
+  for (long r = threadIdx.x; r <= last; r += ET) {
+    const double w = (r == 0 || r == last) ? 0.5 : 1.0;
+    double sum = 0.0;
+    for (int tj = 2 * c; tj <= 2 * c + 1; ++tj)
+      for (int k = 2; k < Nt; ++k) sum += p.pops[((size_t)tj * rp.n_rec + r) * rp.nt_max + k];
+    ion += w * sum;
+  }
+  ion = block_sum<ET>(ion, sh);
   if (threadIdx.x == 0) {
     const double S = step > 0 ? rp.dt * acc : 0.0;
     const double snr = sqrt(2.0 * rp.eta * d.kappa * S);
     const double tau = (double)step * rp.dt;
     const double e = 0.5 * erfc(0.5 * snr) + 0.5 * tau * d.gamma;
     p.eps_a[c] = e;
+    const double T = (step > 0 && last > 0) ? ion * rp.pop_every * rp.dt / tau : 0.0;
+    p.ion[c] = T;
+    p.loss[c] = log10(e + T);
     if (!isfinite(e)) set_error(p.err, DEV_NONFINITE);
   }
 }

@@ -173,6 +173,8 @@ struct DevPtrs {
   double* nphot;   // [n_traj][n_rec]
   double* trace;   // [n_traj][n_rec]
   double* eps_a;   // [n_cand]
+  double* ion;     // [n_cand] ionization penalty T(tau)
+  double* loss;    // [n_cand] log10(eps_a + T)
   void* scratch;   // engine scratch
   long long scratch_bytes;
 };

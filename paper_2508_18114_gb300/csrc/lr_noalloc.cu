@@ -120,6 +120,8 @@ extern "C" lr_status lr_integrate_plain_noalloc(const lr_model* m, int M, const 
   p.nphot = reinterpret_cast<double*>(base + NA_OFF_NPHOT);
   p.trace = reinterpret_cast<double*>(base + NA_OFF_TRACE);
   p.eps_a = nullptr;
+  p.ion = nullptr;
+  p.loss = nullptr;
 
   RunParams rp{};
   rp.n_traj = 1;

@@ -34,7 +34,7 @@ EXPORTS = (
     "lr_set_initial", "lr_set_state", "lr_get_state", "lr_integrate",
     "lr_observables", "lr_sync", "lr_query", "lr_status_string",
     "lr_last_error", "lr_destroy", "lr_integrate_plain_noalloc",
-    "lr_backward_workspace_size", "lr_backward",
+    "lr_backward_workspace_size", "lr_backward", "lr_loss",
 )
 
 
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_integrate_plain_noalloc.argtypes = [C.POINTER(lr_model), i, C.POINTER(lr_pulse), d, vp, vp, d, l, l, vp]
     lib.lr_backward_workspace_size.argtypes = [vp, i, C.POINTER(C.c_size_t)]
     lib.lr_backward.argtypes = [vp, vp, C.c_size_t, vp, vp, i, vp]
+    lib.lr_loss.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("lr_status_string", "lr_last_error", "lr_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -266,6 +267,14 @@ class LowRankBatch:
         ptr = lambda k: C.c_void_p(tensors[k].data_ptr()) if k in tensors else None  # noqa: E731
         self._check(self._lib.lr_observables(self._h, ptr("beta"), ptr("pops"), ptr("nphot"),
                                              ptr("trace"), ptr("eps_a"), C.c_void_p(_stream_ptr(stream))))
+
+    def loss(self, stream=None):
+        """(ionization T, loss log10(eps_a + T)) per candidate (lr_loss)."""
+        n = len(self.models)
+        ion, loss = np.empty(n), np.empty(n)
+        self._check(self._lib.lr_loss(self._h, ion.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
+                                      C.c_void_p(_stream_ptr(stream))))
+        return ion, loss
 
     def backward(self, d_eps_a, ckpt_every=200, stream=None):
         """dL/dtheta [n_cand, 8] for cotangents dL/deps_a (lr_backward)."""

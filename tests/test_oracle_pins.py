@@ -390,3 +390,39 @@ def test_fd_gradient_richardson_consistent():
     g2 = gradient.fd_gradient(wl, 0, rel=5e-5)
     assert np.all(np.isfinite(g1)) and np.abs(g1).max() > 1e-3
     assert np.allclose(g1, g2, rtol=1e-5, atol=1e-7 * np.abs(g1).max())
+
+
+# ---------------------------------------------------------------- loss / SPSA (Sec. S3.B/C)
+
+def test_ionization_closed_forms():
+    n, dt_rec, tau = 41, 0.25, 10.0
+    t = np.arange(n) * dt_rec
+    pg = np.zeros((n, 4))
+    pe = np.zeros((n, 4))
+    pg[:, 2] = 0.01                      # constant level-2 population
+    pe[:, 3] = 0.002 * t                 # linear level-3 population (trapezoid exact)
+    pe[:, 1] = 0.7                       # levels < 2 do not count
+    want = (0.01 * t[-1] + 0.001 * t[-1] ** 2) / tau
+    assert signal.ionization(pg, pe, dt_rec, tau) == pytest.approx(want, rel=1e-13)
+    assert signal.loss(1e-3, 0.0) == pytest.approx(-3.0, abs=1e-15)
+
+
+def test_spsa_step_on_quadratic():
+    """One SPSA step on L = sum_i (theta_i - t_i)^2 / s_i^2 equals the closed form
+    g_i = sum_j 2 s_j Delta_j (theta_j - t_j)/s_j^2 / Delta_i (exact difference of
+    a quadratic), and the loss decreases along the chain."""
+    from oracle import spsa
+    target = np.array([0.3, 47.2, 2.0, 1.0])
+    scale = np.array([0.05, 0.01, 0.2, 0.1])
+    th0 = np.array([0.5, 47.25, 2.5, 1.3])
+
+    def L(th):
+        return float(np.sum(((th - target) / scale) ** 2))
+    rng = np.random.default_rng(3)
+    deltas = rng.choice([-1.0, 1.0], size=(60, 4))
+    hist, losses = spsa.spsa(lambda a, b: (L(a), L(b)), 0, th0, deltas, scale, a=0.5, c=0.1, A=5.0)
+    ak, ck = spsa.gains(0, 0.5, 0.1, 5.0)
+    d0 = deltas[0]
+    gq = np.sum(2 * scale * d0 * (th0 - target) / scale ** 2) / d0
+    assert np.allclose(hist[1], th0 - ak * scale * gq, rtol=1e-12, atol=1e-12)
+    assert L(hist[-1]) < 1e-6 * L(hist[0])
