@@ -426,7 +426,7 @@ def run_adjoint(args):
     print(json.dumps({"metric": "adjoint_traj_steps_per_s", "value": value, "unit": "traj*steps/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
                       "higher_is_better": True, "dtype": "f64", "config": desc,
-                      "grad_evals_per_s": value / (2 * desc["steps_per_pulse"]) * (len(cands) / len(cands)),
+                      "grad_evals_per_s": value / (2 * desc["steps_per_pulse"]),
                       "grad_norm": float(np.abs(g).max())}))
     b.close()
 

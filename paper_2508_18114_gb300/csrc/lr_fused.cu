@@ -42,7 +42,7 @@ struct Args {
   int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop;   // s_*: offsets inside one slot
   int o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
   const int* order;
-  void* zs_glob;      // global stage buffers, per cluster [2][Nmax*Mp]
+  void* zs_glob;      // global stage buffers, per cluster [C][2][R][Mp+1]
   void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
 };
 
@@ -135,8 +135,11 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   T* dtab = sq + TAB;                                           // [3][TAB][2]: diagonal energies (hi, lo)
   const int ldg = Mp + 1;
 
-  T2* zs_local = reinterpret_cast<T2*>(smem + a.o_zs);
-  T2* zs_glob = reinterpret_cast<T2*>(a.zs_glob) + (size_t)cid * 2 * a.Nmax * Mp;
+  // Stage buffers: in shared memory, or (when they do not fit) in a global
+  // scratch region with the same per-CTA layout [C][2][R][lds] that stays L2
+  // resident; both are addressed by local row.
+  T2* zs_local = a.zs_smem ? reinterpret_cast<T2*>(smem + a.o_zs)
+                           : reinterpret_cast<T2*>(a.zs_glob) + ((size_t)cid * C + q) * 2 * zs_buf;
   T2* accg = reinterpret_cast<T2*>(a.acc_glob) + (size_t)cid * a.Nmax * Mp;
 
   const double dt = a.rp.dt;
@@ -154,22 +157,19 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
     const int dro = three ? Nf : Nr;
     T2* Zn = reinterpret_cast<T2*>(a.p.Zn) + d.z_off;
     const PulseDev pulse = a.p.pulse[d.cand];
-    // remote Z_s bases (smem mode)
+    // Z_s bases of the neighbouring ranks (DSMEM or the neighbours' global regions)
     T2* zs_m = zs_local;
     T2* zs_p = zs_local;
     if (a.zs_smem) {
       zs_m = cluster.map_shared_rank(zs_local, q > 0 ? q - 1 : q);
       zs_p = cluster.map_shared_rank(zs_local, q < C - 1 ? q + 1 : q);
+    } else {
+      zs_m = zs_local - (q > 0 ? 2 * zs_buf : 0);
+      zs_p = zs_local + (q < C - 1 ? 2 * zs_buf : 0);
     }
 
-    // global row of local row l
-    auto grow = [&](int l) {
-      const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
-      return (it * Nr + P.r_lo + irl) * Nf + iff;
-    };
     // pointer to the start of row (it, ir, iff) of Z_s buffer b (any owner)
     auto zrow = [&](int b, int it2, int ir2, int iff2) -> const T2* {
-      if (!a.zs_smem) return zs_glob + ((size_t)b * a.Nmax + (size_t)((it2 * Nr + ir2) * Nf + iff2)) * Mp;
       if (ir2 < P.r_lo) {
         const int l = (it2 * Pm.nr + (ir2 - Pm.r_lo)) * Nf + iff2;
         return zs_m + (size_t)b * zs_buf + (size_t)l * lds;
@@ -182,9 +182,11 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
       return zs_local + (size_t)b * zs_buf + (size_t)l * lds;
     };
     // own row l of buffer b (writable)
-    auto own = [&](int b, int l) -> T2* {
-      if (!a.zs_smem) return zs_glob + ((size_t)b * a.Nmax + (size_t)grow(l)) * Mp;
-      return zs_local + (size_t)b * zs_buf + (size_t)l * lds;
+    auto own = [&](int b, int l) -> T2* { return zs_local + (size_t)b * zs_buf + (size_t)l * lds; };
+    // global row of local row l
+    auto grow = [&](int l) {
+      const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
+      return (it * Nr + P.r_lo + irl) * Nf + iff;
     };
 
     // ---- per-trajectory tables: sqrt(k) and the separable diagonal of H,
@@ -325,8 +327,10 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               for (int i = 0; i < TP; ++i)
 #pragma unroll
                 for (int j = 0; j < TP; ++j) rr[i][j] = ri[i][j] = br[i][j] = bi[i][j] = 0;
+              // mode indices of row l, advanced by 32 rows per iteration without divisions
+              int it = lane / P.st, irl = (lane - it * P.st) / Nf, iff = lane - it * P.st - irl * Nf;
+              const int dq = 32 / Nf, dr = 32 - dq * Nf;
               for (int l = lane; l < P.R; l += 32) {
-                const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
                 const int iro = three ? iff : irl;     // with two modes C == 1 and r_lo == 0
                 const T sr = iro + 1 < dro ? sq[iro + 1] : (T)0;
                 const T sb = it + 1 < Nt ? sq[it + 1] : (T)0;
@@ -354,6 +358,16 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                     br[i][j] = fma(wb[i].x, yb[j].x, fma(-wb[i].y, yb[j].y, br[i][j]));
                     bi[i][j] = fma(wb[i].x, yb[j].y, fma(wb[i].y, yb[j].x, bi[i][j]));
                   }
+                iff += dr;
+                irl += dq;
+                if (iff >= Nf) {
+                  iff -= Nf;
+                  ++irl;
+                }
+                while (irl >= P.nr) {
+                  irl -= P.nr;
+                  ++it;
+                }
               }
 #pragma unroll
               for (int i = 0; i < TP; ++i)
@@ -910,10 +924,19 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
       }
       const int n_traj = (int)traj.size();
       const int used = std::min(ncl, n_traj);
-      // cost model: the slowest team, with waves of trajectories per team
+      // Cost model, fitted to measurements on GB300 (N = 2000, M = 20 batch):
+      // a stage costs ~0.16 us per row per CTA with the stage state in shared
+      // memory (x1.3 in L2), plus a fixed ~60 us per team (the M x M phase and
+      // the cluster barrier, ~M sequential elimination steps) that does not
+      // shrink with C; teams run trajectories in waves.
       const double waves = std::ceil((double)n_traj / used);
-      const double per_team = std::max(waves * tot_work / n_traj, max_work) / C;
-      const double t = per_team * (1.0 + 0.04 * (C - 1)) * (zs_smem ? 1.0 : 1.5);
+      double t = 0.0;
+      for (const TrajDev& d : traj) {
+        const double rows = (double)rows_per_cta(d, C) * (zs_smem ? 1.0 : 1.3) * (d.M * d.M) / 400.0;
+        const double fixed = 375.0 * d.M / 20.0 * (C > 1 ? 1.0 : 0.95);
+        t += rows + fixed;
+      }
+      t = std::max(waves * t / n_traj, 0.0) * 1.0;
       if (t < best) {
         best = t;
         plan->ok = 1;
@@ -928,7 +951,6 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
         plan->gram_mode = prec == LR_PREC_FP32_G64 ? 1 : 0;
         plan->es = (int)es;
       }
-      break;   // smem mode preferred when it fits
     }
   }
   if (!plan->ok) return false;
@@ -945,7 +967,8 @@ size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj) {
   // order list, then global stage buffers (only without smem residency) and accumulators per team
   size_t b = ((sizeof(int) * n_traj + 255) / 256) * 256;
   const size_t es = plan.es;
-  if (!plan.zs_smem) b += ((2 * (size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
+  if (!plan.zs_smem)
+    b += ((2 * (size_t)plan.R * (plan.Mp + 1) * es * plan.C * plan.n_clusters + 255) / 256) * 256;
   b += (((size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
   return b;
 }
@@ -983,7 +1006,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.order = reinterpret_cast<const int*>(sc);
   if (!plan.zs_smem) {
     a.zs_glob = sc + off;
-    off += ((2 * (size_t)plan.Nmax * plan.Mp * es * plan.n_clusters + 255) / 256) * 256;
+    off += ((2 * (size_t)plan.R * (plan.Mp + 1) * es * plan.C * plan.n_clusters + 255) / 256) * 256;
   }
   a.acc_glob = sc + off;
   cudaError_t e = cudaMemcpyAsync(sc, plan.order.data(), sizeof(int) * rp.n_traj, cudaMemcpyHostToDevice, s);
