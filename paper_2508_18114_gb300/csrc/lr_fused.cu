@@ -101,7 +101,33 @@ __device__ __forceinline__ double dw_value(const DW& s) { return (double)s.hi + 
 
 // ----------------------------------------------------------------- the kernel
 
-template <typename T2, int GRAM_DW>
+// Vector load of 4 consecutive complex values (16-byte loads when the row
+// stride keeps them aligned: the L2-resident layout).
+template <int ZSM, typename T2>
+__device__ __forceinline__ void load4(const T2* p, T2 (&v)[4]) {
+  if constexpr (ZSM == 0 && sizeof(T2) == 8) {
+    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
+    v[0] = cm<T2>(x.x, x.y);
+    v[1] = cm<T2>(x.z, x.w);
+    v[2] = cm<T2>(y.x, y.y);
+    v[3] = cm<T2>(y.z, y.w);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = p[u];
+  }
+}
+template <int ZSM, typename T2>
+__device__ __forceinline__ void store4(T2* p, const T2 (&v)[4]) {
+  if constexpr (ZSM == 0 && sizeof(T2) == 8) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[u] = v[u];
+  }
+}
+
+template <typename T2, int GRAM_DW, int ZSM>
 __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   using T = typename Real<T2>::t;
   constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
@@ -113,9 +139,10 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   const int cid = blockIdx.x / C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Mp = a.Mp;
-  // shared-memory row stride of Z_s: odd in complex elements, so lanes that
-  // read consecutive rows hit distinct banks
-  const int lds = Mp + 1;
+  // row stride of Z_s: odd in complex elements in shared memory, so lanes that
+  // read consecutive rows hit distinct banks; 32-byte aligned rows in L2 for
+  // 16-byte vector loads
+  const int lds = ZSM ? Mp + 1 : Mp;
   const long long zs_buf = (long long)a.R * lds;  // elements per smem Z_s buffer
 
   double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);     // [Mp][Mp+1]  G -> L -> G^-1
@@ -249,10 +276,15 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 for (int l = lane; l < P.R; l += 32) {
                   const T2* z = own(cur, l);
                   T2 zi[TP], zj[TP];
+                  if constexpr (TP == 4) {
+                    load4<ZSM>(z + i0, zi);
+                    load4<ZSM>(z + j0, zj);
+                  } else {
 #pragma unroll
-                  for (int i = 0; i < TP; ++i) zi[i] = z[i0 + i];
+                    for (int i = 0; i < TP; ++i) zi[i] = z[i0 + i];
 #pragma unroll
-                  for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
+                    for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
+                  }
 #pragma unroll
                   for (int i = 0; i < TP; ++i)
 #pragma unroll
@@ -337,17 +369,24 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 const T2* z = own(cur, l);
                 const T2* zr = own(cur, iro + 1 < dro ? l + 1 : l);
                 const T2* zb = own(cur, it + 1 < Nt ? l + P.st : l);
-                T2 wr[TP], wb[TP], yr[TP], yb[TP];
+                T2 wr[TP], wb[TP], yr[TP], yb[TP], zz[TP];
+                if constexpr (TP == 4) {
+                  load4<ZSM>(z + i0, zz);
+                  load4<ZSM>(zr + j0, yr);
+                  load4<ZSM>(zb + j0, yb);
+                } else {
 #pragma unroll
-                for (int i = 0; i < TP; ++i) {
-                  const T2 zi = z[i0 + i];
-                  wr[i] = cm<T2>(sr * zi.x, -sr * zi.y);   // sr conj(z_i)
-                  wb[i] = cm<T2>(sb * zi.x, -sb * zi.y);
+                  for (int i = 0; i < TP; ++i) zz[i] = z[i0 + i];
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) {
+                    yr[j] = zr[j0 + j];
+                    yb[j] = zb[j0 + j];
+                  }
                 }
 #pragma unroll
-                for (int j = 0; j < TP; ++j) {
-                  yr[j] = zr[j0 + j];
-                  yb[j] = zb[j0 + j];
+                for (int i = 0; i < TP; ++i) {
+                  wr[i] = cm<T2>(sr * zz[i].x, -sr * zz[i].y);   // sr conj(z_i)
+                  wb[i] = cm<T2>(sb * zz[i].x, -sb * zz[i].y);
                 }
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
@@ -656,14 +695,17 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                   dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
                 }
                 const T dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
-                const T2* z = own(cur, l) + m0;
+                T2 z[4];
+                load4<ZSM>(own(cur, l) + m0, z);
                 T hr[4], hi[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                   hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
                   hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
                 }
-                auto add_row = [&](const T2* v, T w) {
+                auto add_row = [&](const T2* vp, T w) {
+                  T2 v[4];
+                  load4<ZSM>(vp, v);
 #pragma unroll
                   for (int u = 0; u < 4; ++u) {
                     hr[u] = fma(w, v[u].x, hr[u]);
@@ -761,7 +803,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             for (int r = 0; r < TR; ++r) {
               const int n = nrow[r];
               if (n < 0) continue;
-              T2* zo = own(nxt, l0 + r) + m0;
+              T2 zo[4];
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const int m = m0 + u;
@@ -788,6 +830,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                   zo[u] = z1;
                 }
               }
+              store4<ZSM>(own(nxt, l0 + r) + m0, zo);
             }
           }
           cur = nxt;
@@ -842,10 +885,15 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
   return L;
 }
 
-const void* kernel_ptr(lr_precision prec) {
-  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0>;
-  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0>;
-  return (const void*)fz::fused_kernel<float2, 1>;
+const void* kernel_ptr(lr_precision prec, int zs_smem) {
+  if (zs_smem) {
+    if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 1>;
+    if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 1>;
+    return (const void*)fz::fused_kernel<float2, 1, 1>;
+  }
+  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 0>;
+  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 0>;
+  return (const void*)fz::fused_kernel<float2, 1, 0>;
 }
 
 int rows_per_cta(const TrajDev& d, int C) {
@@ -878,14 +926,17 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
     tot_work += w;
   }
   const int Mp = (Mmax + 3) / 4 * 4;
-  const void* kern = kernel_ptr(prec);
-  cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+  const void* kerns[2] = {kernel_ptr(prec, 0), kernel_ptr(prec, 1)};
+  int smem_maxs[2];
+  for (int z = 0; z < 2; ++z) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kerns[z]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    smem_maxs[z] = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute(kerns[z], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
-  const int smem_max = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   // Overrides for tuning and tests: LR_FUSED_C = cluster size,
   // LR_FUSED_ZS = "global" keeps the stage state in L2 instead of shared memory.
   int force_c = 0, force_global = 0;
@@ -900,8 +951,9 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
     for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
     for (int zs_smem = 1; zs_smem >= 0; --zs_smem) {
       if (force_global && zs_smem) continue;
+      const void* kern = kerns[zs_smem];
       const SmemLayout L = layout(R, Mp, zs_smem, es);
-      if (L.total > smem_max) continue;
+      if (L.total > smem_maxs[zs_smem]) continue;
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess) {
         cudaGetLastError();
         continue;
@@ -1011,7 +1063,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.acc_glob = sc + off;
   cudaError_t e = cudaMemcpyAsync(sc, plan.order.data(), sizeof(int) * rp.n_traj, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  const void* kern = kernel_ptr(prec);
+  const void* kern = kernel_ptr(prec, plan.zs_smem);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1027,9 +1079,14 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0>, a);
-  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0>, a);
-  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1>, a);
+  if (plan.zs_smem) {
+    if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 1>, a);
+    if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 1>, a);
+    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 1>, a);
+  }
+  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 0>, a);
+  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 0>, a);
+  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0>, a);
 }
 
 }  // namespace lr
