@@ -285,15 +285,28 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
 #pragma unroll
                     for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
                   }
+                  if (ti == tj2) {
+                    // diagonal tile: only the upper triangle is needed
 #pragma unroll
-                  for (int i = 0; i < TP; ++i)
+                    for (int i = 0; i < TP; ++i)
 #pragma unroll
-                    for (int j = 0; j < TP; ++j) {   // conj(zi) * zj
-                      dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
-                      dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
-                      dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
-                      dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
-                    }
+                      for (int j = i; j < TP; ++j) {   // conj(zi) * zj
+                        dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
+                        dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
+                        dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
+                        dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
+                      }
+                  } else {
+#pragma unroll
+                    for (int i = 0; i < TP; ++i)
+#pragma unroll
+                      for (int j = 0; j < TP; ++j) {   // conj(zi) * zj
+                        dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
+                        dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
+                        dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
+                        dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
+                      }
+                  }
                 }
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
