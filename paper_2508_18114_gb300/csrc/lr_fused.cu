@@ -988,7 +988,10 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
         continue;
       }
       const int n_traj = (int)traj.size();
-      const int used = std::min(ncl, n_traj);
+      // only as many teams as the waves need: the same number of waves, less
+      // scratch, and every team runs the same number of trajectories
+      const int waves_needed = (n_traj + ncl - 1) / ncl;
+      const int used = std::min((n_traj + waves_needed - 1) / waves_needed, n_traj);
       // Cost model, fitted to measurements on GB300 (N = 2000, M = 20 batch):
       // a stage costs ~0.16 us per row per CTA with the stage state in shared
       // memory (x1.3 in L2), plus a fixed ~60 us per team (the M x M phase and
