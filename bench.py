@@ -364,9 +364,11 @@ def run_ours(args):
         bq.set_initial(wl.init_seed, wl.eps)
         bq.integrate(wl.dt, ns)
         og = bq.observables()
+        qinfo = bq.query()
         bq.close()
         bo = ora["beta"]
-        err = {"sample": "candidate 0, g and e, %d RK4 steps" % ns,
+        err = {"sample": "candidate 0, g and e, %d RK4 steps (team %d, tensor passes %d)"
+                         % (ns, qinfo.team_size, qinfo.tensor_passes),
                "beta_rel": float(np.abs(og["beta"] - bo).max() / np.abs(bo).max()),
                "pops_abs": float(max(np.abs(og["pops"][j][:, :ora["pops"][j].shape[1]] - ora["pops"][j]).max()
                                      for j in range(2))),
@@ -375,13 +377,16 @@ def run_ours(args):
     if rank == 0:
         desc = workload_desc(wl, prec)
         desc.update({"parallelism": "dp%d (independent replicas)" % world, "engine": engine,
-                     "team_size": info.team_size, "chunk_rk4_steps": chunk,
+                     "team_size": info.team_size, "stage_state": "shared memory" if info.stage_in_smem else "L2",
+                     "projection": ("tcgen05 TF32 x%d" % info.tensor_passes) if info.tensor_passes else "CUDA cores",
+                     "chunk_rk4_steps": chunk,
                      "l2": "flushed (256 MiB write) between timed steps"})
         line = {
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == "fp64" else "f32 (f64 Gram/Cholesky/signal)",
+            "dtype": {"fp64": "f64", "tf32_g64": "f32 (tf32 projection; f64 Gram/Cholesky/signal)",
+                      "fp32": "f32 (f64 Cholesky/signal)"}.get(prec, "f32 (f64 Gram/Cholesky/signal)"),
             "data": "synthetic (seeded pulses and initial states)", "config": desc,
             "pulse_evals_per_s": value / (2 * spp),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -89,8 +89,16 @@ typedef enum {
  * FP32_G64: Z, the operator apply, the projection term and the RK4 stages in
  * complex64; the Gram matrix Z^dag Z (exact FP32 products, FP64-class
  * double-word accumulation), its Cholesky factor, the solves and the readout
- * signal in FP64. */
-typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1, LR_PREC_FP32 = 2 } lr_precision;
+ * signal in FP64. Where the fused engine keeps the stage state in L2 it may
+ * run the projection term (the Y_k X_k^dag product of Eq. S5) on the tensor
+ * cores as three TF32 passes of a two-term split (FP32-class products,
+ * lr_info.tensor_passes = 3).
+ * TF32_G64: as FP32_G64 with the projection term in ONE TF32 tensor-core pass
+ * (operands rounded to 10-bit mantissas, FP32 accumulation): the reduced-
+ * precision variant, for measuring its error; FUSED engine only, and only
+ * for batches whose operand tiles fit in shared memory (else
+ * LR_ERR_UNSUPPORTED). */
+typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1, LR_PREC_FP32 = 2, LR_PREC_TF32_G64 = 3 } lr_precision;
 
 /* PLAIN: straightforward HBM-resident kernels, several launches per RK4
  * stage (the reference GPU path). FUSED: one persistent launch per
@@ -136,6 +144,8 @@ typedef struct {
   long step;          /* RK4 steps taken since lr_set_initial / lr_set_state */
   lr_engine engine;   /* engine actually used */
   int team_size;      /* CTAs per trajectory (FUSED) */
+  int stage_in_smem;  /* FUSED: 1 stage state in shared memory, 0 in L2 */
+  int tensor_passes;  /* FUSED: TF32 tensor-core passes of the projection term (0: CUDA cores) */
 } lr_info;
 
 /* Create a context for n_cand candidates (2 n_cand trajectories).

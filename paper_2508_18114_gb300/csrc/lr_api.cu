@@ -115,7 +115,8 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   *out = nullptr;
   if (n_cand <= 0 || !models || !ranks || !opt) return LR_ERR_ARG;
   if (opt->max_steps < 1 || opt->pop_every < 1 || !(opt->eta > 0.0 && opt->eta <= 1.0)) return LR_ERR_ARG;
-  if (opt->precision != LR_PREC_FP64 && opt->precision != LR_PREC_FP32_G64 && opt->precision != LR_PREC_FP32)
+  if (opt->precision != LR_PREC_FP64 && opt->precision != LR_PREC_FP32_G64 && opt->precision != LR_PREC_FP32 &&
+      opt->precision != LR_PREC_TF32_G64)
     return LR_ERR_ARG;
   if (opt->engine != LR_ENGINE_AUTO && opt->engine != LR_ENGINE_PLAIN && opt->engine != LR_ENGINE_FUSED)
     return LR_ERR_ARG;
@@ -457,6 +458,8 @@ lr_status lr_query(const lr_ctx* c, lr_info* info) {
   info->step = c->step;
   info->engine = c->engine;
   info->team_size = c->engine == LR_ENGINE_FUSED ? c->fused.C : 0;
+  info->stage_in_smem = c->engine == LR_ENGINE_FUSED ? c->fused.zs_smem : 0;
+  info->tensor_passes = c->engine == LR_ENGINE_FUSED ? c->fused.tc : 0;
   return LR_OK;
 }
 

@@ -14,6 +14,14 @@
 //               buffer, the accumulator and Z_n are updated in L2.
 // Partial slots and Z_s buffers are double-buffered by stage parity, so the
 // single barrier per stage separates every write from the reads of it.
+//
+// Tensor-core projection (TC > 0, stage state in L2): the projection term of F
+// is a real GEMM per 128-row tile, D[l][2m+c] = sum_K A[l][K] B[2m+c][K] with
+// A[l] = (s_r rZ_s[l], s_b bZ_s[l]) as interleaved (re, im) floats (K = 4 Mp)
+// and B the real 2x2-block embedding of XT. It runs as tcgen05.mma kind::tf32
+// with both operands in shared memory (K-major, no swizzle) and D in tensor
+// memory: 3 passes (big*big + big*small + small*big of a two-term TF32 split,
+// FP32-class products) or 1 pass (plain TF32).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -41,6 +49,7 @@ struct Args {
   // byte offsets in dynamic shared memory
   int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop;   // s_*: offsets inside one slot
   int o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
+  int o_ta, o_tb, o_td, npad, ldd;   // tensor-core operand tiles and D staging (TC > 0)
   const int* order;
   void* zs_glob;      // global stage buffers, per cluster [C][2][R][Mp+1]
   void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
@@ -127,8 +136,55 @@ __device__ __forceinline__ void store4(T2* p, const T2 (&v)[4]) {
   }
 }
 
-template <typename T2, int GRAM_DW, int ZSM>
+// ----------------------------------------------------------------- tcgen05 helpers
+// Operand tiles are K-major without swizzle: 8-row x 16-byte core matrices,
+// rows of a core 16 bytes apart, cores of consecutive 8-row groups 128 bytes
+// apart (stride offset) and cores consecutive in K rows*16 bytes apart
+// (leading offset).
+constexpr int TC_ROWS = 128;   // MMA M (rows of Z_s per tile), one TMEM lane per row
+constexpr int TC_COLS = 64;    // TMEM columns allocated (N = 2 Mp padded to 16 <= 64)
+
+__device__ __forceinline__ int kmaj_off(int row, int k, int rows) {
+  return (k >> 2) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | (uint64_t)((lbo >> 4) & 0x3FFF) << 16 |
+         (uint64_t)((sbo >> 4) & 0x3FFF) << 32 | (uint64_t)1 << 46;
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// wait (at most ~1 s of SM clock) for the phase with the given parity;
+// false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+}
+
+template <typename T2, int GRAM_DW, int ZSM, int TC>
 __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
+  static_assert(TC == 0 || (ZSM == 0 && sizeof(T2) == 8), "tensor-core projection: FP32 state in L2 only");
   using T = typename Real<T2>::t;
   constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
   constexpr int TR = sizeof(T) == 4 ? 4 : 2;     // phase-F rows per thread tile
@@ -152,7 +208,9 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   T2* XT = reinterpret_cast<T2*>(smem + a.o_xs);               // [2][Mp][Mp] (l, m)
   // misc (FP64 scalars): [0] pulse coefficient, [1] not-PD flag, [8..24) photon
   // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
-  // photons, [96..128) 1/L[k][k], [128..) bulk-precision coefficient and steps
+  // photons, [96..128) 1/L[k][k], [128..131) bulk-precision coefficient and
+  // steps, [140] phase-P task counter, [141] tensor-core timeout flag, [142]
+  // tensor-core mbarrier, [143] TMEM base address
   double* misc = reinterpret_cast<double*>(smem + a.o_misc);
   // row-ordered lower-triangle index table: entry e = i(i+1)/2 + j -> (i, j)
   __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
@@ -171,6 +229,39 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
 
   const double dt = a.rp.dt;
   const int pe = a.rp.pop_every;
+
+  // ---- tensor-core projection: operand tiles, D staging, TMEM and its mbarrier
+  float* ta_big = reinterpret_cast<float*>(smem + a.o_ta);
+  float* ta_small = ta_big + TC_ROWS * 4 * Mp;
+  float* tb_big = reinterpret_cast<float*>(smem + a.o_tb);
+  float* tb_small = tb_big + a.npad * 4 * Mp;
+  float* Ds = reinterpret_cast<float*>(smem + a.o_td);   // [TC_ROWS][ldd]
+  const uint32_t mbar = smem_u32(misc + 142);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 143);
+  uint32_t tmem = 0, tc_phase = 0;
+  if constexpr (TC > 0) {
+    // B rows beyond 2 Mp stay zero for the whole launch
+    for (int e = tid; e < (a.npad - 2 * Mp) * 4 * Mp; e += NT) {
+      const int n = 2 * Mp + e / (4 * Mp), k = e % (4 * Mp);
+      tb_big[kmaj_off(n, k, a.npad) / 4] = 0.0f;
+      if (TC == 3) tb_small[kmaj_off(n, k, a.npad) / 4] = 0.0f;
+    }
+    if (tid == 0) {
+      *reinterpret_cast<int*>(misc + 141) = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                   "r"(TC_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = *tslot;
+  }
 
   for (int it_idx = cid; it_idx < a.rp.n_traj; it_idx += a.n_clusters) {
     const int tj = a.order[it_idx];
@@ -654,7 +745,21 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
             const T s = (T)sk[k];
             XT[k * MM + lm] = cm<T2>(s * xr, -s * xi);
+            if constexpr (TC > 0) {
+              // real 2x2 block of X = (xr', xi') at B rows (2m, 2m+1), K columns
+              // (k 2Mp + 2l, +1): [xr', -xi'; xi', xr'] maps (re, im) of A to D
+              const float Xr = (float)(s * xr), Xi = (float)(-s * xi);
+              const int kk = k * 2 * Mp + 2 * l;
+              const float vals[4] = {Xr, -Xi, Xi, Xr};
+              for (int u = 0; u < 4; ++u) {
+                const int o = kmaj_off(2 * m + (u >> 1), kk + (u & 1), a.npad) / 4;
+                const float big = tf32_rna(vals[u]);
+                tb_big[o] = big;
+                if (TC == 3) tb_small[o] = tf32_rna(vals[u] - big);
+              }
+            }
           }
+          if constexpr (TC > 0) async_proxy_fence();
           __syncthreads();
         }
 
@@ -668,9 +773,98 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           const T c = tb[0], hs_hi = tb[1], hs_lo = tb[2], h6_hi = tb[3], h6_lo = tb[4];
           const int nxt = cur ^ 1;
           const int mq = Mp / 4;
-          const int nrt = (P.R + TR - 1) / TR;
+          const int nrt_all = (P.R + TR - 1) / TR;
           const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
           const int MM = Mp * Mp;
+          // with the tensor-core projection the rows go in tiles of TC_ROWS
+          const int n_sub = TC > 0 ? (P.R + TC_ROWS - 1) / TC_ROWS : 1;
+          for (int sub = 0; sub < n_sub; ++sub) {
+          const int row_lo = TC > 0 ? sub * TC_ROWS : 0;
+          const int nrt = TC > 0 ? (min(P.R - row_lo, TC_ROWS) + TR - 1) / TR : nrt_all;
+          if constexpr (TC > 0) {
+            // A tile: row r = local row row_lo + r; float4 chunk c4 holds complex
+            // columns 2cj, 2cj+1 of s_r rZ_s (c4 < Mp/2) or s_b bZ_s (c4 >= Mp/2)
+            for (int e = tid; e < TC_ROWS * Mp; e += NT) {
+              const int r = e % TC_ROWS, c4 = e / TC_ROWS;
+              const int l = row_lo + r;
+              const int jump = c4 >= Mp / 2 ? 1 : 0;
+              const int cj = c4 - jump * (Mp / 2);
+              float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (l < P.R) {
+                const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
+                const T2* src = nullptr;
+                float sc = 0.f;
+                if (jump == 0) {
+                  const int iro = three ? iff : P.r_lo + irl;
+                  if (iro + 1 < dro) {
+                    src = own(cur, l + 1);
+                    sc = sq[iro + 1];
+                  }
+                } else if (it + 1 < Nt) {
+                  src = own(cur, l + P.st);
+                  sc = sq[it + 1];
+                }
+                if (src) {
+                  v = reinterpret_cast<const float4*>(src)[cj];
+                  v.x *= sc;
+                  v.y *= sc;
+                  v.z *= sc;
+                  v.w *= sc;
+                }
+              }
+              const int o = kmaj_off(r, 4 * c4, TC_ROWS) / 4;
+              const float4 big = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+              *reinterpret_cast<float4*>(ta_big + o) = big;
+              if (TC == 3)
+                *reinterpret_cast<float4*>(ta_small + o) = make_float4(
+                    tf32_rna(v.x - big.x), tf32_rna(v.y - big.y), tf32_rna(v.z - big.z), tf32_rna(v.w - big.w));
+            }
+            async_proxy_fence();
+            __syncthreads();
+            if (tid == 0) {
+              tc_fence_after();
+              const uint32_t lboA = TC_ROWS * 16, lboB = (uint32_t)a.npad * 16;
+              const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.npad >> 3) << 17) |
+                                     ((uint32_t)(TC_ROWS >> 4) << 24);
+              for (int pass = 0; pass < TC; ++pass) {
+                const uint32_t A0 = smem_u32(pass == 2 ? ta_small : ta_big);
+                const uint32_t B0 = smem_u32(pass == 1 ? tb_small : tb_big);
+                for (int ks = 0; ks < Mp / 2; ++ks)   // K = 4 Mp in steps of 8
+                  tc_mma(tmem, tc_desc(A0 + ks * 2 * lboA, lboA, 128), tc_desc(B0 + ks * 2 * lboB, lboB, 128), idesc,
+                         (pass | ks) != 0);
+              }
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                           : "memory");
+            }
+            // after a timeout (flag in misc[141]) the CTA stops waiting: the
+            // error word already reports the failure and the launch ends
+            volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
+            if (*tc_abort == 0 && !mbar_wait(mbar, tc_phase)) {
+              *tc_abort = 1;
+              set_error(a.p.err, DEV_TIMEOUT);
+            }
+            tc_phase ^= 1u;
+            tc_fence_after();
+            // D rows to shared memory: warp w reads TMEM lanes 32 (w % 4) + lane
+            {
+              const int qd = warp & 3, row = qd * 32 + lane;
+              for (int g8 = warp >> 2; g8 < a.npad / 8; g8 += NWARP / 4) {
+                uint32_t v[8];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                    : "r"(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(g8 * 8)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float4* dst = reinterpret_cast<float4*>(Ds + row * a.ldd + g8 * 8);
+                dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                     __uint_as_float(v[3]));
+                dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]),
+                                     __uint_as_float(v[7]));
+              }
+            }
+            tc_fence_before();
+            __syncthreads();
+          }
           for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
             T fr[TR][4], fi[TR][4];
@@ -678,7 +872,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             const T2* yrp[TR];
             const T2* ybp[TR];
             int nrow[TR];
-            const int l0 = rt * TR;
+            const int l0 = row_lo + rt * TR;
             int it = l0 / P.st, irl = (l0 - it * P.st) / Nf, iff = l0 - it * P.st - irl * Nf;
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
@@ -793,6 +987,21 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               }
             }
             // projection terms: + sr (rZ_s) XT_r + sb (bZ_s) XT_b
+            if constexpr (TC > 0) {
+              for (int r = 0; r < TR; ++r) {
+                const float4* dp = reinterpret_cast<const float4*>(Ds + (l0 + r - row_lo) * a.ldd + 2 * m0);
+                const float4 d0 = dp[0], d1 = dp[1];
+                fr[r][0] += d0.x;
+                fi[r][0] += d0.y;
+                fr[r][1] += d0.z;
+                fi[r][1] += d0.w;
+                fr[r][2] += d1.x;
+                fi[r][2] += d1.y;
+                fr[r][3] += d1.z;
+                fi[r][3] += d1.w;
+              }
+            }
+            if constexpr (TC == 0) {
             for (int k = 0; k < M; ++k) {
               T2 xr[4], xb[4];
 #pragma unroll
@@ -810,6 +1019,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                   fi[r][u] = fma(ar, xr[u].y, fma(ai, xr[u].x, fma(br, xb[u].y, fma(bi, xb[u].x, fi[r][u]))));
                 }
               }
+            }
             }
             // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
 #pragma unroll
@@ -846,6 +1056,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               store4<ZSM>(own(nxt, l0 + r) + m0, zo);
             }
           }
+          if constexpr (TC > 0) __syncthreads();   // D staging and operand tiles are reused by the next tile
+          }
           cur = nxt;
           __syncthreads();
         }
@@ -854,6 +1066,12 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
     }
     // every CTA is done reading its peers' shared memory before it is reused
     cluster.sync();
+  }
+  if constexpr (TC > 0) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
   }
 }
 
@@ -864,12 +1082,14 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
 namespace {
 
 struct SmemLayout {
-  int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop, o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab, total;
+  int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop, o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
+  int o_ta, o_tb, o_td, npad, ldd, total;
 };
 
 int al16(int x) { return (x + 15) / 16 * 16; }
+int al128(int x) { return (x + 127) / 128 * 128; }
 
-SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
+SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
   SmemLayout L{};
   int o = 0;
   L.o_zs = o;
@@ -894,19 +1114,42 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es) {
   o += al16(144 * (int)sizeof(double));
   L.o_tab = o;
   o += al16(fz::TAB * 7 * (int)(es / 2));
+  L.o_ta = L.o_tb = L.o_td = o;
+  L.npad = (2 * Mp + 15) / 16 * 16;
+  L.ldd = L.npad + 4;
+  if (tc > 0) {
+    const int nbuf = tc == 3 ? 2 : 1;   // big (and small) halves of the TF32 split
+    const int K = 4 * Mp;
+    o = al128(o);
+    L.o_ta = o;
+    o += nbuf * fz::TC_ROWS * K * 4;
+    L.o_tb = o;
+    o += al128(nbuf * L.npad * K * 4);
+    // D staging reuses the A tile's big half when it fits there
+    if (L.ldd <= K) {
+      L.o_td = L.o_ta;
+    } else {
+      L.o_td = o;
+      o += al128(fz::TC_ROWS * L.ldd * 4);
+    }
+  }
   L.total = o;
   return L;
 }
 
-const void* kernel_ptr(lr_precision prec, int zs_smem) {
+// tc: tensor-core passes of the projection (0: CUDA cores; 3 or 1: tcgen05,
+// L2-resident stage state and FP32 state with the double-word Gram only)
+const void* kernel_ptr(lr_precision prec, int zs_smem, int tc) {
+  if (tc == 3) return (const void*)fz::fused_kernel<float2, 1, 0, 3>;
+  if (tc == 1) return (const void*)fz::fused_kernel<float2, 1, 0, 1>;
   if (zs_smem) {
-    if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 1>;
-    if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 1>;
-    return (const void*)fz::fused_kernel<float2, 1, 1>;
+    if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 1, 0>;
+    if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 1, 0>;
+    return (const void*)fz::fused_kernel<float2, 1, 1, 0>;
   }
-  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 0>;
-  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 0>;
-  return (const void*)fz::fused_kernel<float2, 1, 0>;
+  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 0, 0>;
+  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 0, 0>;
+  return (const void*)fz::fused_kernel<float2, 1, 0, 0>;
 }
 
 int rows_per_cta(const TrajDev& d, int C) {
@@ -939,34 +1182,46 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
     tot_work += w;
   }
   const int Mp = (Mmax + 3) / 4 * 4;
-  const void* kerns[2] = {kernel_ptr(prec, 0), kernel_ptr(prec, 1)};
-  int smem_maxs[2];
-  for (int z = 0; z < 2; ++z) {
+  // Variants (stage state placement, tensor-core passes of the projection).
+  // Overrides for tuning and tests: LR_FUSED_C = cluster size, LR_FUSED_ZS =
+  // "global" keeps the stage state in L2, LR_FUSED_TC = 0 keeps the FP32_G64
+  // projection on the CUDA cores (3: only the tensor-core variant).
+  int force_c = 0, force_global = 0, force_tc = -1;
+  if (const char* e = getenv("LR_FUSED_C")) force_c = atoi(e);
+  if (const char* e = getenv("LR_FUSED_ZS")) force_global = strcmp(e, "global") == 0;
+  if (const char* e = getenv("LR_FUSED_TC")) force_tc = atoi(e);
+  struct Variant {
+    int zs_smem, tc;
+  };
+  std::vector<Variant> vars;
+  if (prec == LR_PREC_TF32_G64) {
+    vars.push_back({0, 1});
+  } else {
+    if (force_tc != 3) {
+      if (!force_global) vars.push_back({1, 0});
+      vars.push_back({0, 0});
+    }
+    if (prec == LR_PREC_FP32_G64 && force_tc != 0) vars.push_back({0, 3});
+  }
+  double best = 1e300;
+  for (const Variant& v : vars) {
+    const int zs_smem = v.zs_smem, tc = v.tc;
+    const void* kern = kernel_ptr(prec, zs_smem, tc);
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, kerns[z]) != cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
-    smem_maxs[z] = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
-    cudaFuncSetAttribute(kerns[z], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  }
-  // Overrides for tuning and tests: LR_FUSED_C = cluster size,
-  // LR_FUSED_ZS = "global" keeps the stage state in L2 instead of shared memory.
-  int force_c = 0, force_global = 0;
-  if (const char* e = getenv("LR_FUSED_C")) force_c = atoi(e);
-  if (const char* e = getenv("LR_FUSED_ZS")) force_global = strcmp(e, "global") == 0;
-  double best = 1e300;
-  for (int C = 1; C <= 16; ++C) {
-    if (two && C > 1) break;
-    if (C > min_nr) break;
-    if (force_c > 0 && C != force_c) continue;
-    int R = 0;
-    for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
-    for (int zs_smem = 1; zs_smem >= 0; --zs_smem) {
-      if (force_global && zs_smem) continue;
-      const void* kern = kerns[zs_smem];
-      const SmemLayout L = layout(R, Mp, zs_smem, es);
-      if (L.total > smem_maxs[zs_smem]) continue;
+    const int smem_max = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int C = 1; C <= 16; ++C) {
+      if (two && C > 1) break;
+      if (C > min_nr) break;
+      if (force_c > 0 && C != force_c) continue;
+      int R = 0;
+      for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
+      const SmemLayout L = layout(R, Mp, zs_smem, es, tc);
+      if (L.total > smem_max) continue;
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess) {
         cudaGetLastError();
         continue;
@@ -994,17 +1249,20 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
       const int used = std::min((n_traj + waves_needed - 1) / waves_needed, n_traj);
       // Cost model, fitted to measurements on GB300 (N = 2000, M = 20 batch):
       // a stage costs ~0.16 us per row per CTA with the stage state in shared
-      // memory (x1.3 in L2), plus a fixed ~60 us per team (the M x M phase and
-      // the cluster barrier, ~M sequential elimination steps) that does not
-      // shrink with C; teams run trajectories in waves.
+      // memory (x1.3 in L2; x1.95 and x1.75 in L2 with the projection on the
+      // tensor cores in 3 and 1 passes: the 128-row tiles serialise operand
+      // staging, MMA and epilogue), plus a fixed ~60 us per team (the M x M
+      // phase and the cluster barrier, ~M sequential elimination steps) that
+      // does not shrink with C; teams run trajectories in waves.
+      const double row_cost = zs_smem ? 1.0 : (tc == 3 ? 1.95 : tc == 1 ? 1.75 : 1.3);
       const double waves = std::ceil((double)n_traj / used);
       double t = 0.0;
       for (const TrajDev& d : traj) {
-        const double rows = (double)rows_per_cta(d, C) * (zs_smem ? 1.0 : 1.3) * (d.M * d.M) / 400.0;
+        const double rows = (double)rows_per_cta(d, C) * row_cost * (d.M * d.M) / 400.0;
         const double fixed = 375.0 * d.M / 20.0 * (C > 1 ? 1.0 : 0.95);
         t += rows + fixed;
       }
-      t = std::max(waves * t / n_traj, 0.0) * 1.0;
+      t = waves * t / n_traj;
       if (t < best) {
         best = t;
         plan->ok = 1;
@@ -1013,10 +1271,11 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
         plan->threads = fz::NT;
         plan->smem = L.total;
         plan->zs_smem = zs_smem;
+        plan->tc = tc;
         plan->Mp = Mp;
         plan->R = R;
         plan->Nmax = Nmax;
-        plan->gram_mode = prec == LR_PREC_FP32_G64 ? 1 : 0;
+        plan->gram_mode = prec == LR_PREC_FP32_G64 || prec == LR_PREC_TF32_G64 ? 1 : 0;
         plan->es = (int)es;
       }
     }
@@ -1044,7 +1303,7 @@ size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj) {
 cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunParams& rp, lr_precision prec,
                             long step0, long n_steps, cudaStream_t s) {
   const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
-  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es);
+  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es, plan.tc);
   fz::Args a{};
   a.p = p;
   a.rp = rp;
@@ -1069,6 +1328,11 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.o_xs = L.o_xs;
   a.o_misc = L.o_misc;
   a.o_tab = L.o_tab;
+  a.o_ta = L.o_ta;
+  a.o_tb = L.o_tb;
+  a.o_td = L.o_td;
+  a.npad = L.npad;
+  a.ldd = L.ldd;
   char* sc = static_cast<char*>(p.scratch);
   size_t off = ((sizeof(int) * rp.n_traj + 255) / 256) * 256;
   a.order = reinterpret_cast<const int*>(sc);
@@ -1079,7 +1343,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.acc_glob = sc + off;
   cudaError_t e = cudaMemcpyAsync(sc, plan.order.data(), sizeof(int) * rp.n_traj, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  const void* kern = kernel_ptr(prec, plan.zs_smem);
+  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1095,14 +1359,16 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if (plan.tc == 3) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 3>, a);
+  if (plan.tc == 1) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 1>, a);
   if (plan.zs_smem) {
-    if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 1>, a);
-    if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 1>, a);
-    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 1>, a);
+    if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 1, 0>, a);
+    if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 1, 0>, a);
+    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 1, 0>, a);
   }
-  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 0>, a);
-  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 0>, a);
-  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0>, a);
+  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 0, 0>, a);
+  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 0, 0>, a);
+  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 0>, a);
 }
 
 }  // namespace lr

@@ -23,6 +23,7 @@ struct FusedPlan {
   int threads;
   int smem;        // dynamic shared memory per CTA (bytes)
   int zs_smem;     // 1: stage state in shared memory, 0: in global scratch (L2)
+  int tc;          // tensor-core passes of the projection term: 0 (CUDA cores), 3 or 1
   int Mp;          // padded rank (multiple of 4)
   int R;           // largest rows per CTA
   int Nmax;        // largest N in the batch

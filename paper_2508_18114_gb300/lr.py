@@ -24,7 +24,7 @@ STATUS = {
     4: "LR_ERR_WORKSPACE", 5: "LR_ERR_NOT_PD", 6: "LR_ERR_NONFINITE",
     7: "LR_ERR_TIMEOUT", 8: "LR_ERR_STATE", 9: "LR_ERR_UNSUPPORTED",
 }
-PRECISION = {"fp64": 0, "fp32_g64": 1, "fp32": 2}
+PRECISION = {"fp64": 0, "fp32_g64": 1, "fp32": 2, "tf32_g64": 3}
 ENGINE = {"auto": 0, "plain": 1, "fused": 2}
 ENGINE_NAME = {v: k for k, v in ENGINE.items()}
 
@@ -65,7 +65,8 @@ class lr_options(C.Structure):
 class lr_info(C.Structure):
     _fields_ = [("n_cand", C.c_int), ("n_traj", C.c_int), ("nt_max", C.c_int),
                 ("n_rec", C.c_long), ("max_steps", C.c_long), ("step", C.c_long),
-                ("engine", C.c_int), ("team_size", C.c_int)]
+                ("engine", C.c_int), ("team_size", C.c_int),
+                ("stage_in_smem", C.c_int), ("tensor_passes", C.c_int)]
 
 
 _lib = None

@@ -44,6 +44,19 @@ def _three_mode_batch(n_steps=400):
     return li.Workload("ragged3", cands, 5e-4, n_steps, 2.0, init_seed=91, eps=1e-5)
 
 
+def _tc_batch(n_steps=400):
+    """Uneven N and M up to 20 (operand tiles fit in shared memory), with
+    576 rows for the largest trajectory: several 128-row tensor-core tiles and
+    a ragged last tile at team sizes 1, 2 and 4."""
+    cands = [
+        li.Candidate(_filter(3, 7, 5), 7, li.pulse_two_segment(41, li.TWO_PI * 7.5)),
+        li.Candidate(_filter(5, 6, 3), 12, li.pulse_two_segment(42, li.TWO_PI * 7.5)),
+        li.Candidate(_filter(6, 12, 8), 20, li.pulse_two_segment(43, li.TWO_PI * 7.5)),
+        li.Candidate(_filter(2, 5, 4), 5, li.pulse_two_segment(44, li.TWO_PI * 7.5)),
+    ]
+    return li.Workload("ragged_tc", cands, 5e-4, n_steps, 2.0, init_seed=92, eps=1e-5)
+
+
 class _env:
     def __init__(self, **kw):
         self.kw = kw
@@ -109,6 +122,52 @@ def test_cluster_shapes_fp32(C):
     gpu = b.observables()
     b.close()
     compare_observables(gpu, ora, 2 * len(wl.candidates), _nts(wl), TOL32, TOL32_POP, "fp32 C=%d" % C)
+
+
+@pytest.mark.parametrize("C,tc", [(1, 3), (2, 3), (4, 3), (2, 0)])
+def test_projection_on_tensor_cores_fp32_g64(C, tc):
+    """FP32_G64 with the projection term as three TF32 tensor-core passes
+    (two-term split of both operands, FP32-class products) against the oracle
+    at the FP32 tolerance; tc = 0 forces the CUDA-core projection. Ragged rows:
+    the 128-row tiles end inside a CTA's rows."""
+    wl = _tc_batch()
+    ora = parallel.run_workload(wl, None, 40)
+    with _env(LR_FUSED_C=C, LR_FUSED_TC=tc):
+        b = runner.make_batch(wl, precision="fp32_g64", engine="fused", pop_every=40)
+    info = b.query()
+    assert info.team_size == C and info.tensor_passes == tc
+    if tc:
+        assert info.stage_in_smem == 0
+    b.set_initial(wl.init_seed, wl.eps)
+    b.integrate(wl.dt, wl.n_steps)
+    gpu = b.observables()
+    b.close()
+    print(compare_observables(gpu, ora, 2 * len(wl.candidates), _nts(wl), TOL32, TOL32_POP,
+                              "fp32_g64 C=%d tc=%d" % (C, tc)))
+
+
+# One TF32 pass rounds both operands of the projection term to 11 significant
+# bits (unit roundoff u = 2^-11 = 4.9e-4). The error this puts into F is a
+# fraction u of the projection term, whose size is set by the decay rates
+# (kappa ~ 0.3/ns here), so over a pulse of length tau it grows to about
+# u kappa tau relative; at tau = 0.2 ns that is 3e-5. Populations and eps_a are
+# held to 50x that, the size of the effect where the Moore-Penrose inverse
+# amplifies it (1/sqrt(eps) ~ 300 for the padding columns).
+TOL_TF32 = 50 * 2.0 ** -11 * (li.TWO_PI * 0.05) * 0.2
+
+
+def test_tf32_variant_error():
+    wl = _tc_batch()
+    ora = parallel.run_workload(wl, None, 40)
+    b = runner.make_batch(wl, precision="tf32_g64", engine="fused", pop_every=40)
+    info = b.query()
+    assert info.tensor_passes == 1 and info.stage_in_smem == 0
+    b.set_initial(wl.init_seed, wl.eps)
+    b.integrate(wl.dt, wl.n_steps)
+    gpu = b.observables()
+    b.close()
+    print("tf32 variant:", compare_observables(gpu, ora, 2 * len(wl.candidates), _nts(wl), TOL_TF32, TOL_TF32,
+                                               "tf32_g64"))
 
 
 def test_fused_resume_is_bitwise():
