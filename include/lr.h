@@ -134,6 +134,9 @@ typedef struct {
   long max_steps;     /* capacity: largest total number of RK4 steps per pulse run */
   int pop_every;      /* record populations, photons, trace every pop_every steps (>= 1) */
   double eta;         /* measurement efficiency in the SNR (the paper uses 0.6) */
+  int record_gram;    /* 1: keep the FP64 Gram matrix Z^dag Z at every record step for
+                         lr_diagnostics (the workspace grows by n_traj * n_rec *
+                         (max_M^2 * 16 + max_M * 8 + 8) bytes); 0: off */
 } lr_options;
 
 typedef struct {
@@ -213,6 +216,23 @@ lr_status lr_observables(lr_ctx* ctx, double* beta, double* pops, double* nphot,
  *   loss[c] = log10(eps_a + T).
  * Synchronises the stream and returns the device error word's status. */
 lr_status lr_loss(lr_ctx* ctx, double* ionization, double* loss, void* stream);
+
+/* Validity diagnostics of the low-rank ansatz (Sec. S1.B, Fig. S1): at every
+ * recorded step, the spectrum of rho = Z Z^dag and its purity tr(rho^2).
+ * The nonzero eigenvalues of rho are those of the Gram matrix G = Z^dag Z
+ * (same nonzero spectrum of A A^dag and A^dag A), and tr(rho^2) = tr(G^2) =
+ * sum_ij |G_ij|^2. Needs lr_options.record_gram = 1; the Gram matrices are
+ * the FP64 ones the engines form at the record steps (step 0, pop_every, ...).
+ * Each (trajectory, record) is diagonalised on the device by cyclic Jacobi
+ * rotations (FP64) of the real symmetric embedding [[Re G, -Im G],
+ * [Im G, Re G]], whose eigenvalues are those of G, each twice.
+ *   purity: host [n_traj][n_rec] doubles, tr(rho^2);
+ *   eig:    host [n_traj][n_rec][max_M] doubles, eigenvalues p_1 >= ... >= p_M
+ *           of trajectory j (entries beyond its rank M are 0);
+ * records after the current step are 0. Either pointer may be NULL. p_M / p_1
+ * is the paper's rank-saturation indicator. Synchronises `stream`. Errors:
+ * LR_ERR_STATE without record_gram, LR_ERR_CUDA. */
+lr_status lr_diagnostics(lr_ctx* ctx, double* purity, double* eig, void* stream);
 
 /* Synchronise the stream and return the device error word's status. */
 lr_status lr_sync(lr_ctx* ctx, void* stream);

@@ -23,7 +23,8 @@ their printed order:
                    orthonormal padding states with weight eps).
 * ``gradient``   - central finite-difference gradient of the assignment error
                    with respect to the pulse parameters.
+* ``diagnostics`` - spectrum of rho = m m^dag and purity tr(rho^2) (Sec. S1.B).
 
 Parity status of each function is stated in its module docstring.
 """
-from . import model, pulse, lowrank, lindblad, signal, init_state, gradient  # noqa: F401
+from . import model, pulse, lowrank, lindblad, signal, init_state, gradient, diagnostics  # noqa: F401

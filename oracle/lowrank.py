@@ -67,16 +67,17 @@ def observables(m: np.ndarray, model):
 
 
 def integrate(m0, model, coef, dt, n_steps, pop_every=1, t0=0.0,
-              return_state=False):
+              return_state=False, gram=False):
     """RK4-integrate Eq. S5 for n_steps steps.
 
     Returns a dict with beta[n_steps+1] (complex), and pops[n_rec, N_t],
-    nr[n_rec], trace[n_rec] at steps 0, pop_every, 2 pop_every, ...
+    nr[n_rec], trace[n_rec] at steps 0, pop_every, 2 pop_every, ...; with
+    gram=True also gram[n_rec, M, M], the Gram matrix m^dag m at those steps.
     """
     rhs = lambda y, t: nosse_rhs(y, t, model, coef)  # noqa: E731
     m = np.array(m0, dtype=complex)
     beta = np.zeros(n_steps + 1, dtype=complex)
-    pops, nrs, traces = [], [], []
+    pops, nrs, traces, grams = [], [], [], []
     for n in range(n_steps + 1):
         if n > 0:
             m = rk4_step(rhs, m, t0 + (n - 1) * dt, dt)
@@ -85,11 +86,15 @@ def integrate(m0, model, coef, dt, n_steps, pop_every=1, t0=0.0,
             pops.append(p)
             nrs.append(nr)
             traces.append(tr)
+            if gram:
+                grams.append(_dag(m) @ m)
             beta[n] = b
         else:
             beta[n] = np.trace(_dag(m) @ (model.r @ m))
     out = {"beta": beta, "pops": np.array(pops), "nr": np.array(nrs),
            "trace": np.array(traces)}
+    if gram:
+        out["gram"] = np.array(grams)
     if return_state:
         out["m"] = m
     return out

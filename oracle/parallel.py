@@ -17,23 +17,24 @@ def _traj_task(args):
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from . import init_state, lowrank, pulse
     from .model import Model
-    cand, traj, level, n_steps, pop_every, dt, tau, seed, eps = args
+    cand, traj, level, n_steps, pop_every, dt, tau, seed, eps, gram = args
     p = cand.model
     mdl = Model.from_params(p)
     psi = mdl.basis_index((level,) + (0,) * (len(p.dims) - 1))
     m0 = init_state.initial_state(mdl.N, cand.M, psi, eps, seed, traj)
     coef = pulse.coefficient(cand.pulse.kind, cand.pulse.p, tau)
-    return lowrank.integrate(m0, mdl, coef, dt, n_steps, pop_every)
+    return lowrank.integrate(m0, mdl, coef, dt, n_steps, pop_every, gram=gram)
 
 
-def _tasks(wl, n_steps, pop_every, candidates, traj_base):
+def _tasks(wl, n_steps, pop_every, candidates, traj_base, gram=False):
     idx = list(range(len(wl.candidates))) if candidates is None else list(candidates)
     ns = wl.n_steps if n_steps is None else n_steps
     tasks = []
     for k, ci in enumerate(idx):
         base = 2 * k if traj_base is None else traj_base[k]
         for lvl in (0, 1):
-            tasks.append((wl.candidates[ci], base + lvl, lvl, ns, pop_every, wl.dt, wl.tau, wl.init_seed, wl.eps))
+            tasks.append((wl.candidates[ci], base + lvl, lvl, ns, pop_every, wl.dt, wl.tau, wl.init_seed, wl.eps,
+                          gram))
     return idx, tasks
 
 
@@ -42,6 +43,8 @@ def _collect(wl, idx, res):
     out = {"beta": np.array([r["beta"] for r in res]),
            "pops": [r["pops"] for r in res], "nphot": [r["nr"] for r in res],
            "trace": [r["trace"] for r in res], "eps_a": []}
+    if "gram" in res[0]:
+        out["gram"] = [r["gram"] for r in res]
     for k, ci in enumerate(idx):
         p = wl.candidates[ci].model
         out["eps_a"].append(signal.assignment_error(res[2 * k]["beta"], res[2 * k + 1]["beta"],
@@ -58,9 +61,9 @@ class OracleJob:
     built from the same candidate list.
     """
 
-    def __init__(self, wl, n_steps=None, pop_every=1, candidates=None, processes=None, traj_base=None):
+    def __init__(self, wl, n_steps=None, pop_every=1, candidates=None, processes=None, traj_base=None, gram=False):
         self.wl = wl
-        self.idx, tasks = _tasks(wl, n_steps, pop_every, candidates, traj_base)
+        self.idx, tasks = _tasks(wl, n_steps, pop_every, candidates, traj_base, gram)
         procs = processes or min(len(tasks), os.cpu_count() or 1)
         self.pool = mp.get_context("spawn").Pool(procs)
         self.async_res = self.pool.map_async(_traj_task, tasks, chunksize=1)
@@ -74,9 +77,10 @@ class OracleJob:
         return _collect(self.wl, self.idx, res)
 
 
-def run_workload(wl, n_steps=None, pop_every=1, candidates=None, processes=None, traj_base=None):
-    """Oracle observables for candidates of a workload (blocking)."""
-    idx, tasks = _tasks(wl, n_steps, pop_every, candidates, traj_base)
+def run_workload(wl, n_steps=None, pop_every=1, candidates=None, processes=None, traj_base=None, gram=False):
+    """Oracle observables for candidates of a workload (blocking); gram=True
+    adds the Gram matrices at the record steps."""
+    idx, tasks = _tasks(wl, n_steps, pop_every, candidates, traj_base, gram)
     procs = processes or min(len(tasks), os.cpu_count() or 1)
     if procs <= 1:
         res = [_traj_task(t) for t in tasks]

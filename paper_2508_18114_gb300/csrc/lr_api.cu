@@ -28,7 +28,7 @@ struct lr_ctx {
   // workspace layout (byte offsets)
   size_t o_traj = 0, o_pulse = 0, o_err = 0, o_zn = 0, o_za = 0, o_zb = 0, o_acc = 0, o_x = 0, o_part = 0,
          o_beta = 0, o_pops = 0, o_nphot = 0, o_trace = 0, o_eps = 0, o_ion = 0, o_loss = 0, o_scratch = 0,
-         total = 0;
+         o_gsnap = 0, o_dpur = 0, o_deig = 0, total = 0;
   size_t scratch_bytes = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -74,6 +74,7 @@ DevPtrs dev_ptrs(const lr_ctx* c) {
   p.loss = reinterpret_cast<double*>(w + c->o_loss);
   p.scratch = c->scratch_bytes ? w + c->o_scratch : nullptr;
   p.scratch_bytes = (long long)c->scratch_bytes;
+  p.gsnap = c->opt.record_gram ? reinterpret_cast<double2*>(w + c->o_gsnap) : nullptr;
   return p;
 }
 
@@ -88,6 +89,7 @@ RunParams run_params(const lr_ctx* c) {
   r.tau = c->tau;
   r.dt = c->dt;
   r.eta = c->opt.eta;
+  r.snap_m = c->opt.record_gram ? c->max_M : 0;
   return r;
 }
 
@@ -120,6 +122,7 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
     return LR_ERR_ARG;
   if (opt->engine != LR_ENGINE_AUTO && opt->engine != LR_ENGINE_PLAIN && opt->engine != LR_ENGINE_FUSED)
     return LR_ERR_ARG;
+  if (opt->record_gram != 0 && opt->record_gram != 1) return LR_ERR_ARG;
   lr_ctx* c = new (std::nothrow) lr_ctx();
   if (!c) return LR_ERR_NOMEM;
   c->n_cand = n_cand;
@@ -217,6 +220,12 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   c->o_eps = take(sizeof(double) * n_cand);
   c->o_ion = take(sizeof(double) * n_cand);
   c->o_loss = take(sizeof(double) * n_cand);
+  if (opt->record_gram) {
+    const size_t nr = (size_t)c->n_traj * c->n_rec;
+    c->o_gsnap = take(sizeof(double2) * nr * c->max_M * c->max_M);
+    c->o_dpur = take(sizeof(double) * nr);
+    c->o_deig = take(sizeof(double) * nr * c->max_M);
+  }
   if (c->engine == LR_ENGINE_FUSED) {
     c->scratch_bytes = lr::fused_scratch_bytes(c->fused, c->n_traj);
     if (c->scratch_bytes) c->o_scratch = take(c->scratch_bytes);
@@ -248,6 +257,12 @@ lr_status lr_bind_workspace(lr_ctx* c, void* dev_ptr, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(c, e, "copying trajectory table");
   e = cudaMemset(c->ws + c->o_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) return cuda_fail(c, e, "clearing error word");
+  if (c->opt.record_gram) {
+    // records that no run writes stay zero matrices
+    e = cudaMemset(c->ws + c->o_gsnap, 0,
+                   sizeof(double2) * (size_t)c->n_traj * c->n_rec * c->max_M * c->max_M);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clearing Gram snapshots");
+  }
   c->have_state = false;
   c->have_pulse = false;
   return LR_OK;
@@ -405,6 +420,27 @@ lr_status lr_loss(lr_ctx* c, double* ionization, double* loss, void* stream) {
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, c->ws + c->o_loss, sizeof(double) * c->n_cand, cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "copying the loss");
+  return check_device_error(c);
+}
+
+lr_status lr_diagnostics(lr_ctx* c, double* purity, double* eig, void* stream) {
+  if (!c) return LR_ERR_ARG;
+  if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
+  if (!c->opt.record_gram) return fail(c, LR_ERR_STATE, "lr_diagnostics needs lr_options.record_gram = 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nr = (size_t)c->n_traj * c->n_rec;
+  double* dpur = reinterpret_cast<double*>(c->ws + c->o_dpur);
+  double* deig = reinterpret_cast<double*>(c->ws + c->o_deig);
+  cudaError_t e = cudaMemsetAsync(dpur, 0, sizeof(double) * nr, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(deig, 0, sizeof(double) * nr * c->max_M, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "clearing diagnostics");
+  const long n_valid = std::min(c->n_rec, c->step / c->opt.pop_every + 1);
+  e = lr::launch_diagnostics(dev_ptrs(c), run_params(c), n_valid, dpur, deig, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernel");
+  if (purity) e = cudaMemcpyAsync(purity, dpur, sizeof(double) * nr, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && eig) e = cudaMemcpyAsync(eig, deig, sizeof(double) * nr * c->max_M, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying diagnostics");
   return check_device_error(c);
 }
 

@@ -636,6 +636,11 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             tb[4] = (T)(h6 - (double)tb[3]);
           }
           __syncthreads();
+          if (record && q == 0 && a.p.gsnap) {
+            // FP64 Gram matrix of this record step, for the diagnostics
+            double2* gs = a.p.gsnap + ((size_t)tj * a.rp.n_rec + step / pe) * a.rp.snap_m * a.rp.snap_m;
+            for (int e = tid; e < M * M; e += NT) gs[(e / M) * a.rp.snap_m + e % M] = Gd[(e / M) * ldg + e % M];
+          }
           if (stage == 0 && q == 0 && tid == 0) {
             double br = 0.0, bi = 0.0;
             for (int i = 0; i < M; ++i) {

@@ -177,6 +177,7 @@ struct DevPtrs {
   double* loss;    // [n_cand] log10(eps_a + T)
   void* scratch;   // engine scratch
   long long scratch_bytes;
+  double2* gsnap;  // [n_traj][n_rec][snap_m][snap_m] Gram matrices at record steps, or null
 };
 
 struct RunParams {
@@ -188,6 +189,7 @@ struct RunParams {
   double tau;   // pulse duration (falling edge placement)
   double dt;
   double eta;
+  int snap_m;   // leading dimension of the Gram snapshots (max M), 0 when not recorded
 };
 
 // lr_common.cu
@@ -196,6 +198,11 @@ cudaError_t launch_initial_state(const DevPtrs& p, const RunParams& rp, int max_
 cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long step, cudaStream_t s);
 // Elementwise complex128 <-> complex64 conversion of n elements.
 cudaError_t launch_convert(const void* src, void* dst, long long n, int to_fp32, cudaStream_t s);
+
+// lr_diag.cu: eigenvalues and purity of the recorded Gram matrices, records
+// [0, n_valid) of every trajectory
+cudaError_t launch_diagnostics(const DevPtrs& p, const RunParams& rp, long n_valid, double* purity, double* eig,
+                               cudaStream_t s);
 
 // lr_plain.cu
 int plain_rows_per_block();

@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(PT) plain_solve(DevPtrs p, RunParams rp, long 
       for (int i = 0; i < M; ++i) tr += L[i][i].x;
       p.trace[(size_t)tj * rp.n_rec + step / rp.pop_every] = tr;
     }
+    if (record && p.gsnap) {
+      double2* gs = p.gsnap + ((size_t)tj * rp.n_rec + step / rp.pop_every) * rp.snap_m * rp.snap_m;
+      for (int e = tid; e < MM; e += blockDim.x) gs[(e / M) * rp.snap_m + e % M] = L[e / M][e % M];
+    }
   }
   __syncthreads();   // the trace above reads the diagonal before it is factorised
   if (!do_solve) return;

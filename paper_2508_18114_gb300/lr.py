@@ -34,7 +34,7 @@ EXPORTS = (
     "lr_set_initial", "lr_set_state", "lr_get_state", "lr_integrate",
     "lr_observables", "lr_sync", "lr_query", "lr_status_string",
     "lr_last_error", "lr_destroy", "lr_integrate_plain_noalloc",
-    "lr_backward_workspace_size", "lr_backward", "lr_loss",
+    "lr_backward_workspace_size", "lr_backward", "lr_loss", "lr_diagnostics",
 )
 
 
@@ -59,7 +59,7 @@ class lr_pulse(C.Structure):
 class lr_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("engine", C.c_int),
                 ("max_steps", C.c_long), ("pop_every", C.c_int),
-                ("eta", C.c_double)]
+                ("eta", C.c_double), ("record_gram", C.c_int)]
 
 
 class lr_info(C.Structure):
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_backward_workspace_size.argtypes = [vp, i, C.POINTER(C.c_size_t)]
     lib.lr_backward.argtypes = [vp, vp, C.c_size_t, vp, vp, i, vp]
     lib.lr_loss.argtypes = [vp, vp, vp, vp]
+    lib.lr_diagnostics.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("lr_status_string", "lr_last_error", "lr_destroy"):
             getattr(lib, name).restype = C.c_int
@@ -163,7 +164,7 @@ class LowRankBatch:
     """
 
     def __init__(self, models, ranks, precision="fp64", engine="auto", max_steps=1000,
-                 pop_every=1, eta=0.6, device="cuda:0"):
+                 pop_every=1, eta=0.6, device="cuda:0", record_gram=False):
         import torch
         self._lib = load_library()
         n = len(models)
@@ -171,7 +172,8 @@ class LowRankBatch:
             raise ValueError("need one rank per model")
         arr = (lr_model * n)(*[make_model(m) for m in models])
         rk = (C.c_int * n)(*[int(r) for r in ranks])
-        opt = lr_options(PRECISION[precision], ENGINE[engine], int(max_steps), int(pop_every), float(eta))
+        opt = lr_options(PRECISION[precision], ENGINE[engine], int(max_steps), int(pop_every), float(eta),
+                         1 if record_gram else 0)
         h = C.c_void_p()
         st = self._lib.lr_create(n, arr, rk, C.byref(opt), C.byref(h))
         if st != 0:
@@ -276,6 +278,17 @@ class LowRankBatch:
         self._check(self._lib.lr_loss(self._h, ion.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
                                       C.c_void_p(_stream_ptr(stream))))
         return ion, loss
+
+    def diagnostics(self, stream=None):
+        """(purity [n_traj, n_rec], eigenvalues [n_traj, n_rec, max_M] descending)
+        of rho = Z Z^dag at the record steps (lr_diagnostics; needs record_gram)."""
+        info = self.query()
+        nrec, mm = info.n_rec, max(self.ranks)
+        pur = np.zeros((self.n_traj, nrec))
+        eig = np.zeros((self.n_traj, nrec, mm))
+        self._check(self._lib.lr_diagnostics(self._h, pur.ctypes.data_as(C.c_void_p), eig.ctypes.data_as(C.c_void_p),
+                                             C.c_void_p(_stream_ptr(stream))))
+        return pur, eig
 
     def backward(self, d_eps_a, ckpt_every=200, stream=None):
         """dL/dtheta [n_cand, 8] for cotangents dL/deps_a (lr_backward)."""

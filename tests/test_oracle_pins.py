@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import init_state, lindblad, lowrank, pulse, signal, gradient
+from oracle import init_state, lindblad, lowrank, pulse, signal, gradient, diagnostics
 from oracle.model import Model
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -426,3 +426,49 @@ def test_spsa_step_on_quadratic():
     gq = np.sum(2 * scale * d0 * (th0 - target) / scale ** 2) / d0
     assert np.allclose(hist[1], th0 - ak * scale * gq, rtol=1e-12, atol=1e-12)
     assert L(hist[-1]) < 1e-6 * L(hist[0])
+
+
+# ---------------------------------------------------------------- diagnostics (Sec. S1.B)
+
+def test_diagnostics_gram_forms_equal_rho_forms():
+    """The M x M Gram forms of the spectrum and purity equal the N x N
+    definitions on rho = m m^dag (independent computations)."""
+    rng = np.random.default_rng(11)
+    m = rng.normal(size=(30, 5)) + 1j * rng.normal(size=(30, 5))
+    G = m.conj().T @ m
+    assert np.allclose(diagnostics.gram_spectrum(G), diagnostics.rho_spectrum(m), rtol=1e-12, atol=0)
+    assert abs(diagnostics.gram_purity(G) - diagnostics.rho_purity(m)) < 1e-11 * diagnostics.rho_purity(m)
+    # rho beyond rank M has no further nonzero eigenvalues
+    rho = m @ m.conj().T
+    assert np.abs(np.linalg.eigvalsh(rho)[:-5]).max() < 1e-10 * np.abs(rho).max()
+
+
+@pytest.mark.parametrize("M", [1, 4, 20])
+def test_diagnostics_initial_state_closed_forms(M):
+    """Fixed-rank initial state (Sec. S1.A): eigenvalues 1 - (M-1) eps (once)
+    and eps (M-1 times), purity (1-(M-1)eps)^2 + (M-1) eps^2, and the rank
+    indicator p_M / p_1 = eps / (1 - (M-1) eps)."""
+    eps = 1e-5
+    m = init_state.initial_state(200, M, 7, eps, seed=3, traj=1)
+    p0 = 1.0 - (M - 1) * eps
+    want = np.array([p0] + [eps] * (M - 1))
+    got = diagnostics.rho_spectrum(m)
+    assert np.allclose(got, want, rtol=1e-10, atol=1e-16)
+    assert abs(diagnostics.rho_purity(m) - (p0 ** 2 + (M - 1) * eps ** 2)) < 1e-13
+    g = diagnostics.gram_spectrum(m.conj().T @ m)
+    assert abs(g[-1] / g[0] - (eps / p0 if M > 1 else 1.0)) < 1e-9 * (eps / p0 if M > 1 else 1.0)
+
+
+def test_diagnostics_full_rank_purity_matches_master_equation():
+    """At M = N the low-rank purity follows the full ME's tr(rho^2) up to the
+    RK4 gap (Eq. S4 vs Eq. S5), and decays under the jumps from a pure-ish start."""
+    mdl = _c1_like(dims=(2, 4))
+    coef = lambda t: 1.1 * math.cos(3.1 * t + 0.2)  # noqa: E731
+    Z0 = init_state.initial_state(mdl.N, mdl.N, 4, 1e-2, seed=2, traj=3)
+    n, dt = 100, 0.02
+    a = lowrank.integrate(Z0, mdl, coef, dt, n, pop_every=n, return_state=True, gram=True)
+    b = lindblad.integrate(Z0 @ Z0.conj().T, mdl, coef, dt, n, pop_every=n, return_state=True)
+    pur_lra = diagnostics.gram_purity(a["gram"][-1])
+    pur_me = float(np.trace(b["rho"] @ b["rho"]).real)
+    assert abs(pur_lra - pur_me) < 1e-5
+    assert diagnostics.gram_purity(a["gram"][0]) > pur_lra
