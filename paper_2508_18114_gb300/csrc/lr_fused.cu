@@ -49,7 +49,7 @@ struct Args {
   // byte offsets in dynamic shared memory
   int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop;   // s_*: offsets inside one slot
   int o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
-  int o_ta, o_tb, o_td, npad, ldd;   // tensor-core operand tiles and D staging (TC > 0)
+  int o_ta, o_tb, npad;   // tensor-core operand tiles (TC > 0), B rows (2 Mp padded to 16)
   const int* order;
   void* zs_glob;      // global stage buffers, per cluster [C][2][R][Mp+1]
   void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
@@ -142,7 +142,9 @@ __device__ __forceinline__ void store4(T2* p, const T2 (&v)[4]) {
 // apart (stride offset) and cores consecutive in K rows*16 bytes apart
 // (leading offset).
 constexpr int TC_ROWS = 128;   // MMA M (rows of Z_s per tile), one TMEM lane per row
-constexpr int TC_COLS = 64;    // TMEM columns allocated (N = 2 Mp padded to 16 <= 64)
+constexpr int TC_ACC = 64;     // TMEM columns per accumulator (N = 2 Mp padded to 16 <= 64)
+constexpr int TC_KSPLIT = 2;   // independent accumulators per pass (halves of K)
+constexpr int TC_COLS = 512;   // TMEM columns allocated: up to 3 passes x TC_KSPLIT accumulators
 
 __device__ __forceinline__ int kmaj_off(int row, int k, int rows) {
   return (k >> 2) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4;
@@ -235,7 +237,6 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   float* ta_small = ta_big + TC_ROWS * 4 * Mp;
   float* tb_big = reinterpret_cast<float*>(smem + a.o_tb);
   float* tb_small = tb_big + a.npad * 4 * Mp;
-  float* Ds = reinterpret_cast<float*>(smem + a.o_td);   // [TC_ROWS][ldd]
   const uint32_t mbar = smem_u32(misc + 142);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 143);
   uint32_t tmem = 0, tc_phase = 0;
@@ -781,34 +782,44 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           const int nrt_all = (P.R + TR - 1) / TR;
           const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
           const int MM = Mp * Mp;
-          // with the tensor-core projection the rows go in tiles of TC_ROWS
-          const int n_sub = TC > 0 ? (P.R + TC_ROWS - 1) / TC_ROWS : 1;
-          for (int sub = 0; sub < n_sub; ++sub) {
-          const int row_lo = TC > 0 ? sub * TC_ROWS : 0;
-          const int nrt = TC > 0 ? (min(P.R - row_lo, TC_ROWS) + TR - 1) / TR : nrt_all;
           if constexpr (TC > 0) {
-            // A tile: row r = local row row_lo + r; float4 chunk c4 holds complex
-            // columns 2cj, 2cj+1 of s_r rZ_s (c4 < Mp/2) or s_b bZ_s (c4 >= Mp/2)
-            for (int e = tid; e < TC_ROWS * Mp; e += NT) {
-              const int r = e % TC_ROWS, c4 = e / TC_ROWS;
-              const int l = row_lo + r;
-              const int jump = c4 >= Mp / 2 ? 1 : 0;
-              const int cj = c4 - jump * (Mp / 2);
-              float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            // ---- projection term on the tensor cores, in tiles of TC_ROWS rows.
+            // Thread (warp w, lane) owns tile row 32 (w % 4) + lane, the TMEM lane
+            // it may read, and column quads w / 4, w / 4 + 3, ... The MMAs of a
+            // tile run while the threads form -i H_eff Z_s for it; the next tile's
+            // operand staging and MMAs overlap the RK4 update of this one.
+            const int qd = warp & 3, grp = warp >> 2;
+            constexpr int QMAX = 3;   // column quads per thread (Mp <= 36)
+            const int n_sub = (P.R + TC_ROWS - 1) / TC_ROWS;
+            const uint32_t lboA = TC_ROWS * 16, lboB = (uint32_t)a.npad * 16;
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.npad >> 3) << 17) |
+                                   ((uint32_t)(TC_ROWS >> 4) << 24);
+            // operand A of the tile starting at row_lo: row tid % TC_ROWS, float4
+            // chunks c4 = tid / TC_ROWS + 3 j; chunk c4 holds complex columns 2cj,
+            // 2cj+1 of s_r rZ_s (c4 < Mp/2) or s_b bZ_s (c4 >= Mp/2)
+            auto build_a = [&](int row_lo) {
+              const int r = tid % TC_ROWS, l = row_lo + r;
+              const T2* srcr = nullptr;
+              const T2* srcb = nullptr;
+              float scr = 0.f, scb = 0.f;
               if (l < P.R) {
                 const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
-                const T2* src = nullptr;
-                float sc = 0.f;
-                if (jump == 0) {
-                  const int iro = three ? iff : P.r_lo + irl;
-                  if (iro + 1 < dro) {
-                    src = own(cur, l + 1);
-                    sc = sq[iro + 1];
-                  }
-                } else if (it + 1 < Nt) {
-                  src = own(cur, l + P.st);
-                  sc = sq[it + 1];
+                const int iro = three ? iff : P.r_lo + irl;
+                if (iro + 1 < dro) {
+                  srcr = own(cur, l + 1);
+                  scr = sq[iro + 1];
                 }
+                if (it + 1 < Nt) {
+                  srcb = own(cur, l + P.st);
+                  scb = sq[it + 1];
+                }
+              }
+              for (int c4 = tid / TC_ROWS; c4 < Mp; c4 += NT / TC_ROWS) {
+                const int jump = c4 >= Mp / 2 ? 1 : 0;
+                const int cj = c4 - jump * (Mp / 2);
+                const T2* src = jump ? srcb : srcr;
+                const float sc = jump ? scb : scr;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (src) {
                   v = reinterpret_cast<const float4*>(src)[cj];
                   v.x *= sc;
@@ -816,60 +827,213 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                   v.z *= sc;
                   v.w *= sc;
                 }
+                const int o = kmaj_off(r, 4 * c4, TC_ROWS) / 4;
+                const float4 big = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+                *reinterpret_cast<float4*>(ta_big + o) = big;
+                if (TC == 3)
+                  *reinterpret_cast<float4*>(ta_small + o) = make_float4(
+                      tf32_rna(v.x - big.x), tf32_rna(v.y - big.y), tf32_rna(v.z - big.z), tf32_rna(v.w - big.w));
               }
-              const int o = kmaj_off(r, 4 * c4, TC_ROWS) / 4;
-              const float4 big = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-              *reinterpret_cast<float4*>(ta_big + o) = big;
-              if (TC == 3)
-                *reinterpret_cast<float4*>(ta_small + o) = make_float4(
-                    tf32_rna(v.x - big.x), tf32_rna(v.y - big.y), tf32_rna(v.z - big.z), tf32_rna(v.w - big.w));
-            }
-            async_proxy_fence();
+              async_proxy_fence();
+            };
+            auto issue = [&]() {
+              if (tid == 0) {
+                tc_fence_after();
+                // K = 4 Mp in steps of 8; each pass and half of K accumulates in
+                // its own TMEM columns so that the MMA chains run side by side
+                const int nks = Mp / 2, half = (nks + 1) / 2;
+                for (int ks = 0; ks < nks; ++ks)
+                  for (int pass = 0; pass < TC; ++pass) {
+                    const uint32_t A0 = smem_u32(pass == 2 ? ta_small : ta_big);
+                    const uint32_t B0 = smem_u32(pass == 1 ? tb_small : tb_big);
+                    const int acc = pass * TC_KSPLIT + (ks >= half ? 1 : 0);
+                    tc_mma(tmem + (uint32_t)(acc * TC_ACC), tc_desc(A0 + ks * 2 * lboA, lboA, 128),
+                           tc_desc(B0 + ks * 2 * lboB, lboB, 128), idesc, ks != 0 && ks != half);
+                  }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                             : "memory");
+              }
+            };
+            build_a(0);
             __syncthreads();
-            if (tid == 0) {
+            issue();
+            for (int sub = 0; sub < n_sub; ++sub) {
+              const int l = sub * TC_ROWS + qd * 32 + lane;
+              const bool in = l < P.R;
+              int it = 0, irl = 0, iff = 0;
+              if (in) {
+                it = l / P.st;
+                const int rem = l - it * P.st;
+                irl = rem / Nf;
+                iff = rem - irl * Nf;
+              }
+              const int ir = P.r_lo + irl, iro = three ? iff : ir;
+              T fr[QMAX][4], fi[QMAX][4];
+              // -i H_eff Z_s for the thread's row and column quads
+              T dh = 0, dl = 0, dim_ = 0;
+              if (in) {
+                const T a0 = dtab[(0 * TAB + it) * 2], a1 = dtab[(1 * TAB + ir) * 2], a2 = dtab[(2 * TAB + iff) * 2];
+                T s1 = a0 + a1;
+                T bp = s1 - a0;
+                T er = (a0 - (s1 - bp)) + (a1 - bp);
+                T s2 = s1 + a2;
+                bp = s2 - s1;
+                er += (s1 - (s2 - bp)) + (a2 - bp);
+                dh = s2;
+                dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
+                dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
+              }
+#pragma unroll
+              for (int qq = 0; qq < QMAX; ++qq) {
+                const int m0 = (grp + 3 * qq) * 4;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) fr[qq][u] = fi[qq][u] = 0;
+                if (m0 >= Mp || !in) continue;
+                T2 z[4];
+                load4<ZSM>(own(cur, l) + m0, z);
+                T hr[4], hi[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
+                  hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
+                }
+                auto add_row = [&](const T2* vp, T w) {
+                  T2 v[4];
+                  load4<ZSM>(vp, v);
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    hr[u] = fma(w, v[u].x, hr[u]);
+                    hi[u] = fma(w, v[u].y, hi[u]);
+                  }
+                };
+                // g (b + b^dag)(a + a^dag)
+#pragma unroll
+                for (int sa = -1; sa <= 1; sa += 2) {
+                  const int it2 = it + sa;
+                  if (it2 < 0 || it2 >= Nt) continue;
+                  const T ct = g * sq[max(it, it2)];
+#pragma unroll
+                  for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
+                    const int ir2 = ir + sb2;
+                    if (ir2 < 0 || ir2 >= Nr) continue;
+                    add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
+                  }
+                }
+                if (three) {
+                  // J (a + a^dag)(f + f^dag)
+#pragma unroll
+                  for (int sa = -1; sa <= 1; sa += 2) {
+                    const int ir2 = ir + sa;
+                    if (ir2 < 0 || ir2 >= Nr) continue;
+                    const T cr = J * sq[max(ir, ir2)];
+#pragma unroll
+                    for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
+                      const int if2 = iff + sb2;
+                      if (if2 < 0 || if2 >= Nf) continue;
+                      add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
+                    }
+                  }
+                  // drive on the filter
+#pragma unroll
+                  for (int sa = -1; sa <= 1; sa += 2) {
+                    const int if2 = iff + sa;
+                    if (if2 < 0 || if2 >= Nf) continue;
+                    add_row(own(cur, l + sa) + m0, c * sq[max(iff, if2)]);
+                  }
+                } else {
+                  // drive on the resonator (two modes, C == 1)
+#pragma unroll
+                  for (int sa = -1; sa <= 1; sa += 2) {
+                    const int ir2 = ir + sa;
+                    if (ir2 < 0 || ir2 >= Nr) continue;
+                    add_row(own(cur, l + sa) + m0, c * sq[max(ir, ir2)]);
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  fr[qq][u] = hi[u];
+                  fi[qq][u] = -hr[u];
+                }
+              }
+              // + projection term D from tensor memory (lane = tile row)
+              volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
+              if (*tc_abort == 0 && !mbar_wait(mbar, tc_phase)) {
+                *tc_abort = 1;
+                set_error(a.p.err, DEV_TIMEOUT);
+              }
+              tc_phase ^= 1u;
               tc_fence_after();
-              const uint32_t lboA = TC_ROWS * 16, lboB = (uint32_t)a.npad * 16;
-              const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.npad >> 3) << 17) |
-                                     ((uint32_t)(TC_ROWS >> 4) << 24);
-              for (int pass = 0; pass < TC; ++pass) {
-                const uint32_t A0 = smem_u32(pass == 2 ? ta_small : ta_big);
-                const uint32_t B0 = smem_u32(pass == 1 ? tb_small : tb_big);
-                for (int ks = 0; ks < Mp / 2; ++ks)   // K = 4 Mp in steps of 8
-                  tc_mma(tmem, tc_desc(A0 + ks * 2 * lboA, lboA, 128), tc_desc(B0 + ks * 2 * lboB, lboB, 128), idesc,
-                         (pass | ks) != 0);
+#pragma unroll
+              for (int qq = 0; qq < QMAX; ++qq) {
+                const int quad = grp + 3 * qq;
+                if (quad * 4 >= Mp) continue;   // uniform across the warp
+                const int n_acc = Mp / 2 > 1 ? TC * TC_KSPLIT : TC;
+                float dsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int acc = 0; acc < n_acc; ++acc) {
+                  uint32_t v[8];
+                  asm volatile(
+                      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                      : "r"(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * TC_ACC + quad * 8)));
+                  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) dsum[u] += __uint_as_float(v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  fr[qq][u] += dsum[2 * u];
+                  fi[qq][u] += dsum[2 * u + 1];
+                }
               }
-              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                           : "memory");
-            }
-            // after a timeout (flag in misc[141]) the CTA stops waiting: the
-            // error word already reports the failure and the launch ends
-            volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
-            if (*tc_abort == 0 && !mbar_wait(mbar, tc_phase)) {
-              *tc_abort = 1;
-              set_error(a.p.err, DEV_TIMEOUT);
-            }
-            tc_phase ^= 1u;
-            tc_fence_after();
-            // D rows to shared memory: warp w reads TMEM lanes 32 (w % 4) + lane
-            {
-              const int qd = warp & 3, row = qd * 32 + lane;
-              for (int g8 = warp >> 2; g8 < a.npad / 8; g8 += NWARP / 4) {
-                uint32_t v[8];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                    : "r"(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(g8 * 8)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float4* dst = reinterpret_cast<float4*>(Ds + row * a.ldd + g8 * 8);
-                dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
-                                     __uint_as_float(v[3]));
-                dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]),
-                                     __uint_as_float(v[7]));
+              tc_fence_before();
+              __syncthreads();   // TMEM and operand A of this tile are free
+              if (sub + 1 < n_sub) {
+                build_a((sub + 1) * TC_ROWS);
+                __syncthreads();
+                issue();
+              }
+              // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
+              if (in) {
+                const int n = (it * Nr + ir) * Nf + iff;
+#pragma unroll
+                for (int qq = 0; qq < QMAX; ++qq) {
+                  const int m0 = (grp + 3 * qq) * 4;
+                  if (m0 >= Mp) continue;
+                  T2 zo[4];
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    const int m = m0 + u;
+                    if (m >= M) {
+                      zo[u] = cm<T2>(0, 0);
+                      continue;
+                    }
+                    const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
+                    const T2 zn = Zn[oz];
+                    if (stage == 0) {
+                      accg[oa] = cm<T2>(fr[qq][u], fi[qq][u]);
+                    } else if (stage < 3) {
+                      const T2 ac = accg[oa];
+                      accg[oa] = cm<T2>(fma((T)2, fr[qq][u], ac.x), fma((T)2, fi[qq][u], ac.y));
+                    }
+                    if (stage < 3) {
+                      zo[u] = cm<T2>(zn.x + fma(hs_lo, fr[qq][u], hs_hi * fr[qq][u]),
+                                     zn.y + fma(hs_lo, fi[qq][u], hs_hi * fi[qq][u]));
+                    } else {
+                      const T2 ac = accg[oa];
+                      const T s_r = ac.x + fr[qq][u], s_i = ac.y + fi[qq][u];
+                      const T2 z1 =
+                          cm<T2>(zn.x + fma(h6_lo, s_r, h6_hi * s_r), zn.y + fma(h6_lo, s_i, h6_hi * s_i));
+                      Zn[oz] = z1;
+                      zo[u] = z1;
+                    }
+                  }
+                  store4<ZSM>(own(nxt, l) + m0, zo);
+                }
               }
             }
-            tc_fence_before();
-            __syncthreads();
-          }
+          } else {
+          const int nrt = nrt_all;
+          const int row_lo = 0;
           for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
             T fr[TR][4], fi[TR][4];
@@ -992,20 +1156,6 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               }
             }
             // projection terms: + sr (rZ_s) XT_r + sb (bZ_s) XT_b
-            if constexpr (TC > 0) {
-              for (int r = 0; r < TR; ++r) {
-                const float4* dp = reinterpret_cast<const float4*>(Ds + (l0 + r - row_lo) * a.ldd + 2 * m0);
-                const float4 d0 = dp[0], d1 = dp[1];
-                fr[r][0] += d0.x;
-                fi[r][0] += d0.y;
-                fr[r][1] += d0.z;
-                fi[r][1] += d0.w;
-                fr[r][2] += d1.x;
-                fi[r][2] += d1.y;
-                fr[r][3] += d1.z;
-                fi[r][3] += d1.w;
-              }
-            }
             if constexpr (TC == 0) {
             for (int k = 0; k < M; ++k) {
               T2 xr[4], xb[4];
@@ -1061,7 +1211,6 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               store4<ZSM>(own(nxt, l0 + r) + m0, zo);
             }
           }
-          if constexpr (TC > 0) __syncthreads();   // D staging and operand tiles are reused by the next tile
           }
           cur = nxt;
           __syncthreads();
@@ -1088,7 +1237,7 @@ namespace {
 
 struct SmemLayout {
   int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop, o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
-  int o_ta, o_tb, o_td, npad, ldd, total;
+  int o_ta, o_tb, npad, total;
 };
 
 int al16(int x) { return (x + 15) / 16 * 16; }
@@ -1119,9 +1268,8 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
   o += al16(144 * (int)sizeof(double));
   L.o_tab = o;
   o += al16(fz::TAB * 7 * (int)(es / 2));
-  L.o_ta = L.o_tb = L.o_td = o;
+  L.o_ta = L.o_tb = o;
   L.npad = (2 * Mp + 15) / 16 * 16;
-  L.ldd = L.npad + 4;
   if (tc > 0) {
     const int nbuf = tc == 3 ? 2 : 1;   // big (and small) halves of the TF32 split
     const int K = 4 * Mp;
@@ -1130,13 +1278,6 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
     o += nbuf * fz::TC_ROWS * K * 4;
     L.o_tb = o;
     o += al128(nbuf * L.npad * K * 4);
-    // D staging reuses the A tile's big half when it fits there
-    if (L.ldd <= K) {
-      L.o_td = L.o_ta;
-    } else {
-      L.o_td = o;
-      o += al128(fz::TC_ROWS * L.ldd * 4);
-    }
   }
   L.total = o;
   return L;
@@ -1254,12 +1395,13 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
       const int used = std::min((n_traj + waves_needed - 1) / waves_needed, n_traj);
       // Cost model, fitted to measurements on GB300 (N = 2000, M = 20 batch):
       // a stage costs ~0.16 us per row per CTA with the stage state in shared
-      // memory (x1.3 in L2; x1.95 and x1.75 in L2 with the projection on the
-      // tensor cores in 3 and 1 passes: the 128-row tiles serialise operand
-      // staging, MMA and epilogue), plus a fixed ~60 us per team (the M x M
-      // phase and the cluster barrier, ~M sequential elimination steps) that
-      // does not shrink with C; teams run trajectories in waves.
-      const double row_cost = zs_smem ? 1.0 : (tc == 3 ? 1.95 : tc == 1 ? 1.75 : 1.3);
+      // memory (x1.3 in L2; x1.7 and x1.55 in L2 with the projection on the
+      // tensor cores in 3 and 1 passes: per 128-row tile the operand staging
+      // and two block barriers cost more than the FMAs they replace), plus a
+      // fixed ~60 us per team (the M x M phase and the cluster barrier, ~M
+      // sequential elimination steps) that does not shrink with C; teams run
+      // trajectories in waves.
+      const double row_cost = zs_smem ? 1.0 : (tc == 3 ? 1.7 : tc == 1 ? 1.55 : 1.3);
       const double waves = std::ceil((double)n_traj / used);
       double t = 0.0;
       for (const TrajDev& d : traj) {
@@ -1335,9 +1477,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.o_tab = L.o_tab;
   a.o_ta = L.o_ta;
   a.o_tb = L.o_tb;
-  a.o_td = L.o_td;
   a.npad = L.npad;
-  a.ldd = L.ldd;
   char* sc = static_cast<char*>(p.scratch);
   size_t off = ((sizeof(int) * rp.n_traj + 255) / 256) * 256;
   a.order = reinterpret_cast<const int*>(sc);
