@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=None, help="RK4 steps of the oracle sample")
     ap.add_argument("--no-plain-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=8, help="RK4 steps timed on the plain FP64 engine")
+    ap.add_argument("--frame", default="lab", choices=["lab", "rwa"],
+                    help="rwa: frame rotating at w_d with the rotating-wave approximation")
+    ap.add_argument("--dt", type=float, default=None, help="RK4 step [ns] (default: the workload's; 2.5e-3 with rwa)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the gradient (lr_backward) of a pulse slice of --chunk steps instead")
     return ap.parse_args()
@@ -70,7 +73,15 @@ def load_workload(args, rank=0):
         n = args.candidates if args.candidates is not None else li.workload(name).n_traj // 2
         kw["n_candidates"] = n
         kw["first"] = rank * n
-    return li.workload(name, **kw)
+    wl = li.workload(name, **kw)
+    frame = getattr(args, "frame", "lab")
+    dt = getattr(args, "dt", None) or (2.5e-3 if frame == "rwa" else None)
+    if frame != "lab" or dt:
+        import dataclasses
+        dt = dt or wl.dt
+        wl = dataclasses.replace(wl, name=wl.name + ("-" + frame if frame != "lab" else ""), frame=frame, dt=dt,
+                                 n_steps=int(round(wl.tau / dt)))
+    return wl
 
 
 def aggregate(ms_local, units_local, dist=None):
@@ -251,7 +262,7 @@ def run_ours(args):
     # of the candidate population, no data-path collective)
     cands = wl.candidates
     b = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision=prec, engine=args.engine,
-                     max_steps=spp, pop_every=max(1, chunk), eta=wl.eta, device=dev)
+                     max_steps=spp, pop_every=max(1, chunk), eta=wl.eta, device=dev, frame=wl.frame)
     b.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
     b.set_initial(wl.init_seed + 7919 * rank, wl.eps)   # replicas of single-candidate workloads differ by seed
     stream = torch.cuda.current_stream(dev)
@@ -331,7 +342,8 @@ def run_ours(args):
     plain = None
     if not args.no_plain_baseline and engine != "plain":
         bp = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision="fp64", engine="plain",
-                          max_steps=args.plain_steps + 1, pop_every=args.plain_steps, eta=wl.eta, device=dev)
+                          max_steps=args.plain_steps + 1, pop_every=args.plain_steps, eta=wl.eta, device=dev,
+                          frame=wl.frame)
         bp.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
         bp.set_initial(wl.init_seed, wl.eps)
         bp.integrate(wl.dt, 1)
@@ -359,7 +371,7 @@ def run_ours(args):
                "sample": "%d RK4 steps of the g and e trajectories of candidate 0 (%.1f s)" % (ns, dt_cpu)}
         # accuracy of this path on the same sample, against the FP64 oracle
         bq = LowRankBatch([cands[0].model], [cands[0].M], precision=prec, engine=args.engine, max_steps=ns,
-                          pop_every=ns, eta=wl.eta, device=dev)
+                          pop_every=ns, eta=wl.eta, device=dev, frame=wl.frame)
         bq.set_pulse([(cands[0].pulse.kind, cands[0].pulse.p)], wl.tau)
         bq.set_initial(wl.init_seed, wl.eps)
         bq.integrate(wl.dt, ns)

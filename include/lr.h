@@ -137,6 +137,16 @@ typedef struct {
   int record_gram;    /* 1: keep the FP64 Gram matrix Z^dag Z at every record step for
                          lr_diagnostics (the workspace grows by n_traj * n_rec *
                          (max_M^2 * 16 + max_M * 8 + 8) bytes); 0: off */
+  int frame;          /* 0: lab frame, H(t) as in lr_pulse (no rotating-wave approximation).
+                         1: frame rotating at each candidate's w_d with the rotating-wave
+                         approximation (the RWA Hamiltonian of Sec. S2): mode frequencies
+                         become detunings w - w_d, the couplings keep g (b^dag a + b a^dag)
+                         and J (a^dag f + a f^dag), and the drive is (Omega(t)/2)
+                         (e^{i phi} r + e^{-i phi} r^dag). The jump operators are unchanged.
+                         beta is then the rotating-frame signal, beta_lab e^{i w_d t}, so
+                         |beta_e - beta_g|, eps_a and all populations keep their meaning.
+                         A slow Hamiltonian allows a larger dt. lr_backward supports frame 0
+                         only. */
 } lr_options;
 
 typedef struct {

@@ -116,6 +116,7 @@ class Workload:
     eta: float = 0.6
     precision: str = "fp64"
     note: str = ""
+    frame: str = "lab"   # "rwa": frame rotating at w_d with the rotating-wave approximation
 
     @property
     def n_traj(self) -> int:

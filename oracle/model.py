@@ -19,9 +19,21 @@ L_2 = sqrt(gamma) b (transmon T1 decay).
 Basis: |i_t> (x) |i_r> [(x) |i_f>], flat index n = (i_t N_r + i_r) N_f + i_f,
 which is numpy's kron(transmon, kron(resonator, filter)) ordering.
 
+Rotating frame (``rwa=(w_d, phi)``): the RWA Hamiltonian of Sec. S2, for
+this model the frame rotating at w_d for every mode with the counter-rotating
+terms dropped:
+
+    H = (wq - w_d) b^dag b + (alpha/2) b^dag b^dag b b + (wr - w_d) a^dag a
+        + g (b^dag a + b a^dag) [+ (wf - w_d) f^dag f + J (a^dag f + a f^dag)]
+        + (Omega(t)/2) X_d,   X_d = e^{i phi} r + e^{-i phi} r^dag,
+
+with the same jump operators (the frame only adds phases to them).
+
 Parity: pinned by the closed-form tests (coherent-state amplitude of a
-driven damped resonator, exponential level decay, Schroedinger evolution
-against a matrix exponential).
+driven damped resonator in both frames, exponential level decay,
+Schroedinger evolution against a matrix exponential); the rotating-frame
+operators by their definitions as the excitation-conserving part of
+H - w_d N and the period average of the rotated drive.
 """
 from __future__ import annotations
 
@@ -50,7 +62,7 @@ class Model:
     """
 
     def __init__(self, dims, wq, alpha, wr, g, kappa, gamma, wf=0.0, J=0.0,
-                 dense=None):
+                 dense=None, rwa=None):
         dims = tuple(int(d) for d in dims)
         if len(dims) not in (2, 3):
             raise ValueError("dims must be (N_t, N_r) or (N_t, N_r, N_f)")
@@ -66,17 +78,29 @@ class Model:
         b = mode_op(0, annihilation(dims[0]))
         a = mode_op(1, annihilation(dims[1]))
         dag = lambda x: x.conj().T.tocsr()  # noqa: E731
-        H0 = (wq * (dag(b) @ b) + 0.5 * alpha * (dag(b) @ dag(b) @ b @ b)
-              + wr * (dag(a) @ a) + g * ((b + dag(b)) @ (a + dag(a))))
+        if rwa is None:
+            H0 = (wq * (dag(b) @ b) + 0.5 * alpha * (dag(b) @ dag(b) @ b @ b)
+                  + wr * (dag(a) @ a) + g * ((b + dag(b)) @ (a + dag(a))))
+        else:
+            wd, phi = float(rwa[0]), float(rwa[1])
+            H0 = ((wq - wd) * (dag(b) @ b) + 0.5 * alpha * (dag(b) @ dag(b) @ b @ b)
+                  + (wr - wd) * (dag(a) @ a) + g * (dag(b) @ a + b @ dag(a)))
         if len(dims) == 3:
             f = mode_op(2, annihilation(dims[2]))
-            H0 = H0 + wf * (dag(f) @ f) + J * ((a + dag(a)) @ (f + dag(f)))
+            if rwa is None:
+                H0 = H0 + wf * (dag(f) @ f) + J * ((a + dag(a)) @ (f + dag(f)))
+            else:
+                H0 = H0 + (wf - wd) * (dag(f) @ f) + J * (dag(a) @ f + a @ dag(f))
             r = f
         else:
             r = a
         self.b, self.a, self.r = b, a, r
         self.H0 = H0.tocsr()
-        self.Xd = (r + dag(r)).tocsr()
+        if rwa is None:
+            self.Xd = (r + dag(r)).tocsr()
+        else:
+            self.Xd = (np.exp(1j * phi) * r + np.exp(-1j * phi) * dag(r)).tocsr()
+        self.rwa = rwa
         self.jumps = [np.sqrt(kappa) * r, np.sqrt(gamma) * b]
         self.jumps_dag = [dag(L) for L in self.jumps]
         self.kappa, self.gamma = float(kappa), float(gamma)
@@ -95,9 +119,9 @@ class Model:
         self.dense = dense
 
     @classmethod
-    def from_params(cls, p, dense=None) -> "Model":
+    def from_params(cls, p, dense=None, rwa=None) -> "Model":
         return cls(p.dims, p.wq, p.alpha, p.wr, p.g, p.kappa, p.gamma,
-                   wf=p.wf, J=p.J, dense=dense)
+                   wf=p.wf, J=p.J, dense=dense, rwa=rwa)
 
     def hamiltonian(self, c: float):
         """H(t) for a given pulse coefficient c(t)."""

@@ -17,12 +17,16 @@ def _traj_task(args):
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from . import init_state, lowrank, pulse
     from .model import Model
-    cand, traj, level, n_steps, pop_every, dt, tau, seed, eps, gram = args
+    cand, traj, level, n_steps, pop_every, dt, tau, seed, eps, gram, frame = args
     p = cand.model
-    mdl = Model.from_params(p)
+    if frame == "rwa":
+        mdl = Model.from_params(p, rwa=pulse.drive_frequency_phase(cand.pulse.kind, cand.pulse.p))
+        coef = pulse.rwa_coefficient(cand.pulse.kind, cand.pulse.p, tau)
+    else:
+        mdl = Model.from_params(p)
+        coef = pulse.coefficient(cand.pulse.kind, cand.pulse.p, tau)
     psi = mdl.basis_index((level,) + (0,) * (len(p.dims) - 1))
     m0 = init_state.initial_state(mdl.N, cand.M, psi, eps, seed, traj)
-    coef = pulse.coefficient(cand.pulse.kind, cand.pulse.p, tau)
     return lowrank.integrate(m0, mdl, coef, dt, n_steps, pop_every, gram=gram)
 
 
@@ -34,7 +38,7 @@ def _tasks(wl, n_steps, pop_every, candidates, traj_base, gram=False):
         base = 2 * k if traj_base is None else traj_base[k]
         for lvl in (0, 1):
             tasks.append((wl.candidates[ci], base + lvl, lvl, ns, pop_every, wl.dt, wl.tau, wl.init_seed, wl.eps,
-                          gram))
+                          gram, getattr(wl, "frame", "lab")))
     return idx, tasks
 
 

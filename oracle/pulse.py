@@ -78,3 +78,16 @@ def coefficient(kind: int, p, tau: float):
         return envelope(kind, p, t, tau) * math.cos(wd * t + phi)
 
     return c
+
+
+def rwa_coefficient(kind: int, p, tau: float):
+    """Return Omega(t)/2 as a callable: in the frame rotating at w_d, with the
+    rotating-wave approximation, the drive Omega(t) cos(w_d t + phi)(r + r^dag)
+    becomes (Omega(t)/2)(e^{i phi} r + e^{-i phi} r^dag), whose operator part
+    is ``Model(..., rwa=(w_d, phi)).Xd``."""
+    p = tuple(float(x) for x in p)
+
+    def c(t: float) -> float:
+        return 0.5 * envelope(kind, p, t, tau)
+
+    return c

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict_
     const int n = (int)(idx / M), m = (int)(idx - (long)n * M);
     const RowIdx ri = row_index(d, n);
     double dre, dim_;
-    heff_diag(d, ri, dre, dim_);
+    heff_diag(d, ri, 0.0, dre, dim_);   // the adjoint runs in the lab frame
     const size_t o = off + (size_t)n * ld + m;
     const double2 f0 = F(o);
     // i H_eff^dag Fbar: diagonal i conj(h) = i dre + dim

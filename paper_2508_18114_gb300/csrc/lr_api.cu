@@ -90,6 +90,7 @@ RunParams run_params(const lr_ctx* c) {
   r.dt = c->dt;
   r.eta = c->opt.eta;
   r.snap_m = c->opt.record_gram ? c->max_M : 0;
+  r.frame = c->opt.frame;
   return r;
 }
 
@@ -123,6 +124,7 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   if (opt->engine != LR_ENGINE_AUTO && opt->engine != LR_ENGINE_PLAIN && opt->engine != LR_ENGINE_FUSED)
     return LR_ERR_ARG;
   if (opt->record_gram != 0 && opt->record_gram != 1) return LR_ERR_ARG;
+  if (opt->frame != 0 && opt->frame != 1) return LR_ERR_ARG;
   lr_ctx* c = new (std::nothrow) lr_ctx();
   if (!c) return LR_ERR_NOMEM;
   c->n_cand = n_cand;
@@ -177,7 +179,7 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   c->tot_elems = z_off;
   c->pulses.assign(n_cand, PulseDev{});
   // engine selection
-  const bool fused_ok = lr::fused_plan(c->traj, opt->precision, &c->fused);
+  const bool fused_ok = lr::fused_plan(c->traj, opt->precision, opt->frame, &c->fused);
   if (opt->engine == LR_ENGINE_FUSED && !fused_ok) {
     delete c;
     return LR_ERR_UNSUPPORTED;
@@ -468,6 +470,7 @@ lr_status lr_backward(lr_ctx* c, void* dev_ws, size_t ws_bytes, const double* d_
   if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
   if (!c->have_pulse || !c->z0_valid || c->step < 1 || !(c->dt > 0.0))
     return fail(c, LR_ERR_STATE, "lr_backward needs a pulse run integrated from step 0 of a kept initial state");
+  if (c->opt.frame != 0) return fail(c, LR_ERR_UNSUPPORTED, "lr_backward supports the lab frame only");
   for (int k = 0; k < c->n_cand; ++k)
     if (!std::isfinite(d_eps_a[k])) return fail(c, LR_ERR_ARG, "non-finite cotangent");
   size_t part = 0;

@@ -1,1235 +1,14 @@
-// FUSED engine: persistent cluster kernel integrating whole pulses.
-//
-// Per RK4 stage of Eq. S5, for one trajectory on a team of C CTAs:
-//   P  (local)  partial sums over the CTA's rows of the stage input Z_s:
-//               G = Z^dag Z (upper tiles), T_r = Z^dag r Z, T_b = Z^dag b Z
-//               (+ level populations and readout photons at recording steps);
-//   B1          one cluster barrier: partials and the new Z_s are visible;
-//   R  (every CTA, redundantly) reduce the C partial slots in rank order,
-//               Cholesky G = L L^dag, L^-1, G^-1 = L^-dag L^-1 (all FP64),
-//               X_k = G^-1 T_k (bulk precision), pre-scaled and conjugate-
-//               transposed: XT_r = kappa/2 X_r^dag, XT_b = gamma/2 X_b^dag;
-//   F  (local + DSMEM halo) F = -i H_eff Z_s + (rZ_s) XT_r + (bZ_s) XT_b and the
-//               RK4 stage update; the next stage input goes to the other Z_s
-//               buffer, the accumulator and Z_n are updated in L2.
-// Partial slots and Z_s buffers are double-buffered by stage parity, so the
-// single barrier per stage separates every write from the reads of it.
-//
-// Tensor-core projection (TC > 0, stage state in L2): the projection term of F
-// is a real GEMM per 128-row tile, D[l][2m+c] = sum_K A[l][K] B[2m+c][K] with
-// A[l] = (s_r rZ_s[l], s_b bZ_s[l]) as interleaved (re, im) floats (K = 4 Mp)
-// and B the real 2x2-block embedding of XT. It runs as tcgen05.mma kind::tf32
-// with both operands in shared memory (K-major, no swizzle) and D in tensor
-// memory: 3 passes (big*big + big*small + small*big of a two-term TF32 split,
-// FP32-class products) or 1 pass (plain TF32).
-#include <cooperative_groups.h>
-
+// FUSED engine, host side: launch planning (variants, team size, cost
+// model), workspace layout and launches. The kernel is in lr_fused_kernel.cuh;
+// its rotating-frame instantiations are compiled in lr_fused_rwa.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 
-#include "lr_fused.cuh"
-
-namespace cg = cooperative_groups;
+#include "lr_fused_kernel.cuh"
 
 namespace lr {
-namespace fz {
-
-constexpr int NT = 384;
-constexpr int NWARP = NT / 32;
-constexpr int TAB = 64;   // mode truncations handled by the fused engine: N_t, N_r, N_f < 64
-
-struct Args {
-  DevPtrs p;
-  RunParams rp;
-  long step0, n_steps;
-  int C, n_clusters, Mp, R, Nmax;
-  int zs_smem;
-  // byte offsets in dynamic shared memory
-  int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop;   // s_*: offsets inside one slot
-  int o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
-  int o_ta, o_tb, npad;   // tensor-core operand tiles (TC > 0), B rows (2 Mp padded to 16)
-  const int* order;
-  void* zs_glob;      // global stage buffers, per cluster [C][2][R][Mp+1]
-  void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
-};
-
-// ----------------------------------------------------------------- complex
-
-template <typename T2> struct Real;
-template <> struct Real<float2> { using t = float; };
-template <> struct Real<double2> { using t = double; };
-
-template <typename T2> __device__ __forceinline__ T2 cm(typename Real<T2>::t r, typename Real<T2>::t i) {
-  T2 v;
-  v.x = r;
-  v.y = i;
-  return v;
-}
-
-// ----------------------------------------------------------------- partition
-
-struct Part {
-  int r_lo, nr, st, R;
-};
-
-__device__ __forceinline__ Part part_of(const TrajDev& d, int C, int q) {
-  Part P;
-  const int base = d.Nr / C, rem = d.Nr % C;
-  P.r_lo = q * base + min(q, rem);
-  P.nr = base + (q < rem ? 1 : 0);
-  P.st = P.nr * d.Nf;
-  P.R = d.Nt * P.st;
-  return P;
-}
-
-// ----------------------------------------------------------------- double-word accumulation
-// Exact FP32 products (p + e = a*b via FMA) accumulated in an unevaluated
-// sum of two floats (hi + lo): ~2^-48 relative, the FP64-class Gram matrix.
-struct DW {
-  float hi, lo;
-};
-__device__ __forceinline__ void dw_add_prod(DW& s, float a, float b) {
-  const float p = a * b;
-  const float e = fmaf(a, b, -p);
-  const float t = s.hi + p;
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (p - bp);
-  s.hi = t;
-  s.lo += err + e;
-}
-__device__ __forceinline__ void dw_add(DW& s, const DW& o) {
-  const float t = s.hi + o.hi;
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (o.hi - bp);
-  s.hi = t;
-  s.lo += err + o.lo;
-}
-__device__ __forceinline__ double dw_value(const DW& s) { return (double)s.hi + (double)s.lo; }
-
-// ----------------------------------------------------------------- the kernel
-
-// Vector load of 4 consecutive complex values (16-byte loads when the row
-// stride keeps them aligned: the L2-resident layout).
-template <int ZSM, typename T2>
-__device__ __forceinline__ void load4(const T2* p, T2 (&v)[4]) {
-  if constexpr (ZSM == 0 && sizeof(T2) == 8) {
-    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
-    v[0] = cm<T2>(x.x, x.y);
-    v[1] = cm<T2>(x.z, x.w);
-    v[2] = cm<T2>(y.x, y.y);
-    v[3] = cm<T2>(y.z, y.w);
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = p[u];
-  }
-}
-template <int ZSM, typename T2>
-__device__ __forceinline__ void store4(T2* p, const T2 (&v)[4]) {
-  if constexpr (ZSM == 0 && sizeof(T2) == 8) {
-    reinterpret_cast<float4*>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
-  } else {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) p[u] = v[u];
-  }
-}
-
-// ----------------------------------------------------------------- tcgen05 helpers
-// Operand tiles are K-major without swizzle: 8-row x 16-byte core matrices,
-// rows of a core 16 bytes apart, cores of consecutive 8-row groups 128 bytes
-// apart (stride offset) and cores consecutive in K rows*16 bytes apart
-// (leading offset).
-constexpr int TC_ROWS = 128;   // MMA M (rows of Z_s per tile), one TMEM lane per row
-constexpr int TC_ACC = 64;     // TMEM columns per accumulator (N = 2 Mp padded to 16 <= 64)
-constexpr int TC_KSPLIT = 2;   // independent accumulators per pass (halves of K)
-constexpr int TC_COLS = 512;   // TMEM columns allocated: up to 3 passes x TC_KSPLIT accumulators
-
-__device__ __forceinline__ int kmaj_off(int row, int k, int rows) {
-  return (k >> 2) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4;
-}
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | (uint64_t)((lbo >> 4) & 0x3FFF) << 16 |
-         (uint64_t)((sbo >> 4) & 0x3FFF) << 32 | (uint64_t)1 << 46;
-}
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// wait (at most ~1 s of SM clock) for the phase with the given parity;
-// false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const long long t0 = clock64();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > 2000000000LL) return false;
-  }
-}
-
-template <typename T2, int GRAM_DW, int ZSM, int TC>
-__global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
-  static_assert(TC == 0 || (ZSM == 0 && sizeof(T2) == 8), "tensor-core projection: FP32 state in L2 only");
-  using T = typename Real<T2>::t;
-  constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
-  constexpr int TR = sizeof(T) == 4 ? 4 : 2;     // phase-F rows per thread tile
-  extern __shared__ __align__(16) unsigned char smem[];
-  cg::cluster_group cluster = cg::this_cluster();
-  const int C = a.C;
-  const int q = (int)cluster.block_rank();
-  const int cid = blockIdx.x / C;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int Mp = a.Mp;
-  // row stride of Z_s: odd in complex elements in shared memory, so lanes that
-  // read consecutive rows hit distinct banks; 32-byte aligned rows in L2 for
-  // 16-byte vector loads
-  const int lds = ZSM ? Mp + 1 : Mp;
-  const long long zs_buf = (long long)a.R * lds;  // elements per smem Z_s buffer
-
-  double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);     // [Mp][Mp+1]  G -> L -> G^-1
-  double2* W = reinterpret_cast<double2*>(smem + a.o_w);       // [Mp][Mp+1]  L^-1
-  T2* Tred = reinterpret_cast<T2*>(smem + a.o_tred);           // [2][Mp*Mp]
-  double* trd = reinterpret_cast<double*>(smem + a.o_trd);     // [Mp] diag of T_r (FP64)
-  T2* XT = reinterpret_cast<T2*>(smem + a.o_xs);               // [2][Mp][Mp] (l, m)
-  // misc (FP64 scalars): [0] pulse coefficient, [1] not-PD flag, [8..24) photon
-  // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
-  // photons, [96..128) 1/L[k][k], [128..131) bulk-precision coefficient and
-  // steps, [140] phase-P task counter, [141] tensor-core timeout flag, [142]
-  // tensor-core mbarrier, [143] TMEM base address
-  double* misc = reinterpret_cast<double*>(smem + a.o_misc);
-  // row-ordered lower-triangle index table: entry e = i(i+1)/2 + j -> (i, j)
-  __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
-  for (int i = tid; i < LR_MAX_RANK; i += NT)
-    for (int j = 0; j <= i; ++j) tri[i * (i + 1) / 2 + j] = make_short2((short)i, (short)j);
-  T* sq = reinterpret_cast<T*>(smem + a.o_tab);                 // sqrt(k), k < TAB
-  T* dtab = sq + TAB;                                           // [3][TAB][2]: diagonal energies (hi, lo)
-  const int ldg = Mp + 1;
-
-  // Stage buffers: in shared memory, or (when they do not fit) in a global
-  // scratch region with the same per-CTA layout [C][2][R][lds] that stays L2
-  // resident; both are addressed by local row.
-  T2* zs_local = a.zs_smem ? reinterpret_cast<T2*>(smem + a.o_zs)
-                           : reinterpret_cast<T2*>(a.zs_glob) + ((size_t)cid * C + q) * 2 * zs_buf;
-  T2* accg = reinterpret_cast<T2*>(a.acc_glob) + (size_t)cid * a.Nmax * Mp;
-
-  const double dt = a.rp.dt;
-  const int pe = a.rp.pop_every;
-
-  // ---- tensor-core projection: operand tiles, D staging, TMEM and its mbarrier
-  float* ta_big = reinterpret_cast<float*>(smem + a.o_ta);
-  float* ta_small = ta_big + TC_ROWS * 4 * Mp;
-  float* tb_big = reinterpret_cast<float*>(smem + a.o_tb);
-  float* tb_small = tb_big + a.npad * 4 * Mp;
-  const uint32_t mbar = smem_u32(misc + 142);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 143);
-  uint32_t tmem = 0, tc_phase = 0;
-  if constexpr (TC > 0) {
-    // B rows beyond 2 Mp stay zero for the whole launch
-    for (int e = tid; e < (a.npad - 2 * Mp) * 4 * Mp; e += NT) {
-      const int n = 2 * Mp + e / (4 * Mp), k = e % (4 * Mp);
-      tb_big[kmaj_off(n, k, a.npad) / 4] = 0.0f;
-      if (TC == 3) tb_small[kmaj_off(n, k, a.npad) / 4] = 0.0f;
-    }
-    if (tid == 0) {
-      *reinterpret_cast<int*>(misc + 141) = 0;
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                   "r"(TC_COLS));
-      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    async_proxy_fence();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    tmem = *tslot;
-  }
-
-  for (int it_idx = cid; it_idx < a.rp.n_traj; it_idx += a.n_clusters) {
-    const int tj = a.order[it_idx];
-    const TrajDev d = a.p.traj[tj];
-    const int M = d.M;
-    const Part P = part_of(d, C, q);
-    const Part Pm = part_of(d, C, q > 0 ? q - 1 : q);
-    const Part Pp = part_of(d, C, q < C - 1 ? q + 1 : q);
-    const int Nf = d.Nf, Nr = d.Nr, Nt = d.Nt;
-    const bool three = d.n_modes == 3;
-    const int dro = three ? Nf : Nr;
-    T2* Zn = reinterpret_cast<T2*>(a.p.Zn) + d.z_off;
-    const PulseDev pulse = a.p.pulse[d.cand];
-    // Z_s bases of the neighbouring ranks (DSMEM or the neighbours' global regions)
-    T2* zs_m = zs_local;
-    T2* zs_p = zs_local;
-    if (a.zs_smem) {
-      zs_m = cluster.map_shared_rank(zs_local, q > 0 ? q - 1 : q);
-      zs_p = cluster.map_shared_rank(zs_local, q < C - 1 ? q + 1 : q);
-    } else {
-      zs_m = zs_local - (q > 0 ? 2 * zs_buf : 0);
-      zs_p = zs_local + (q < C - 1 ? 2 * zs_buf : 0);
-    }
-
-    // pointer to the start of row (it, ir, iff) of Z_s buffer b (any owner)
-    auto zrow = [&](int b, int it2, int ir2, int iff2) -> const T2* {
-      if (ir2 < P.r_lo) {
-        const int l = (it2 * Pm.nr + (ir2 - Pm.r_lo)) * Nf + iff2;
-        return zs_m + (size_t)b * zs_buf + (size_t)l * lds;
-      }
-      if (ir2 >= P.r_lo + P.nr) {
-        const int l = (it2 * Pp.nr + (ir2 - Pp.r_lo)) * Nf + iff2;
-        return zs_p + (size_t)b * zs_buf + (size_t)l * lds;
-      }
-      const int l = (it2 * P.nr + (ir2 - P.r_lo)) * Nf + iff2;
-      return zs_local + (size_t)b * zs_buf + (size_t)l * lds;
-    };
-    // own row l of buffer b (writable)
-    auto own = [&](int b, int l) -> T2* { return zs_local + (size_t)b * zs_buf + (size_t)l * lds; };
-    // global row of local row l
-    auto grow = [&](int l) {
-      const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
-      return (it * Nr + P.r_lo + irl) * Nf + iff;
-    };
-
-    // ---- per-trajectory tables: sqrt(k) and the separable diagonal of H,
-    //      wq i_t + alpha/2 i_t(i_t-1) | wr i_r | wf i_f, each as hi + lo so that
-    //      the bulk precision does not round the mode frequencies
-    for (int k = tid; k < TAB; k += NT) {
-      sq[k] = (T)sqrt((double)k);
-      const double v[3] = {d.wq * k + 0.5 * d.alpha * k * (k - 1.0), d.wr * k, three ? d.wf * k : 0.0};
-      for (int c3 = 0; c3 < 3; ++c3) {
-        const T hi = (T)v[c3];
-        dtab[(c3 * TAB + k) * 2] = hi;
-        dtab[(c3 * TAB + k) * 2 + 1] = (T)(v[c3] - (double)hi);
-      }
-    }
-    if (tid == 0) *reinterpret_cast<int*>(misc + 140) = 0;
-    // ---- load Z_n into Z_s buffer 0 (own rows), zero the rank padding
-    for (int e = tid; e < P.R * Mp; e += NT) {
-      const int l = e / Mp, m = e - l * Mp;
-      own(0, l)[m] = m < M ? Zn[(size_t)grow(l) * M + m] : cm<T2>(0, 0);
-    }
-    __syncthreads();
-
-    int cur = 0;
-    const long s_end = a.step0 + a.n_steps;
-    for (long step = a.step0;; ++step) {
-      const bool last = step == s_end;
-      for (int stage = 0; stage < 4; ++stage) {
-        const int par = stage & 1;
-        const bool record = stage == 0 && (step % pe) == 0;
-        unsigned char* slot = smem + a.o_slot + par * a.slot_bytes;
-        double2* gp = reinterpret_cast<double2*>(slot + a.s_gp);
-        T2* tp = reinterpret_cast<T2*>(slot + a.s_tp);
-        double* popp = reinterpret_cast<double*>(slot + a.s_pop);
-
-        // ================= P: partial sums over own rows of Z_s[cur]
-        {
-          const int nt_ = Mp / TP;
-          const int n_g = nt_ * (nt_ + 1) / 2, n_t = nt_ * nt_;
-          // warps take tasks dynamically (heavier Gram tiles first); every task's
-          // arithmetic is independent of which warp runs it, so results stay bitwise
-          // reproducible
-          int* task_ctr = reinterpret_cast<int*>(misc + 140);
-          for (;;) {
-            int task = 0;
-            if (lane == 0) task = atomicAdd(task_ctr, 1);
-            task = __shfl_sync(0xffffffffu, task, 0);
-            if (task >= n_g + n_t) break;
-            if (task < n_g) {
-              // upper tile (ti <= tj) of G
-              int ti = 0, rem = task;
-              while (rem >= nt_ - ti) { rem -= nt_ - ti; ++ti; }
-              const int tj2 = ti + rem;
-              const int i0 = ti * TP, j0 = tj2 * TP;
-              if constexpr (GRAM_DW) {
-                DW acc[TP][TP][2];
-#pragma unroll
-                for (int i = 0; i < TP; ++i)
-#pragma unroll
-                  for (int j = 0; j < TP; ++j) acc[i][j][0] = acc[i][j][1] = DW{0.f, 0.f};
-                for (int l = lane; l < P.R; l += 32) {
-                  const T2* z = own(cur, l);
-                  T2 zi[TP], zj[TP];
-                  if constexpr (TP == 4) {
-                    load4<ZSM>(z + i0, zi);
-                    load4<ZSM>(z + j0, zj);
-                  } else {
-#pragma unroll
-                    for (int i = 0; i < TP; ++i) zi[i] = z[i0 + i];
-#pragma unroll
-                    for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
-                  }
-                  if (ti == tj2) {
-                    // diagonal tile: only the upper triangle is needed
-#pragma unroll
-                    for (int i = 0; i < TP; ++i)
-#pragma unroll
-                      for (int j = i; j < TP; ++j) {   // conj(zi) * zj
-                        dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
-                        dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
-                        dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
-                        dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
-                      }
-                  } else {
-#pragma unroll
-                    for (int i = 0; i < TP; ++i)
-#pragma unroll
-                      for (int j = 0; j < TP; ++j) {   // conj(zi) * zj
-                        dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
-                        dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
-                        dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
-                        dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
-                      }
-                  }
-                }
-#pragma unroll
-                for (int i = 0; i < TP; ++i)
-#pragma unroll
-                  for (int j = 0; j < TP; ++j)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                      for (int o = 16; o > 0; o >>= 1) {
-                        DW t;
-                        t.hi = __shfl_xor_sync(0xffffffffu, acc[i][j][c].hi, o);
-                        t.lo = __shfl_xor_sync(0xffffffffu, acc[i][j][c].lo, o);
-                        dw_add(acc[i][j][c], t);
-                      }
-                if (lane == 0)
-#pragma unroll
-                  for (int i = 0; i < TP; ++i)
-#pragma unroll
-                    for (int j = 0; j < TP; ++j)
-                      gp[(i0 + i) * Mp + j0 + j] = mk(dw_value(acc[i][j][0]), dw_value(acc[i][j][1]));
-              } else {
-                T gr[TP][TP], gi[TP][TP];
-#pragma unroll
-                for (int i = 0; i < TP; ++i)
-#pragma unroll
-                  for (int j = 0; j < TP; ++j) gr[i][j] = gi[i][j] = 0;
-                for (int l = lane; l < P.R; l += 32) {
-                  const T2* z = own(cur, l);
-                  T2 zi[TP], zj[TP];
-#pragma unroll
-                  for (int i = 0; i < TP; ++i) zi[i] = z[i0 + i];
-#pragma unroll
-                  for (int j = 0; j < TP; ++j) zj[j] = z[j0 + j];
-#pragma unroll
-                  for (int i = 0; i < TP; ++i)
-#pragma unroll
-                    for (int j = 0; j < TP; ++j) {
-                      gr[i][j] = fma(zi[i].x, zj[j].x, fma(zi[i].y, zj[j].y, gr[i][j]));
-                      gi[i][j] = fma(zi[i].x, zj[j].y, fma(-zi[i].y, zj[j].x, gi[i][j]));
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < TP; ++i)
-#pragma unroll
-                  for (int j = 0; j < TP; ++j)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                      gr[i][j] += __shfl_xor_sync(0xffffffffu, gr[i][j], o);
-                      gi[i][j] += __shfl_xor_sync(0xffffffffu, gi[i][j], o);
-                    }
-                if (lane == 0)
-#pragma unroll
-                  for (int i = 0; i < TP; ++i)
-#pragma unroll
-                    for (int j = 0; j < TP; ++j) gp[(i0 + i) * Mp + j0 + j] = mk((double)gr[i][j], (double)gi[i][j]);
-              }
-            } else {
-              // tile of T_r and T_b
-              const int t2 = task - n_g, ti = t2 / nt_, tj2 = t2 - ti * nt_;
-              const int i0 = ti * TP, j0 = tj2 * TP;
-              T rr[TP][TP], ri[TP][TP], br[TP][TP], bi[TP][TP];
-#pragma unroll
-              for (int i = 0; i < TP; ++i)
-#pragma unroll
-                for (int j = 0; j < TP; ++j) rr[i][j] = ri[i][j] = br[i][j] = bi[i][j] = 0;
-              // mode indices of row l, advanced by 32 rows per iteration without divisions
-              int it = lane / P.st, irl = (lane - it * P.st) / Nf, iff = lane - it * P.st - irl * Nf;
-              const int dq = 32 / Nf, dr = 32 - dq * Nf;
-              for (int l = lane; l < P.R; l += 32) {
-                const int iro = three ? iff : irl;     // with two modes C == 1 and r_lo == 0
-                const T sr = iro + 1 < dro ? sq[iro + 1] : (T)0;
-                const T sb = it + 1 < Nt ? sq[it + 1] : (T)0;
-                const T2* z = own(cur, l);
-                const T2* zr = own(cur, iro + 1 < dro ? l + 1 : l);
-                const T2* zb = own(cur, it + 1 < Nt ? l + P.st : l);
-                T2 wr[TP], wb[TP], yr[TP], yb[TP], zz[TP];
-                if constexpr (TP == 4) {
-                  load4<ZSM>(z + i0, zz);
-                  load4<ZSM>(zr + j0, yr);
-                  load4<ZSM>(zb + j0, yb);
-                } else {
-#pragma unroll
-                  for (int i = 0; i < TP; ++i) zz[i] = z[i0 + i];
-#pragma unroll
-                  for (int j = 0; j < TP; ++j) {
-                    yr[j] = zr[j0 + j];
-                    yb[j] = zb[j0 + j];
-                  }
-                }
-#pragma unroll
-                for (int i = 0; i < TP; ++i) {
-                  wr[i] = cm<T2>(sr * zz[i].x, -sr * zz[i].y);   // sr conj(z_i)
-                  wb[i] = cm<T2>(sb * zz[i].x, -sb * zz[i].y);
-                }
-#pragma unroll
-                for (int i = 0; i < TP; ++i)
-#pragma unroll
-                  for (int j = 0; j < TP; ++j) {
-                    rr[i][j] = fma(wr[i].x, yr[j].x, fma(-wr[i].y, yr[j].y, rr[i][j]));
-                    ri[i][j] = fma(wr[i].x, yr[j].y, fma(wr[i].y, yr[j].x, ri[i][j]));
-                    br[i][j] = fma(wb[i].x, yb[j].x, fma(-wb[i].y, yb[j].y, br[i][j]));
-                    bi[i][j] = fma(wb[i].x, yb[j].y, fma(wb[i].y, yb[j].x, bi[i][j]));
-                  }
-                iff += dr;
-                irl += dq;
-                if (iff >= Nf) {
-                  iff -= Nf;
-                  ++irl;
-                }
-                while (irl >= P.nr) {
-                  irl -= P.nr;
-                  ++it;
-                }
-              }
-#pragma unroll
-              for (int i = 0; i < TP; ++i)
-#pragma unroll
-                for (int j = 0; j < TP; ++j)
-#pragma unroll
-                  for (int o = 16; o > 0; o >>= 1) {
-                    rr[i][j] += __shfl_xor_sync(0xffffffffu, rr[i][j], o);
-                    ri[i][j] += __shfl_xor_sync(0xffffffffu, ri[i][j], o);
-                    br[i][j] += __shfl_xor_sync(0xffffffffu, br[i][j], o);
-                    bi[i][j] += __shfl_xor_sync(0xffffffffu, bi[i][j], o);
-                  }
-              if (lane == 0)
-#pragma unroll
-                for (int i = 0; i < TP; ++i)
-#pragma unroll
-                  for (int j = 0; j < TP; ++j) {
-                    tp[(i0 + i) * Mp + j0 + j] = cm<T2>(rr[i][j], ri[i][j]);
-                    tp[Mp * Mp + (i0 + i) * Mp + j0 + j] = cm<T2>(br[i][j], bi[i][j]);
-                  }
-            }
-          }
-          if (record) {
-            // level populations and readout photons of own rows (FP64)
-            for (int lv = warp; lv < Nt; lv += NWARP) {
-              double s = 0.0, ph = 0.0;
-              for (int r = lane; r < P.st; r += 32) {
-                const int l = lv * P.st + r;
-                const int irl = r / Nf, iff = r - irl * Nf;
-                const int iro = three ? iff : irl;
-                const T2* z = own(cur, l);
-                double w = 0.0;
-                for (int m = 0; m < M; ++m) w += (double)z[m].x * z[m].x + (double)z[m].y * z[m].y;
-                s += w;
-                ph += iro * w;
-              }
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) {
-                s += __shfl_xor_sync(0xffffffffu, s, o);
-                ph += __shfl_xor_sync(0xffffffffu, ph, o);
-              }
-              if (lane == 0) {
-                popp[lv] = s;
-                misc[8 + lv] = ph;
-              }
-            }
-            __syncthreads();
-            if (tid == 0) {
-              double ph = 0.0;
-              for (int lv = 0; lv < Nt; ++lv) ph += misc[8 + lv];
-              popp[LR_MAX_NT] = ph;
-            }
-          }
-        }
-        // ================= B1
-        cluster.sync();
-
-        // ================= R: reduce in rank order, FP64 Cholesky and inverse
-        {
-          const int MM = Mp * Mp;
-          for (int e = tid; e < 3 * MM; e += NT) {
-            const int mat = e / MM, ij = e - mat * MM, i = ij / Mp, j = ij - i * Mp;
-            if (mat == 0) {
-              if (i > j || j >= M) continue;
-              // issue the remote loads four at a time, then sum in rank order
-              double re = 0.0, im = 0.0;
-              for (int r0 = 0; r0 < C; r0 += 4) {
-                double2 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  v[u] = r0 + u < C ? cluster.map_shared_rank(gp, r0 + u)[i * Mp + j] : mk(0.0, 0.0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  re += v[u].x;
-                  im += v[u].y;
-                }
-              }
-              if (i == j) {
-                Gd[i * ldg + i] = mk(re, 0.0);
-              } else {
-                Gd[i * ldg + j] = mk(re, im);
-                Gd[j * ldg + i] = mk(re, -im);
-              }
-            } else {
-              T re = 0, im = 0;
-              for (int r0 = 0; r0 < C; r0 += 4) {
-                T2 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  v[u] = r0 + u < C ? cluster.map_shared_rank(tp, r0 + u)[(mat - 1) * MM + ij] : cm<T2>(0, 0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  re += v[u].x;
-                  im += v[u].y;
-                }
-              }
-              Tred[(mat - 1) * MM + ij] = cm<T2>(re, im);
-              if (mat == 1 && i == j) {
-                trd[i] = (double)re;
-                misc[32 + i] = (double)im;
-              }
-            }
-          }
-          if (record && tid < LR_MAX_NT + 1) {
-            double s = 0.0;
-            const bool use = tid < Nt || tid == LR_MAX_NT;
-            if (use)
-              for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(popp, r)[tid];
-            misc[64 + tid] = s;
-          }
-          if (tid == 0) {
-            const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
-            misc[0] = pulse_coefficient(pulse, a.rp.tau, ts);
-            misc[1] = 0.0;   // not-PD flag
-            *reinterpret_cast<int*>(misc + 140) = 0;   // phase-P task counter of the next stage
-            // bulk-precision copies: coefficient, step sizes split as hi + lo
-            T* tb = reinterpret_cast<T*>(misc + 128);
-            const double hs = stage == 2 ? dt : 0.5 * dt, h6 = dt / 6.0;
-            tb[0] = (T)misc[0];
-            tb[1] = (T)hs;
-            tb[2] = (T)(hs - (double)tb[1]);
-            tb[3] = (T)h6;
-            tb[4] = (T)(h6 - (double)tb[3]);
-          }
-          __syncthreads();
-          if (record && q == 0 && a.p.gsnap) {
-            // FP64 Gram matrix of this record step, for the diagnostics
-            double2* gs = a.p.gsnap + ((size_t)tj * a.rp.n_rec + step / pe) * a.rp.snap_m * a.rp.snap_m;
-            for (int e = tid; e < M * M; e += NT) gs[(e / M) * a.rp.snap_m + e % M] = Gd[(e / M) * ldg + e % M];
-          }
-          if (stage == 0 && q == 0 && tid == 0) {
-            double br = 0.0, bi = 0.0;
-            for (int i = 0; i < M; ++i) {
-              br += trd[i];
-              bi += misc[32 + i];
-            }
-            a.p.beta[(size_t)tj * (a.rp.max_steps + 1) + step] = mk(br, bi);
-            if (!isfinite(br) || !isfinite(bi)) set_error(a.p.err, DEV_NONFINITE);
-            if (record) {
-              const long rec = step / pe;
-              double trace = 0.0;
-              for (int lv = 0; lv < a.rp.nt_max; ++lv) {
-                const double v = lv < Nt ? misc[64 + lv] : 0.0;
-                a.p.pops[((size_t)tj * a.rp.n_rec + rec) * a.rp.nt_max + lv] = v;
-                trace += v;
-              }
-              a.p.nphot[(size_t)tj * a.rp.n_rec + rec] = misc[64 + LR_MAX_NT];
-              a.p.trace[(size_t)tj * a.rp.n_rec + rec] = trace;
-            }
-          }
-          if (last) break;
-          // FP64 G = L D L^dag (unit lower L, right-looking, in place in Gd), then
-          // W = L^-1 (unit lower) and G^-1 = W^dag D^-1 W. One FP64 reciprocal per
-          // pivot (formed once and shared: FP64 runs at 2 FMA/clk/SM here) and two
-          // block barriers per elimination step.
-          double* dinv = misc + 96;     // [M] 1 / D[k]
-          // keep the diagonal of G: a pivot below 1e-13 of it is a numerical breakdown
-          for (int k = tid; k < M; k += NT) W[k * ldg] = Gd[k * ldg + k];
-          __syncthreads();
-          for (int k = 0; k < M; ++k) {
-            if (tid == 0) {
-              const double piv = Gd[k * ldg + k].x;
-              if (!(piv > 1e-13 * W[k * ldg].x) || !isfinite(piv) || piv < 1e-30) {
-                misc[1] = 1.0;
-                dinv[k] = 1.0;
-              } else {
-                // reciprocal by Newton-Raphson, r <- r (2 - piv r), from the FP32
-                // estimate: 24 -> 48 -> 96 correct bits, two FP64 FMA pairs on the
-                // serial path instead of a full FP64 division
-                double r = (double)(1.0f / (float)piv);
-                r = r * fma(-piv, r, 2.0);
-                r = r * fma(-piv, r, 2.0);
-                dinv[k] = r;
-              }
-            }
-            __syncthreads();
-            const double rk = dinv[k];
-            const int w = M - k - 1;
-            // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k
-            for (int e = tid; e < w * (w + 1) / 2; e += NT) {
-              const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
-              const double2 x = Gd[i * ldg + k], y = Gd[j * ldg + k], g = Gd[i * ldg + j];
-              Gd[i * ldg + j] = mk(g.x - rk * (x.x * y.x + x.y * y.y), g.y - rk * (x.y * y.x - x.x * y.y));
-            }
-            __syncthreads();
-          }
-          if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
-          // unit lower L[i][k] = G[i][k] / D[k]; W = L^-1 row by row (unit diagonal)
-          for (int e = tid; e < M * M; e += NT) {
-            const int i = e / M, j = e - i * M;
-            W[i * ldg + j] = mk(i == j ? 1.0 : 0.0, 0.0);
-            if (i > j) {
-              const double2 v = Gd[i * ldg + j];
-              Gd[i * ldg + j] = mk(v.x * dinv[j], v.y * dinv[j]);
-            }
-          }
-          __syncthreads();
-          for (int k = 0; k < M - 1; ++k) {
-            // rows i > k: W[i][j] -= L[i][k] W[k][j], j <= k (W[k] is final)
-            const int rows = M - k - 1;
-            for (int e = tid; e < rows * (k + 1); e += NT) {
-              const int i = k + 1 + e / (k + 1), j = e % (k + 1);
-              const double2 l = Gd[i * ldg + k], wv = W[k * ldg + j], o = W[i * ldg + j];
-              W[i * ldg + j] = mk(o.x - (l.x * wv.x - l.y * wv.y), o.y - (l.x * wv.y + l.y * wv.x));
-            }
-            __syncthreads();
-          }
-          // G^-1 = W^dag D^-1 W (Hermitian), rounded once to the bulk precision
-          T2* Gi = reinterpret_cast<T2*>(Gd);   // L is no longer needed: reuse its storage
-          for (int e = tid; e < M * M; e += NT) {
-            const int i = e / M, j = e - i * M;
-            if (i > j) continue;
-            double re = 0.0, im = 0.0;
-            for (int k = j; k < M; ++k) {          // W[k][i], W[k][j] nonzero for k >= max(i, j) = j
-              const double2 x = W[k * ldg + i], y = W[k * ldg + j];   // conj(x) y / D[k]
-              re += dinv[k] * (x.x * y.x + x.y * y.y);
-              im += dinv[k] * (x.x * y.y - x.y * y.x);
-            }
-            Gi[i * Mp + j] = cm<T2>((T)re, (T)im);
-            if (i != j) Gi[j * Mp + i] = cm<T2>((T)re, (T)-im);
-          }
-          __syncthreads();
-          // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
-          const double sk[2] = {0.5 * d.kappa, 0.5 * d.gamma};
-          for (int e = tid; e < 2 * MM; e += NT) {
-            const int k = e / MM, lm = e - k * MM, l = lm / Mp, m = lm - l * Mp;
-            T xr = 0, xi = 0;
-            if (l < M && m < M) {
-              const T2* Tk = Tred + k * MM;
-              for (int j = 0; j < M; ++j) {
-                const T2 gv = Gi[m * Mp + j];
-                const T gr = gv.x, gi = gv.y;
-                const T2 t = Tk[j * Mp + l];
-                xr = fma(gr, t.x, fma(-gi, t.y, xr));
-                xi = fma(gr, t.y, fma(gi, t.x, xi));
-              }
-            }
-            const T s = (T)sk[k];
-            XT[k * MM + lm] = cm<T2>(s * xr, -s * xi);
-            if constexpr (TC > 0) {
-              // real 2x2 block of X = (xr', xi') at B rows (2m, 2m+1), K columns
-              // (k 2Mp + 2l, +1): [xr', -xi'; xi', xr'] maps (re, im) of A to D
-              const float Xr = (float)(s * xr), Xi = (float)(-s * xi);
-              const int kk = k * 2 * Mp + 2 * l;
-              const float vals[4] = {Xr, -Xi, Xi, Xr};
-              for (int u = 0; u < 4; ++u) {
-                const int o = kmaj_off(2 * m + (u >> 1), kk + (u & 1), a.npad) / 4;
-                const float big = tf32_rna(vals[u]);
-                tb_big[o] = big;
-                if (TC == 3) tb_small[o] = tf32_rna(vals[u] - big);
-              }
-            }
-          }
-          if constexpr (TC > 0) async_proxy_fence();
-          __syncthreads();
-        }
-
-        // ================= F: right-hand side and RK4 stage update
-        // Thread tile: TR consecutive rows x 4 columns. Pass 1 forms -i H_eff Z_s
-        // per row, pass 2 adds the projection terms with every XT load shared by
-        // the TR rows, pass 3 applies the RK4 stage update.
-        {
-          // coefficient and split step sizes h = hi + lo (no systematic FP32 step error)
-          const T* tb = reinterpret_cast<const T*>(misc + 128);
-          const T c = tb[0], hs_hi = tb[1], hs_lo = tb[2], h6_hi = tb[3], h6_lo = tb[4];
-          const int nxt = cur ^ 1;
-          const int mq = Mp / 4;
-          const int nrt_all = (P.R + TR - 1) / TR;
-          const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
-          const int MM = Mp * Mp;
-          if constexpr (TC > 0) {
-            // ---- projection term on the tensor cores, in tiles of TC_ROWS rows.
-            // Thread (warp w, lane) owns tile row 32 (w % 4) + lane, the TMEM lane
-            // it may read, and column quads w / 4, w / 4 + 3, ... The MMAs of a
-            // tile run while the threads form -i H_eff Z_s for it; the next tile's
-            // operand staging and MMAs overlap the RK4 update of this one.
-            const int qd = warp & 3, grp = warp >> 2;
-            constexpr int QMAX = 3;   // column quads per thread (Mp <= 36)
-            const int n_sub = (P.R + TC_ROWS - 1) / TC_ROWS;
-            const uint32_t lboA = TC_ROWS * 16, lboB = (uint32_t)a.npad * 16;
-            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(a.npad >> 3) << 17) |
-                                   ((uint32_t)(TC_ROWS >> 4) << 24);
-            // operand A of the tile starting at row_lo: row tid % TC_ROWS, float4
-            // chunks c4 = tid / TC_ROWS + 3 j; chunk c4 holds complex columns 2cj,
-            // 2cj+1 of s_r rZ_s (c4 < Mp/2) or s_b bZ_s (c4 >= Mp/2)
-            auto build_a = [&](int row_lo) {
-              const int r = tid % TC_ROWS, l = row_lo + r;
-              const T2* srcr = nullptr;
-              const T2* srcb = nullptr;
-              float scr = 0.f, scb = 0.f;
-              if (l < P.R) {
-                const int it = l / P.st, rem = l - it * P.st, irl = rem / Nf, iff = rem - irl * Nf;
-                const int iro = three ? iff : P.r_lo + irl;
-                if (iro + 1 < dro) {
-                  srcr = own(cur, l + 1);
-                  scr = sq[iro + 1];
-                }
-                if (it + 1 < Nt) {
-                  srcb = own(cur, l + P.st);
-                  scb = sq[it + 1];
-                }
-              }
-              for (int c4 = tid / TC_ROWS; c4 < Mp; c4 += NT / TC_ROWS) {
-                const int jump = c4 >= Mp / 2 ? 1 : 0;
-                const int cj = c4 - jump * (Mp / 2);
-                const T2* src = jump ? srcb : srcr;
-                const float sc = jump ? scb : scr;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (src) {
-                  v = reinterpret_cast<const float4*>(src)[cj];
-                  v.x *= sc;
-                  v.y *= sc;
-                  v.z *= sc;
-                  v.w *= sc;
-                }
-                const int o = kmaj_off(r, 4 * c4, TC_ROWS) / 4;
-                const float4 big = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-                *reinterpret_cast<float4*>(ta_big + o) = big;
-                if (TC == 3)
-                  *reinterpret_cast<float4*>(ta_small + o) = make_float4(
-                      tf32_rna(v.x - big.x), tf32_rna(v.y - big.y), tf32_rna(v.z - big.z), tf32_rna(v.w - big.w));
-              }
-              async_proxy_fence();
-            };
-            auto issue = [&]() {
-              if (tid == 0) {
-                tc_fence_after();
-                // K = 4 Mp in steps of 8; each pass and half of K accumulates in
-                // its own TMEM columns so that the MMA chains run side by side
-                const int nks = Mp / 2, half = (nks + 1) / 2;
-                for (int ks = 0; ks < nks; ++ks)
-                  for (int pass = 0; pass < TC; ++pass) {
-                    const uint32_t A0 = smem_u32(pass == 2 ? ta_small : ta_big);
-                    const uint32_t B0 = smem_u32(pass == 1 ? tb_small : tb_big);
-                    const int acc = pass * TC_KSPLIT + (ks >= half ? 1 : 0);
-                    tc_mma(tmem + (uint32_t)(acc * TC_ACC), tc_desc(A0 + ks * 2 * lboA, lboA, 128),
-                           tc_desc(B0 + ks * 2 * lboB, lboB, 128), idesc, ks != 0 && ks != half);
-                  }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                             : "memory");
-              }
-            };
-            build_a(0);
-            __syncthreads();
-            issue();
-            for (int sub = 0; sub < n_sub; ++sub) {
-              const int l = sub * TC_ROWS + qd * 32 + lane;
-              const bool in = l < P.R;
-              int it = 0, irl = 0, iff = 0;
-              if (in) {
-                it = l / P.st;
-                const int rem = l - it * P.st;
-                irl = rem / Nf;
-                iff = rem - irl * Nf;
-              }
-              const int ir = P.r_lo + irl, iro = three ? iff : ir;
-              T fr[QMAX][4], fi[QMAX][4];
-              // -i H_eff Z_s for the thread's row and column quads
-              T dh = 0, dl = 0, dim_ = 0;
-              if (in) {
-                const T a0 = dtab[(0 * TAB + it) * 2], a1 = dtab[(1 * TAB + ir) * 2], a2 = dtab[(2 * TAB + iff) * 2];
-                T s1 = a0 + a1;
-                T bp = s1 - a0;
-                T er = (a0 - (s1 - bp)) + (a1 - bp);
-                T s2 = s1 + a2;
-                bp = s2 - s1;
-                er += (s1 - (s2 - bp)) + (a2 - bp);
-                dh = s2;
-                dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
-                dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
-              }
-#pragma unroll
-              for (int qq = 0; qq < QMAX; ++qq) {
-                const int m0 = (grp + 3 * qq) * 4;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) fr[qq][u] = fi[qq][u] = 0;
-                if (m0 >= Mp || !in) continue;
-                T2 z[4];
-                load4<ZSM>(own(cur, l) + m0, z);
-                T hr[4], hi[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
-                  hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
-                }
-                auto add_row = [&](const T2* vp, T w) {
-                  T2 v[4];
-                  load4<ZSM>(vp, v);
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    hr[u] = fma(w, v[u].x, hr[u]);
-                    hi[u] = fma(w, v[u].y, hi[u]);
-                  }
-                };
-                // g (b + b^dag)(a + a^dag)
-#pragma unroll
-                for (int sa = -1; sa <= 1; sa += 2) {
-                  const int it2 = it + sa;
-                  if (it2 < 0 || it2 >= Nt) continue;
-                  const T ct = g * sq[max(it, it2)];
-#pragma unroll
-                  for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
-                    const int ir2 = ir + sb2;
-                    if (ir2 < 0 || ir2 >= Nr) continue;
-                    add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
-                  }
-                }
-                if (three) {
-                  // J (a + a^dag)(f + f^dag)
-#pragma unroll
-                  for (int sa = -1; sa <= 1; sa += 2) {
-                    const int ir2 = ir + sa;
-                    if (ir2 < 0 || ir2 >= Nr) continue;
-                    const T cr = J * sq[max(ir, ir2)];
-#pragma unroll
-                    for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
-                      const int if2 = iff + sb2;
-                      if (if2 < 0 || if2 >= Nf) continue;
-                      add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
-                    }
-                  }
-                  // drive on the filter
-#pragma unroll
-                  for (int sa = -1; sa <= 1; sa += 2) {
-                    const int if2 = iff + sa;
-                    if (if2 < 0 || if2 >= Nf) continue;
-                    add_row(own(cur, l + sa) + m0, c * sq[max(iff, if2)]);
-                  }
-                } else {
-                  // drive on the resonator (two modes, C == 1)
-#pragma unroll
-                  for (int sa = -1; sa <= 1; sa += 2) {
-                    const int ir2 = ir + sa;
-                    if (ir2 < 0 || ir2 >= Nr) continue;
-                    add_row(own(cur, l + sa) + m0, c * sq[max(ir, ir2)]);
-                  }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  fr[qq][u] = hi[u];
-                  fi[qq][u] = -hr[u];
-                }
-              }
-              // + projection term D from tensor memory (lane = tile row)
-              volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
-              if (*tc_abort == 0 && !mbar_wait(mbar, tc_phase)) {
-                *tc_abort = 1;
-                set_error(a.p.err, DEV_TIMEOUT);
-              }
-              tc_phase ^= 1u;
-              tc_fence_after();
-#pragma unroll
-              for (int qq = 0; qq < QMAX; ++qq) {
-                const int quad = grp + 3 * qq;
-                if (quad * 4 >= Mp) continue;   // uniform across the warp
-                const int n_acc = Mp / 2 > 1 ? TC * TC_KSPLIT : TC;
-                float dsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int acc = 0; acc < n_acc; ++acc) {
-                  uint32_t v[8];
-                  asm volatile(
-                      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                      : "r"(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * TC_ACC + quad * 8)));
-                  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                  for (int u = 0; u < 8; ++u) dsum[u] += __uint_as_float(v[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  fr[qq][u] += dsum[2 * u];
-                  fi[qq][u] += dsum[2 * u + 1];
-                }
-              }
-              tc_fence_before();
-              __syncthreads();   // TMEM and operand A of this tile are free
-              if (sub + 1 < n_sub) {
-                build_a((sub + 1) * TC_ROWS);
-                __syncthreads();
-                issue();
-              }
-              // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
-              if (in) {
-                const int n = (it * Nr + ir) * Nf + iff;
-#pragma unroll
-                for (int qq = 0; qq < QMAX; ++qq) {
-                  const int m0 = (grp + 3 * qq) * 4;
-                  if (m0 >= Mp) continue;
-                  T2 zo[4];
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    const int m = m0 + u;
-                    if (m >= M) {
-                      zo[u] = cm<T2>(0, 0);
-                      continue;
-                    }
-                    const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
-                    const T2 zn = Zn[oz];
-                    if (stage == 0) {
-                      accg[oa] = cm<T2>(fr[qq][u], fi[qq][u]);
-                    } else if (stage < 3) {
-                      const T2 ac = accg[oa];
-                      accg[oa] = cm<T2>(fma((T)2, fr[qq][u], ac.x), fma((T)2, fi[qq][u], ac.y));
-                    }
-                    if (stage < 3) {
-                      zo[u] = cm<T2>(zn.x + fma(hs_lo, fr[qq][u], hs_hi * fr[qq][u]),
-                                     zn.y + fma(hs_lo, fi[qq][u], hs_hi * fi[qq][u]));
-                    } else {
-                      const T2 ac = accg[oa];
-                      const T s_r = ac.x + fr[qq][u], s_i = ac.y + fi[qq][u];
-                      const T2 z1 =
-                          cm<T2>(zn.x + fma(h6_lo, s_r, h6_hi * s_r), zn.y + fma(h6_lo, s_i, h6_hi * s_i));
-                      Zn[oz] = z1;
-                      zo[u] = z1;
-                    }
-                  }
-                  store4<ZSM>(own(nxt, l) + m0, zo);
-                }
-              }
-            }
-          } else {
-          const int nrt = nrt_all;
-          const int row_lo = 0;
-          for (int tile = tid; tile < nrt * mq; tile += NT) {
-            const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
-            T fr[TR][4], fi[TR][4];
-            T sr[TR], sb[TR];
-            const T2* yrp[TR];
-            const T2* ybp[TR];
-            int nrow[TR];
-            const int l0 = row_lo + rt * TR;
-            int it = l0 / P.st, irl = (l0 - it * P.st) / Nf, iff = l0 - it * P.st - irl * Nf;
-#pragma unroll
-            for (int r = 0; r < TR; ++r) {
-              const int l = l0 + r;
-              sr[r] = 0;
-              sb[r] = 0;
-              yrp[r] = own(cur, 0);
-              ybp[r] = own(cur, 0);
-              nrow[r] = -1;
-#pragma unroll
-              for (int u = 0; u < 4; ++u) fr[r][u] = fi[r][u] = 0;
-              if (l < P.R) {
-                const int ir = P.r_lo + irl;
-                const int iro = three ? iff : ir;
-                nrow[r] = (it * Nr + ir) * Nf + iff;
-                // H_eff diagonal: real part as an unevaluated sum dh + dl
-                T dh, dl;
-                {
-                  const T a0 = dtab[(0 * TAB + it) * 2], a1 = dtab[(1 * TAB + ir) * 2], a2 = dtab[(2 * TAB + iff) * 2];
-                  T s1 = a0 + a1;
-                  T bp = s1 - a0;
-                  T er = (a0 - (s1 - bp)) + (a1 - bp);
-                  T s2 = s1 + a2;
-                  bp = s2 - s1;
-                  er += (s1 - (s2 - bp)) + (a2 - bp);
-                  dh = s2;
-                  dl = er + dtab[(0 * TAB + it) * 2 + 1] + dtab[(1 * TAB + ir) * 2 + 1] + dtab[(2 * TAB + iff) * 2 + 1];
-                }
-                const T dim_ = (T)(-0.5) * (ka * (T)iro + ga * (T)it);
-                T2 z[4];
-                load4<ZSM>(own(cur, l) + m0, z);
-                T hr[4], hi[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  hr[u] = fma(dh, z[u].x, fma(dl, z[u].x, -dim_ * z[u].y));
-                  hi[u] = fma(dh, z[u].y, fma(dl, z[u].y, dim_ * z[u].x));
-                }
-                auto add_row = [&](const T2* vp, T w) {
-                  T2 v[4];
-                  load4<ZSM>(vp, v);
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    hr[u] = fma(w, v[u].x, hr[u]);
-                    hi[u] = fma(w, v[u].y, hi[u]);
-                  }
-                };
-                // g (b + b^dag)(a + a^dag)
-#pragma unroll
-                for (int sa = -1; sa <= 1; sa += 2) {
-                  const int it2 = it + sa;
-                  if (it2 < 0 || it2 >= Nt) continue;
-                  const T ct = g * sq[max(it, it2)];
-#pragma unroll
-                  for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
-                    const int ir2 = ir + sb2;
-                    if (ir2 < 0 || ir2 >= Nr) continue;
-                    add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
-                  }
-                }
-                if (three) {
-                  // J (a + a^dag)(f + f^dag)
-#pragma unroll
-                  for (int sa = -1; sa <= 1; sa += 2) {
-                    const int ir2 = ir + sa;
-                    if (ir2 < 0 || ir2 >= Nr) continue;
-                    const T cr = J * sq[max(ir, ir2)];
-#pragma unroll
-                    for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
-                      const int if2 = iff + sb2;
-                      if (if2 < 0 || if2 >= Nf) continue;
-                      add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
-                    }
-                  }
-                  // drive on the filter
-#pragma unroll
-                  for (int sa = -1; sa <= 1; sa += 2) {
-                    const int if2 = iff + sa;
-                    if (if2 < 0 || if2 >= Nf) continue;
-                    add_row(own(cur, l + sa) + m0, c * sq[max(iff, if2)]);
-                  }
-                } else {
-                  // drive on the resonator (two modes, C == 1)
-#pragma unroll
-                  for (int sa = -1; sa <= 1; sa += 2) {
-                    const int ir2 = ir + sa;
-                    if (ir2 < 0 || ir2 >= Nr) continue;
-                    add_row(own(cur, l + sa) + m0, c * sq[max(ir, ir2)]);
-                  }
-                }
-                // F = -i H_eff z
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  fr[r][u] = hi[u];
-                  fi[r][u] = -hr[u];
-                }
-                if (iro + 1 < dro) {
-                  sr[r] = sq[iro + 1];
-                  yrp[r] = own(cur, l + 1);
-                }
-                if (it + 1 < Nt) {
-                  sb[r] = sq[it + 1];
-                  ybp[r] = own(cur, l + P.st);
-                }
-              }
-              // next local row
-              if (++iff == Nf) {
-                iff = 0;
-                if (++irl == P.nr) {
-                  irl = 0;
-                  ++it;
-                }
-              }
-            }
-            // projection terms: + sr (rZ_s) XT_r + sb (bZ_s) XT_b
-            if constexpr (TC == 0) {
-            for (int k = 0; k < M; ++k) {
-              T2 xr[4], xb[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                xr[u] = XT[k * Mp + m0 + u];
-                xb[u] = XT[MM + k * Mp + m0 + u];
-              }
-#pragma unroll
-              for (int r = 0; r < TR; ++r) {
-                const T2 y0 = yrp[r][k], y1 = ybp[r][k];
-                const T ar = sr[r] * y0.x, ai = sr[r] * y0.y, br = sb[r] * y1.x, bi = sb[r] * y1.y;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  fr[r][u] = fma(ar, xr[u].x, fma(-ai, xr[u].y, fma(br, xb[u].x, fma(-bi, xb[u].y, fr[r][u]))));
-                  fi[r][u] = fma(ar, xr[u].y, fma(ai, xr[u].x, fma(br, xb[u].y, fma(bi, xb[u].x, fi[r][u]))));
-                }
-              }
-            }
-            }
-            // RK4 update (weights 1/6, 1/3, 1/3, 1/6)
-#pragma unroll
-            for (int r = 0; r < TR; ++r) {
-              const int n = nrow[r];
-              if (n < 0) continue;
-              T2 zo[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int m = m0 + u;
-                if (m >= M) {
-                  zo[u] = cm<T2>(0, 0);
-                  continue;
-                }
-                const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
-                const T2 zn = Zn[oz];
-                if (stage == 0) {
-                  accg[oa] = cm<T2>(fr[r][u], fi[r][u]);
-                } else if (stage < 3) {
-                  const T2 ac = accg[oa];
-                  accg[oa] = cm<T2>(fma((T)2, fr[r][u], ac.x), fma((T)2, fi[r][u], ac.y));
-                }
-                if (stage < 3) {
-                  zo[u] = cm<T2>(zn.x + fma(hs_lo, fr[r][u], hs_hi * fr[r][u]),
-                                 zn.y + fma(hs_lo, fi[r][u], hs_hi * fi[r][u]));
-                } else {
-                  const T2 ac = accg[oa];
-                  const T s_r = ac.x + fr[r][u], s_i = ac.y + fi[r][u];
-                  const T2 z1 = cm<T2>(zn.x + fma(h6_lo, s_r, h6_hi * s_r), zn.y + fma(h6_lo, s_i, h6_hi * s_i));
-                  Zn[oz] = z1;
-                  zo[u] = z1;
-                }
-              }
-              store4<ZSM>(own(nxt, l0 + r) + m0, zo);
-            }
-          }
-          }
-          cur = nxt;
-          __syncthreads();
-        }
-      }
-      if (last) break;
-    }
-    // every CTA is done reading its peers' shared memory before it is reused
-    cluster.sync();
-  }
-  if constexpr (TC > 0) {
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
-  }
-}
-
-}  // namespace fz
 
 // ----------------------------------------------------------------- host side
 
@@ -1285,17 +64,18 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
 
 // tc: tensor-core passes of the projection (0: CUDA cores; 3 or 1: tcgen05,
 // L2-resident stage state and FP32 state with the double-word Gram only)
-const void* kernel_ptr(lr_precision prec, int zs_smem, int tc) {
-  if (tc == 3) return (const void*)fz::fused_kernel<float2, 1, 0, 3>;
-  if (tc == 1) return (const void*)fz::fused_kernel<float2, 1, 0, 1>;
+const void* kernel_ptr(lr_precision prec, int zs_smem, int tc, int frame) {
+  if (frame) return fz::rwa_kernel_ptr(prec, zs_smem);
+  if (tc == 3) return (const void*)fz::fused_kernel<float2, 1, 0, 3, 0>;
+  if (tc == 1) return (const void*)fz::fused_kernel<float2, 1, 0, 1, 0>;
   if (zs_smem) {
-    if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 1, 0>;
-    if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 1, 0>;
-    return (const void*)fz::fused_kernel<float2, 1, 1, 0>;
+    if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 1, 0, 0>;
+    if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 1, 0, 0>;
+    return (const void*)fz::fused_kernel<float2, 1, 1, 0, 0>;
   }
-  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 0, 0>;
-  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 0, 0>;
-  return (const void*)fz::fused_kernel<float2, 1, 0, 0>;
+  if (prec == LR_PREC_FP64) return (const void*)fz::fused_kernel<double2, 0, 0, 0, 0>;
+  if (prec == LR_PREC_FP32) return (const void*)fz::fused_kernel<float2, 0, 0, 0, 0>;
+  return (const void*)fz::fused_kernel<float2, 1, 0, 0, 0>;
 }
 
 int rows_per_cta(const TrajDev& d, int C) {
@@ -1304,7 +84,7 @@ int rows_per_cta(const TrajDev& d, int C) {
 
 }  // namespace
 
-bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* plan) {
+bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, FusedPlan* plan) {
   *plan = FusedPlan{};
   int dev = 0;
   cudaDeviceProp prop{};
@@ -1341,18 +121,19 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
   };
   std::vector<Variant> vars;
   if (prec == LR_PREC_TF32_G64) {
+    if (frame) return false;   // the tensor-core variants are built for the lab frame only
     vars.push_back({0, 1});
   } else {
     if (force_tc != 3) {
       if (!force_global) vars.push_back({1, 0});
       vars.push_back({0, 0});
     }
-    if (prec == LR_PREC_FP32_G64 && force_tc != 0) vars.push_back({0, 3});
+    if (prec == LR_PREC_FP32_G64 && force_tc != 0 && !frame) vars.push_back({0, 3});
   }
   double best = 1e300;
   for (const Variant& v : vars) {
     const int zs_smem = v.zs_smem, tc = v.tc;
-    const void* kern = kernel_ptr(prec, zs_smem, tc);
+    const void* kern = kernel_ptr(prec, zs_smem, tc, frame);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
       cudaGetLastError();
@@ -1419,6 +200,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* 
         plan->smem = L.total;
         plan->zs_smem = zs_smem;
         plan->tc = tc;
+        plan->frame = frame;
         plan->Mp = Mp;
         plan->R = R;
         plan->Nmax = Nmax;
@@ -1488,7 +270,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.acc_glob = sc + off;
   cudaError_t e = cudaMemcpyAsync(sc, plan.order.data(), sizeof(int) * rp.n_traj, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc);
+  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1504,16 +286,17 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (plan.tc == 3) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 3>, a);
-  if (plan.tc == 1) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 1>, a);
+  if (plan.frame) return fz::rwa_launch(cfg, prec, plan.zs_smem, a);
+  if (plan.tc == 3) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 3, 0>, a);
+  if (plan.tc == 1) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 1, 0>, a);
   if (plan.zs_smem) {
-    if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 1, 0>, a);
-    if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 1, 0>, a);
-    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 1, 0>, a);
+    if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 1, 0, 0>, a);
+    if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 1, 0, 0>, a);
+    return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 1, 0, 0>, a);
   }
-  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 0, 0>, a);
-  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 0, 0>, a);
-  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 0>, a);
+  if (prec == LR_PREC_FP64) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<double2, 0, 0, 0, 0>, a);
+  if (prec == LR_PREC_FP32) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 0, 0, 0, 0>, a);
+  return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 0, 0>, a);
 }
 
 }  // namespace lr

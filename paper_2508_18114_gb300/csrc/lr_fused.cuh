@@ -24,6 +24,7 @@ struct FusedPlan {
   int smem;        // dynamic shared memory per CTA (bytes)
   int zs_smem;     // 1: stage state in shared memory, 0: in global scratch (L2)
   int tc;          // tensor-core passes of the projection term: 0 (CUDA cores), 3 or 1
+  int frame;       // 0 lab frame, 1 rotating frame with the rotating-wave approximation
   int Mp;          // padded rank (multiple of 4)
   int R;           // largest rows per CTA
   int Nmax;        // largest N in the batch
@@ -34,7 +35,7 @@ struct FusedPlan {
 
 // Decide whether the fused engine supports this batch and with which shape.
 // Needs a CUDA device (occupancy queries); returns false without one.
-bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, FusedPlan* plan);
+bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, FusedPlan* plan);
 size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj);
 cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunParams& rp, lr_precision prec,
                             long step0, long n_steps, cudaStream_t s);

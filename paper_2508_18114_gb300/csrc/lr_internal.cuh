@@ -54,22 +54,34 @@ __device__ __forceinline__ double logistic(double t, double t0, double s) {
   return 1.0 / (1.0 + exp(-(t - t0) / s));
 }
 
-// Omega(t) cos(w_d t + phi): the coefficient of (r + r^dag) in H(t).
-__device__ __forceinline__ double pulse_coefficient(const PulseDev& P, double tau, double t) {
-  double env, wd, phi;
+// Envelope Omega(t) of Sec. S2.C.
+__device__ __forceinline__ double pulse_envelope(const PulseDev& P, double tau, double t) {
   if (P.kind == 0) {
     const double s = P.p[2] / 5.0, t0 = 6.0 * s;
-    env = P.p[0] * logistic(t, t0, s) * (1.0 - logistic(t, tau - t0, s));
-    wd = P.p[1];
-    phi = P.p[3];
-  } else {
-    const double sr = P.p[3] / 5.0, sf = P.p[4] / 5.0, sm = P.p[5] / 5.0;
-    env = P.p[0] * logistic(t, 6.0 * sr, sr) + (P.p[1] - P.p[0]) * logistic(t, P.p[2], sm) -
-          P.p[1] * logistic(t, tau - 6.0 * sf, sf);
-    wd = P.p[6];
-    phi = P.p[7];
+    return P.p[0] * logistic(t, t0, s) * (1.0 - logistic(t, tau - t0, s));
   }
-  return env * cos(wd * t + phi);
+  const double sr = P.p[3] / 5.0, sf = P.p[4] / 5.0, sm = P.p[5] / 5.0;
+  return P.p[0] * logistic(t, 6.0 * sr, sr) + (P.p[1] - P.p[0]) * logistic(t, P.p[2], sm) -
+         P.p[1] * logistic(t, tau - 6.0 * sf, sf);
+}
+__device__ __forceinline__ double pulse_drive_frequency(const PulseDev& P) { return P.kind == 0 ? P.p[1] : P.p[6]; }
+__device__ __forceinline__ double pulse_phase(const PulseDev& P) { return P.kind == 0 ? P.p[3] : P.p[7]; }
+
+// Omega(t) cos(w_d t + phi): the coefficient of (r + r^dag) in H(t).
+__device__ __forceinline__ double pulse_coefficient(const PulseDev& P, double tau, double t) {
+  const double env = pulse_envelope(P, tau, t);
+  return env * cos(pulse_drive_frequency(P) * t + pulse_phase(P));
+}
+
+// Drive in the frame rotating at w_d with the rotating-wave approximation
+// (the RWA Hamiltonian of Sec. S2): (Omega(t)/2)(e^{i phi} r + e^{-i phi} r^dag).
+// Returns the weight of the r term, w = (Omega/2) e^{i phi}; the r^dag term
+// carries conj(w).
+__device__ __forceinline__ double2 pulse_rwa_drive(const PulseDev& P, double tau, double t) {
+  const double h = 0.5 * pulse_envelope(P, tau, t);
+  double sn, cs;
+  sincos(pulse_phase(P), &sn, &cs);
+  return make_double2(h * cs, h * sn);
 }
 
 // d c(t) / d theta_i for the pulse parameters (kind 0: 4 entries, kind 1: 8),
@@ -147,9 +159,12 @@ __device__ __forceinline__ int readout_dim(const TrajDev& d) {
 }
 
 // Diagonal of H_eff = H - (i/2) sum_k L_k^dag L_k (real and imaginary part).
-__device__ __forceinline__ void heff_diag(const TrajDev& d, const RowIdx& r, double& re, double& im) {
+// wfr: frame frequency (0 in the lab frame, w_d in the rotating frame, where
+// every mode frequency becomes a detuning w - w_d).
+__device__ __forceinline__ void heff_diag(const TrajDev& d, const RowIdx& r, double wfr, double& re, double& im) {
   const double it = r.it;
-  re = d.wq * it + 0.5 * d.alpha * it * (it - 1.0) + d.wr * r.ir + (d.n_modes == 3 ? d.wf * r.iff : 0.0);
+  re = (d.wq - wfr) * it + 0.5 * d.alpha * it * (it - 1.0) + (d.wr - wfr) * r.ir +
+       (d.n_modes == 3 ? (d.wf - wfr) * r.iff : 0.0);
   im = -0.5 * (d.kappa * readout_index(d, r) + d.gamma * it);
 }
 
@@ -190,6 +205,7 @@ struct RunParams {
   double dt;
   double eta;
   int snap_m;   // leading dimension of the Gram snapshots (max M), 0 when not recorded
+  int frame;    // 0: lab frame; 1: frame rotating at each candidate's w_d, rotating-wave approximation
 };
 
 // lr_common.cu

@@ -221,27 +221,40 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
   const int tj = blockIdx.y;
   const TrajDev d = p.traj[tj];
   __shared__ double2 sX[2][LR_MAX_RANK * LR_MAX_RANK];
-  __shared__ double coef;
+  __shared__ double coef, coef_i, wfr;
   const int M = d.M, MM = M * M, ld = d.ld;
   const double2* X = p.X + (size_t)tj * 2 * LR_MAX_RANK * LR_MAX_RANK;
   for (int e = threadIdx.x; e < 2 * MM; e += blockDim.x) {
     const int k = e / MM, ij = e - k * MM;
     sX[k][ij] = X[k * LR_MAX_RANK * LR_MAX_RANK + ij];
   }
-  if (threadIdx.x == 0) coef = pulse_coefficient(p.pulse[d.cand], rp.tau, t);
+  if (threadIdx.x == 0) {
+    const PulseDev P = p.pulse[d.cand];
+    if (rp.frame) {
+      const double2 w = pulse_rwa_drive(P, rp.tau, t);
+      coef = w.x;
+      coef_i = w.y;
+      wfr = pulse_drive_frequency(P);
+    } else {
+      coef = pulse_coefficient(P, rp.tau, t);
+      coef_i = 0.0;
+      wfr = 0.0;
+    }
+  }
   __syncthreads();
   const double2* Z = Zin + d.z_off;
   double2* Zn = reinterpret_cast<double2*>(p.Zn) + d.z_off;
   double2* acc = reinterpret_cast<double2*>(p.acc) + d.z_off;
   double2* Zo = Zout ? Zout + d.z_off : nullptr;
   const int st = d.Nr * d.Nf, sr = d.Nf;
-  const double c = coef, dt = rp.dt;
+  const double c = coef, ci = coef_i, dt = rp.dt;
+  const bool rwa = rp.frame != 0;
   const long total = (long)d.N * M;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int n = (int)(idx / M), m = (int)(idx - (long)n * M);
     const RowIdx ri = row_index(d, n);
     double dre, dim_;
-    heff_diag(d, ri, dre, dim_);
+    heff_diag(d, ri, wfr, dre, dim_);
     const double2 z = Z[(size_t)n * ld + m];
     double hr = dre * z.x - dim_ * z.y, hi = dre * z.y + dim_ * z.x;
     // g (b + b^dag)(a + a^dag)
@@ -252,6 +265,7 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
       for (int bb = -1; bb <= 1; bb += 2) {
         const int ir2 = ri.ir + bb;
         if (ir2 < 0 || ir2 >= d.Nr) continue;
+        if (rwa && a == bb) continue;   // RWA keeps g (b^dag a + b a^dag) only
         const double w = d.g * ct * sqrt((double)max(ri.ir, ir2));
         const double2 v = Z[(size_t)(n + a * st + bb * sr) * ld + m];
         hr += w * v.x;
@@ -267,6 +281,7 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
         for (int bb = -1; bb <= 1; bb += 2) {
           const int if2 = ri.iff + bb;
           if (if2 < 0 || if2 >= d.Nf) continue;
+          if (rwa && a == bb) continue;   // RWA keeps J (a^dag f + a f^dag) only
           const double w = d.J * cr * sqrt((double)max(ri.iff, if2));
           const double2 v = Z[(size_t)(n + a * sr + bb) * ld + m];
           hr += w * v.x;
@@ -274,15 +289,17 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
         }
       }
     }
-    // drive c(t) (r + r^dag) on the readout mode (stride 1)
+    // drive on the readout mode (stride 1): lab frame c(t) (r + r^dag); RWA
+    // w r + conj(w) r^dag with w = c + i ci (row n gets r from n+1, r^dag from n-1)
     const int iro = readout_index(d, ri), dro = readout_dim(d);
     for (int a = -1; a <= 1; a += 2) {
       const int i2 = iro + a;
       if (i2 < 0 || i2 >= dro) continue;
-      const double w = c * sqrt((double)max(iro, i2));
+      const double s = sqrt((double)max(iro, i2));
+      const double wr = c * s, wi = (a > 0 ? ci : -ci) * s;
       const double2 v = Z[(size_t)(n + a) * ld + m];
-      hr += w * v.x;
-      hi += w * v.y;
+      hr += wr * v.x - wi * v.y;
+      hi += wr * v.y + wi * v.x;
     }
     // F = -i H_eff Z
     double fr = hi, fi = -hr;

@@ -26,6 +26,7 @@ STATUS = {
 }
 PRECISION = {"fp64": 0, "fp32_g64": 1, "fp32": 2, "tf32_g64": 3}
 ENGINE = {"auto": 0, "plain": 1, "fused": 2}
+FRAME = {"lab": 0, "rwa": 1}
 ENGINE_NAME = {v: k for k, v in ENGINE.items()}
 
 # exported names declared in include/lr.h
@@ -59,7 +60,7 @@ class lr_pulse(C.Structure):
 class lr_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("engine", C.c_int),
                 ("max_steps", C.c_long), ("pop_every", C.c_int),
-                ("eta", C.c_double), ("record_gram", C.c_int)]
+                ("eta", C.c_double), ("record_gram", C.c_int), ("frame", C.c_int)]
 
 
 class lr_info(C.Structure):
@@ -164,7 +165,7 @@ class LowRankBatch:
     """
 
     def __init__(self, models, ranks, precision="fp64", engine="auto", max_steps=1000,
-                 pop_every=1, eta=0.6, device="cuda:0", record_gram=False):
+                 pop_every=1, eta=0.6, device="cuda:0", record_gram=False, frame="lab"):
         import torch
         self._lib = load_library()
         n = len(models)
@@ -173,7 +174,7 @@ class LowRankBatch:
         arr = (lr_model * n)(*[make_model(m) for m in models])
         rk = (C.c_int * n)(*[int(r) for r in ranks])
         opt = lr_options(PRECISION[precision], ENGINE[engine], int(max_steps), int(pop_every), float(eta),
-                         1 if record_gram else 0)
+                         1 if record_gram else 0, FRAME[frame])
         h = C.c_void_p()
         st = self._lib.lr_create(n, arr, rk, C.byref(opt), C.byref(h))
         if st != 0:

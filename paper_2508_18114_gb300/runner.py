@@ -13,11 +13,13 @@ from .lr import LowRankBatch
 
 def make_batch(wl, precision=None, engine="auto", pop_every=1, max_steps=None, candidates=None,
                device="cuda:0", record_gram=False) -> LowRankBatch:
+    """Batch for a workload's candidates, in the workload's frame (lab or rwa)."""
     cands = wl.candidates if candidates is None else [wl.candidates[i] for i in candidates]
     prec = precision or getattr(wl, "precision", "fp64")
     ms = wl.n_steps if max_steps is None else max_steps
     b = LowRankBatch([c.model for c in cands], [c.M for c in cands], precision=prec, engine=engine,
-                     max_steps=ms, pop_every=pop_every, eta=wl.eta, device=device, record_gram=record_gram)
+                     max_steps=ms, pop_every=pop_every, eta=wl.eta, device=device, record_gram=record_gram,
+                     frame=getattr(wl, "frame", "lab"))
     b.set_pulse([(c.pulse.kind, c.pulse.p) for c in cands], wl.tau)
     return b
 

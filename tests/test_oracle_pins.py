@@ -472,3 +472,79 @@ def test_diagnostics_full_rank_purity_matches_master_equation():
     pur_me = float(np.trace(b["rho"] @ b["rho"]).real)
     assert abs(pur_lra - pur_me) < 1e-5
     assert diagnostics.gram_purity(a["gram"][0]) > pur_lra
+
+
+# ---------------------------------------------------------------- rotating frame + RWA (Sec. S2)
+
+def _excitation_number(mdl):
+    """N = b^dag b + a^dag a [+ f^dag f] on the product basis (diagonal)."""
+    levels = np.array(np.unravel_index(np.arange(mdl.N), mdl.dims)).sum(axis=0)
+    return levels.astype(float)
+
+
+@pytest.mark.parametrize("dims", [(3, 4), (3, 3, 2)])
+def test_rwa_hamiltonian_is_excitation_conserving_part(dims):
+    """The RWA Hamiltonian equals the part of H_lab - w_d N that conserves the
+    excitation number N (the blocks N -> N of the lab Hamiltonian in the frame
+    rotating at w_d); the counter-rotating terms are the N -> N+-2 blocks."""
+    wd = 2.7
+    lab = small_model(dims)
+    rwa = Model(dims, wq=2.0, alpha=-0.4, wr=3.0, g=0.3, kappa=0.5, gamma=0.2, wf=3.2, J=0.25,
+                dense=True, rwa=(wd, 0.0))
+    nexc = _excitation_number(lab)
+    shifted = lab.H0 - wd * np.diag(nexc)
+    secular = np.where(nexc[:, None] == nexc[None, :], shifted, 0.0)
+    assert np.allclose(rwa.H0, secular, atol=1e-13)
+    assert np.abs(shifted - secular).max() > 0.1     # the lab model has counter-rotating terms
+
+
+def test_rwa_drive_is_period_average_of_rotated_lab_drive():
+    """(1/T) int_0^T U(t) cos(w_d t + phi) (r + r^dag) U(t)^dag dt with
+    U = exp(i w_d t N), T = 2 pi / w_d, equals (1/2)(e^{i phi} r + e^{-i phi} r^dag)."""
+    wd, phi = 2.3, 0.7
+    lab = small_model((2, 3, 3))
+    rwa = Model((2, 3, 3), wq=2.0, alpha=-0.4, wr=3.0, g=0.3, kappa=0.5, gamma=0.2, wf=3.2, J=0.25,
+                dense=True, rwa=(wd, phi))
+    nexc = _excitation_number(lab)
+    T, K = 2 * math.pi / wd, 4000
+    avg = np.zeros_like(lab.Xd)
+    for k in range(K):       # rectangle rule: exact for trigonometric polynomials of degree < K
+        t = k * T / K
+        u = np.exp(1j * wd * t * nexc)
+        avg += (u[:, None] * lab.Xd * u.conj()[None, :]) * math.cos(wd * t + phi) / K
+    assert np.allclose(avg, 0.5 * rwa.Xd, atol=1e-12)
+
+
+def test_rwa_driven_damped_resonator_closed_form():
+    """Rotating frame, constant drive (Omega/2)(e^{i phi} a + e^{-i phi} a^dag),
+    detuning Delta: <a>(t) = a_ss (1 - exp(-(i Delta + kappa/2) t)),
+    a_ss = -i (Omega/2) e^{-i phi} / (i Delta + kappa/2); rank 1 is exact."""
+    wr, wd, kappa, om, phi = 5.0, 4.6, 0.5, 0.8, 0.3
+    mdl = Model((1, 30), wq=0.0, alpha=0.0, wr=wr, g=0.0, kappa=kappa, gamma=0.0, dense=True, rwa=(wd, phi))
+    coef = lambda t: 0.5 * om  # noqa: E731
+    dt, n = 2e-3, 4000
+    z0 = np.zeros((mdl.N, 1), complex)
+    z0[0, 0] = 1
+    out = lowrank.integrate(z0, mdl, coef, dt, n, pop_every=400)
+    t = np.arange(n + 1) * dt
+    lam = 1j * (wr - wd) + 0.5 * kappa
+    want = -1j * 0.5 * om * np.exp(-1j * phi) / lam * (1 - np.exp(-lam * t))
+    assert np.max(np.abs(out["beta"] - want)) < 1e-10
+    assert np.allclose(out["nr"], np.abs(want[::400]) ** 2, atol=1e-10)
+
+
+def test_rwa_tracks_lab_frame_for_a_weak_near_resonant_drive():
+    """Physics check of the approximation: for a weak drive near resonance
+    (Omega, |w_r - w_d| << w_d) the lab-frame amplitude times e^{i w_d t}
+    follows the RWA amplitude to O(Omega / w_d)."""
+    wr, wd, kappa, om, phi = 30.0, 29.7, 0.5, 0.3, 0.3
+    lab = Model((1, 12), wq=0.0, alpha=0.0, wr=wr, g=0.0, kappa=kappa, gamma=0.0, dense=True)
+    rwa = Model((1, 12), wq=0.0, alpha=0.0, wr=wr, g=0.0, kappa=kappa, gamma=0.0, dense=True, rwa=(wd, phi))
+    dt, n = 5e-4, 8000
+    z0 = np.zeros((lab.N, 1), complex)
+    z0[0, 0] = 1
+    a = lowrank.integrate(z0, lab, lambda t: om * math.cos(wd * t + phi), dt, n, pop_every=n)
+    b = lowrank.integrate(z0, rwa, lambda t: 0.5 * om, dt, n, pop_every=n)
+    t = np.arange(n + 1) * dt
+    diff = np.abs(a["beta"] * np.exp(1j * wd * t) - b["beta"]).max()
+    assert diff < 3 * om / wd * np.abs(b["beta"]).max()
