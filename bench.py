@@ -293,7 +293,9 @@ def run_ours(args):
     engine = lrmod.ENGINE_NAME[info.engine]
 
     # algorithmic work and roofline of the integrate kernel(s)
-    fl = sum(2 * flops_per_stage(c.model.N, c.M) for c in cands) * 4 * chunk   # per bench step
+    # operator nonzeros per row: diagonal + g (4, or 2 with the RWA) [+ J (4 or 2)] + drive (2)
+    nnz = lambda c: 1 + (2 if wl.frame == "rwa" else 4) * (2 if c.model.n_modes == 3 else 1) + 2  # noqa: E731
+    fl = sum(2 * flops_per_stage(c.model.N, c.M, nnz=nnz(c)) for c in cands) * 4 * chunk   # per bench step
     peaks, peak_src = measured_peaks()
     mhz = clocks.get("sm_mhz") or 2070.0
     if prec == "fp64":
