@@ -113,6 +113,85 @@ __device__ __forceinline__ void dw_add(DW& s, const DW& o) {
 }
 __device__ __forceinline__ double dw_value(const DW& s) { return (double)s.hi + (double)s.lo; }
 
+// Double-word arithmetic for the M x M phase (Dekker's product via FMA,
+// Knuth's two-sum; results normalised, ~2^-48 relative).
+__device__ __forceinline__ DW dw_make(double x) {
+  DW r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ DW dw_sum(DW a, DW b) {
+  const float s = a.hi + b.hi, bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  DW r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ DW dw_neg(DW a) {
+  a.hi = -a.hi;
+  a.lo = -a.lo;
+  return a;
+}
+__device__ __forceinline__ DW dw_mul(DW a, DW b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  DW r;
+  r.hi = p + e;
+  r.lo = e - (r.hi - p);
+  return r;
+}
+// 1/p for p > 0: Newton's iteration r <- r + r (1 - p r) once, in double-word,
+// from the FP32 quotient (24 -> ~48 bits)
+__device__ __forceinline__ DW dw_recip(DW p) {
+  DW r0;
+  r0.hi = 1.0f / p.hi;
+  r0.lo = 0.0f;
+  DW one;
+  one.hi = 1.0f;
+  one.lo = 0.0f;
+  const DW e = dw_sum(one, dw_neg(dw_mul(p, r0)));
+  return dw_sum(r0, dw_mul(r0, e));
+}
+struct DWC {
+  DW re, im;
+};
+// x conj(y)
+__device__ __forceinline__ DWC dwc_mul_conj(const DWC& x, const DWC& y) {
+  DWC r;
+  r.re = dw_sum(dw_mul(x.re, y.re), dw_mul(x.im, y.im));
+  r.im = dw_sum(dw_mul(x.im, y.re), dw_neg(dw_mul(x.re, y.im)));
+  return r;
+}
+// x y
+__device__ __forceinline__ DWC dwc_mul(const DWC& x, const DWC& y) {
+  DWC r;
+  r.re = dw_sum(dw_mul(x.re, y.re), dw_neg(dw_mul(x.im, y.im)));
+  r.im = dw_sum(dw_mul(x.re, y.im), dw_mul(x.im, y.re));
+  return r;
+}
+__device__ __forceinline__ DWC dwc_sub(const DWC& a, const DWC& b) {
+  DWC r;
+  r.re = dw_sum(a.re, dw_neg(b.re));
+  r.im = dw_sum(a.im, dw_neg(b.im));
+  return r;
+}
+__device__ __forceinline__ DWC dwc_add(const DWC& a, const DWC& b) {
+  DWC r;
+  r.re = dw_sum(a.re, b.re);
+  r.im = dw_sum(a.im, b.im);
+  return r;
+}
+__device__ __forceinline__ DWC dwc_scale(const DWC& a, DW s) {
+  DWC r;
+  r.re = dw_mul(a.re, s);
+  r.im = dw_mul(a.im, s);
+  return r;
+}
+
 // ----------------------------------------------------------------- the kernel
 
 // Vector load of 4 consecutive complex values (16-byte loads when the row
@@ -680,77 +759,155 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
           }
           if (last) break;
-          // FP64 G = L D L^dag (unit lower L, right-looking, in place in Gd), then
-          // W = L^-1 (unit lower) and G^-1 = W^dag D^-1 W. One FP64 reciprocal per
-          // pivot (formed once and shared: FP64 runs at 2 FMA/clk/SM here) and two
-          // block barriers per elimination step.
-          double* dinv = misc + 96;     // [M] 1 / D[k]
-          // keep the diagonal of G: a pivot below 1e-13 of it is a numerical breakdown
-          for (int k = tid; k < M; k += NT) W[k * ldg] = Gd[k * ldg + k];
-          __syncthreads();
-          for (int k = 0; k < M; ++k) {
-            if (tid == 0) {
-              const double piv = Gd[k * ldg + k].x;
-              if (!(piv > 1e-13 * W[k * ldg].x) || !isfinite(piv) || piv < 1e-30) {
-                misc[1] = 1.0;
-                dinv[k] = 1.0;
-              } else {
-                // reciprocal by Newton-Raphson, r <- r (2 - piv r), from the FP32
-                // estimate: 24 -> 48 -> 96 correct bits, two FP64 FMA pairs on the
-                // serial path instead of a full FP64 division
-                double r = (double)(1.0f / (float)piv);
-                r = r * fma(-piv, r, 2.0);
-                r = r * fma(-piv, r, 2.0);
-                dinv[k] = r;
+          T2* Gi = reinterpret_cast<T2*>(Gd);   // G^-1 reuses the storage of L once L is no longer needed
+          if constexpr (sizeof(T) == 4) {
+            // FP32 state: the same factorisation and inverse in double-word FP32
+            // (~2^-48 relative, FP64-class like the Gram matrix), on the FP32 pipes:
+            // on this GPU an FP64 warp instruction holds its SMSP's FP64 pipe for
+            // ~60 cycles, and G^-1 is rounded to FP32 at the end anyway. G, L and W
+            // use the storage of their FP64 counterparts (16 bytes per entry).
+            DWC* Gw = reinterpret_cast<DWC*>(Gd);
+            DWC* Ww = reinterpret_cast<DWC*>(W);
+            DW* dinv = reinterpret_cast<DW*>(misc + 96);   // [M] 1 / D[k]
+            float* diag0 = reinterpret_cast<float*>(W);    // W[k][0] slot: the diagonal of G
+            for (int e = tid; e < M * (M + 1) / 2; e += NT) {
+              const int i = tri[e].x, j = tri[e].y;
+              const double2 v = Gd[i * ldg + j];
+              DWC g;
+              g.re = dw_make(v.x);
+              g.im = dw_make(v.y);
+              if (i == j) diag0[i * ldg * 4] = (float)v.x;
+              Gw[i * ldg + j] = g;
+            }
+            __syncthreads();
+            for (int k = 0; k < M; ++k) {
+              if (tid == 0) {
+                const DW piv = Gw[k * ldg + k].re;
+                if (!(piv.hi > 1e-13f * diag0[k * ldg * 4]) || !isfinite(piv.hi) || piv.hi < 1e-30f) {
+                  misc[1] = 1.0;
+                  dinv[k].hi = 1.0f;
+                  dinv[k].lo = 0.0f;
+                } else {
+                  dinv[k] = dw_recip(piv);
+                }
+              }
+              __syncthreads();
+              const DW rk = dinv[k];
+              const int w = M - k - 1;
+              // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k
+              for (int e = tid; e < w * (w + 1) / 2; e += NT) {
+                const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
+                const DWC t = dwc_scale(dwc_mul_conj(Gw[i * ldg + k], Gw[j * ldg + k]), rk);
+                Gw[i * ldg + j] = dwc_sub(Gw[i * ldg + j], t);
+              }
+              __syncthreads();
+            }
+            if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
+            // unit lower L[i][k] = G[i][k] / D[k]; W = L^-1 row by row (unit diagonal)
+            for (int e = tid; e < M * M; e += NT) {
+              const int i = e / M, j = e - i * M;
+              DWC o;
+              o.re.hi = i == j ? 1.0f : 0.0f;
+              o.re.lo = o.im.hi = o.im.lo = 0.0f;
+              Ww[i * ldg + j] = o;
+              if (i > j) Gw[i * ldg + j] = dwc_scale(Gw[i * ldg + j], dinv[j]);
+            }
+            __syncthreads();
+            for (int k = 0; k < M - 1; ++k) {
+              // rows i > k: W[i][j] -= L[i][k] W[k][j], j <= k (W[k] is final)
+              const int rows = M - k - 1;
+              for (int e = tid; e < rows * (k + 1); e += NT) {
+                const int i = k + 1 + e / (k + 1), j = e % (k + 1);
+                Ww[i * ldg + j] = dwc_sub(Ww[i * ldg + j], dwc_mul(Gw[i * ldg + k], Ww[k * ldg + j]));
+              }
+              __syncthreads();
+            }
+            // G^-1 = W^dag D^-1 W (Hermitian): entry (i, j), i <= j, is
+            // sum_{k >= j} conj(W[k][i]) W[k][j] / D[k], rounded once to FP32
+            for (int e = tid; e < M * M; e += NT) {
+              const int i = e / M, j = e - i * M;
+              if (i > j) continue;
+              DWC acc;
+              acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
+              for (int k = j; k < M; ++k)   // W[k][j] conj(W[k][i]) = conj of the term
+                acc = dwc_add(acc, dwc_scale(dwc_mul_conj(Ww[k * ldg + j], Ww[k * ldg + i]), dinv[k]));
+              const T re = acc.re.hi + acc.re.lo, im = acc.im.hi + acc.im.lo;
+              Gi[i * Mp + j] = cm<T2>(re, im);
+              if (i != j) Gi[j * Mp + i] = cm<T2>(re, -im);
+            }
+            __syncthreads();
+          } else {
+            // FP64 G = L D L^dag (unit lower L, right-looking, in place in Gd), then
+            // W = L^-1 (unit lower) and G^-1 = W^dag D^-1 W. One FP64 reciprocal per
+            // pivot (formed once and shared: FP64 runs at 2 FMA/clk/SM here) and two
+            // block barriers per elimination step.
+            double* dinv = misc + 96;     // [M] 1 / D[k]
+            // keep the diagonal of G: a pivot below 1e-13 of it is a numerical breakdown
+            for (int k = tid; k < M; k += NT) W[k * ldg] = Gd[k * ldg + k];
+            __syncthreads();
+            for (int k = 0; k < M; ++k) {
+              if (tid == 0) {
+                const double piv = Gd[k * ldg + k].x;
+                if (!(piv > 1e-13 * W[k * ldg].x) || !isfinite(piv) || piv < 1e-30) {
+                  misc[1] = 1.0;
+                  dinv[k] = 1.0;
+                } else {
+                  // reciprocal by Newton-Raphson, r <- r (2 - piv r), from the FP32
+                  // estimate: 24 -> 48 -> 96 correct bits, two FP64 FMA pairs on the
+                  // serial path instead of a full FP64 division
+                  double r = (double)(1.0f / (float)piv);
+                  r = r * fma(-piv, r, 2.0);
+                  r = r * fma(-piv, r, 2.0);
+                  dinv[k] = r;
+                }
+              }
+              __syncthreads();
+              const double rk = dinv[k];
+              const int w = M - k - 1;
+              // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k
+              for (int e = tid; e < w * (w + 1) / 2; e += NT) {
+                const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
+                const double2 x = Gd[i * ldg + k], y = Gd[j * ldg + k], g = Gd[i * ldg + j];
+                Gd[i * ldg + j] = mk(g.x - rk * (x.x * y.x + x.y * y.y), g.y - rk * (x.y * y.x - x.x * y.y));
+              }
+              __syncthreads();
+            }
+            if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
+            // unit lower L[i][k] = G[i][k] / D[k]; W = L^-1 row by row (unit diagonal)
+            for (int e = tid; e < M * M; e += NT) {
+              const int i = e / M, j = e - i * M;
+              W[i * ldg + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+              if (i > j) {
+                const double2 v = Gd[i * ldg + j];
+                Gd[i * ldg + j] = mk(v.x * dinv[j], v.y * dinv[j]);
               }
             }
             __syncthreads();
-            const double rk = dinv[k];
-            const int w = M - k - 1;
-            // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k
-            for (int e = tid; e < w * (w + 1) / 2; e += NT) {
-              const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
-              const double2 x = Gd[i * ldg + k], y = Gd[j * ldg + k], g = Gd[i * ldg + j];
-              Gd[i * ldg + j] = mk(g.x - rk * (x.x * y.x + x.y * y.y), g.y - rk * (x.y * y.x - x.x * y.y));
+            for (int k = 0; k < M - 1; ++k) {
+              // rows i > k: W[i][j] -= L[i][k] W[k][j], j <= k (W[k] is final)
+              const int rows = M - k - 1;
+              for (int e = tid; e < rows * (k + 1); e += NT) {
+                const int i = k + 1 + e / (k + 1), j = e % (k + 1);
+                const double2 l = Gd[i * ldg + k], wv = W[k * ldg + j], o = W[i * ldg + j];
+                W[i * ldg + j] = mk(o.x - (l.x * wv.x - l.y * wv.y), o.y - (l.x * wv.y + l.y * wv.x));
+              }
+              __syncthreads();
+            }
+            // G^-1 = W^dag D^-1 W (Hermitian), rounded once to the bulk precision
+            for (int e = tid; e < M * M; e += NT) {
+              const int i = e / M, j = e - i * M;
+              if (i > j) continue;
+              double re = 0.0, im = 0.0;
+              for (int k = j; k < M; ++k) {          // W[k][i], W[k][j] nonzero for k >= max(i, j) = j
+                const double2 x = W[k * ldg + i], y = W[k * ldg + j];   // conj(x) y / D[k]
+                re += dinv[k] * (x.x * y.x + x.y * y.y);
+                im += dinv[k] * (x.x * y.y - x.y * y.x);
+              }
+              Gi[i * Mp + j] = cm<T2>((T)re, (T)im);
+              if (i != j) Gi[j * Mp + i] = cm<T2>((T)re, (T)-im);
             }
             __syncthreads();
           }
-          if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
-          // unit lower L[i][k] = G[i][k] / D[k]; W = L^-1 row by row (unit diagonal)
-          for (int e = tid; e < M * M; e += NT) {
-            const int i = e / M, j = e - i * M;
-            W[i * ldg + j] = mk(i == j ? 1.0 : 0.0, 0.0);
-            if (i > j) {
-              const double2 v = Gd[i * ldg + j];
-              Gd[i * ldg + j] = mk(v.x * dinv[j], v.y * dinv[j]);
-            }
-          }
-          __syncthreads();
-          for (int k = 0; k < M - 1; ++k) {
-            // rows i > k: W[i][j] -= L[i][k] W[k][j], j <= k (W[k] is final)
-            const int rows = M - k - 1;
-            for (int e = tid; e < rows * (k + 1); e += NT) {
-              const int i = k + 1 + e / (k + 1), j = e % (k + 1);
-              const double2 l = Gd[i * ldg + k], wv = W[k * ldg + j], o = W[i * ldg + j];
-              W[i * ldg + j] = mk(o.x - (l.x * wv.x - l.y * wv.y), o.y - (l.x * wv.y + l.y * wv.x));
-            }
-            __syncthreads();
-          }
-          // G^-1 = W^dag D^-1 W (Hermitian), rounded once to the bulk precision
-          T2* Gi = reinterpret_cast<T2*>(Gd);   // L is no longer needed: reuse its storage
-          for (int e = tid; e < M * M; e += NT) {
-            const int i = e / M, j = e - i * M;
-            if (i > j) continue;
-            double re = 0.0, im = 0.0;
-            for (int k = j; k < M; ++k) {          // W[k][i], W[k][j] nonzero for k >= max(i, j) = j
-              const double2 x = W[k * ldg + i], y = W[k * ldg + j];   // conj(x) y / D[k]
-              re += dinv[k] * (x.x * y.x + x.y * y.y);
-              im += dinv[k] * (x.x * y.y - x.y * y.x);
-            }
-            Gi[i * Mp + j] = cm<T2>((T)re, (T)im);
-            if (i != j) Gi[j * Mp + i] = cm<T2>((T)re, (T)-im);
-          }
-          __syncthreads();
           // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
           const double sk[2] = {0.5 * d.kappa, 0.5 * d.gamma};
           for (int e = tid; e < 2 * MM; e += NT) {
