@@ -435,6 +435,23 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           // arithmetic is independent of which warp runs it, so results stay bitwise
           // reproducible
           int* task_ctr = reinterpret_cast<int*>(misc + 140);
+          if (tid == NT - 1) {
+            // drive coefficient of this stage (FP64 pulse shape), off the serial
+            // M x M phase: read by phase F after the barriers that follow
+            const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
+            if (FRAME) {
+              // RWA drive w r + conj(w) r^dag, w = (Omega/2) e^{i phi}
+              const double2 w = pulse_rwa_drive(pulse, a.rp.tau, ts);
+              misc[0] = w.x;
+              misc[2] = w.y;
+            } else {
+              misc[0] = pulse_coefficient(pulse, a.rp.tau, ts);
+              misc[2] = 0.0;
+            }
+            T* tb = reinterpret_cast<T*>(misc + 128);
+            tb[0] = (T)misc[0];
+            tb[5] = (T)misc[2];
+          }
           for (;;) {
             int task = 0;
             if (lane == 0) task = atomicAdd(task_ctr, 1);
@@ -710,27 +727,15 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             misc[64 + tid] = s;
           }
           if (tid == 0) {
-            const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
-            if (FRAME) {
-              // RWA drive w r + conj(w) r^dag, w = (Omega/2) e^{i phi}
-              const double2 w = pulse_rwa_drive(pulse, a.rp.tau, ts);
-              misc[0] = w.x;
-              misc[2] = w.y;
-            } else {
-              misc[0] = pulse_coefficient(pulse, a.rp.tau, ts);
-              misc[2] = 0.0;
-            }
             misc[1] = 0.0;   // not-PD flag
             *reinterpret_cast<int*>(misc + 140) = 0;   // phase-P task counter of the next stage
             // bulk-precision copies: coefficient, step sizes split as hi + lo
             T* tb = reinterpret_cast<T*>(misc + 128);
             const double hs = stage == 2 ? dt : 0.5 * dt, h6 = dt / 6.0;
-            tb[0] = (T)misc[0];
             tb[1] = (T)hs;
             tb[2] = (T)(hs - (double)tb[1]);
             tb[3] = (T)h6;
             tb[4] = (T)(h6 - (double)tb[3]);
-            tb[5] = (T)misc[2];
           }
           __syncthreads();
           if (record && q == 0 && a.p.gsnap) {
@@ -779,49 +784,54 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               if (i == j) diag0[i * ldg * 4] = (float)v.x;
               Gw[i * ldg + j] = g;
             }
+            // pivot k: breakdown check against the original diagonal, then 1 / D[k]
+            auto pivot = [&](int k) {
+              const DW piv = Gw[k * ldg + k].re;
+              if (!(piv.hi > 1e-13f * diag0[k * ldg * 4]) || !isfinite(piv.hi) || piv.hi < 1e-30f) {
+                misc[1] = 1.0;
+                dinv[k].hi = 1.0f;
+                dinv[k].lo = 0.0f;
+              } else {
+                dinv[k] = dw_recip(piv);
+              }
+            };
+            __syncthreads();
+            if (tid == 0) pivot(0);
             __syncthreads();
             for (int k = 0; k < M; ++k) {
-              if (tid == 0) {
-                const DW piv = Gw[k * ldg + k].re;
-                if (!(piv.hi > 1e-13f * diag0[k * ldg * 4]) || !isfinite(piv.hi) || piv.hi < 1e-30f) {
-                  misc[1] = 1.0;
-                  dinv[k].hi = 1.0f;
-                  dinv[k].lo = 0.0f;
-                } else {
-                  dinv[k] = dw_recip(piv);
-                }
-              }
-              __syncthreads();
               const DW rk = dinv[k];
               const int w = M - k - 1;
-              // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k
+              // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k;
+              // entry 0 (the next pivot) belongs to thread 0, which then forms
+              // 1 / D[k+1] before the barrier: one barrier per elimination step
               for (int e = tid; e < w * (w + 1) / 2; e += NT) {
                 const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
                 const DWC t = dwc_scale(dwc_mul_conj(Gw[i * ldg + k], Gw[j * ldg + k]), rk);
                 Gw[i * ldg + j] = dwc_sub(Gw[i * ldg + j], t);
               }
+              if (tid == 0 && k + 1 < M) pivot(k + 1);
               __syncthreads();
             }
             if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
-            // unit lower L[i][k] = G[i][k] / D[k]; W = L^-1 row by row (unit diagonal)
-            for (int e = tid; e < M * M; e += NT) {
-              const int i = e / M, j = e - i * M;
-              DWC o;
-              o.re.hi = i == j ? 1.0f : 0.0f;
-              o.re.lo = o.im.hi = o.im.lo = 0.0f;
-              Ww[i * ldg + j] = o;
-              if (i > j) Gw[i * ldg + j] = dwc_scale(Gw[i * ldg + j], dinv[j]);
+            // W = L^-1 (unit lower, L[i][k] = G[i][k] / D[k]) by columns: column j
+            // by warp j mod NWARP, lane i = row i, forward substitution
+            // W[i][j] = delta_ij - sum_{j <= k < i} L[i][k] W[k][j] with W[k][j]
+            // broadcast from lane k (no block barrier)
+            for (int j = warp; j < M; j += NWARP) {
+              DWC wv;
+              wv.re.hi = lane == j ? 1.0f : 0.0f;
+              wv.re.lo = wv.im.hi = wv.im.lo = 0.0f;
+              for (int k = j; k < M - 1; ++k) {
+                DWC wk;
+                wk.re.hi = __shfl_sync(0xffffffffu, wv.re.hi, k);
+                wk.re.lo = __shfl_sync(0xffffffffu, wv.re.lo, k);
+                wk.im.hi = __shfl_sync(0xffffffffu, wv.im.hi, k);
+                wk.im.lo = __shfl_sync(0xffffffffu, wv.im.lo, k);
+                if (lane > k && lane < M) wv = dwc_sub(wv, dwc_mul(dwc_scale(Gw[lane * ldg + k], dinv[k]), wk));
+              }
+              if (lane < M) Ww[lane * ldg + j] = wv;
             }
             __syncthreads();
-            for (int k = 0; k < M - 1; ++k) {
-              // rows i > k: W[i][j] -= L[i][k] W[k][j], j <= k (W[k] is final)
-              const int rows = M - k - 1;
-              for (int e = tid; e < rows * (k + 1); e += NT) {
-                const int i = k + 1 + e / (k + 1), j = e % (k + 1);
-                Ww[i * ldg + j] = dwc_sub(Ww[i * ldg + j], dwc_mul(Gw[i * ldg + k], Ww[k * ldg + j]));
-              }
-              __syncthreads();
-            }
             // G^-1 = W^dag D^-1 W (Hermitian): entry (i, j), i <= j, is
             // sum_{k >= j} conj(W[k][i]) W[k][j] / D[k], rounded once to FP32
             for (int e = tid; e < M * M; e += NT) {
