@@ -962,6 +962,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           const T* tb = reinterpret_cast<const T*>(misc + 128);
           const T c = tb[0], hs_hi = tb[1], hs_lo = tb[2], h6_hi = tb[3], h6_lo = tb[4], ci = tb[5];
           constexpr bool rwa = FRAME != 0;
+          // Z_n rows start on 16-byte boundaries for the paired FP32 accesses
+          const bool zn_vec = sizeof(T2) == 8 && (M % 2) == 0 && (d.z_off % 2) == 0;
           const int nxt = cur ^ 1;
           const int mq = Mp / 4;
           const int nrt_all = (P.R + TR - 1) / TR;
@@ -1301,6 +1303,19 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                     hi[u] = fma(wr, v[u].y, fma(wi, v[u].x, hi[u]));
                   }
                 };
+                // Rows (it, ir -+ 1, iff), wherever their owner keeps them; the
+                // other resonator neighbours are constant offsets from these two:
+                // one transmon slab (the owner's P.st rows) or one row away.
+                const T2* pl[2] = {nullptr, nullptr};
+                size_t sl[2] = {0, 0};
+                if (ir > 0) {
+                  pl[0] = zrow(cur, it, ir - 1, iff);
+                  sl[0] = (size_t)(ir - 1 < P.r_lo ? Pm.st : P.st) * lds;
+                }
+                if (ir + 1 < Nr) {
+                  pl[1] = zrow(cur, it, ir + 1, iff);
+                  sl[1] = (size_t)(ir + 1 >= P.r_lo + P.nr ? Pp.st : P.st) * lds;
+                }
                 // g (b + b^dag)(a + a^dag)
 #pragma unroll
                 for (int sa = -1; sa <= 1; sa += 2) {
@@ -1312,7 +1327,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                     const int ir2 = ir + sb2;
                     if (ir2 < 0 || ir2 >= Nr) continue;
                     if (rwa && sa == sb2) continue;   // RWA: g (b^dag a + b a^dag) only
-                    add_row(zrow(cur, it2, ir2, iff) + m0, ct * sq[max(ir, ir2)]);
+                    const int h = sb2 > 0;
+                    add_row((sa > 0 ? pl[h] + sl[h] : pl[h] - sl[h]) + m0, ct * sq[max(ir, ir2)]);
                   }
                 }
                 if (three) {
@@ -1322,12 +1338,13 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                     const int ir2 = ir + sa;
                     if (ir2 < 0 || ir2 >= Nr) continue;
                     const T cr = J * sq[max(ir, ir2)];
+                    const int h = sa > 0;
 #pragma unroll
                     for (int sb2 = -1; sb2 <= 1; sb2 += 2) {
                       const int if2 = iff + sb2;
                       if (if2 < 0 || if2 >= Nf) continue;
                       if (rwa && sa == sb2) continue;   // RWA: J (a^dag f + a f^dag) only
-                      add_row(zrow(cur, it, ir2, if2) + m0, cr * sq[max(iff, if2)]);
+                      add_row((sb2 > 0 ? pl[h] + lds : pl[h] - lds) + m0, cr * sq[max(iff, if2)]);
                     }
                   }
                   // drive on the filter
@@ -1403,6 +1420,58 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               const int n = nrow[r];
               if (n < 0) continue;
               T2 zo[4];
+              if constexpr (sizeof(T2) == 8) {
+                // FP32 state: columns in pairs, 16-byte loads and stores (Z_n rows
+                // are 16-byte aligned when M and the trajectory offset are even;
+                // accumulator rows, of Mp = 4k columns, always are)
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                  const int u0 = 2 * pr, m = m0 + u0;
+                  if (m >= M) {
+                    zo[u0] = zo[u0 + 1] = cm<T2>(0, 0);
+                    continue;
+                  }
+                  const bool two = m + 1 < M;
+                  const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
+                  T2 zn0, zn1 = cm<T2>(0, 0);
+                  if (zn_vec) {
+                    const float4 v = *reinterpret_cast<const float4*>(Zn + oz);
+                    zn0 = cm<T2>(v.x, v.y);
+                    zn1 = cm<T2>(v.z, v.w);
+                  } else {
+                    zn0 = Zn[oz];
+                    if (two) zn1 = Zn[oz + 1];
+                  }
+                  float4* ap = reinterpret_cast<float4*>(accg + oa);
+                  const T f0r = fr[r][u0], f0i = fi[r][u0], f1r = fr[r][u0 + 1], f1i = fi[r][u0 + 1];
+                  if (stage < 3) {
+                    if (stage == 0) {
+                      *ap = make_float4(f0r, f0i, f1r, f1i);
+                    } else {
+                      const float4 ac = *ap;
+                      *ap = make_float4(fma((T)2, f0r, ac.x), fma((T)2, f0i, ac.y), fma((T)2, f1r, ac.z),
+                                        fma((T)2, f1i, ac.w));
+                    }
+                    zo[u0] = cm<T2>(zn0.x + fma(hs_lo, f0r, hs_hi * f0r), zn0.y + fma(hs_lo, f0i, hs_hi * f0i));
+                    zo[u0 + 1] = two ? cm<T2>(zn1.x + fma(hs_lo, f1r, hs_hi * f1r), zn1.y + fma(hs_lo, f1i, hs_hi * f1i))
+                                     : cm<T2>(0, 0);
+                  } else {
+                    const float4 ac = *ap;
+                    const T s0r = ac.x + f0r, s0i = ac.y + f0i, s1r = ac.z + f1r, s1i = ac.w + f1i;
+                    zo[u0] = cm<T2>(zn0.x + fma(h6_lo, s0r, h6_hi * s0r), zn0.y + fma(h6_lo, s0i, h6_hi * s0i));
+                    zo[u0 + 1] = two ? cm<T2>(zn1.x + fma(h6_lo, s1r, h6_hi * s1r), zn1.y + fma(h6_lo, s1i, h6_hi * s1i))
+                                     : cm<T2>(0, 0);
+                    if (zn_vec) {
+                      *reinterpret_cast<float4*>(Zn + oz) = make_float4(zo[u0].x, zo[u0].y, zo[u0 + 1].x, zo[u0 + 1].y);
+                    } else {
+                      Zn[oz] = zo[u0];
+                      if (two) Zn[oz + 1] = zo[u0 + 1];
+                    }
+                  }
+                }
+                store4<ZSM>(own(nxt, l0 + r) + m0, zo);
+                continue;
+              }
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const int m = m0 + u;
