@@ -1394,7 +1394,40 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               }
             }
             // projection terms: + sr (rZ_s) XT_r + sb (bZ_s) XT_b
-            if constexpr (TC == 0) {
+            if constexpr (TC == 0 && ZSM == 0 && sizeof(T2) == 8) {
+              // FP32 state in L2: k in pairs with 16-byte loads of the Y rows
+              // (Mp-wide, 32-byte aligned) and of XT; the padding columns and rows
+              // up to Mp are zero, and every accumulator sees the same k order
+              for (int k = 0; k < Mp; k += 2) {
+                float4 yr2[TR], yb2[TR];
+#pragma unroll
+                for (int r = 0; r < TR; ++r) {
+                  yr2[r] = *reinterpret_cast<const float4*>(yrp[r] + k);
+                  yb2[r] = *reinterpret_cast<const float4*>(ybp[r] + k);
+                }
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                  const float4* xrp = reinterpret_cast<const float4*>(XT + (k + kk) * Mp + m0);
+                  const float4* xbp = reinterpret_cast<const float4*>(XT + MM + (k + kk) * Mp + m0);
+                  const float4 xa0 = xrp[0], xa1 = xrp[1], xb0 = xbp[0], xb1 = xbp[1];
+                  const T2 xr[4] = {cm<T2>(xa0.x, xa0.y), cm<T2>(xa0.z, xa0.w), cm<T2>(xa1.x, xa1.y),
+                                    cm<T2>(xa1.z, xa1.w)};
+                  const T2 xb[4] = {cm<T2>(xb0.x, xb0.y), cm<T2>(xb0.z, xb0.w), cm<T2>(xb1.x, xb1.y),
+                                    cm<T2>(xb1.z, xb1.w)};
+#pragma unroll
+                  for (int r = 0; r < TR; ++r) {
+                    const T y0x = kk ? yr2[r].z : yr2[r].x, y0y = kk ? yr2[r].w : yr2[r].y;
+                    const T y1x = kk ? yb2[r].z : yb2[r].x, y1y = kk ? yb2[r].w : yb2[r].y;
+                    const T ar = sr[r] * y0x, ai = sr[r] * y0y, br = sb[r] * y1x, bi = sb[r] * y1y;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                      fr[r][u] = fma(ar, xr[u].x, fma(-ai, xr[u].y, fma(br, xb[u].x, fma(-bi, xb[u].y, fr[r][u]))));
+                      fi[r][u] = fma(ar, xr[u].y, fma(ai, xr[u].x, fma(br, xb[u].y, fma(bi, xb[u].x, fi[r][u]))));
+                    }
+                  }
+                }
+              }
+            } else if constexpr (TC == 0) {
             for (int k = 0; k < M; ++k) {
               T2 xr[4], xb[4];
 #pragma unroll
