@@ -352,6 +352,10 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
     const int tj = a.order[it_idx];
     const TrajDev d = a.p.traj[tj];
     const int M = d.M;
+    // this trajectory's rank padded to 4: the extent of its tile grids and
+    // column quads (storage keeps the batch-wide stride Mp; the tensor-core
+    // GEMM spans all of Mp)
+    const int Mq = TC > 0 ? Mp : (M + 3) / 4 * 4;
     const Part P = part_of(d, C, q);
     const Part Pm = part_of(d, C, q > 0 ? q - 1 : q);
     const Part Pp = part_of(d, C, q < C - 1 ? q + 1 : q);
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
 
         // ================= P: partial sums over own rows of Z_s[cur]
         {
-          const int nt_ = Mp / TP;
+          const int nt_ = Mq / TP;
           const int n_g = nt_ * (nt_ + 1) / 2, n_t = nt_ * nt_;
           // warps take tasks dynamically (heavier Gram tiles first); every task's
           // arithmetic is independent of which warp runs it, so results stay bitwise
@@ -675,9 +679,9 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
 
         // ================= R: reduce in rank order, FP64 Cholesky and inverse
         {
-          const int MM = Mp * Mp;
-          for (int e = tid; e < 3 * MM; e += NT) {
-            const int mat = e / MM, ij = e - mat * MM, i = ij / Mp, j = ij - i * Mp;
+          const int MM = Mp * Mp, MMq = Mq * Mq;
+          for (int e = tid; e < 3 * MMq; e += NT) {
+            const int mat = e / MMq, iq = e - mat * MMq, i = iq / Mq, j = iq - i * Mq, ij = i * Mp + j;
             if (mat == 0) {
               if (i > j || j >= M) continue;
               // issue the remote loads four at a time, then sum in rank order
@@ -920,8 +924,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           }
           // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
           const double sk[2] = {0.5 * d.kappa, 0.5 * d.gamma};
-          for (int e = tid; e < 2 * MM; e += NT) {
-            const int k = e / MM, lm = e - k * MM, l = lm / Mp, m = lm - l * Mp;
+          for (int e = tid; e < 2 * Mq * Mq; e += NT) {
+            const int k = e / (Mq * Mq), lq = e - k * (Mq * Mq), l = lq / Mq, m = lq - l * Mq, lm = l * Mp + m;
             T xr = 0, xi = 0;
             if (l < M && m < M) {
               const T2* Tk = Tred + k * MM;
@@ -965,7 +969,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           // Z_n rows start on 16-byte boundaries for the paired FP32 accesses
           const bool zn_vec = sizeof(T2) == 8 && (M % 2) == 0 && (d.z_off % 2) == 0;
           const int nxt = cur ^ 1;
-          const int mq = Mp / 4;
+          const int mq = Mq / 4;
           const int nrt_all = (P.R + TR - 1) / TR;
           const T g = (T)d.g, J = (T)d.J, ka = (T)d.kappa, ga = (T)d.gamma;
           const int MM = Mp * Mp;
@@ -1398,7 +1402,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               // FP32 state in L2: k in pairs with 16-byte loads of the Y rows
               // (Mp-wide, 32-byte aligned) and of XT; the padding columns and rows
               // up to Mp are zero, and every accumulator sees the same k order
-              for (int k = 0; k < Mp; k += 2) {
+              for (int k = 0; k < Mq; k += 2) {
                 float4 yr2[TR], yb2[TR];
 #pragma unroll
                 for (int r = 0; r < TR; ++r) {
