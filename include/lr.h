@@ -202,7 +202,17 @@ lr_status lr_get_state(lr_ctx* ctx, int traj, double* host_Z, void* stream);
 /* Advance every trajectory by n_steps RK4 steps of size dt from the current
  * step counter (t = step * dt), recording beta at every step and the other
  * observables every pop_every steps, then recompute eps_a of every candidate
- * over [0, step*dt]. dt must not change within one pulse run. Async. */
+ * over [0, step*dt]. dt must not change within one pulse run. Async.
+ *
+ * CUDA graphs (FUSED engine): the call may be captured into a CUDA graph on
+ * `stream` (it then issues three kernels: the persistent integrator, the
+ * eps_a epilogue and a one-thread step advance, with no copy or host sync).
+ * The step counter lives in device memory, so every replay of the graph
+ * continues the pulse run by n_steps. A replay that would pass max_steps
+ * runs nothing and leaves LR_ERR_STATE for the next synchronising call.
+ * Capture does not execute, but it advances the host's copy of the counter:
+ * call lr_sync after capturing, and after replays, to bring it back in line
+ * with the device. The PLAIN engine refuses capture (LR_ERR_UNSUPPORTED). */
 lr_status lr_integrate(lr_ctx* ctx, double dt, long n_steps, void* stream);
 
 /* Copy recorded observables out (any pointer may be NULL to skip it; each
@@ -244,7 +254,9 @@ lr_status lr_loss(lr_ctx* ctx, double* ionization, double* loss, void* stream);
  * LR_ERR_STATE without record_gram, LR_ERR_CUDA. */
 lr_status lr_diagnostics(lr_ctx* ctx, double* purity, double* eig, void* stream);
 
-/* Synchronise the stream and return the device error word's status. */
+/* Synchronise the stream, update the host's copy of the step counter from
+ * the device (after CUDA graph replays) and return the device error word's
+ * status. */
 lr_status lr_sync(lr_ctx* ctx, void* stream);
 
 /* Gradient of the assignment errors with respect to the pulse parameters,

@@ -28,7 +28,7 @@ struct lr_ctx {
   // workspace layout (byte offsets)
   size_t o_traj = 0, o_pulse = 0, o_err = 0, o_zn = 0, o_za = 0, o_zb = 0, o_acc = 0, o_x = 0, o_part = 0,
          o_beta = 0, o_pops = 0, o_nphot = 0, o_trace = 0, o_eps = 0, o_ion = 0, o_loss = 0, o_scratch = 0,
-         o_gsnap = 0, o_dpur = 0, o_deig = 0, total = 0;
+         o_gsnap = 0, o_dpur = 0, o_deig = 0, o_dstep = 0, total = 0;
   size_t scratch_bytes = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -75,6 +75,7 @@ DevPtrs dev_ptrs(const lr_ctx* c) {
   p.scratch = c->scratch_bytes ? w + c->o_scratch : nullptr;
   p.scratch_bytes = (long long)c->scratch_bytes;
   p.gsnap = c->opt.record_gram ? reinterpret_cast<double2*>(w + c->o_gsnap) : nullptr;
+  p.dstep = reinterpret_cast<long long*>(w + c->o_dstep);
   return p;
 }
 
@@ -96,6 +97,15 @@ RunParams run_params(const lr_ctx* c) {
 
 bool ready(lr_ctx* c) { return c->ws != nullptr; }
 
+// The host copy of the step counter from the device one (graph replays advance
+// only the device counter).
+cudaError_t refresh_step(lr_ctx* c) {
+  long long v = 0;
+  cudaError_t e = cudaMemcpy(&v, c->ws + c->o_dstep, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) c->step = (long)v;
+  return e;
+}
+
 lr_status check_device_error(lr_ctx* c) {
   unsigned e = 0;
   cudaError_t ce = cudaMemcpy(&e, c->ws + c->o_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
@@ -105,6 +115,8 @@ lr_status check_device_error(lr_ctx* c) {
     case lr::DEV_NOT_PD: return fail(c, LR_ERR_NOT_PD, "Gram matrix lost positive definiteness (Cholesky breakdown)");
     case lr::DEV_NONFINITE: return fail(c, LR_ERR_NONFINITE, "non-finite value in the state or readout signal");
     case lr::DEV_TIMEOUT: return fail(c, LR_ERR_TIMEOUT, "a device-side wait ran out of its budget");
+    case lr::DEV_CAPACITY:
+      return fail(c, LR_ERR_STATE, "an integrate (e.g. a replayed graph) would have passed max_steps; it did not run");
     default: return fail(c, LR_ERR_CUDA, "unknown device error word");
   }
 }
@@ -219,6 +231,7 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   c->o_pops = take(sizeof(double) * (size_t)c->n_traj * c->n_rec * c->nt_max);
   c->o_nphot = take(sizeof(double) * (size_t)c->n_traj * c->n_rec);
   c->o_trace = take(sizeof(double) * (size_t)c->n_traj * c->n_rec);
+  c->o_dstep = take(sizeof(long long));
   c->o_eps = take(sizeof(double) * n_cand);
   c->o_ion = take(sizeof(double) * n_cand);
   c->o_loss = take(sizeof(double) * n_cand);
@@ -259,6 +272,12 @@ lr_status lr_bind_workspace(lr_ctx* c, void* dev_ptr, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(c, e, "copying trajectory table");
   e = cudaMemset(c->ws + c->o_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) return cuda_fail(c, e, "clearing error word");
+  e = cudaMemset(c->ws + c->o_dstep, 0, sizeof(long long));
+  if (e != cudaSuccess) return cuda_fail(c, e, "clearing the step counter");
+  if (c->engine == LR_ENGINE_FUSED) {
+    e = lr::fused_prepare(c->fused, c->opt.precision, c->ws + c->o_scratch, c->n_traj);
+    if (e != cudaSuccess) return cuda_fail(c, e, "preparing the fused engine");
+  }
   if (c->opt.record_gram) {
     // records that no run writes stay zero matrices
     e = cudaMemset(c->ws + c->o_gsnap, 0,
@@ -306,6 +325,8 @@ lr_status lr_set_initial(lr_ctx* c, uint64_t seed, double eps, void* stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "initial state kernel");
   e = cudaMemsetAsync(c->ws + c->o_err, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "clearing error word");
+  e = cudaMemsetAsync(c->ws + c->o_dstep, 0, sizeof(long long), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "clearing the step counter");
   const size_t es = c->opt.precision == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
   e = cudaMemcpyAsync(c->ws + c->o_z0, c->ws + c->o_zn, es * c->tot_elems, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "keeping the initial state");
@@ -336,6 +357,8 @@ lr_status lr_set_state(lr_ctx* c, int traj, const double* host_Z, long step, voi
     e = cudaMemcpyAsync(c->ws + c->o_z0 + es * d.z_off, c->ws + c->o_zn + es * d.z_off, es * n,
                         cudaMemcpyDeviceToDevice, s);
   }
+  const long long dstep = step;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->ws + c->o_dstep, &dstep, sizeof(dstep), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "setting state");
   if (step != c->step) c->step = step;
@@ -376,6 +399,10 @@ lr_status lr_integrate(lr_ctx* c, double dt, long n_steps, void* stream) {
   if (c->step > 0 && c->dt != 0.0 && c->dt != dt) return fail(c, LR_ERR_STATE, "dt changed within a pulse run");
   c->dt = dt;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "capture status");
+  if (cap != cudaStreamCaptureStatusNone && c->engine != LR_ENGINE_FUSED)
+    return fail(c, LR_ERR_UNSUPPORTED, "graph capture of lr_integrate needs the fused engine");
   DevPtrs p = dev_ptrs(c);
   RunParams rp = run_params(c);
   cudaError_t e;
@@ -385,7 +412,7 @@ lr_status lr_integrate(lr_ctx* c, double dt, long n_steps, void* stream) {
     e = lr::fused_integrate(c->fused, p, rp, c->opt.precision, c->step, n_steps, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "integrate launch");
   c->step += n_steps;
-  e = lr::launch_eps_a(p, run_params(c), c->step, s);
+  e = lr::launch_eps_a(p, rp, n_steps, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "eps_a launch");
   return LR_OK;
 }
@@ -409,6 +436,7 @@ lr_status lr_observables(lr_ctx* c, double* beta, double* pops, double* nphot, d
     if (e != cudaSuccess) return cuda_fail(c, e, "copying observables");
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = refresh_step(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronising");
   return check_device_error(c);
 }
@@ -430,6 +458,11 @@ lr_status lr_diagnostics(lr_ctx* c, double* purity, double* eig, void* stream) {
   if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
   if (!c->opt.record_gram) return fail(c, LR_ERR_STATE, "lr_diagnostics needs lr_options.record_gram = 1");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    cudaError_t e0 = cudaStreamSynchronize(s);
+    if (e0 == cudaSuccess) e0 = refresh_step(c);
+    if (e0 != cudaSuccess) return cuda_fail(c, e0, "synchronising");
+  }
   const size_t nr = (size_t)c->n_traj * c->n_rec;
   double* dpur = reinterpret_cast<double*>(c->ws + c->o_dpur);
   double* deig = reinterpret_cast<double*>(c->ws + c->o_deig);
@@ -450,6 +483,7 @@ lr_status lr_sync(lr_ctx* c, void* stream) {
   if (!c) return LR_ERR_ARG;
   if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = refresh_step(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronising");
   return check_device_error(c);
 }
@@ -468,6 +502,11 @@ lr_status lr_backward(lr_ctx* c, void* dev_ws, size_t ws_bytes, const double* d_
                       int ckpt_every, void* stream) {
   if (!c || !d_eps_a || !d_theta || ckpt_every < 1) return LR_ERR_ARG;
   if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
+  {
+    cudaError_t e0 = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e0 == cudaSuccess) e0 = refresh_step(c);
+    if (e0 != cudaSuccess) return cuda_fail(c, e0, "synchronising");
+  }
   if (!c->have_pulse || !c->z0_valid || c->step < 1 || !(c->dt > 0.0))
     return fail(c, LR_ERR_STATE, "lr_backward needs a pulse run integrated from step 0 of a kept initial state");
   if (c->opt.frame != 0) return fail(c, LR_ERR_UNSUPPORTED, "lr_backward supports the lab frame only");

@@ -125,9 +125,14 @@ cudaError_t launch_initial_state(const DevPtrs& p, const RunParams& rp, int /*ma
 
 // One block per candidate: trapezoid of |beta_e - beta_g|^2 over the step grid,
 // SNR = sqrt(2 eta kappa S), eps_a = erfc(SNR/2)/2 + tau gamma/2.
-__global__ void __launch_bounds__(ET) eps_a_kernel(DevPtrs p, RunParams rp, long step) {
+__global__ void __launch_bounds__(ET) eps_a_kernel(DevPtrs p, RunParams rp, long n_added) {
   __shared__ double sh[33];
   const int c = blockIdx.x;
+  const long step = (long)*p.dstep + n_added;
+  if (step < 0 || step > rp.max_steps) {   // the integrate before it refused to run past capacity
+    if (c == 0 && threadIdx.x == 0) set_error(p.err, DEV_CAPACITY);
+    return;
+  }
   const TrajDev d = p.traj[2 * c];
   const double2* bg = p.beta + (size_t)(2 * c) * (rp.max_steps + 1);
   const double2* be = p.beta + (size_t)(2 * c + 1) * (rp.max_steps + 1);
@@ -164,8 +169,19 @@ __global__ void __launch_bounds__(ET) eps_a_kernel(DevPtrs p, RunParams rp, long
   }
 }
 
-cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long step, cudaStream_t s) {
-  eps_a_kernel<<<rp.n_cand, ET, 0, s>>>(p, rp, step);
+// Advance the device step counter once every block of eps_a_kernel has read it
+// (a kernel of its own, ordered after it in the stream); a run past capacity
+// leaves the counter where it was.
+__global__ void advance_step_kernel(long long* dstep, long n_added, long max_steps) {
+  const long long s = *dstep + n_added;
+  if (s >= 0 && s <= max_steps) *dstep = s;
+}
+
+cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long n_added, cudaStream_t s) {
+  eps_a_kernel<<<rp.n_cand, ET, 0, s>>>(p, rp, n_added);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  advance_step_kernel<<<1, 1, 0, s>>>(p.dstep, n_added, rp.max_steps);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,17 @@ const void* kernel_ptr(lr_precision prec, int zs_smem, int tc, int frame) {
   return (const void*)fz::fused_kernel<float2, 1, 0, 0, 0>;
 }
 
+// Raise (never lower) a kernel's dynamic shared-memory limit, so that contexts
+// planned later cannot shrink it under a context (or a captured graph) that
+// needs more.
+cudaError_t raise_smem_limit(const void* kern, int bytes) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 int rows_per_cta(const TrajDev& d, int C) {
   return d.Nt * ((d.Nr + C - 1) / C) * d.Nf;
 }
@@ -149,7 +160,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
       for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
       const SmemLayout L = layout(R, Mp, zs_smem, es, tc);
       if (L.total > smem_max) continue;
-      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total) != cudaSuccess) {
+      if (raise_smem_limit(kern, L.total) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
@@ -229,6 +240,17 @@ size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj) {
   return b;
 }
 
+cudaError_t fused_prepare(const FusedPlan& plan, lr_precision prec, void* scratch, int n_traj) {
+  cudaError_t e = cudaMemcpy(scratch, plan.order.data(), sizeof(int) * n_traj, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es, plan.tc);
+  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame);
+  e = raise_smem_limit(kern, L.total);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunParams& rp, lr_precision prec,
                             long step0, long n_steps, cudaStream_t s) {
   const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
@@ -268,12 +290,18 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
     off += ((2 * (size_t)plan.R * (plan.Mp + 1) * es * plan.C * plan.n_clusters + 255) / 256) * 256;
   }
   a.acc_glob = sc + off;
-  cudaError_t e = cudaMemcpyAsync(sc, plan.order.data(), sizeof(int) * rp.n_traj, cudaMemcpyHostToDevice, s);
+  // the trajectory order is in the scratch since fused_prepare; the kernel's
+  // attributes are raised here only outside a stream capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
   if (e != cudaSuccess) return e;
-  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame);
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-  if (e != cudaSuccess) return e;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (cap == cudaStreamCaptureStatusNone) {
+    const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame);
+    e = raise_smem_limit(kern, L.total);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.C * plan.n_clusters);
   cfg.blockDim = dim3(fz::NT);

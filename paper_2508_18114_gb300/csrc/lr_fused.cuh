@@ -37,6 +37,10 @@ struct FusedPlan {
 // Needs a CUDA device (occupancy queries); returns false without one.
 bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, FusedPlan* plan);
 size_t fused_scratch_bytes(const FusedPlan& plan, int n_traj);
+// Once the workspace is bound: upload the trajectory order to the scratch and
+// raise the kernel's shared-memory limit (synchronous), so that fused_integrate
+// makes no host-to-device copy and can be captured in a CUDA graph.
+cudaError_t fused_prepare(const FusedPlan& plan, lr_precision prec, void* scratch, int n_traj);
 cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunParams& rp, lr_precision prec,
                             long step0, long n_steps, cudaStream_t s);
 

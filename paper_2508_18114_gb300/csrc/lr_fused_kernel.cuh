@@ -274,6 +274,15 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   using T = typename Real<T2>::t;
   constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
   constexpr int TR = sizeof(T) == 4 ? 4 : 2;     // phase-F rows per thread tile
+  // first step of this launch: the device step counter (so that a replayed
+  // capture of the launch continues the pulse run), else the argument
+  const long step0 = a.p.dstep ? (long)*a.p.dstep : a.step0;
+  if (step0 < 0 || step0 + a.n_steps > a.rp.max_steps) {
+    // every thread of every CTA reads the same value: the whole grid leaves
+    // here, before any barrier, tensor-memory allocation or write
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.p.err, DEV_CAPACITY);
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = a.C;
@@ -420,8 +429,8 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
     __syncthreads();
 
     int cur = 0;
-    const long s_end = a.step0 + a.n_steps;
-    for (long step = a.step0;; ++step) {
+    const long s_end = step0 + a.n_steps;
+    for (long step = step0;; ++step) {
       const bool last = step == s_end;
       for (int stage = 0; stage < 4; ++stage) {
         const int par = stage & 1;

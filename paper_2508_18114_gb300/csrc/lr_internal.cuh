@@ -32,7 +32,7 @@ struct PulseDev {
 };
 
 // Device error word values (first error wins).
-enum DevErr : unsigned { DEV_OK = 0, DEV_NOT_PD = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3 };
+enum DevErr : unsigned { DEV_OK = 0, DEV_NOT_PD = 1, DEV_NONFINITE = 2, DEV_TIMEOUT = 3, DEV_CAPACITY = 4 };
 
 __device__ __forceinline__ void set_error(unsigned* err, unsigned code) {
   atomicCAS(err, 0u, code);
@@ -193,6 +193,7 @@ struct DevPtrs {
   void* scratch;   // engine scratch
   long long scratch_bytes;
   double2* gsnap;  // [n_traj][n_rec][snap_m][snap_m] Gram matrices at record steps, or null
+  long long* dstep;  // RK4 steps taken in the pulse run (device copy), or null
 };
 
 struct RunParams {
@@ -211,7 +212,9 @@ struct RunParams {
 // lr_common.cu
 cudaError_t launch_initial_state(const DevPtrs& p, const RunParams& rp, int max_N, int prec_fp32,
                                  uint64_t seed, double eps, cudaStream_t s);
-cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long step, cudaStream_t s);
+// eps_a, T(tau) and Lambda at step *p.dstep + n_added (the integrate that
+// precedes it in the stream took n_added steps), then *p.dstep += n_added.
+cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long n_added, cudaStream_t s);
 // Elementwise complex128 <-> complex64 conversion of n elements.
 cudaError_t launch_convert(const void* src, void* dst, long long n, int to_fp32, cudaStream_t s);
 

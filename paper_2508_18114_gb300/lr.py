@@ -244,6 +244,21 @@ class LowRankBatch:
     def integrate(self, dt: float, n_steps: int, stream=None):
         self._check(self._lib.lr_integrate(self._h, float(dt), int(n_steps), C.c_void_p(_stream_ptr(stream))))
 
+    def capture_integrate(self, dt: float, n_steps: int):
+        """A CUDA graph (torch.cuda.CUDAGraph) of lr_integrate(dt, n_steps) on
+        the fused engine: every graph.replay() continues the pulse run by
+        n_steps (the step counter is read and advanced on the device). Call
+        sync() after replays to refresh the host's view of the step counter."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.graph(g, stream=side):
+            self._check(self._lib.lr_integrate(self._h, float(dt), int(n_steps), C.c_void_p(side.cuda_stream)))
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        self.sync()   # capture ran nothing: bring the host's step counter back
+        return g
+
     def sync(self, stream=None):
         self._check(self._lib.lr_sync(self._h, C.c_void_p(_stream_ptr(stream))))
 
