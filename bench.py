@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=None, help="RK4 steps of the oracle sample")
     ap.add_argument("--no-plain-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=8, help="RK4 steps timed on the plain FP64 engine")
+    ap.add_argument("--no-graph", action="store_true", help="time direct lr_integrate calls instead of graph replays")
     ap.add_argument("--frame", default="lab", choices=["lab", "rwa"],
                     help="rwa: frame rotating at w_d with the rotating-wave approximation")
     ap.add_argument("--dt", type=float, default=None, help="RK4 step [ns] (default: the workload's; 2.5e-3 with rwa)")
@@ -271,6 +272,9 @@ def run_ours(args):
     for _ in range(args.warmup):
         b.integrate(wl.dt, chunk)
     b.sync()
+    # the fused engine's integrate is timed as a captured CUDA graph, replayed
+    # once per bench step (each replay continues the pulse run)
+    graph = b.capture_integrate(wl.dt, chunk) if b.engine == "fused" and not args.no_graph else None
     sampler = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -281,7 +285,10 @@ def run_ours(args):
     for k in range(args.steps):
         flush.zero_()                       # L2 flush between timed iterations (not timed)
         ev[k][0].record(stream)
-        b.integrate(wl.dt, chunk)
+        if graph is not None:
+            graph.replay()
+        else:
+            b.integrate(wl.dt, chunk)
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -318,10 +325,12 @@ def run_ours(args):
                 "peak_source": "%s pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
                                % (pipe, FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK, mhz),
                 "flops_per_step": fl}
+    # kernels per bench step: the integrator's (plain: 3 per RK4 stage pair and
+    # records; fused: one persistent launch), the eps_a epilogue and the step advance
     if engine == "plain":
-        launches = (12 * chunk + 2) + 1
+        launches = (12 * chunk + 2) + 2
     else:
-        launches = 2
+        launches = 3
     launches *= args.steps
 
     # end to end through the public API with host buffers
@@ -401,6 +410,7 @@ def run_ours(args):
                      "team_size": info.team_size, "stage_state": "shared memory" if info.stage_in_smem else "L2",
                      "projection": ("tcgen05 TF32 x%d" % info.tensor_passes) if info.tensor_passes else "CUDA cores",
                      "chunk_rk4_steps": chunk,
+                     "launch": "CUDA graph replay" if graph is not None else "direct lr_integrate",
                      "l2": "flushed (256 MiB write) between timed steps"})
         line = {
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
