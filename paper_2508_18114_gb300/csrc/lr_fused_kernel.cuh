@@ -517,25 +517,34 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                       }
                   }
                 }
+                // reduce-scatter over the warp (recursive halving): at offset o
+                // every lane keeps the half of its values named by bit o of
+                // its lane and adds the partner's copy; lane L ends with the
+                // sum of value L = (i, j, re/im) of the 4 x 4 tile
+                DW v[32];
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
                   for (int j = 0; j < TP; ++j)
 #pragma unroll
-                    for (int c = 0; c < 2; ++c)
+                    for (int c = 0; c < 2; ++c) v[(i * 4 + j) * 2 + c] = acc[i][j][c];
 #pragma unroll
-                      for (int o = 16; o > 0; o >>= 1) {
-                        DW t;
-                        t.hi = __shfl_xor_sync(0xffffffffu, acc[i][j][c].hi, o);
-                        t.lo = __shfl_xor_sync(0xffffffffu, acc[i][j][c].lo, o);
-                        dw_add(acc[i][j][c], t);
-                      }
-                if (lane == 0)
+                for (int lev = 0; lev < 5; ++lev) {
+                  const int o = 16 >> lev;
+                  const bool up = (lane & o) != 0;
 #pragma unroll
-                  for (int i = 0; i < TP; ++i)
-#pragma unroll
-                    for (int j = 0; j < TP; ++j)
-                      gp[(i0 + i) * Mp + j0 + j] = mk(dw_value(acc[i][j][0]), dw_value(acc[i][j][1]));
+                  for (int k = 0; k < (16 >> lev); ++k) {
+                    DW keep = up ? v[k + (16 >> lev)] : v[k];
+                    const DW send = up ? v[k] : v[k + (16 >> lev)];
+                    DW t;
+                    t.hi = __shfl_xor_sync(0xffffffffu, send.hi, o);
+                    t.lo = __shfl_xor_sync(0xffffffffu, send.lo, o);
+                    dw_add(keep, t);
+                    v[k] = keep;
+                  }
+                }
+                reinterpret_cast<double*>(gp)[2 * ((i0 + (lane >> 3)) * Mp + j0 + ((lane >> 1) & 3)) + (lane & 1)] =
+                    dw_value(v[0]);
               } else {
                 T gr[TP][TP], gi[TP][TP];
 #pragma unroll
@@ -630,25 +639,54 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                   ++it;
                 }
               }
-#pragma unroll
-              for (int i = 0; i < TP; ++i)
-#pragma unroll
-                for (int j = 0; j < TP; ++j)
-#pragma unroll
-                  for (int o = 16; o > 0; o >>= 1) {
-                    rr[i][j] += __shfl_xor_sync(0xffffffffu, rr[i][j], o);
-                    ri[i][j] += __shfl_xor_sync(0xffffffffu, ri[i][j], o);
-                    br[i][j] += __shfl_xor_sync(0xffffffffu, br[i][j], o);
-                    bi[i][j] += __shfl_xor_sync(0xffffffffu, bi[i][j], o);
-                  }
-              if (lane == 0)
+              if constexpr (TP == 4) {
+                // reduce-scatter of the 64 partial sums (recursive halving, as
+                // for the Gram tiles): lane L ends with the (re, im) pair of
+                // entry L = (jump, i, j)
+                T v[64];
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
                   for (int j = 0; j < TP; ++j) {
-                    tp[(i0 + i) * Mp + j0 + j] = cm<T2>(rr[i][j], ri[i][j]);
-                    tp[Mp * Mp + (i0 + i) * Mp + j0 + j] = cm<T2>(br[i][j], bi[i][j]);
+                    v[(i * 4 + j) * 2] = rr[i][j];
+                    v[(i * 4 + j) * 2 + 1] = ri[i][j];
+                    v[(16 + i * 4 + j) * 2] = br[i][j];
+                    v[(16 + i * 4 + j) * 2 + 1] = bi[i][j];
                   }
+#pragma unroll
+                for (int lev = 0; lev < 5; ++lev) {
+                  const int o = 16 >> lev;
+                  const bool up = (lane & o) != 0;
+#pragma unroll
+                  for (int k = 0; k < (32 >> lev); ++k) {
+                    const T keep = up ? v[k + (32 >> lev)] : v[k];
+                    const T send = up ? v[k] : v[k + (32 >> lev)];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                  }
+                }
+                const int jb = lane >> 4, ii = (lane >> 2) & 3, jj = lane & 3;
+                tp[jb * Mp * Mp + (i0 + ii) * Mp + j0 + jj] = cm<T2>(v[0], v[1]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                      rr[i][j] += __shfl_xor_sync(0xffffffffu, rr[i][j], o);
+                      ri[i][j] += __shfl_xor_sync(0xffffffffu, ri[i][j], o);
+                      br[i][j] += __shfl_xor_sync(0xffffffffu, br[i][j], o);
+                      bi[i][j] += __shfl_xor_sync(0xffffffffu, bi[i][j], o);
+                    }
+                if (lane == 0)
+#pragma unroll
+                  for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TP; ++j) {
+                      tp[(i0 + i) * Mp + j0 + j] = cm<T2>(rr[i][j], ri[i][j]);
+                      tp[Mp * Mp + (i0 + i) * Mp + j0 + j] = cm<T2>(br[i][j], bi[i][j]);
+                    }
+              }
             }
           }
           if (record) {
