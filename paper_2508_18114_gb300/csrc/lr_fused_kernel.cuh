@@ -192,6 +192,33 @@ __device__ __forceinline__ DWC dwc_scale(const DWC& a, DW s) {
   return r;
 }
 
+// Reduce-scatter of NV = 2^p partial sums over a warp (recursive halving): at
+// offset o each lane keeps the half of its values named by bit o of its lane
+// and adds the partner's copy; offsets left once a single value remains add
+// across the rest of the warp. Lane L ends with the total of value
+// L >> (5 - p) in v[0] (p <= 5), or of values 2L and 2L + 1 in v[0], v[1]
+// (p = 6). The order of the additions is fixed.
+template <int NV, typename V>
+__device__ __forceinline__ void warp_reduce_scatter(V (&v)[NV], int lane) {
+#pragma unroll
+  for (int lev = 0; lev < 5; ++lev) {
+    const int o = 16 >> lev;
+    constexpr int n0 = NV;
+    const int n = n0 >> lev;
+    if (n >= 2) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < n / 2; ++k) {
+        const V keep = up ? v[k + n / 2] : v[k];
+        const V send = up ? v[k] : v[k + n / 2];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+}
+
 // ----------------------------------------------------------------- the kernel
 
 // Vector load of 4 consecutive complex values (16-byte loads when the row
@@ -566,20 +593,21 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                       gi[i][j] = fma(zi[i].x, zj[j].y, fma(-zi[i].y, zj[j].x, gi[i][j]));
                     }
                 }
+                // reduce-scatter: value (i TP + j) 2 + c, c = re / im
+                constexpr int NVg = 2 * TP * TP, SH = TP == 4 ? 0 : 2;   // 2^p values, lane L holds L >> (5 - p)
+                T v[NVg];
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
-                  for (int j = 0; j < TP; ++j)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                      gr[i][j] += __shfl_xor_sync(0xffffffffu, gr[i][j], o);
-                      gi[i][j] += __shfl_xor_sync(0xffffffffu, gi[i][j], o);
-                    }
-                if (lane == 0)
-#pragma unroll
-                  for (int i = 0; i < TP; ++i)
-#pragma unroll
-                    for (int j = 0; j < TP; ++j) gp[(i0 + i) * Mp + j0 + j] = mk((double)gr[i][j], (double)gi[i][j]);
+                  for (int j = 0; j < TP; ++j) {
+                    v[(i * TP + j) * 2] = gr[i][j];
+                    v[(i * TP + j) * 2 + 1] = gi[i][j];
+                  }
+                warp_reduce_scatter(v, lane);
+                if ((lane & ((1 << SH) - 1)) == 0) {
+                  const int idx = lane >> SH, e2 = idx >> 1;
+                  reinterpret_cast<double*>(gp)[2 * ((i0 + e2 / TP) * Mp + j0 + e2 % TP) + (idx & 1)] = (double)v[0];
+                }
               }
             } else {
               // tile of T_r and T_b
@@ -667,25 +695,22 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 const int jb = lane >> 4, ii = (lane >> 2) & 3, jj = lane & 3;
                 tp[jb * Mp * Mp + (i0 + ii) * Mp + j0 + jj] = cm<T2>(v[0], v[1]);
               } else {
+                // TP = 2: 16 values ((jump 4 + i 2 + j) 2 + c), lane L holds L >> 1
+                T v[16];
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
-                  for (int j = 0; j < TP; ++j)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                      rr[i][j] += __shfl_xor_sync(0xffffffffu, rr[i][j], o);
-                      ri[i][j] += __shfl_xor_sync(0xffffffffu, ri[i][j], o);
-                      br[i][j] += __shfl_xor_sync(0xffffffffu, br[i][j], o);
-                      bi[i][j] += __shfl_xor_sync(0xffffffffu, bi[i][j], o);
-                    }
-                if (lane == 0)
-#pragma unroll
-                  for (int i = 0; i < TP; ++i)
-#pragma unroll
-                    for (int j = 0; j < TP; ++j) {
-                      tp[(i0 + i) * Mp + j0 + j] = cm<T2>(rr[i][j], ri[i][j]);
-                      tp[Mp * Mp + (i0 + i) * Mp + j0 + j] = cm<T2>(br[i][j], bi[i][j]);
-                    }
+                  for (int j = 0; j < TP; ++j) {
+                    v[(i * 2 + j) * 2] = rr[i][j];
+                    v[(i * 2 + j) * 2 + 1] = ri[i][j];
+                    v[(4 + i * 2 + j) * 2] = br[i][j];
+                    v[(4 + i * 2 + j) * 2 + 1] = bi[i][j];
+                  }
+                warp_reduce_scatter(v, lane);
+                if ((lane & 1) == 0) {
+                  const int idx = lane >> 1, e = idx >> 1, jb = e >> 2, ii = (e >> 1) & 1, jj = e & 1;
+                  reinterpret_cast<T*>(tp)[2 * (jb * Mp * Mp + (i0 + ii) * Mp + j0 + jj) + (idx & 1)] = v[0];
+                }
               }
             }
           }
