@@ -313,12 +313,12 @@ def run_ours(args):
         pipe = "FP32 FMA"
     achieved = fl / (ms * 1e-3 / args.steps) / 1e12
     # DRAM bytes per launch from one ncu capture of this kernel on a 76-trajectory, 10-step case
-    # of the same workload (2.485 MB per trajectory-step at the same number of resident teams),
+    # of the same workload (2.462 MB per trajectory-step at the same number of resident teams),
     # scaled by the trajectory-steps of one launch; only for the kernel that capture measured
     traffic = None
     if (wl.name == "c4" and prec == "fp32_g64" and engine == "fused" and info.team_size == 2
             and not info.stage_in_smem and info.tensor_passes == 0):
-        traffic = 2.485e6 * ntraj * chunk
+        traffic = 2.462e6 * ntraj * chunk
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "kernel": "integrate (%s engine)" % engine,
