@@ -24,7 +24,12 @@ their printed order:
 * ``gradient``   - central finite-difference gradient of the assignment error
                    with respect to the pulse parameters.
 * ``diagnostics`` - spectrum of rho = m m^dag and purity tr(rho^2) (Sec. S1.B).
+* ``paper_model`` - the paper's own model: charge-basis transmon, normal modes
+                   of the resonator-filter pair, the Hamiltonian in the frame of
+                   the drive with its e^{+-2i w_d t} terms (Sec. S2.A, S2.D,
+                   S2.E), and RK4 integrators of Eq. S5 and Eq. S4 with
+                   time-dependent operators.
 
 Parity status of each function is stated in its module docstring.
 """
-from . import model, pulse, lowrank, lindblad, signal, init_state, gradient, diagnostics  # noqa: F401
+from . import model, pulse, lowrank, lindblad, signal, init_state, gradient, diagnostics, paper_model  # noqa: F401
