@@ -321,6 +321,129 @@ const char* lr_status_string(lr_status s);
 const char* lr_last_error(const lr_ctx* ctx);
 void lr_destroy(lr_ctx* ctx);
 
+
+/* ======================================================================
+ * The paper's own model (Sec. S2.A, S2.D, S2.E) on a sparse-operator engine.
+ *
+ * Basis |j_l> (x) |j_u> (x) |j_t>: the lower and upper normal modes of the
+ * resonator-filter pair and the transmon eigenstates, flat index
+ * n = (j_l N_u + j_u) N_t + j_t. The Hamiltonian is the one in the frame of
+ * the drive with its counter-rotating e^{+-2i w_d t} terms (Eq.
+ * S(hamiltonian_rotated)); the dissipators are kappa D[f] + gamma D[b] (Eq. 2)
+ * in the same frame.
+ *
+ * Every operator X(t) is a sum of time channels,
+ *     X(t) = sum_{a,q} Omega(t)^a e^{i q w_d t} X_{a,q},
+ *     a in {0, 1}, q in {-2, ..., 2}, channel index 5 a + q + 2,
+ * stored as CSR entries (row, column, complex value, channel). Omega(t) is the
+ * real pulse envelope of Sec. S2.C (lr_pulse kinds 0 and 1; the pulse phase
+ * must be 0 and its w_d must equal the model's).
+ * ====================================================================== */
+
+#define LR_SPARSE_MAX_JUMPS 3
+#define LR_PAPER_DERIVED 16  /* length of lr_paper_model_build's `derived` output */
+
+/* Physical parameters of the paper's model (Sec. S2.B), rad/ns and 1/ns. */
+typedef struct {
+  int Nl, Nu, Nt;       /* cutoffs: lower normal mode, upper normal mode, transmon (Nt <= LR_MAX_NT) */
+  int n_cut;            /* charge basis |n| <= n_cut of the transmon diagonalisation (>= Nt, <= 64) */
+  double Ec, Ej;        /* transmon charging and Josephson energies */
+  double wr, wf;        /* bare resonator and filter frequencies */
+  double g, J;          /* transmon-resonator and resonator-filter couplings */
+  double kappa, gamma;  /* filter and transmon decay rates */
+  double wd;            /* drive frequency = frame frequency */
+} lr_paper_params;
+
+/* Operator set of the sparse engine. K = n_jumps; operator o occupies rows
+ * rowptr[o (N+1)] .. rowptr[o (N+1) + N] of the entry arrays:
+ *   o = 0        A(t) = -i H_eff(t) = -i H(t) - 1/2 sum_k L_k(t)^dag L_k(t),
+ *   o = 1 .. K   the jump operators L_k(t),
+ *   o = K + 1    the readout operator r (static: every entry in channel 2),
+ *                beta(t) = tr(rho r).
+ * Within a row the entries may come in any order; every row's entries of an
+ * operator are contiguous. Arrays are host memory owned by the caller and read
+ * only during lr_sparse_create. */
+typedef struct {
+  int N;                      /* Hilbert-space dimension (1 .. 2^24) */
+  int n_jumps;                /* K, 1 .. LR_SPARSE_MAX_JUMPS */
+  int n_levels;               /* population bins, 1 .. LR_MAX_NT */
+  long nnz;                   /* entries of all operators */
+  double wd;                  /* w_d of the time channels [rad/ns] */
+  const int* rowptr;          /* [(K + 2) (N + 1)], non-decreasing within each operator, values in [0, nnz] */
+  const int* col;             /* [nnz] column in [0, N) */
+  const double* val;          /* [2 nnz] complex values (re, im) */
+  const unsigned char* chan;  /* [nnz] channel 0 .. 9 */
+  const int* level;           /* [N] population bin in [0, n_levels) of each basis state */
+} lr_sparse_model;
+
+typedef struct lr_sparse lr_sparse;
+
+/* Sizes of the paper's model for `p`: N = Nl Nu Nt and the total entry count
+ * of its four operators (A, L_1 = sqrt(kappa) f in the rotated frame,
+ * L_2 = sqrt(gamma) b, r = c_l). LR_ERR_ARG for cutoffs out of range. Host only. */
+lr_status lr_paper_model_size(const lr_paper_params* p, int* N, long* nnz);
+
+/* Builds the operator set of the paper's model into caller-allocated host
+ * arrays sized by lr_paper_model_size: rowptr [4 (N+1)], col [nnz],
+ * val [2 nnz], chan [nnz], level [N] (the transmon index j_t). Steps:
+ *  - transmon: 4 Ec n^2 - Ej cos(phi) in the charge basis (offset charge 0),
+ *    cyclic Jacobi eigensolver, lowest Nt levels eps_j, charge matrix elements
+ *    n_{j,j+1} > 0 (sign convention); only nearest neighbours are kept
+ *    (the approximation of Sec. S2.E);
+ *  - normal modes: w_l, w_u in closed form (momentum-coupled oscillators) and
+ *    the null vectors of Omega - w (Sec. S2.D), normalised to
+ *    alpha^2 + beta^2 - gamma^2 - delta^2 = 1 with beta > 0; then
+ *    a = sum_i (alpha_i c_i - gamma_i c_i^dag), f = sum_i (beta_i c_i - delta_i c_i^dag);
+ *  - A(t) from Eq. S(hamiltonian_rotated) and
+ *    L_1(t) = sqrt(kappa) (s23 c_l + s24 c_u + e^{2i w_d t} (s21 c_u^dag + s22 c_l^dag)),
+ *    L_2 = sqrt(gamma) sum_j sqrt(j) |j-1><j|, r = c_l.
+ * Products of truncated operators are truncated products (an intermediate
+ * state outside the cutoffs contributes zero). Entries with the same row,
+ * column and channel are merged; each row is sorted by (column, channel).
+ * `derived` (optional, LR_PAPER_DERIVED doubles): w_l, w_u, mu_l, mu_u, nu_l,
+ * nu_u, s21, s22, s23, s24, eps_1 - eps_0 (0 when Nt < 2),
+ * eps_2 - 2 eps_1 + eps_0 (0 when Nt < 3), then zeros. Host only. */
+lr_status lr_paper_model_build(const lr_paper_params* p, int* rowptr, int* col, double* val,
+                               unsigned char* chan, int* level, double* derived);
+
+/* Creates a sparse-engine context for n_traj trajectories of rank M
+ * (1 <= M <= min(N, LR_MAX_RANK)) on one operator set; trajectory i uses
+ * pulses[i]. Copies the operator arrays (they may be freed afterwards).
+ * tau places the falling pulse edge; max_steps and pop_every size the
+ * recorded observables as for lr_options. The engine is FP64 throughout:
+ * per RK4 stage an apply kernel (A Z, L_k Z, r Z from the CSR rows, one
+ * thread per element of Z), a row-block Gram kernel (Z^dag Z, Z^dag L_k Z
+ * and the observables), a per-trajectory solve (Cholesky, X_k = G^-1 Z^dag L_k Z)
+ * and an update kernel (F = A Z + 1/2 sum_k (L_k Z) X_k^dag, RK4). */
+lr_status lr_sparse_create(const lr_sparse_model* model, int n_traj, int M, const lr_pulse* pulses,
+                           double tau, long max_steps, int pop_every, lr_sparse** out);
+/* Bytes of device workspace the context needs (256-byte aligned). */
+lr_status lr_sparse_workspace_size(const lr_sparse* s, size_t* bytes);
+/* Binds a caller-owned device buffer (>= lr_sparse_workspace_size, 256-byte
+ * aligned) and uploads the operators and pulses (sync on `stream`). */
+lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, size_t bytes, void* stream);
+/* Fixed-rank initial state of Sec. S1.A for every trajectory (same recipe and
+ * random numbers as lr_set_initial), with the pure state |psi[i]> (a basis
+ * index, e.g. |0_l, 0_u, g> = 0 and |0_l, 0_u, e> = 1); step counter reset. Async. */
+lr_status lr_sparse_set_initial(lr_sparse* s, const int* psi, uint64_t seed, double eps, void* stream);
+/* Host state [n_traj][N][M] complex128 (interleaved re, im) -> device;
+ * step counter set to `step` (0 <= step <= max_steps). Sync. */
+lr_status lr_sparse_set_state(lr_sparse* s, const double* Z, long step, void* stream);
+/* Device state -> host [n_traj][N][M] complex128. Sync. */
+lr_status lr_sparse_get_state(const lr_sparse* s, double* Z, void* stream);
+/* n_steps RK4 steps of size dt [ns] from the current step; records beta at
+ * every step and populations, photons and trace every pop_every steps.
+ * LR_ERR_STATE past max_steps. Async. */
+lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, void* stream);
+/* Copies the records to host arrays (any may be NULL): beta [n_traj][max_steps+1]
+ * complex128, pops [n_traj][n_rec][n_levels], nphot and trace [n_traj][n_rec]
+ * (n_rec = max_steps / pop_every + 1). Syncs `stream` and returns the device
+ * error status (LR_ERR_NOT_PD, LR_ERR_NONFINITE). */
+lr_status lr_sparse_observables(lr_sparse* s, double* beta, double* pops, double* nphot, double* trace,
+                                void* stream);
+const char* lr_sparse_last_error(const lr_sparse* s);
+void lr_sparse_destroy(lr_sparse* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,683 @@
+// Sparse-operator engine (FP64) for operator sets given as CSR rows with time
+// channels: the paper's own model of Sec. S2 (built by lr_paper_model.cu) or
+// any other H_eff(t), L_k(t), r with that structure.
+//
+// One RK4 stage of Eq. S5 is four launches:
+//   sp_apply  - one thread per element (n, m) of the stage input Zs:
+//               W = A(t) Zs with A = -i H_eff, Y_k = L_k(t) Zs, and at stage 1
+//               of every step Yr = r Zs; the ten channel factors
+//               Omega(t)^a e^{i q w_d t} are formed once per block;
+//   sp_gram   - per block of SP_R rows: partial sums of G = Zs^dag Zs (upper
+//               triangle), T_k = Zs^dag Y_k, and at stage 1 tr(Zs^dag Yr) =
+//               tr(rho r), plus level populations, |Yr|^2 and |Zs|^2 at
+//               recording steps;
+//   sp_solve  - one block per trajectory: reduce the partials in block order,
+//               record beta and the observables, Cholesky G = L L^dag and
+//               X_k = G^-1 T_k (the Moore-Penrose projection Zs^+ L_k Zs);
+//   sp_update - F = W + 1/2 sum_k Y_k X_k^dag, then the classical RK4 stage.
+// After the last step an observation pass (apply r, Gram, solve without
+// Cholesky) records beta and the observables of the final state.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lr_internal.cuh"
+
+namespace lr {
+namespace {
+
+constexpr int SP_T = 256;   // threads per block
+constexpr int SP_R = 16;    // rows per Gram block
+constexpr int NCH = 10;     // time channels
+
+struct SpDev {
+  const int* rowptr;
+  const int* col;
+  const double2* val;
+  const unsigned char* chan;
+  const int* level;
+  const PulseDev* pulse;
+  unsigned* err;
+  double2 *Z, *Zs, *acc, *W, *Y, *Yr, *X;
+  double* part;
+  double2* beta;
+  double *pops, *nphot, *trace;
+};
+
+struct SpParams {
+  int N, M, K, T, n_levels, nblk;
+  long long NM;      // N * M
+  long long ps;      // doubles per partial block
+  double wd, tau;
+  long max_steps, n_rec;
+  int pop_every;
+};
+
+enum : int { MODE_SOLVE = 1, MODE_OBS = 2, MODE_BETA = 4 };
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// conj(a) * b + c
+__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 c) {
+  return mk(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+
+__device__ void channel_factors(const PulseDev& P, const SpParams& p, double t, double2* chi) {
+  const int c = threadIdx.x;
+  if (c < NCH) {
+    const int a = c / 5, q = c % 5 - 2;
+    const double om = a ? pulse_envelope(P, p.tau, t) : 1.0;
+    double sn, cs;
+    sincos((double)q * p.wd * t, &sn, &cs);
+    chi[c] = mk(om * cs, om * sn);
+  }
+}
+
+// out[e] = sum over the row's entries of chi[ch] val Zs[col][m]
+__device__ __forceinline__ double2 row_apply(const SpDev& d, const SpParams& p, int op, int n, int m,
+                                             const double2* __restrict__ Zs, const double2* chi) {
+  const int* rp = d.rowptr + (size_t)op * (p.N + 1);
+  double2 acc = mk(0.0, 0.0);
+  for (int e = rp[n]; e < rp[n + 1]; ++e) {
+    const double2 v = cmul(chi[d.chan[e]], d.val[e]);
+    acc = cfma(v, Zs[(size_t)d.col[e] * p.M + m], acc);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(SP_T) sp_apply(SpDev d, SpParams p, double t, int with_r, int only_r) {
+  __shared__ double2 chi[NCH];
+  const int tj = blockIdx.y;
+  channel_factors(d.pulse[tj], p, t, chi);
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * SP_T + threadIdx.x;
+  if (e >= p.NM) return;
+  const int n = (int)(e / p.M), m = (int)(e - (long long)n * p.M);
+  const size_t off = (size_t)tj * p.NM;
+  const double2* Zs = d.Zs + off;
+  if (!only_r) {
+    d.W[off + e] = row_apply(d, p, 0, n, m, Zs, chi);
+    for (int k = 0; k < p.K; ++k) d.Y[((size_t)k * p.T + tj) * p.NM + e] = row_apply(d, p, 1 + k, n, m, Zs, chi);
+  }
+  if (with_r) d.Yr[off + e] = row_apply(d, p, 1 + p.K, n, m, Zs, chi);
+}
+
+__global__ void __launch_bounds__(SP_T) sp_gram(SpDev d, SpParams p, int mode) {
+  __shared__ double2 sZ[SP_R][LR_MAX_RANK], sY[LR_SPARSE_MAX_JUMPS + 1][SP_R][LR_MAX_RANK];
+  __shared__ double sw[SP_R], sr[SP_R];
+  __shared__ int slev[SP_R];
+  const int tj = blockIdx.y, b = blockIdx.x, M = p.M, K = p.K;
+  const int r0 = b * SP_R, rows = min(SP_R, p.N - r0);
+  const size_t off = (size_t)tj * p.NM;
+  const bool solve = mode & MODE_SOLVE, obs = mode & MODE_OBS, beta = mode & MODE_BETA;
+  for (int e = threadIdx.x; e < SP_R * M; e += SP_T) {
+    const int i = e / M, m = e - (e / M) * M;
+    double2 z = mk(0, 0), yr = mk(0, 0);
+    if (i < rows) {
+      const size_t idx = off + (size_t)(r0 + i) * M + m;
+      z = d.Zs[idx];
+      if (beta) yr = d.Yr[idx];
+      if (solve)
+        for (int k = 0; k < K; ++k) sY[k][i][m] = d.Y[(size_t)k * p.T * p.NM + idx];
+    } else if (solve) {
+      for (int k = 0; k < K; ++k) sY[k][i][m] = mk(0, 0);
+    }
+    sZ[i][m] = z;
+    sY[LR_SPARSE_MAX_JUMPS][i][m] = yr;
+    if (m == 0) slev[i] = i < rows ? d.level[r0 + i] : -1;
+  }
+  __syncthreads();
+  double* out = d.part + ((size_t)tj * p.nblk + b) * p.ps;
+  const int MM = M * M;
+  if (solve) {
+    for (int e = threadIdx.x; e < (1 + K) * MM; e += SP_T) {
+      const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
+      if (mat == 0 && i > j) continue;
+      double2 s = mk(0.0, 0.0);
+      for (int r = 0; r < rows; ++r) s = cfma_conj(sZ[r][i], mat == 0 ? sZ[r][j] : sY[mat - 1][r][j], s);
+      out[2 * e] = s.x;
+      out[2 * e + 1] = s.y;
+    }
+  }
+  const size_t o2 = (size_t)2 * (1 + K) * MM;   // beta re, im, nphot, trace, pops[n_levels]
+  if (beta || obs) {
+    for (int i = threadIdx.x; i < SP_R; i += SP_T) {
+      double w = 0.0, q = 0.0;
+      if (i < rows)
+        for (int m = 0; m < M; ++m) {
+          const double2 z = sZ[i][m], y = sY[LR_SPARSE_MAX_JUMPS][i][m];
+          w += z.x * z.x + z.y * z.y;
+          q += y.x * y.x + y.y * y.y;
+        }
+      sw[i] = w;
+      sr[i] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 bsum = mk(0.0, 0.0);
+      double nph = 0.0, tr = 0.0;
+      for (int r = 0; r < rows; ++r) {
+        for (int m = 0; m < M; ++m) bsum = cfma_conj(sZ[r][m], sY[LR_SPARSE_MAX_JUMPS][r][m], bsum);
+        nph += sr[r];
+        tr += sw[r];
+      }
+      out[o2] = bsum.x;
+      out[o2 + 1] = bsum.y;
+      out[o2 + 2] = nph;
+      out[o2 + 3] = tr;
+    }
+    if (obs)
+      for (int l = threadIdx.x; l < p.n_levels; l += SP_T) {
+        double acc = 0.0;
+        for (int r = 0; r < rows; ++r) acc += slev[r] == l ? sw[r] : 0.0;
+        out[o2 + 4 + l] = acc;
+      }
+  }
+}
+
+__global__ void __launch_bounds__(SP_T) sp_solve(SpDev d, SpParams p, long step, int mode) {
+  __shared__ double2 L[LR_MAX_RANK][LR_MAX_RANK + 1];
+  __shared__ double2 B[LR_MAX_RANK][LR_MAX_RANK + 1];   // right-hand sides of one T_k, B[column][row]
+  __shared__ int bad;
+  const int tj = blockIdx.x, M = p.M, K = p.K, MM = M * M, tid = threadIdx.x;
+  const double* P = d.part + (size_t)tj * p.nblk * p.ps;
+  const size_t o2 = (size_t)2 * (1 + K) * MM;
+  if (tid == 0) bad = 0;
+  if (mode & (MODE_BETA | MODE_OBS)) {
+    const int nv = 4 + p.n_levels;
+    for (int v = tid; v < nv; v += SP_T) {
+      double s = 0.0;
+      for (int b = 0; b < p.nblk; ++b) s += P[b * p.ps + o2 + v];
+      if (v < 2) {
+        if (mode & MODE_BETA) {
+          double* bt = reinterpret_cast<double*>(d.beta + (size_t)tj * (p.max_steps + 1) + step);
+          bt[v] = s;
+          if (!isfinite(s)) set_error(d.err, DEV_NONFINITE);
+        }
+      } else if (mode & MODE_OBS) {
+        const long rec = step / p.pop_every;
+        if (v == 2) d.nphot[(size_t)tj * p.n_rec + rec] = s;
+        else if (v == 3) d.trace[(size_t)tj * p.n_rec + rec] = s;
+        else d.pops[((size_t)tj * p.n_rec + rec) * p.n_levels + (v - 4)] = s;
+      }
+    }
+  }
+  if (!(mode & MODE_SOLVE)) return;
+  for (int e = tid; e < MM; e += SP_T) {   // G, upper triangle, into the lower triangle of L
+    const int i = e / M, j = e - (e / M) * M;
+    if (i > j) continue;
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < p.nblk; ++b) {
+      re += P[b * p.ps + 2 * e];
+      im += P[b * p.ps + 2 * e + 1];
+    }
+    L[j][i] = i == j ? mk(re, 0.0) : mk(re, -im);   // G_ji = conj(G_ij)
+  }
+  __syncthreads();
+  // right-looking Cholesky G = L L^dag on the lower triangle
+  for (int k = 0; k < M; ++k) {
+    if (tid == 0) {
+      const double piv = L[k][k].x;
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        bad = 1;
+        L[k][k] = mk(1.0, 0.0);
+      } else {
+        L[k][k] = mk(sqrt(piv), 0.0);
+      }
+    }
+    __syncthreads();
+    const double inv = 1.0 / L[k][k].x;
+    for (int i = k + 1 + tid; i < M; i += SP_T) L[i][k] = mk(L[i][k].x * inv, L[i][k].y * inv);
+    __syncthreads();
+    const int rem = M - k - 1;
+    for (int e = tid; e < rem * rem; e += SP_T) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      if (j > i) continue;
+      const double2 a = L[i][k], c = L[j][k];   // L_ij -= L_ik conj(L_jk)
+      L[i][j] = mk(L[i][j].x - (a.x * c.x + a.y * c.y), L[i][j].y - (a.y * c.x - a.x * c.y));
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) set_error(d.err, DEV_NOT_PD);
+    return;
+  }
+  double2* X = d.X + (size_t)tj * K * MM;
+  for (int k = 0; k < K; ++k) {
+    for (int e = tid; e < MM; e += SP_T) {   // T_k entry (i, j) -> B[j][i]
+      const int i = e / M, j = e - (e / M) * M;
+      const size_t q = (size_t)2 * ((1 + k) * MM + e);
+      double re = 0.0, im = 0.0;
+      for (int b = 0; b < p.nblk; ++b) {
+        re += P[b * p.ps + q];
+        im += P[b * p.ps + q + 1];
+      }
+      B[j][i] = mk(re, im);
+    }
+    __syncthreads();
+    // X_k = G^-1 T_k: forward L y = t, then back L^dag x = y, one thread per column
+    for (int c = tid; c < M; c += SP_T) {
+      for (int i = 0; i < M; ++i) {
+        double2 s = B[c][i];
+        for (int j = 0; j < i; ++j)
+          s = mk(s.x - (L[i][j].x * B[c][j].x - L[i][j].y * B[c][j].y),
+                 s.y - (L[i][j].x * B[c][j].y + L[i][j].y * B[c][j].x));
+        const double dinv = 1.0 / L[i][i].x;
+        B[c][i] = mk(s.x * dinv, s.y * dinv);
+      }
+      for (int i = M - 1; i >= 0; --i) {
+        double2 s = B[c][i];
+        for (int j = i + 1; j < M; ++j)
+          s = mk(s.x - (L[j][i].x * B[c][j].x + L[j][i].y * B[c][j].y),
+                 s.y - (L[j][i].x * B[c][j].y - L[j][i].y * B[c][j].x));
+        const double dinv = 1.0 / L[i][i].x;
+        B[c][i] = mk(s.x * dinv, s.y * dinv);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < MM; e += SP_T) {   // X[k][i][j] = (X_k)_ij = B[j][i]
+      const int i = e / M, j = e - (e / M) * M;
+      X[(size_t)k * MM + e] = B[j][i];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage, double dt) {
+  __shared__ double2 sX[LR_MAX_RANK * LR_MAX_RANK];
+  const int tj = blockIdx.y, M = p.M, MM = M * M;
+  const long long e = (long long)blockIdx.x * SP_T + threadIdx.x;
+  const bool live = e < p.NM;
+  const int n = live ? (int)(e / M) : 0, m = live ? (int)(e - (long long)n * M) : 0;
+  const size_t off = (size_t)tj * p.NM;
+  double2 F = live ? d.W[off + e] : mk(0, 0);
+  for (int k = 0; k < p.K; ++k) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < MM; i += SP_T) sX[i] = d.X[((size_t)tj * p.K + k) * MM + i];
+    __syncthreads();
+    if (live) {   // F += 1/2 sum_j Y_k[n][j] conj(X_k[m][j])
+      const double2* y = d.Y + ((size_t)k * p.T + tj) * p.NM + (size_t)n * M;
+      double2 s = mk(0.0, 0.0);
+      for (int j = 0; j < M; ++j) {
+        const double2 a = y[j], x = sX[m * M + j];
+        s = mk(fma(a.x, x.x, fma(a.y, x.y, s.x)), fma(a.y, x.x, fma(-a.x, x.y, s.y)));
+      }
+      F = mk(F.x + 0.5 * s.x, F.y + 0.5 * s.y);
+    }
+  }
+  if (!live) return;
+  const double w = (stage == 0 || stage == 3) ? 1.0 : 2.0;
+  const double2 a0 = stage == 0 ? mk(0.0, 0.0) : d.acc[off + e];
+  const double2 a = mk(a0.x + w * F.x, a0.y + w * F.y);
+  const double2 z = d.Z[off + e];
+  if (stage < 3) {
+    const double c = stage == 2 ? dt : 0.5 * dt;
+    d.acc[off + e] = a;
+    d.Zs[off + e] = mk(z.x + c * F.x, z.y + c * F.y);
+  } else {
+    const double2 zn = mk(z.x + dt / 6.0 * a.x, z.y + dt / 6.0 * a.y);
+    if (!isfinite(zn.x) || !isfinite(zn.y)) set_error(d.err, DEV_NONFINITE);
+    d.Z[off + e] = zn;
+    d.Zs[off + e] = zn;
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace lr
+
+using namespace lr;
+
+struct lr_sparse {
+  int N, M, K, T, n_levels, nblk;
+  long nnz, max_steps, n_rec, step;
+  int pop_every;
+  double wd, tau;
+  std::vector<int> rowptr, col, level;
+  std::vector<double> val;
+  std::vector<unsigned char> chan;
+  std::vector<PulseDev> pulses;
+  char* ws;
+  size_t ws_bytes;
+  // offsets into the workspace
+  size_t o_rowptr, o_col, o_val, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X,
+      o_part, o_beta, o_pops, o_nphot, o_trace, total;
+  std::string msg;
+};
+
+namespace {
+
+lr_status fail(lr_sparse* s, lr_status st, const char* m) {
+  if (s) s->msg = m;
+  return st;
+}
+
+lr_status cuda_fail(lr_sparse* s, cudaError_t e) {
+  if (s) s->msg = cudaGetErrorString(e);
+  return LR_ERR_CUDA;
+}
+
+void layout(lr_sparse* s) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = o;
+    o = align256(o + bytes);
+    return r;
+  };
+  const size_t state = (size_t)s->T * s->N * s->M * sizeof(double2);
+  s->o_rowptr = take((size_t)(s->K + 2) * (s->N + 1) * sizeof(int));
+  s->o_col = take((size_t)s->nnz * sizeof(int));
+  s->o_val = take((size_t)s->nnz * sizeof(double2));
+  s->o_chan = take((size_t)s->nnz);
+  s->o_level = take((size_t)s->N * sizeof(int));
+  s->o_pulse = take((size_t)s->T * sizeof(PulseDev));
+  s->o_traj = take((size_t)s->T * sizeof(TrajDev));
+  s->o_err = take(sizeof(unsigned));
+  s->o_Z = take(state);
+  s->o_Zs = take(state);
+  s->o_acc = take(state);
+  s->o_W = take(state);
+  s->o_Y = take(state * s->K);
+  s->o_Yr = take(state);
+  s->o_X = take((size_t)s->T * s->K * s->M * s->M * sizeof(double2));
+  const size_t ps = (size_t)2 * (1 + s->K) * s->M * s->M + 4 + s->n_levels;
+  s->o_part = take((size_t)s->T * s->nblk * ps * sizeof(double));
+  s->o_beta = take((size_t)s->T * (s->max_steps + 1) * sizeof(double2));
+  s->o_pops = take((size_t)s->T * s->n_rec * s->n_levels * sizeof(double));
+  s->o_nphot = take((size_t)s->T * s->n_rec * sizeof(double));
+  s->o_trace = take((size_t)s->T * s->n_rec * sizeof(double));
+  s->total = o;
+}
+
+SpDev dev(const lr_sparse* s) {
+  char* w = s->ws;
+  SpDev d;
+  d.rowptr = reinterpret_cast<const int*>(w + s->o_rowptr);
+  d.col = reinterpret_cast<const int*>(w + s->o_col);
+  d.val = reinterpret_cast<const double2*>(w + s->o_val);
+  d.chan = reinterpret_cast<const unsigned char*>(w + s->o_chan);
+  d.level = reinterpret_cast<const int*>(w + s->o_level);
+  d.pulse = reinterpret_cast<const PulseDev*>(w + s->o_pulse);
+  d.err = reinterpret_cast<unsigned*>(w + s->o_err);
+  d.Z = reinterpret_cast<double2*>(w + s->o_Z);
+  d.Zs = reinterpret_cast<double2*>(w + s->o_Zs);
+  d.acc = reinterpret_cast<double2*>(w + s->o_acc);
+  d.W = reinterpret_cast<double2*>(w + s->o_W);
+  d.Y = reinterpret_cast<double2*>(w + s->o_Y);
+  d.Yr = reinterpret_cast<double2*>(w + s->o_Yr);
+  d.X = reinterpret_cast<double2*>(w + s->o_X);
+  d.part = reinterpret_cast<double*>(w + s->o_part);
+  d.beta = reinterpret_cast<double2*>(w + s->o_beta);
+  d.pops = reinterpret_cast<double*>(w + s->o_pops);
+  d.nphot = reinterpret_cast<double*>(w + s->o_nphot);
+  d.trace = reinterpret_cast<double*>(w + s->o_trace);
+  return d;
+}
+
+SpParams params(const lr_sparse* s) {
+  SpParams p;
+  p.N = s->N;
+  p.M = s->M;
+  p.K = s->K;
+  p.T = s->T;
+  p.n_levels = s->n_levels;
+  p.nblk = s->nblk;
+  p.NM = (long long)s->N * s->M;
+  p.ps = (long long)2 * (1 + s->K) * s->M * s->M + 4 + s->n_levels;
+  p.wd = s->wd;
+  p.tau = s->tau;
+  p.max_steps = s->max_steps;
+  p.n_rec = s->n_rec;
+  p.pop_every = s->pop_every;
+  return p;
+}
+
+// Trajectory records for the initial-state kernel: with N_r = N_f = 1 its
+// pure state is the basis state level0.
+std::vector<TrajDev> trajectories(const lr_sparse* s, const int* psi) {
+  std::vector<TrajDev> traj(s->T);
+  for (int i = 0; i < s->T; ++i) {
+    TrajDev t;
+    memset(&t, 0, sizeof(t));
+    t.N = s->N;
+    t.M = s->M;
+    t.ld = s->M;
+    t.Nt = 1;
+    t.Nr = 1;
+    t.Nf = 1;
+    t.n_modes = 3;
+    t.cand = i;
+    t.level0 = psi ? psi[i] : 0;
+    t.z_off = (long long)i * s->N * s->M;
+    traj[i] = t;
+  }
+  return traj;
+}
+
+}  // namespace
+
+extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int M, const lr_pulse* pulses, double tau,
+                                      long max_steps, int pop_every, lr_sparse** out) {
+  if (!out) return LR_ERR_ARG;
+  *out = nullptr;
+  if (!m || !pulses || !m->rowptr || !m->col || !m->val || !m->chan || !m->level) return LR_ERR_ARG;
+  if (m->N < 1 || m->N > (1 << 24) || m->n_jumps < 1 || m->n_jumps > LR_SPARSE_MAX_JUMPS) return LR_ERR_ARG;
+  if (m->n_levels < 1 || m->n_levels > LR_MAX_NT || m->nnz < 0 || m->nnz > (1L << 31) - 1) return LR_ERR_ARG;
+  if (n_traj < 1 || n_traj > 65535 || M < 1 || M > LR_MAX_RANK || M > m->N) return LR_ERR_ARG;
+  if (!(tau > 0.0) || max_steps < 1 || pop_every < 1 || !isfinite(m->wd)) return LR_ERR_ARG;
+  const int K = m->n_jumps, N = m->N;
+  for (int o = 0; o < K + 2; ++o) {
+    const int* rp = m->rowptr + (size_t)o * (N + 1);
+    for (int n = 0; n < N; ++n)
+      if (rp[n] < 0 || rp[n] > rp[n + 1] || rp[n + 1] > m->nnz) return LR_ERR_ARG;
+    for (int e = rp[0]; e < rp[N]; ++e)
+      if (o == K + 1 && m->chan[e] != 2) return LR_ERR_ARG;   // static readout operator
+  }
+  for (long e = 0; e < m->nnz; ++e)
+    if (m->col[e] < 0 || m->col[e] >= N || m->chan[e] >= NCH || !isfinite(m->val[2 * e]) || !isfinite(m->val[2 * e + 1]))
+      return LR_ERR_ARG;
+  for (int n = 0; n < N; ++n)
+    if (m->level[n] < 0 || m->level[n] >= m->n_levels) return LR_ERR_ARG;
+  for (int i = 0; i < n_traj; ++i) {
+    const lr_pulse& P = pulses[i];
+    if (P.kind != 0 && P.kind != 1) return LR_ERR_ARG;
+    const double wdp = P.kind == 0 ? P.p[1] : P.p[6], phi = P.kind == 0 ? P.p[3] : P.p[7];
+    if (phi != 0.0 || fabs(wdp - m->wd) > 1e-12 * fabs(m->wd)) return LR_ERR_ARG;
+    for (int k = 0; k < 8; ++k)
+      if (!isfinite(P.p[k])) return LR_ERR_ARG;
+  }
+  lr_sparse* s = new (std::nothrow) lr_sparse();
+  if (!s) return LR_ERR_NOMEM;
+  s->N = N;
+  s->M = M;
+  s->K = K;
+  s->T = n_traj;
+  s->n_levels = m->n_levels;
+  s->nblk = (N + SP_R - 1) / SP_R;
+  s->nnz = m->nnz;
+  s->max_steps = max_steps;
+  s->pop_every = pop_every;
+  s->n_rec = max_steps / pop_every + 1;
+  s->step = 0;
+  s->wd = m->wd;
+  s->tau = tau;
+  s->rowptr.assign(m->rowptr, m->rowptr + (size_t)(K + 2) * (N + 1));
+  s->col.assign(m->col, m->col + m->nnz);
+  s->val.assign(m->val, m->val + 2 * m->nnz);
+  s->chan.assign(m->chan, m->chan + m->nnz);
+  s->level.assign(m->level, m->level + N);
+  s->pulses.resize(n_traj);
+  for (int i = 0; i < n_traj; ++i) {
+    s->pulses[i].kind = pulses[i].kind;
+    for (int k = 0; k < 8; ++k) s->pulses[i].p[k] = pulses[i].p[k];
+  }
+  s->ws = nullptr;
+  s->ws_bytes = 0;
+  layout(s);
+  *out = s;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_workspace_size(const lr_sparse* s, size_t* bytes) {
+  if (!s || !bytes) return LR_ERR_ARG;
+  *bytes = s->total;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, size_t bytes, void* stream) {
+  if (!s || !workspace) return LR_ERR_ARG;
+  if (bytes < s->total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(s, LR_ERR_WORKSPACE, "workspace too small or not 256-byte aligned");
+  s->ws = static_cast<char*>(workspace);
+  s->ws_bytes = bytes;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const std::vector<TrajDev> traj = trajectories(s, nullptr);
+  std::vector<double2> val(s->nnz);
+  for (long e = 0; e < s->nnz; ++e) val[e] = make_double2(s->val[2 * e], s->val[2 * e + 1]);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(s->ws, 0, s->total, st)) != cudaSuccess) return cuda_fail(s, e);
+  struct Up {
+    size_t off;
+    const void* src;
+    size_t bytes;
+  } ups[] = {{s->o_rowptr, s->rowptr.data(), s->rowptr.size() * sizeof(int)},
+             {s->o_col, s->col.data(), s->col.size() * sizeof(int)},
+             {s->o_val, val.data(), val.size() * sizeof(double2)},
+             {s->o_chan, s->chan.data(), s->chan.size()},
+             {s->o_level, s->level.data(), s->level.size() * sizeof(int)},
+             {s->o_pulse, s->pulses.data(), s->pulses.size() * sizeof(PulseDev)},
+             {s->o_traj, traj.data(), traj.size() * sizeof(TrajDev)}};
+  for (const Up& u : ups)
+    if (u.bytes && (e = cudaMemcpyAsync(s->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(s, e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
+  s->step = 0;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_set_initial(lr_sparse* s, const int* psi, uint64_t seed, double eps, void* stream) {
+  if (!s || !psi) return LR_ERR_ARG;
+  if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
+  if (!(eps >= 0.0) || !((s->M - 1) * eps < 1.0)) return fail(s, LR_ERR_ARG, "eps out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < s->T; ++i)
+    if (psi[i] < 0 || psi[i] >= s->N) return fail(s, LR_ERR_ARG, "psi index out of range");
+  const std::vector<TrajDev> traj = trajectories(s, psi);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s->ws + s->o_traj, traj.data(), traj.size() * sizeof(TrajDev), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return cuda_fail(s, e);
+  SpDev d = dev(s);
+  DevPtrs p;
+  memset(&p, 0, sizeof(p));
+  p.traj = reinterpret_cast<const TrajDev*>(s->ws + s->o_traj);
+  p.Za = d.W;   // FP64 scratch of the state's layout
+  p.Zn = d.Z;
+  RunParams rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.n_traj = s->T;
+  if ((e = launch_initial_state(p, rp, s->N, 0, seed, eps, st)) != cudaSuccess) return cuda_fail(s, e);
+  if ((e = cudaMemcpyAsync(d.Zs, d.Z, (size_t)s->T * s->N * s->M * sizeof(double2), cudaMemcpyDeviceToDevice, st)) !=
+      cudaSuccess)
+    return cuda_fail(s, e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
+  s->step = 0;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_set_state(lr_sparse* s, const double* Z, long step, void* stream) {
+  if (!s || !Z) return LR_ERR_ARG;
+  if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
+  if (step < 0 || step > s->max_steps) return fail(s, LR_ERR_ARG, "step out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)s->T * s->N * s->M * sizeof(double2);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(s->ws + s->o_Z, Z, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(s, e);
+  if ((e = cudaMemcpyAsync(s->ws + s->o_Zs, s->ws + s->o_Z, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return cuda_fail(s, e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
+  s->step = step;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_get_state(const lr_sparse* s, double* Z, void* stream) {
+  if (!s || !Z || !s->ws) return LR_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LR_ERR_CUDA;
+  if (cudaMemcpy(Z, s->ws + s->o_Z, (size_t)s->T * s->N * s->M * sizeof(double2), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return LR_ERR_CUDA;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, void* stream) {
+  if (!s) return LR_ERR_ARG;
+  if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
+  if (!(dt > 0.0) || !isfinite(dt) || n_steps < 0) return fail(s, LR_ERR_ARG, "bad dt or n_steps");
+  if (s->step + n_steps > s->max_steps) return fail(s, LR_ERR_STATE, "integration past max_steps");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SpDev d = dev(s);
+  const SpParams p = params(s);
+  const dim3 ge((unsigned)((p.NM + SP_T - 1) / SP_T), (unsigned)s->T), gg((unsigned)s->nblk, (unsigned)s->T);
+  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  for (long i = 0; i <= n_steps; ++i) {
+    const long step = s->step + i;
+    const double t = (double)step * dt;
+    const bool rec = step % s->pop_every == 0;
+    if (i == n_steps) {   // observation of the final state
+      const int mode = MODE_BETA | (rec ? MODE_OBS : 0);
+      sp_apply<<<ge, SP_T, 0, st>>>(d, p, t, 1, 1);
+      sp_gram<<<gg, SP_T, 0, st>>>(d, p, mode);
+      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
+      break;
+    }
+    for (int stg = 0; stg < 4; ++stg) {
+      const int mode = MODE_SOLVE | (stg == 0 ? MODE_BETA | (rec ? MODE_OBS : 0) : 0);
+      sp_apply<<<ge, SP_T, 0, st>>>(d, p, t + cst[stg] * dt, stg == 0, 0);
+      sp_gram<<<gg, SP_T, 0, st>>>(d, p, mode);
+      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
+      sp_update<<<ge, SP_T, 0, st>>>(d, p, stg, dt);
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->step += n_steps;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_observables(lr_sparse* s, double* beta, double* pops, double* nphot, double* trace,
+                                           void* stream) {
+  if (!s) return LR_ERR_ARG;
+  if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
+  unsigned err = 0;
+  if ((e = cudaMemcpy(&err, s->ws + s->o_err, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(s, e);
+  struct Down {
+    void* dst;
+    size_t off, bytes;
+  } downs[] = {{beta, s->o_beta, (size_t)s->T * (s->max_steps + 1) * sizeof(double2)},
+               {pops, s->o_pops, (size_t)s->T * s->n_rec * s->n_levels * sizeof(double)},
+               {nphot, s->o_nphot, (size_t)s->T * s->n_rec * sizeof(double)},
+               {trace, s->o_trace, (size_t)s->T * s->n_rec * sizeof(double)}};
+  for (const Down& dn : downs)
+    if (dn.dst && (e = cudaMemcpy(dn.dst, s->ws + dn.off, dn.bytes, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(s, e);
+  if (err == DEV_NOT_PD) return fail(s, LR_ERR_NOT_PD, "Gram matrix not positive definite");
+  if (err == DEV_NONFINITE) return fail(s, LR_ERR_NONFINITE, "non-finite state or signal");
+  if (err) return fail(s, LR_ERR_CUDA, "device error");
+  return LR_OK;
+}
+
+extern "C" const char* lr_sparse_last_error(const lr_sparse* s) { return s ? s->msg.c_str() : "null context"; }
+
+extern "C" void lr_sparse_destroy(lr_sparse* s) { delete s; }

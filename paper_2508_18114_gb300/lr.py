@@ -36,6 +36,9 @@ EXPORTS = (
     "lr_observables", "lr_sync", "lr_query", "lr_status_string",
     "lr_last_error", "lr_destroy", "lr_integrate_plain_noalloc",
     "lr_backward_workspace_size", "lr_backward", "lr_loss", "lr_diagnostics",
+    "lr_paper_model_size", "lr_paper_model_build", "lr_sparse_create", "lr_sparse_workspace_size",
+    "lr_sparse_bind_workspace", "lr_sparse_set_initial", "lr_sparse_set_state", "lr_sparse_get_state",
+    "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_last_error", "lr_sparse_destroy",
 )
 
 
@@ -105,8 +108,23 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_backward.argtypes = [vp, vp, C.c_size_t, vp, vp, i, vp]
     lib.lr_loss.argtypes = [vp, vp, vp, vp]
     lib.lr_diagnostics.argtypes = [vp, vp, vp, vp]
+    lib.lr_paper_model_size.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_long)]
+    lib.lr_paper_model_build.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.lr_sparse_create.argtypes = [vp, i, i, vp, d, l, i, C.POINTER(vp)]
+    lib.lr_sparse_workspace_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+    lib.lr_sparse_bind_workspace.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.lr_sparse_set_initial.argtypes = [vp, vp, C.c_uint64, d, vp]
+    lib.lr_sparse_set_state.argtypes = [vp, vp, l, vp]
+    lib.lr_sparse_get_state.argtypes = [vp, vp, vp]
+    lib.lr_sparse_integrate.argtypes = [vp, d, l, vp]
+    lib.lr_sparse_observables.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.lr_sparse_last_error.argtypes = [vp]
+    lib.lr_sparse_last_error.restype = C.c_char_p
+    lib.lr_sparse_destroy.argtypes = [vp]
+    lib.lr_sparse_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("lr_status_string", "lr_last_error", "lr_destroy"):
+        if name not in ("lr_status_string", "lr_last_error", "lr_destroy", "lr_sparse_last_error",
+                        "lr_sparse_destroy"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

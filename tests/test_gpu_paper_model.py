@@ -1,0 +1,98 @@
+"""GPU parity of the sparse-operator engine on the paper's own model (Sec. S2)
+against the FP64 oracle (Eq. S5 with the time-dependent operators of the frame
+of the drive), through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import init_state
+from oracle import paper_model as pm
+from oracle import pulse as opulse
+
+pytestmark = pytest.mark.gpu
+
+TP = 2.0 * np.pi
+SEED, EPS = 20250818, 1e-5
+
+
+def _params(**over):
+    P = dict(Ec=TP * 0.315, Ej=51 * TP * 0.315, wr=TP * 7.2, wf=TP * 7.21, g=TP * 0.15, J=TP * 0.03,
+             kappa=TP * 0.03, gamma=TP * 8e-6, wd=TP * 7.18)
+    P.update(over)
+    return P
+
+
+def _run(dims, M, pulses, tau, dt, n_steps, pop_every, check_traj, params, split=None):
+    import torch
+    from paper_2508_18114_gb300 import sparse
+    Nl, Nu, Nt = dims
+    model = sparse.paper_model(Nl, Nu, Nt, **params)
+    T = len(pulses)
+    psi = [i % 2 for i in range(T)]          # |0_l, 0_u, g> and |0_l, 0_u, e>
+    b = sparse.SparseBatch(model, M, pulses, tau, n_steps, pop_every=pop_every)
+    b.set_initial(psi, SEED, EPS)
+    if split:
+        b.integrate(dt, split)
+        b.integrate(dt, n_steps - split)
+    else:
+        b.integrate(dt, n_steps)
+    got = b.observables()
+    torch.cuda.synchronize()
+    ora_model = pm.PaperModel(Nl, Nu, Nt, frame="rot", **params)
+    for tj in check_traj:
+        kind, p = pulses[tj]
+        env = lambda t, kind=kind, p=p: opulse.envelope(kind, p, t, tau)  # noqa: E731
+        m0 = init_state.initial_state(ora_model.N, M, psi[tj], EPS, SEED, tj)
+        want = pm.integrate(m0, ora_model, env, dt, n_steps, pop_every=pop_every, low_rank=True)
+        bs = np.abs(want["beta"]).max()
+        assert np.abs(got["beta"][tj] - want["beta"]).max() <= 1e-10 * max(bs, 1e-3), tj
+        assert np.abs(got["pops"][tj] - want["pops"]).max() <= 1e-10, tj
+        assert np.abs(got["nphot"][tj] - want["nr"]).max() <= 1e-10 * max(want["nr"].max(), 1.0), tj
+        assert np.abs(got["trace"][tj] - want["trace"]).max() <= 1e-11, tj
+    return got
+
+
+def test_small_model_parity():
+    """N = 72 (6 x 3 x 4), M = 4, two candidates x {g, e}, strong short drive."""
+    P = _params(g=TP * 0.3, kappa=1.0, gamma=0.05)
+    wd = P["wd"]
+    tau = 0.4
+    pulses = [(0, [TP * 1.0, wd, 0.05, 0.0]), (0, [TP * 0.6, wd, 0.08, 0.0])] * 2
+    pulses = [pulses[0], pulses[0], pulses[1], pulses[1]]
+    got = _run((6, 3, 4), 4, pulses, tau, 5e-4, 800, 100, [0, 1, 3], P)
+    assert np.abs(got["beta"][0]).max() > 1e-2           # the drive does displace the readout mode
+
+
+def test_ragged_blocks_and_split_integrate():
+    """N = 150 (10 x 3 x 5): nine full 16-row blocks and a 6-row tail; two
+    integrate calls continue one run; two-segment pulse."""
+    P = _params(kappa=2.0, gamma=0.1)
+    wd = P["wd"]
+    tau = 0.3
+    pulses = [(1, [TP * 0.8, TP * 0.3, 0.15, 0.05, 0.05, 0.03, wd, 0.0])] * 2
+    _run((10, 3, 5), 6, pulses, tau, 5e-4, 600, 50, [0, 1], P, split=257)
+
+
+def test_full_size_sampled():
+    """The paper's Hilbert-space size N = 2000 (N_l = 100, N_u = 4, N_t = 5)
+    at M = 20, eight trajectories, 40 steps; trajectories 0 and 7 against the oracle."""
+    P = _params()
+    wd = P["wd"]
+    tau = 40.0
+    pulses = [(0, [TP * (0.10 + 0.01 * (i // 2)), wd, 2.5, 0.0]) for i in range(8)]
+    _run((100, 4, 5), 20, pulses, tau, 5e-4, 40, 10, [0, 7], P)
+
+
+def test_capacity_and_errors():
+    from paper_2508_18114_gb300 import lr, sparse
+    P = _params()
+    model = sparse.paper_model(4, 2, 3, **P)
+    b = sparse.SparseBatch(model, 3, [(0, [1.0, P["wd"], 0.5, 0.0])] * 2, 1.0, 10)
+    b.set_initial([0, 1], SEED, EPS)
+    b.integrate(1e-3, 10)
+    with pytest.raises(lr.LrError) as e:
+        b.integrate(1e-3, 1)
+    assert e.value.status == 8                           # LR_ERR_STATE past max_steps
+    with pytest.raises(lr.LrError):
+        b.set_initial([0, 99], SEED, EPS)                 # basis index out of range
+    obs = b.observables()
+    assert np.all(np.isfinite(obs["beta"]))
