@@ -208,6 +208,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "paper":
+        return run_reference_paper(args)
     wl = load_workload(args)
     prec = args.precision or getattr(wl, "precision", "fp64")
     ns = args.cpu_steps or default_cpu_steps(wl)
@@ -228,6 +230,31 @@ def run_reference(args):
         "pulse_evals_per_s": value / (2 * desc["steps_per_pulse"]),
         "cpu_baseline": {"value": value, "unit": "traj*steps/s", "cores": ntraj, "kind": "oracle",
                          "sample": "%d RK4 steps of the g and e trajectories of candidate 0 per step" % ns},
+        "e2e": {"value": value, "unit": "traj*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_reference_paper(args):
+    import lr_inputs as li
+    from oracle import paper_model as pm
+    wl = li.paper(args.candidates if args.candidates is not None else 256)
+    model_o = pm.PaperModel(*wl.dims, frame="rot", **wl.params)
+    ns = args.cpu_steps or 400
+    for _ in range(args.warmup):
+        paper_oracle_sample(wl, model_o, max(2, ns // 10))
+    tt = 0.0
+    for _ in range(args.steps):
+        tt += paper_oracle_sample(wl, model_o, ns)[1]
+    value = ns * args.steps / tt
+    line = {
+        "impl": "reference", "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper: normal-mode model of Sec. S2, N=%d, M=%d, dt=%g ns"
+                               % (model_o.N, wl.M, wl.dt), "parallelism": "cpu oracle, one trajectory"},
+        "cpu_baseline": {"value": value, "unit": "traj*steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d RK4 steps of trajectory 0 per step" % ns},
         "e2e": {"value": value, "unit": "traj*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -467,9 +494,155 @@ def run_adjoint(args):
     b.close()
 
 
+# ------------------------------------------------- the paper's own model
+def paper_flops_per_stage(model, M):
+    """Algorithmic flops of one RK4 stage of one trajectory on the sparse engine
+    (complex MAC = 8): one MAC per operator entry and column for A Z and L_k Z,
+    the Gram upper triangle and Z^dag L_k Z per row, the projection term
+    Y_k X_k^dag per element, the RK4 update ~ 12 N M."""
+    N, K = model["N"], model["n_jumps"]
+    rp = model["rowptr"]
+    entries = sum(int(rp[o * (N + 1) + N] - rp[o * (N + 1)]) for o in range(K + 1))
+    return 8 * entries * M + 8 * N * (M * (M + 1) // 2 + K * M * M) + 8 * K * N * M * M + 12 * N * M
+
+
+def paper_oracle_sample(wl, model_o, n_steps, traj=0):
+    """FP64 oracle on one trajectory of the paper's model: (traj-steps/s, seconds, result)."""
+    from oracle import init_state
+    from oracle import paper_model as pm
+    from oracle import pulse as opulse
+    kind, p = wl.pulses[traj // 2]
+    env = lambda t: opulse.envelope(kind, p, t, wl.tau)  # noqa: E731
+    m0 = init_state.initial_state(model_o.N, wl.M, traj % 2, wl.eps, wl.init_seed, traj)
+    t0 = time.perf_counter()
+    out = pm.integrate(m0, model_o, env, wl.dt, n_steps, pop_every=n_steps, low_rank=True)
+    dt = time.perf_counter() - t0
+    return n_steps / dt, dt, out
+
+
+def run_paper(args):
+    """Sparse-operator engine on the paper's normal-mode model (FP64)."""
+    import numpy as np
+    import torch
+    import lr_inputs as li
+    from paper_2508_18114_gb300 import sparse
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.candidates if args.candidates is not None else 256
+    wl = li.paper(n, first=rank * n)
+    model = sparse.paper_model(*wl.dims, **wl.params)
+    T = 2 * n
+    pulses = [q for q in wl.pulses for _ in (0, 1)]
+    spp = int(round(wl.tau / wl.dt))
+    chunk = args.chunk or 40
+    total = chunk * (args.warmup + args.steps)
+    prec = args.precision or "fp32_g64"
+    b = sparse.SparseBatch(model, wl.M, pulses, wl.tau, spp, pop_every=chunk, device=dev, precision=prec)
+    psi = [i % 2 for i in range(T)]
+    b.set_initial(psi, wl.init_seed + 7919 * rank, wl.eps)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        b.integrate(wl.dt, chunk)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        b.integrate(wl.dt, chunk)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms_local = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    value, ms, _ = aggregate(ms_local, T * chunk * args.steps, dist)
+    mhz = clocks.get("sm_mhz") or 2070.0
+    fl = paper_flops_per_stage(model, wl.M) * 4 * chunk * T
+    fma_clk = FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK
+    peak = SMS * fma_clk * 2 * mhz * 1e6 / 1e12
+    achieved = fl / (ms * 1e-3 / args.steps) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "integrate (sparse engine, 4 launches per RK4 stage)",
+                "peak_source": "%s FMA pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
+                               % ("FP64" if prec == "fp64" else "FP32", fma_clk, mhz), "flops_per_step": fl}
+    launches = (16 * chunk + 3) * args.steps
+
+    e2e = None
+    if not args.no_e2e:
+        Zh = b.get_state()
+        step0 = b.max_steps - chunk      # any slice inside the pulse run
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 2))
+        obs = None
+        for _ in range(reps):
+            b.set_state(Zh, step=step0)
+            b.integrate(wl.dt, chunk)
+            obs = b.observables()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * T * chunk * reps / te, "unit": "traj*steps/s", "h2d_bytes_per_step": int(Zh.nbytes),
+               "d2h_bytes_per_step": int(sum(v.nbytes for v in obs.values()))}
+
+    cpu = err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import paper_model as pm
+        model_o = pm.PaperModel(*wl.dims, frame="rot", **wl.params)
+        ns = args.cpu_steps or 400
+        v, dt_cpu, ora = paper_oracle_sample(wl, model_o, ns, traj=1)
+        cpu = {"value": v, "unit": "traj*steps/s", "cores": 1, "kind": "oracle",
+               "sample": "%d RK4 steps of trajectory 1 (candidate 0, |e>) (%.1f s)" % (ns, dt_cpu)}
+        bq = sparse.SparseBatch(model, wl.M, pulses[:2], wl.tau, ns, pop_every=ns, device=dev, precision=prec)
+        bq.set_initial([0, 1], wl.init_seed, wl.eps)
+        bq.integrate(wl.dt, ns)
+        og = bq.observables()
+        bo = ora["beta"]
+        err = {"sample": "candidate 0, |e>, %d RK4 steps" % ns,
+               "beta_rel": float(np.abs(og["beta"][1] - bo).max() / np.abs(bo).max()),
+               "pops_abs": float(np.abs(og["pops"][1] - ora["pops"]).max())}
+        del bq
+
+    if rank == 0:
+        line = {
+            "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32 (f64 Gram/Cholesky/signal)",
+            "data": "synthetic (seeded flat-top pulses, seeded initial states)",
+            "config": {"workload": "paper: %d candidates x {g,e} = %d trajectories, normal-mode model of Sec. S2 "
+                                   "(rotated frame, counter-rotating terms kept), N=%d (%s), M=%d, dt=%g ns, "
+                                   "tau=%g ns, %s" % (n, T, model["N"], "x".join(map(str, wl.dims)), wl.M,
+                                                      wl.dt, wl.tau, prec),
+                       "trajectories": T, "N": model["N"], "M": wl.M, "nnz": int(model["nnz"]),
+                       "engine": "sparse", "chunk_rk4_steps": chunk,
+                       "parallelism": "dp%d (independent replicas)" % world,
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "pulse_evals_per_s": value / (2 * spp),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "error_vs_oracle": err,
+        }
+        print(json.dumps(line))
+    del b
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload == "paper" and args.impl != "reference":
+        run_paper(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.adjoint:
         run_adjoint(args)

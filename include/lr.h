@@ -410,13 +410,17 @@ lr_status lr_paper_model_build(const lr_paper_params* p, int* rowptr, int* col, 
  * (1 <= M <= min(N, LR_MAX_RANK)) on one operator set; trajectory i uses
  * pulses[i]. Copies the operator arrays (they may be freed afterwards).
  * tau places the falling pulse edge; max_steps and pop_every size the
- * recorded observables as for lr_options. The engine is FP64 throughout:
- * per RK4 stage an apply kernel (A Z, L_k Z, r Z from the CSR rows, one
- * thread per element of Z), a row-block Gram kernel (Z^dag Z, Z^dag L_k Z
- * and the observables), a per-trajectory solve (Cholesky, X_k = G^-1 Z^dag L_k Z)
- * and an update kernel (F = A Z + 1/2 sum_k (L_k Z) X_k^dag, RK4). */
-lr_status lr_sparse_create(const lr_sparse_model* model, int n_traj, int M, const lr_pulse* pulses,
-                           double tau, long max_steps, int pop_every, lr_sparse** out);
+ * recorded observables as for lr_options. Per RK4 stage: an apply kernel
+ * (A Z, L_k Z, r Z from the CSR rows, one thread per element of Z), a
+ * row-block Gram kernel (Z^dag Z, Z^dag L_k Z and the observables), a
+ * per-trajectory solve (Cholesky, X_k = G^-1 Z^dag L_k Z) and an update
+ * kernel (F = A Z + 1/2 sum_k (L_k Z) X_k^dag, RK4).
+ * precision: LR_PREC_FP64 (complex128 throughout) or LR_PREC_FP32_G64 (state,
+ * apply, Z^dag L_k Z, projection term and RK4 in complex64; the Gram matrix
+ * accumulated in FP64 from the exact products of the FP32 entries; Cholesky,
+ * solves and observables in FP64); others give LR_ERR_UNSUPPORTED. */
+lr_status lr_sparse_create(const lr_sparse_model* model, int n_traj, int M, lr_precision precision,
+                           const lr_pulse* pulses, double tau, long max_steps, int pop_every, lr_sparse** out);
 /* Bytes of device workspace the context needs (256-byte aligned). */
 lr_status lr_sparse_workspace_size(const lr_sparse* s, size_t* bytes);
 /* Binds a caller-owned device buffer (>= lr_sparse_workspace_size, 256-byte

@@ -19,8 +19,12 @@ from the transmon ground state |g> and the first excited state |e>):
 * ``c4`` - 256 candidates on the c2 model (N=2000, M=20).
 * ``c5`` - 64 candidates on transmon 10 x resonator 40 x filter 20
   (N=8000), M=32.
+* ``paper`` - the paper's own normal-mode model (Sec. S2.B parameters),
+  lower x upper normal mode x transmon = 100 x 4 x 5 (N=2000), M=20, 256
+  flat-top pulses at the frame frequency.
 """
 from .configs import (  # noqa: F401
     TWO_PI, Candidate, ModelParams, PulseParams, Workload, SplitMix64Stream,
     workload, sizes, c1, c2, c3, c4, c5, pulse_flat_top, pulse_two_segment,
+    PaperWorkload, paper, paper_params,
 )

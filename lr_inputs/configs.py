@@ -214,6 +214,43 @@ def c5(n_candidates: int = 64, n_steps: Optional[int] = None, first: int = 0) ->
     return Workload("c5", cands, dt, ns, ns * dt, init_seed=1005, precision="fp32_g64")
 
 
+@dataclasses.dataclass(frozen=True)
+class PaperWorkload:
+    """Inputs of the paper's own model: parameters of Sec. S2.B (rad/ns, 1/ns),
+    cutoffs, rank, step and a population of flat-top pulses (Sec. S2.C, ramp
+    2.5 ns, drive at the frame frequency w_d, no phase)."""
+    name: str
+    params: dict
+    dims: tuple
+    M: int
+    dt: float
+    tau: float
+    eps: float
+    init_seed: int
+    pulses: tuple        # ((kind, p), ...) per candidate
+
+
+def paper_params() -> dict:
+    """Sec. S2.B: E_c/2pi = 315 MHz, E_j/E_c = 51, g/2pi = 150 MHz,
+    J/2pi = 30 MHz, w_r/2pi = 7.2 GHz, w_f/2pi = 7.21 GHz, kappa/2pi = 30 MHz
+    (filter), gamma/2pi = 8 kHz (transmon), w_d/2pi = 7.18 GHz."""
+    Ec = TWO_PI * 0.315
+    return dict(Ec=Ec, Ej=51.0 * Ec, wr=TWO_PI * 7.2, wf=TWO_PI * 7.21, g=TWO_PI * 0.15, J=TWO_PI * 0.03,
+                kappa=TWO_PI * 0.03, gamma=TWO_PI * 8e-6, wd=TWO_PI * 7.18)
+
+
+def paper(n_candidates: int = 256, first: int = 0, dims=(100, 4, 5), M: int = 20) -> PaperWorkload:
+    """Candidates first .. first + n_candidates - 1: flat-top amplitudes
+    Omega/2pi drawn in (0, 300] MHz around the paper's 150 MHz square pulse.
+    N = N_l N_u N_t = 2000 at the default cutoffs (the paper's Fig. 2 size)."""
+    P = paper_params()
+    pulses = []
+    for i in range(first, first + n_candidates):
+        s = SplitMix64Stream(8 + i)
+        pulses.append((0, (s.uniform_open_low(TWO_PI * 0.3), P["wd"], 2.5, 0.0)))
+    return PaperWorkload("paper", P, tuple(dims), M, 5e-4, 40.0, 1e-5, 1008, tuple(pulses))
+
+
 def workload(name: str, **kw) -> Workload:
     return {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c5": c5}[name](**kw)
 

@@ -6,8 +6,9 @@
 //   sp_apply  - one thread per element (n, m) of the stage input Zs:
 //               W = A(t) Zs with A = -i H_eff, Y_k = L_k(t) Zs, and at stage 1
 //               of every step Yr = r Zs; the ten channel factors
-//               Omega(t)^a e^{i q w_d t} are formed once per block;
-//   sp_gram   - per block of SP_R rows: partial sums of G = Zs^dag Zs (upper
+//               Omega(t)^a e^{i q w_d t} of the step's four stage times come
+//               from sp_chi, one small launch per step;
+//   sp_gram   - per block of 16 (FP64) or 32 (FP32) rows: partial sums of G = Zs^dag Zs (upper
 //               triangle), T_k = Zs^dag Y_k, and at stage 1 tr(Zs^dag Yr) =
 //               tr(rho r), plus level populations, |Yr|^2 and |Zs|^2 at
 //               recording steps;
@@ -17,6 +18,11 @@
 //   sp_update - F = W + 1/2 sum_k Y_k X_k^dag, then the classical RK4 stage.
 // After the last step an observation pass (apply r, Gram, solve without
 // Cholesky) records beta and the observables of the final state.
+//
+// Precisions: FP64 throughout, or FP32_G64 - the state, the operator apply,
+// T_k, the projection term and the RK4 update in FP32, the Gram matrix
+// accumulated in FP64 from the exact products of FP32 entries (an FP32
+// product has 48 significant bits), Cholesky, solves and the signal in FP64.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -31,22 +37,47 @@ namespace lr {
 namespace {
 
 constexpr int SP_T = 256;   // threads per block
-constexpr int SP_R = 16;    // rows per Gram block
+// rows per Gram block: 16 complex128 or 32 complex64 rows of Z and of the K + 1
+// operator images fit the 48 KB of static shared memory
+template <typename T2> __host__ __device__ constexpr int rows_per_block();
+template <> __host__ __device__ constexpr int rows_per_block<double2>() { return 16; }
+template <> __host__ __device__ constexpr int rows_per_block<float2>() { return 32; }
 constexpr int NCH = 10;     // time channels
 
 struct SpDev {
   const int* rowptr;
   const int* col;
   const double2* val;
+  const float2* valf;   // FP32 copy of val
   const unsigned char* chan;
   const int* level;
   const PulseDev* pulse;
   unsigned* err;
-  double2 *Z, *Zs, *acc, *W, *Y, *Yr, *X;
+  void *Z, *Zs, *acc, *W, *Y, *Yr;   // state-type arrays (double2 or float2)
+  double2* X;
+  double2* chi;   // [T][4][NCH] channel factors at the four stage times of the current step
   double* part;
   double2* beta;
   double *pops, *nphot, *trace;
 };
+
+template <typename T2> struct Scalar;
+template <> struct Scalar<double2> { using type = double; };
+template <> struct Scalar<float2> { using type = float; };
+
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+template <typename T2> __device__ __forceinline__ T2 from_d(double2 v);
+template <> __device__ __forceinline__ double2 from_d<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <typename T2> __device__ __forceinline__ T2 mk2(typename Scalar<T2>::type r, typename Scalar<T2>::type i) {
+  T2 v;
+  v.x = r;
+  v.y = i;
+  return v;
+}
+__device__ __forceinline__ const double2& op_val(const SpDev& d, int e, double2) { return d.val[e]; }
+__device__ __forceinline__ const float2& op_val(const SpDev& d, int e, float2) { return d.valf[e]; }
 
 struct SpParams {
   int N, M, K, T, n_levels, nblk;
@@ -59,74 +90,103 @@ struct SpParams {
 
 enum : int { MODE_SOLVE = 1, MODE_OBS = 2, MODE_BETA = 4 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
-  return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  return mk2<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T2> __device__ __forceinline__ T2 cfma(T2 a, T2 b, T2 c) {
+  return mk2<T2>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 // conj(a) * b + c
-__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 c) {
-  return mk(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+template <typename T2> __device__ __forceinline__ T2 cfma_conj(T2 a, T2 b, T2 c) {
+  return mk2<T2>(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 
-__device__ void channel_factors(const PulseDev& P, const SpParams& p, double t, double2* chi) {
-  const int c = threadIdx.x;
-  if (c < NCH) {
-    const int a = c / 5, q = c % 5 - 2;
-    const double om = a ? pulse_envelope(P, p.tau, t) : 1.0;
-    double sn, cs;
-    sincos((double)q * p.wd * t, &sn, &cs);
-    chi[c] = mk(om * cs, om * sn);
-  }
+// Double-word FP32 accumulator (hi + lo): s += a b with the product split
+// exactly by one FMA (TwoProduct) and the sum by Knuth's TwoSum.
+struct DWs {
+  float hi, lo;
+};
+__device__ __forceinline__ void dw_acc(DWs& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+// Channel factors Omega(t)^a e^{i q w_d t} of one trajectory at the four RK4
+// stage times t, t + dt/2, t + dt/2, t + dt (one thread per factor).
+__global__ void __launch_bounds__(64) sp_chi(SpDev d, SpParams p, double t, double dt) {
+  const int tj = blockIdx.x, c = threadIdx.x;
+  if (c >= 4 * NCH) return;
+  const int stage = c / NCH, ch = c - stage * NCH;
+  const double ts = t + (stage == 0 ? 0.0 : stage == 3 ? dt : 0.5 * dt);
+  const int a = ch / 5, q = ch % 5 - 2;
+  const double om = a ? pulse_envelope(d.pulse[tj], p.tau, ts) : 1.0;
+  double sn, cs;
+  sincos((double)q * p.wd * ts, &sn, &cs);
+  d.chi[(size_t)tj * 4 * NCH + c] = mk(om * cs, om * sn);
 }
 
 // out[e] = sum over the row's entries of chi[ch] val Zs[col][m]
-__device__ __forceinline__ double2 row_apply(const SpDev& d, const SpParams& p, int op, int n, int m,
-                                             const double2* __restrict__ Zs, const double2* chi) {
+template <typename T2>
+__device__ __forceinline__ T2 row_apply(const SpDev& d, const SpParams& p, int op, int n, int m,
+                                        const T2* __restrict__ Zs, const T2* chi) {
   const int* rp = d.rowptr + (size_t)op * (p.N + 1);
-  double2 acc = mk(0.0, 0.0);
+  T2 acc = mk2<T2>(0, 0);
   for (int e = rp[n]; e < rp[n + 1]; ++e) {
-    const double2 v = cmul(chi[d.chan[e]], d.val[e]);
+    const T2 v = cmul(chi[d.chan[e]], op_val(d, e, T2()));
     acc = cfma(v, Zs[(size_t)d.col[e] * p.M + m], acc);
   }
   return acc;
 }
 
-__global__ void __launch_bounds__(SP_T) sp_apply(SpDev d, SpParams p, double t, int with_r, int only_r) {
-  __shared__ double2 chi[NCH];
+template <typename T2>
+__global__ void __launch_bounds__(SP_T) sp_apply(SpDev d, SpParams p, int stage, int with_r, int only_r) {
+  __shared__ T2 chi[NCH];
   const int tj = blockIdx.y;
-  channel_factors(d.pulse[tj], p, t, chi);
+  if (threadIdx.x < NCH) chi[threadIdx.x] = from_d<T2>(d.chi[((size_t)tj * 4 + stage) * NCH + threadIdx.x]);
   __syncthreads();
   const long long e = (long long)blockIdx.x * SP_T + threadIdx.x;
   if (e >= p.NM) return;
   const int n = (int)(e / p.M), m = (int)(e - (long long)n * p.M);
   const size_t off = (size_t)tj * p.NM;
-  const double2* Zs = d.Zs + off;
+  const T2* Zs = static_cast<const T2*>(d.Zs) + off;
   if (!only_r) {
-    d.W[off + e] = row_apply(d, p, 0, n, m, Zs, chi);
-    for (int k = 0; k < p.K; ++k) d.Y[((size_t)k * p.T + tj) * p.NM + e] = row_apply(d, p, 1 + k, n, m, Zs, chi);
+    static_cast<T2*>(d.W)[off + e] = row_apply(d, p, 0, n, m, Zs, chi);
+    for (int k = 0; k < p.K; ++k)
+      static_cast<T2*>(d.Y)[((size_t)k * p.T + tj) * p.NM + e] = row_apply(d, p, 1 + k, n, m, Zs, chi);
   }
-  if (with_r) d.Yr[off + e] = row_apply(d, p, 1 + p.K, n, m, Zs, chi);
+  if (with_r) static_cast<T2*>(d.Yr)[off + e] = row_apply(d, p, 1 + p.K, n, m, Zs, chi);
 }
 
+template <typename T2>
 __global__ void __launch_bounds__(SP_T) sp_gram(SpDev d, SpParams p, int mode) {
-  __shared__ double2 sZ[SP_R][LR_MAX_RANK], sY[LR_SPARSE_MAX_JUMPS + 1][SP_R][LR_MAX_RANK];
-  __shared__ double sw[SP_R], sr[SP_R];
-  __shared__ int slev[SP_R];
+  using T = typename Scalar<T2>::type;
+  constexpr int R = rows_per_block<T2>();
+  __shared__ T2 sZ[R][LR_MAX_RANK], sY[LR_SPARSE_MAX_JUMPS + 1][R][LR_MAX_RANK];
+  __shared__ T rsum[R][4];
+  __shared__ int slev[R];
   const int tj = blockIdx.y, b = blockIdx.x, M = p.M, K = p.K;
-  const int r0 = b * SP_R, rows = min(SP_R, p.N - r0);
+  const int r0 = b * R, rows = min(R, p.N - r0);
   const size_t off = (size_t)tj * p.NM;
   const bool solve = mode & MODE_SOLVE, obs = mode & MODE_OBS, beta = mode & MODE_BETA;
-  for (int e = threadIdx.x; e < SP_R * M; e += SP_T) {
+  const T2* Zs = static_cast<const T2*>(d.Zs);
+  const T2* Yk = static_cast<const T2*>(d.Y);
+  const T2* Yr = static_cast<const T2*>(d.Yr);
+  for (int e = threadIdx.x; e < R * M; e += SP_T) {
     const int i = e / M, m = e - (e / M) * M;
-    double2 z = mk(0, 0), yr = mk(0, 0);
+    T2 z = mk2<T2>(0, 0), yr = mk2<T2>(0, 0);
     if (i < rows) {
       const size_t idx = off + (size_t)(r0 + i) * M + m;
-      z = d.Zs[idx];
-      if (beta) yr = d.Yr[idx];
+      z = Zs[idx];
+      if (beta) yr = Yr[idx];
       if (solve)
-        for (int k = 0; k < K; ++k) sY[k][i][m] = d.Y[(size_t)k * p.T * p.NM + idx];
+        for (int k = 0; k < K; ++k) sY[k][i][m] = Yk[(size_t)k * p.T * p.NM + idx];
     } else if (solve) {
-      for (int k = 0; k < K; ++k) sY[k][i][m] = mk(0, 0);
+      for (int k = 0; k < K; ++k) sY[k][i][m] = mk2<T2>(0, 0);
     }
     sZ[i][m] = z;
     sY[LR_SPARSE_MAX_JUMPS][i][m] = yr;
@@ -139,45 +199,65 @@ __global__ void __launch_bounds__(SP_T) sp_gram(SpDev d, SpParams p, int mode) {
     for (int e = threadIdx.x; e < (1 + K) * MM; e += SP_T) {
       const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
       if (mat == 0 && i > j) continue;
-      double2 s = mk(0.0, 0.0);
-      for (int r = 0; r < rows; ++r) s = cfma_conj(sZ[r][i], mat == 0 ? sZ[r][j] : sY[mat - 1][r][j], s);
+      double2 s;
+      if (mat == 0) {
+        if constexpr (sizeof(T) == 4) {   // G from exact FP32 products, double-word sums
+          DWs re{0.f, 0.f}, im{0.f, 0.f};
+          for (int r = 0; r < rows; ++r) {   // conj(a) c
+            const float2 a = sZ[r][i], c = sZ[r][j];
+            dw_acc(re, a.x, c.x);
+            dw_acc(re, a.y, c.y);
+            dw_acc(im, a.x, c.y);
+            dw_acc(im, -a.y, c.x);
+          }
+          s = mk((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+        } else {
+          s = mk(0.0, 0.0);
+          for (int r = 0; r < rows; ++r) s = cfma_conj(to_d(sZ[r][i]), to_d(sZ[r][j]), s);
+        }
+      } else {   // T_k in the state's arithmetic
+        T2 t = mk2<T2>(0, 0);
+        for (int r = 0; r < rows; ++r) t = cfma_conj(sZ[r][i], sY[mat - 1][r][j], t);
+        s = to_d(t);
+      }
       out[2 * e] = s.x;
       out[2 * e + 1] = s.y;
     }
   }
   const size_t o2 = (size_t)2 * (1 + K) * MM;   // beta re, im, nphot, trace, pops[n_levels]
   if (beta || obs) {
-    for (int i = threadIdx.x; i < SP_R; i += SP_T) {
-      double w = 0.0, q = 0.0;
-      if (i < rows)
-        for (int m = 0; m < M; ++m) {
-          const double2 z = sZ[i][m], y = sY[LR_SPARSE_MAX_JUMPS][i][m];
-          w += z.x * z.x + z.y * z.y;
-          q += y.x * y.x + y.y * y.y;
-        }
-      sw[i] = w;
-      sr[i] = q;
+    // one warp per row, lanes over m: conj(z) r z, |r z|^2, |z|^2 in the state's
+    // arithmetic; then one lane per row; fixed-order shuffle sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < R; r += SP_T / 32) {
+      T v[4] = {0, 0, 0, 0};
+      if (r < rows && lane < M) {
+        const T2 z = sZ[r][lane], y = sY[LR_SPARSE_MAX_JUMPS][r][lane];
+        v[0] = fma(z.x, y.x, z.y * y.y);
+        v[1] = fma(z.x, y.y, -z.y * y.x);
+        v[2] = fma(y.x, y.x, y.y * y.y);
+        v[3] = fma(z.x, z.x, z.y * z.y);
+      }
+      for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 4; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+      if (lane == 0)
+        for (int c = 0; c < 4; ++c) rsum[r][c] = v[c];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double2 bsum = mk(0.0, 0.0);
-      double nph = 0.0, tr = 0.0;
-      for (int r = 0; r < rows; ++r) {
-        for (int m = 0; m < M; ++m) bsum = cfma_conj(sZ[r][m], sY[LR_SPARSE_MAX_JUMPS][r][m], bsum);
-        nph += sr[r];
-        tr += sw[r];
-      }
-      out[o2] = bsum.x;
-      out[o2 + 1] = bsum.y;
-      out[o2 + 2] = nph;
-      out[o2 + 3] = tr;
+    if (warp == 0) {
+      T v[4];
+      for (int c = 0; c < 4; ++c) v[c] = lane < rows ? rsum[lane][c] : (T)0;
+      for (int o = 16; o > 0; o >>= 1)
+        for (int c = 0; c < 4; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+      if (lane == 0)
+        for (int c = 0; c < 4; ++c) out[o2 + c] = (double)v[c];
+      if (obs)
+        for (int l = 0; l < p.n_levels; ++l) {
+          T w = (lane < rows && slev[lane] == l) ? rsum[lane][3] : (T)0;
+          for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+          if (lane == 0) out[o2 + 4 + l] = (double)w;
+        }
     }
-    if (obs)
-      for (int l = threadIdx.x; l < p.n_levels; l += SP_T) {
-        double acc = 0.0;
-        for (int r = 0; r < rows; ++r) acc += slev[r] == l ? sw[r] : 0.0;
-        out[o2 + 4 + l] = acc;
-      }
   }
 }
 
@@ -289,42 +369,51 @@ __global__ void __launch_bounds__(SP_T) sp_solve(SpDev d, SpParams p, long step,
   }
 }
 
-__global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage, double dt) {
-  __shared__ double2 sX[LR_MAX_RANK * LR_MAX_RANK];
+template <typename T2>
+__global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage, double dt_) {
+  using T = typename Scalar<T2>::type;
+  __shared__ T2 sX[LR_MAX_RANK * LR_MAX_RANK];
   const int tj = blockIdx.y, M = p.M, MM = M * M;
   const long long e = (long long)blockIdx.x * SP_T + threadIdx.x;
   const bool live = e < p.NM;
   const int n = live ? (int)(e / M) : 0, m = live ? (int)(e - (long long)n * M) : 0;
   const size_t off = (size_t)tj * p.NM;
-  double2 F = live ? d.W[off + e] : mk(0, 0);
+  T2* Z = static_cast<T2*>(d.Z);
+  T2* Zs = static_cast<T2*>(d.Zs);
+  T2* acc = static_cast<T2*>(d.acc);
+  const T2* Yk = static_cast<const T2*>(d.Y);
+  T2 F = live ? static_cast<const T2*>(d.W)[off + e] : mk2<T2>(0, 0);
+  const T half = (T)0.5;
   for (int k = 0; k < p.K; ++k) {
     __syncthreads();
-    for (int i = threadIdx.x; i < MM; i += SP_T) sX[i] = d.X[((size_t)tj * p.K + k) * MM + i];
+    for (int i = threadIdx.x; i < MM; i += SP_T) sX[i] = from_d<T2>(d.X[((size_t)tj * p.K + k) * MM + i]);
     __syncthreads();
     if (live) {   // F += 1/2 sum_j Y_k[n][j] conj(X_k[m][j])
-      const double2* y = d.Y + ((size_t)k * p.T + tj) * p.NM + (size_t)n * M;
-      double2 s = mk(0.0, 0.0);
+      const T2* y = Yk + ((size_t)k * p.T + tj) * p.NM + (size_t)n * M;
+      T2 s = mk2<T2>(0, 0);
       for (int j = 0; j < M; ++j) {
-        const double2 a = y[j], x = sX[m * M + j];
-        s = mk(fma(a.x, x.x, fma(a.y, x.y, s.x)), fma(a.y, x.x, fma(-a.x, x.y, s.y)));
+        const T2 a = y[j], x = sX[m * M + j];
+        s = mk2<T2>(fma(a.x, x.x, fma(a.y, x.y, s.x)), fma(a.y, x.x, fma(-a.x, x.y, s.y)));
       }
-      F = mk(F.x + 0.5 * s.x, F.y + 0.5 * s.y);
+      F = mk2<T2>(fma(half, s.x, F.x), fma(half, s.y, F.y));
     }
   }
   if (!live) return;
-  const double w = (stage == 0 || stage == 3) ? 1.0 : 2.0;
-  const double2 a0 = stage == 0 ? mk(0.0, 0.0) : d.acc[off + e];
-  const double2 a = mk(a0.x + w * F.x, a0.y + w * F.y);
-  const double2 z = d.Z[off + e];
+  const T dt = (T)dt_;
+  const T w = (stage == 0 || stage == 3) ? (T)1 : (T)2;
+  const T2 a0 = stage == 0 ? mk2<T2>(0, 0) : acc[off + e];
+  const T2 a = mk2<T2>(fma(w, F.x, a0.x), fma(w, F.y, a0.y));
+  const T2 z = Z[off + e];
   if (stage < 3) {
-    const double c = stage == 2 ? dt : 0.5 * dt;
-    d.acc[off + e] = a;
-    d.Zs[off + e] = mk(z.x + c * F.x, z.y + c * F.y);
+    const T c = stage == 2 ? dt : (T)0.5 * dt;
+    acc[off + e] = a;
+    Zs[off + e] = mk2<T2>(fma(c, F.x, z.x), fma(c, F.y, z.y));
   } else {
-    const double2 zn = mk(z.x + dt / 6.0 * a.x, z.y + dt / 6.0 * a.y);
+    const T c = dt / (T)6;
+    const T2 zn = mk2<T2>(fma(c, a.x, z.x), fma(c, a.y, z.y));
     if (!isfinite(zn.x) || !isfinite(zn.y)) set_error(d.err, DEV_NONFINITE);
-    d.Z[off + e] = zn;
-    d.Zs[off + e] = zn;
+    Z[off + e] = zn;
+    Zs[off + e] = zn;
   }
 }
 
@@ -337,6 +426,7 @@ using namespace lr;
 
 struct lr_sparse {
   int N, M, K, T, n_levels, nblk;
+  int fp32;   // 1: FP32_G64 state arithmetic
   long nnz, max_steps, n_rec, step;
   int pop_every;
   double wd, tau;
@@ -347,7 +437,7 @@ struct lr_sparse {
   char* ws;
   size_t ws_bytes;
   // offsets into the workspace
-  size_t o_rowptr, o_col, o_val, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X,
+  size_t o_rowptr, o_col, o_val, o_valf, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X, o_chi,
       o_part, o_beta, o_pops, o_nphot, o_trace, total;
   std::string msg;
 };
@@ -371,10 +461,12 @@ void layout(lr_sparse* s) {
     o = align256(o + bytes);
     return r;
   };
-  const size_t state = (size_t)s->T * s->N * s->M * sizeof(double2);
+  const size_t state = (size_t)s->T * s->N * s->M * (s->fp32 ? sizeof(float2) : sizeof(double2));
+  const size_t state64 = (size_t)s->T * s->N * s->M * sizeof(double2);
   s->o_rowptr = take((size_t)(s->K + 2) * (s->N + 1) * sizeof(int));
   s->o_col = take((size_t)s->nnz * sizeof(int));
   s->o_val = take((size_t)s->nnz * sizeof(double2));
+  s->o_valf = take((size_t)s->nnz * sizeof(float2));
   s->o_chan = take((size_t)s->nnz);
   s->o_level = take((size_t)s->N * sizeof(int));
   s->o_pulse = take((size_t)s->T * sizeof(PulseDev));
@@ -383,10 +475,11 @@ void layout(lr_sparse* s) {
   s->o_Z = take(state);
   s->o_Zs = take(state);
   s->o_acc = take(state);
-  s->o_W = take(state);
+  s->o_W = take(state64);   // also the FP64 scratch of set_initial / set_state / get_state
   s->o_Y = take(state * s->K);
   s->o_Yr = take(state);
   s->o_X = take((size_t)s->T * s->K * s->M * s->M * sizeof(double2));
+  s->o_chi = take((size_t)s->T * 4 * NCH * sizeof(double2));
   const size_t ps = (size_t)2 * (1 + s->K) * s->M * s->M + 4 + s->n_levels;
   s->o_part = take((size_t)s->T * s->nblk * ps * sizeof(double));
   s->o_beta = take((size_t)s->T * (s->max_steps + 1) * sizeof(double2));
@@ -402,23 +495,55 @@ SpDev dev(const lr_sparse* s) {
   d.rowptr = reinterpret_cast<const int*>(w + s->o_rowptr);
   d.col = reinterpret_cast<const int*>(w + s->o_col);
   d.val = reinterpret_cast<const double2*>(w + s->o_val);
+  d.valf = reinterpret_cast<const float2*>(w + s->o_valf);
   d.chan = reinterpret_cast<const unsigned char*>(w + s->o_chan);
   d.level = reinterpret_cast<const int*>(w + s->o_level);
   d.pulse = reinterpret_cast<const PulseDev*>(w + s->o_pulse);
   d.err = reinterpret_cast<unsigned*>(w + s->o_err);
-  d.Z = reinterpret_cast<double2*>(w + s->o_Z);
-  d.Zs = reinterpret_cast<double2*>(w + s->o_Zs);
-  d.acc = reinterpret_cast<double2*>(w + s->o_acc);
-  d.W = reinterpret_cast<double2*>(w + s->o_W);
-  d.Y = reinterpret_cast<double2*>(w + s->o_Y);
-  d.Yr = reinterpret_cast<double2*>(w + s->o_Yr);
+  d.Z = w + s->o_Z;
+  d.Zs = w + s->o_Zs;
+  d.acc = w + s->o_acc;
+  d.W = w + s->o_W;
+  d.Y = w + s->o_Y;
+  d.Yr = w + s->o_Yr;
   d.X = reinterpret_cast<double2*>(w + s->o_X);
+  d.chi = reinterpret_cast<double2*>(w + s->o_chi);
   d.part = reinterpret_cast<double*>(w + s->o_part);
   d.beta = reinterpret_cast<double2*>(w + s->o_beta);
   d.pops = reinterpret_cast<double*>(w + s->o_pops);
   d.nphot = reinterpret_cast<double*>(w + s->o_nphot);
   d.trace = reinterpret_cast<double*>(w + s->o_trace);
   return d;
+}
+
+size_t state_bytes(const lr_sparse* s) {
+  return (size_t)s->T * s->N * s->M * (s->fp32 ? sizeof(float2) : sizeof(double2));
+}
+
+template <typename T2>
+void launch_step_kernels(const lr_sparse* s, const SpDev& d, const SpParams& p, long step0, long n_steps, double dt,
+                         cudaStream_t st) {
+  const dim3 ge((unsigned)((p.NM + SP_T - 1) / SP_T), (unsigned)s->T), gg((unsigned)s->nblk, (unsigned)s->T);
+  for (long i = 0; i <= n_steps; ++i) {
+    const long step = step0 + i;
+    const double t = (double)step * dt;
+    const bool rec = step % s->pop_every == 0;
+    sp_chi<<<s->T, 64, 0, st>>>(d, p, t, dt);
+    if (i == n_steps) {   // observation of the final state
+      const int mode = MODE_BETA | (rec ? MODE_OBS : 0);
+      sp_apply<T2><<<ge, SP_T, 0, st>>>(d, p, 0, 1, 1);
+      sp_gram<T2><<<gg, SP_T, 0, st>>>(d, p, mode);
+      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
+      break;
+    }
+    for (int stg = 0; stg < 4; ++stg) {
+      const int mode = MODE_SOLVE | (stg == 0 ? MODE_BETA | (rec ? MODE_OBS : 0) : 0);
+      sp_apply<T2><<<ge, SP_T, 0, st>>>(d, p, stg, stg == 0, 0);
+      sp_gram<T2><<<gg, SP_T, 0, st>>>(d, p, mode);
+      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
+      sp_update<T2><<<ge, SP_T, 0, st>>>(d, p, stg, dt);
+    }
+  }
 }
 
 SpParams params(const lr_sparse* s) {
@@ -463,8 +588,9 @@ std::vector<TrajDev> trajectories(const lr_sparse* s, const int* psi) {
 
 }  // namespace
 
-extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int M, const lr_pulse* pulses, double tau,
-                                      long max_steps, int pop_every, lr_sparse** out) {
+extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int M, lr_precision precision,
+                                      const lr_pulse* pulses, double tau, long max_steps, int pop_every,
+                                      lr_sparse** out) {
   if (!out) return LR_ERR_ARG;
   *out = nullptr;
   if (!m || !pulses || !m->rowptr || !m->col || !m->val || !m->chan || !m->level) return LR_ERR_ARG;
@@ -472,6 +598,7 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   if (m->n_levels < 1 || m->n_levels > LR_MAX_NT || m->nnz < 0 || m->nnz > (1L << 31) - 1) return LR_ERR_ARG;
   if (n_traj < 1 || n_traj > 65535 || M < 1 || M > LR_MAX_RANK || M > m->N) return LR_ERR_ARG;
   if (!(tau > 0.0) || max_steps < 1 || pop_every < 1 || !isfinite(m->wd)) return LR_ERR_ARG;
+  if (precision != LR_PREC_FP64 && precision != LR_PREC_FP32_G64) return LR_ERR_UNSUPPORTED;
   const int K = m->n_jumps, N = m->N;
   for (int o = 0; o < K + 2; ++o) {
     const int* rp = m->rowptr + (size_t)o * (N + 1);
@@ -497,10 +624,12 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   if (!s) return LR_ERR_NOMEM;
   s->N = N;
   s->M = M;
+  s->fp32 = precision == LR_PREC_FP32_G64;
   s->K = K;
   s->T = n_traj;
   s->n_levels = m->n_levels;
-  s->nblk = (N + SP_R - 1) / SP_R;
+  const int R = s->fp32 ? rows_per_block<float2>() : rows_per_block<double2>();
+  s->nblk = (N + R - 1) / R;
   s->nnz = m->nnz;
   s->max_steps = max_steps;
   s->pop_every = pop_every;
@@ -540,7 +669,11 @@ extern "C" lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, siz
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const std::vector<TrajDev> traj = trajectories(s, nullptr);
   std::vector<double2> val(s->nnz);
-  for (long e = 0; e < s->nnz; ++e) val[e] = make_double2(s->val[2 * e], s->val[2 * e + 1]);
+  std::vector<float2> valf(s->nnz);
+  for (long e = 0; e < s->nnz; ++e) {
+    val[e] = make_double2(s->val[2 * e], s->val[2 * e + 1]);
+    valf[e] = make_float2((float)s->val[2 * e], (float)s->val[2 * e + 1]);
+  }
   cudaError_t e;
   if ((e = cudaMemsetAsync(s->ws, 0, s->total, st)) != cudaSuccess) return cuda_fail(s, e);
   struct Up {
@@ -550,6 +683,7 @@ extern "C" lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, siz
   } ups[] = {{s->o_rowptr, s->rowptr.data(), s->rowptr.size() * sizeof(int)},
              {s->o_col, s->col.data(), s->col.size() * sizeof(int)},
              {s->o_val, val.data(), val.size() * sizeof(double2)},
+             {s->o_valf, valf.data(), valf.size() * sizeof(float2)},
              {s->o_chan, s->chan.data(), s->chan.size()},
              {s->o_level, s->level.data(), s->level.size() * sizeof(int)},
              {s->o_pulse, s->pulses.data(), s->pulses.size() * sizeof(PulseDev)},
@@ -583,9 +717,8 @@ extern "C" lr_status lr_sparse_set_initial(lr_sparse* s, const int* psi, uint64_
   RunParams rp;
   memset(&rp, 0, sizeof(rp));
   rp.n_traj = s->T;
-  if ((e = launch_initial_state(p, rp, s->N, 0, seed, eps, st)) != cudaSuccess) return cuda_fail(s, e);
-  if ((e = cudaMemcpyAsync(d.Zs, d.Z, (size_t)s->T * s->N * s->M * sizeof(double2), cudaMemcpyDeviceToDevice, st)) !=
-      cudaSuccess)
+  if ((e = launch_initial_state(p, rp, s->N, s->fp32, seed, eps, st)) != cudaSuccess) return cuda_fail(s, e);
+  if ((e = cudaMemcpyAsync(d.Zs, d.Z, state_bytes(s), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
     return cuda_fail(s, e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
   s->step = 0;
@@ -597,10 +730,18 @@ extern "C" lr_status lr_sparse_set_state(lr_sparse* s, const double* Z, long ste
   if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
   if (step < 0 || step > s->max_steps) return fail(s, LR_ERR_ARG, "step out of range");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t bytes = (size_t)s->T * s->N * s->M * sizeof(double2);
+  const long long n = (long long)s->T * s->N * s->M;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(s->ws + s->o_Z, Z, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(s, e);
-  if ((e = cudaMemcpyAsync(s->ws + s->o_Zs, s->ws + s->o_Z, bytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+  if (s->fp32) {   // host complex128 -> FP64 scratch -> complex64 state
+    if ((e = cudaMemcpyAsync(s->ws + s->o_W, Z, n * sizeof(double2), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(s, e);
+    if ((e = launch_convert(s->ws + s->o_W, s->ws + s->o_Z, n, 1, st)) != cudaSuccess) return cuda_fail(s, e);
+  } else if ((e = cudaMemcpyAsync(s->ws + s->o_Z, Z, n * sizeof(double2), cudaMemcpyHostToDevice, st)) !=
+             cudaSuccess) {
+    return cuda_fail(s, e);
+  }
+  if ((e = cudaMemcpyAsync(s->ws + s->o_Zs, s->ws + s->o_Z, state_bytes(s), cudaMemcpyDeviceToDevice, st)) !=
+      cudaSuccess)
     return cuda_fail(s, e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
   s->step = step;
@@ -610,10 +751,14 @@ extern "C" lr_status lr_sparse_set_state(lr_sparse* s, const double* Z, long ste
 extern "C" lr_status lr_sparse_get_state(const lr_sparse* s, double* Z, void* stream) {
   if (!s || !Z || !s->ws) return LR_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n = (long long)s->T * s->N * s->M;
+  const char* src = s->ws + s->o_Z;
+  if (s->fp32) {   // complex64 state -> FP64 scratch (W is only used within a stage)
+    if (launch_convert(s->ws + s->o_Z, s->ws + s->o_W, n, 0, st) != cudaSuccess) return LR_ERR_CUDA;
+    src = s->ws + s->o_W;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return LR_ERR_CUDA;
-  if (cudaMemcpy(Z, s->ws + s->o_Z, (size_t)s->T * s->N * s->M * sizeof(double2), cudaMemcpyDeviceToHost) !=
-      cudaSuccess)
-    return LR_ERR_CUDA;
+  if (cudaMemcpy(Z, src, n * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess) return LR_ERR_CUDA;
   return LR_OK;
 }
 
@@ -625,27 +770,10 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const SpDev d = dev(s);
   const SpParams p = params(s);
-  const dim3 ge((unsigned)((p.NM + SP_T - 1) / SP_T), (unsigned)s->T), gg((unsigned)s->nblk, (unsigned)s->T);
-  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
-  for (long i = 0; i <= n_steps; ++i) {
-    const long step = s->step + i;
-    const double t = (double)step * dt;
-    const bool rec = step % s->pop_every == 0;
-    if (i == n_steps) {   // observation of the final state
-      const int mode = MODE_BETA | (rec ? MODE_OBS : 0);
-      sp_apply<<<ge, SP_T, 0, st>>>(d, p, t, 1, 1);
-      sp_gram<<<gg, SP_T, 0, st>>>(d, p, mode);
-      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
-      break;
-    }
-    for (int stg = 0; stg < 4; ++stg) {
-      const int mode = MODE_SOLVE | (stg == 0 ? MODE_BETA | (rec ? MODE_OBS : 0) : 0);
-      sp_apply<<<ge, SP_T, 0, st>>>(d, p, t + cst[stg] * dt, stg == 0, 0);
-      sp_gram<<<gg, SP_T, 0, st>>>(d, p, mode);
-      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
-      sp_update<<<ge, SP_T, 0, st>>>(d, p, stg, dt);
-    }
-  }
+  if (s->fp32)
+    launch_step_kernels<float2>(s, d, p, s->step, n_steps, dt, st);
+  else
+    launch_step_kernels<double2>(s, d, p, s->step, n_steps, dt, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e);
   s->step += n_steps;

@@ -110,7 +110,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_diagnostics.argtypes = [vp, vp, vp, vp]
     lib.lr_paper_model_size.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_long)]
     lib.lr_paper_model_build.argtypes = [vp, vp, vp, vp, vp, vp, vp]
-    lib.lr_sparse_create.argtypes = [vp, i, i, vp, d, l, i, C.POINTER(vp)]
+    lib.lr_sparse_create.argtypes = [vp, i, i, i, vp, d, l, i, C.POINTER(vp)]
     lib.lr_sparse_workspace_size.argtypes = [vp, C.POINTER(C.c_size_t)]
     lib.lr_sparse_bind_workspace.argtypes = [vp, vp, C.c_size_t, vp]
     lib.lr_sparse_set_initial.argtypes = [vp, vp, C.c_uint64, d, vp]

@@ -14,7 +14,7 @@ from typing import Sequence
 
 import numpy as np
 
-from .lr import LrError, _stream_ptr, load_library, make_pulse, lr_pulse
+from .lr import PRECISION, LrError, _stream_ptr, load_library, make_pulse, lr_pulse
 
 N_JUMPS_PAPER = 2       # kappa D[f] and gamma D[b]
 PAPER_DERIVED = ("w_l", "w_u", "mu_l", "mu_u", "nu_l", "nu_u", "s21", "s22", "s23", "s24",
@@ -62,10 +62,11 @@ def paper_model(Nl: int, Nu: int, Nt: int, Ec: float, Ej: float, wr: float, wf: 
 
 class SparseBatch:
     """n_traj trajectories of rank M on one operator set (a ``paper_model`` dict
-    or any dict with the same keys); pulse i drives trajectory i."""
+    or any dict with the same keys); pulse i drives trajectory i. precision:
+    "fp64" or "fp32_g64"."""
 
     def __init__(self, model: dict, M: int, pulses: Sequence, tau: float, max_steps: int,
-                 pop_every: int = 1, device="cuda:0"):
+                 pop_every: int = 1, device="cuda:0", precision: str = "fp64"):
         import torch
         self._lib = load_library()
         self.model = model
@@ -80,8 +81,9 @@ class SparseBatch:
         self.n_traj = len(pl)
         arr = (lr_pulse * self.n_traj)(*pl)
         h = C.c_void_p()
-        st = self._lib.lr_sparse_create(C.byref(m), self.n_traj, int(M), arr, float(tau), int(max_steps),
-                                        int(pop_every), C.byref(h))
+        self.precision = precision
+        st = self._lib.lr_sparse_create(C.byref(m), self.n_traj, int(M), PRECISION[precision], arr, float(tau),
+                                        int(max_steps), int(pop_every), C.byref(h))
         if st != 0:
             raise LrError(st, "lr_sparse_create")
         self._h = h

@@ -100,21 +100,22 @@ def test_sparse_create_validates_arguments(sparse_mod):
     wd = m["wd"]
     arrs = [np.ascontiguousarray(m[k]) for k in ("rowptr", "col", "val", "chan", "level")]
 
-    def create(model_over=None, M=2, pulse=(0, [1.0, wd, 0.5, 0.0]), n=2):
+    def create(model_over=None, M=2, pulse=(0, [1.0, wd, 0.5, 0.0]), n=2, prec=0):
         a = [x.copy() for x in arrs]
         if model_over:
             model_over(a)
         sm = sparse_mod.lr_sparse_model(m["N"], 2, 3, m["nnz"], wd, *[C.c_void_p(x.ctypes.data) for x in a])
         pl = (lr.lr_pulse * n)(*[lr.make_pulse(*pulse)] * n)
         h = C.c_void_p()
-        st = lib.lr_sparse_create(C.byref(sm), n, M, pl, 4.0, 100, 1, C.byref(h))
+        st = lib.lr_sparse_create(C.byref(sm), n, M, prec, pl, 4.0, 100, 1, C.byref(h))
         if st == 0:
             sz = C.c_size_t()
             assert lib.lr_sparse_workspace_size(h, C.byref(sz)) == 0 and sz.value > 0
             lib.lr_sparse_destroy(h)
         return st
 
-    assert create() == 0
+    assert create() == 0 and create(prec=1) == 0
+    assert create(prec=2) == 9 and create(prec=3) == 9             # LR_ERR_UNSUPPORTED
     assert create(M=0) == 1 and create(M=33) == 1 and create(n=0) == 1
     assert create(pulse=(0, [1.0, wd, 0.5, 0.3])) == 1            # pulse phase must be 0
     assert create(pulse=(0, [1.0, wd * 1.001, 0.5, 0.0])) == 1    # drive frequency = frame frequency
