@@ -8,13 +8,15 @@
 //               of every step Yr = r Zs; the ten channel factors
 //               Omega(t)^a e^{i q w_d t} of the step's four stage times come
 //               from sp_chi, one small launch per step;
-//   sp_gram   - per block of 16 (FP64) or 32 (FP32) rows: partial sums of G = Zs^dag Zs (upper
+//   sp_gram   - per block, over row tiles of 16 (FP64) or 32 (FP32) rows held in
+//               shared memory, register sums of G = Zs^dag Zs (upper
 //               triangle), T_k = Zs^dag Y_k, and at stage 1 tr(Zs^dag Yr) =
 //               tr(rho r), plus level populations, |Yr|^2 and |Zs|^2 at
 //               recording steps;
 //   sp_solve  - one block per trajectory: reduce the partials in block order,
 //               record beta and the observables, Cholesky G = L L^dag and
-//               X_k = G^-1 T_k (the Moore-Penrose projection Zs^+ L_k Zs);
+//               X_k = G^-1 T_k (the Moore-Penrose projection Zs^+ L_k Zs) by
+//               right-looking substitutions over all K M columns at once;
 //   sp_update - F = W + 1/2 sum_k Y_k X_k^dag, then the classical RK4 stage.
 // After the last step an observation pass (apply r, Gram, solve without
 // Cholesky) records beta and the observables of the final state.
@@ -27,6 +29,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -55,6 +58,7 @@ struct SpDev {
   unsigned* err;
   void *Z, *Zs, *acc, *W, *Y, *Yr;   // state-type arrays (double2 or float2)
   double2* X;
+  float2* Xf;     // FP32 copy of X for the FP32 update
   double2* chi;   // [T][4][NCH] channel factors at the four stage times of the current step
   double* part;
   double2* beta;
@@ -80,7 +84,8 @@ __device__ __forceinline__ const double2& op_val(const SpDev& d, int e, double2)
 __device__ __forceinline__ const float2& op_val(const SpDev& d, int e, float2) { return d.valf[e]; }
 
 struct SpParams {
-  int N, M, K, T, n_levels, nblk;
+  int N, M, K, T, n_levels, nblk;   // nblk: Gram blocks (partial sums) per trajectory
+  int ntile;                        // row tiles per trajectory (rows_per_block rows each)
   long long NM;      // N * M
   long long ps;      // doubles per partial block
   double wd, tau;
@@ -162,110 +167,156 @@ __global__ void __launch_bounds__(SP_T) sp_apply(SpDev d, SpParams p, int stage,
   if (with_r) static_cast<T2*>(d.Yr)[off + e] = row_apply(d, p, 1 + p.K, n, m, Zs, chi);
 }
 
-template <typename T2>
+// Register accumulator of one G or T_k entry: double-word FP32 (re.hi, re.lo,
+// im.hi, im.lo) for G in the FP32 variant, plain sums otherwise.
+template <typename T2> struct Acc;
+template <> struct Acc<double2> {
+  double2 v;
+  __device__ void zero() { v = mk(0.0, 0.0); }
+  __device__ void add_g(double2 a, double2 c) { v = cfma_conj(a, c, v); }
+  __device__ void add_t(double2 a, double2 c) { v = cfma_conj(a, c, v); }
+  __device__ double2 g() const { return v; }
+  __device__ double2 t() const { return v; }
+};
+template <> struct Acc<float2> {
+  DWs re, im;
+  __device__ void zero() { re = im = DWs{0.f, 0.f}; }
+  __device__ void add_g(float2 a, float2 c) {   // conj(a) c, exact products
+    dw_acc(re, a.x, c.x);
+    dw_acc(re, a.y, c.y);
+    dw_acc(im, a.x, c.y);
+    dw_acc(im, -a.y, c.x);
+  }
+  __device__ void add_t(float2 a, float2 c) {   // conj(a) c in FP32 (re.hi, im.hi)
+    re.hi = fmaf(a.x, c.x, fmaf(a.y, c.y, re.hi));
+    im.hi = fmaf(a.x, c.y, fmaf(-a.y, c.x, im.hi));
+  }
+  __device__ double2 g() const { return mk((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo); }
+  __device__ double2 t() const { return mk((double)re.hi, (double)im.hi); }
+};
+
+// Entries per thread of the (1 + K) M^2 partial sums: up to (1 + 3) 32^2 / 256.
+constexpr int ACC_MAX = (1 + LR_SPARSE_MAX_JUMPS) * LR_MAX_RANK * LR_MAX_RANK / SP_T;
+
+// NACC: accumulators per thread, >= (1 + K) M^2 / SP_T (4, 8 or ACC_MAX)
+template <typename T2, int NACC>
 __global__ void __launch_bounds__(SP_T) sp_gram(SpDev d, SpParams p, int mode) {
   using T = typename Scalar<T2>::type;
   constexpr int R = rows_per_block<T2>();
   __shared__ T2 sZ[R][LR_MAX_RANK], sY[LR_SPARSE_MAX_JUMPS + 1][R][LR_MAX_RANK];
   __shared__ T rsum[R][4];
+  __shared__ T stot[4 + LR_MAX_NT];   // signal, photons, trace, populations (written by thread 0)
   __shared__ int slev[R];
-  const int tj = blockIdx.y, b = blockIdx.x, M = p.M, K = p.K;
-  const int r0 = b * R, rows = min(R, p.N - r0);
+  const int tj = blockIdx.y, b = blockIdx.x, M = p.M, K = p.K, MM = M * M;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t off = (size_t)tj * p.NM;
   const bool solve = mode & MODE_SOLVE, obs = mode & MODE_OBS, beta = mode & MODE_BETA;
   const T2* Zs = static_cast<const T2*>(d.Zs);
   const T2* Yk = static_cast<const T2*>(d.Y);
   const T2* Yr = static_cast<const T2*>(d.Yr);
-  for (int e = threadIdx.x; e < R * M; e += SP_T) {
-    const int i = e / M, m = e - (e / M) * M;
-    T2 z = mk2<T2>(0, 0), yr = mk2<T2>(0, 0);
-    if (i < rows) {
-      const size_t idx = off + (size_t)(r0 + i) * M + m;
-      z = Zs[idx];
-      if (beta) yr = Yr[idx];
-      if (solve)
-        for (int k = 0; k < K; ++k) sY[k][i][m] = Yk[(size_t)k * p.T * p.NM + idx];
-    } else if (solve) {
-      for (int k = 0; k < K; ++k) sY[k][i][m] = mk2<T2>(0, 0);
-    }
-    sZ[i][m] = z;
-    sY[LR_SPARSE_MAX_JUMPS][i][m] = yr;
-    if (m == 0) slev[i] = i < rows ? d.level[r0 + i] : -1;
-  }
-  __syncthreads();
-  double* out = d.part + ((size_t)tj * p.nblk + b) * p.ps;
-  const int MM = M * M;
-  if (solve) {
-    for (int e = threadIdx.x; e < (1 + K) * MM; e += SP_T) {
-      const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
-      if (mat == 0 && i > j) continue;
-      double2 s;
-      if (mat == 0) {
-        if constexpr (sizeof(T) == 4) {   // G from exact FP32 products, double-word sums
-          DWs re{0.f, 0.f}, im{0.f, 0.f};
-          for (int r = 0; r < rows; ++r) {   // conj(a) c
-            const float2 a = sZ[r][i], c = sZ[r][j];
-            dw_acc(re, a.x, c.x);
-            dw_acc(re, a.y, c.y);
-            dw_acc(im, a.x, c.y);
-            dw_acc(im, -a.y, c.x);
-          }
-          s = mk((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
-        } else {
-          s = mk(0.0, 0.0);
-          for (int r = 0; r < rows; ++r) s = cfma_conj(to_d(sZ[r][i]), to_d(sZ[r][j]), s);
-        }
-      } else {   // T_k in the state's arithmetic
-        T2 t = mk2<T2>(0, 0);
-        for (int r = 0; r < rows; ++r) t = cfma_conj(sZ[r][i], sY[mat - 1][r][j], t);
-        s = to_d(t);
+  const int n_ent = (1 + K) * MM;
+  Acc<T2> acc[NACC];
+#pragma unroll
+  for (int q = 0; q < NACC; ++q) acc[q].zero();
+  if (tid < 4 + LR_MAX_NT) stot[tid] = 0;
+  // row tiles b, b + nblk, b + 2 nblk, ... in increasing order
+  for (int tile = b; tile < p.ntile; tile += p.nblk) {
+    const int r0 = tile * R, rows = min(R, p.N - r0);
+    __syncthreads();   // the previous tile is consumed
+    for (int e = tid; e < R * M; e += SP_T) {
+      const int i = e / M, m = e - (e / M) * M;
+      T2 z = mk2<T2>(0, 0), yr = mk2<T2>(0, 0);
+      if (i < rows) {
+        const size_t idx = off + (size_t)(r0 + i) * M + m;
+        z = Zs[idx];
+        if (beta) yr = Yr[idx];
+        if (solve)
+          for (int k = 0; k < K; ++k) sY[k][i][m] = Yk[(size_t)k * p.T * p.NM + idx];
+      } else if (solve) {
+        for (int k = 0; k < K; ++k) sY[k][i][m] = mk2<T2>(0, 0);
       }
-      out[2 * e] = s.x;
-      out[2 * e + 1] = s.y;
-    }
-  }
-  const size_t o2 = (size_t)2 * (1 + K) * MM;   // beta re, im, nphot, trace, pops[n_levels]
-  if (beta || obs) {
-    // one warp per row, lanes over m: conj(z) r z, |r z|^2, |z|^2 in the state's
-    // arithmetic; then one lane per row; fixed-order shuffle sums
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp; r < R; r += SP_T / 32) {
-      T v[4] = {0, 0, 0, 0};
-      if (r < rows && lane < M) {
-        const T2 z = sZ[r][lane], y = sY[LR_SPARSE_MAX_JUMPS][r][lane];
-        v[0] = fma(z.x, y.x, z.y * y.y);
-        v[1] = fma(z.x, y.y, -z.y * y.x);
-        v[2] = fma(y.x, y.x, y.y * y.y);
-        v[3] = fma(z.x, z.x, z.y * z.y);
-      }
-      for (int o = 16; o > 0; o >>= 1)
-        for (int c = 0; c < 4; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-      if (lane == 0)
-        for (int c = 0; c < 4; ++c) rsum[r][c] = v[c];
+      sZ[i][m] = z;
+      sY[LR_SPARSE_MAX_JUMPS][i][m] = yr;
+      if (m == 0) slev[i] = i < rows ? d.level[r0 + i] : -1;
     }
     __syncthreads();
-    if (warp == 0) {
-      T v[4];
-      for (int c = 0; c < 4; ++c) v[c] = lane < rows ? rsum[lane][c] : (T)0;
-      for (int o = 16; o > 0; o >>= 1)
-        for (int c = 0; c < 4; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-      if (lane == 0)
-        for (int c = 0; c < 4; ++c) out[o2 + c] = (double)v[c];
-      if (obs)
-        for (int l = 0; l < p.n_levels; ++l) {
-          T w = (lane < rows && slev[lane] == l) ? rsum[lane][3] : (T)0;
-          for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-          if (lane == 0) out[o2 + 4 + l] = (double)w;
+    if (solve) {
+#pragma unroll
+      for (int q = 0; q < NACC; ++q) {
+        const int e = tid + q * SP_T;
+        if (e < n_ent) {
+          const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
+          if (mat == 0) {
+            if (i <= j)
+              for (int r = 0; r < rows; ++r) acc[q].add_g(sZ[r][i], sZ[r][j]);
+          } else {
+            for (int r = 0; r < rows; ++r) acc[q].add_t(sZ[r][i], sY[mat - 1][r][j]);
+          }
         }
+      }
     }
+    if (beta || obs) {
+      // one warp per row, lanes over m: conj(z) r z, |r z|^2, |z|^2 in the
+      // state's arithmetic; then one lane per row; fixed-order shuffle sums
+      for (int r = warp; r < R; r += SP_T / 32) {
+        T v[4] = {0, 0, 0, 0};
+        if (r < rows && lane < M) {
+          const T2 z = sZ[r][lane], y = sY[LR_SPARSE_MAX_JUMPS][r][lane];
+          v[0] = fma(z.x, y.x, z.y * y.y);
+          v[1] = fma(z.x, y.y, -z.y * y.x);
+          v[2] = fma(y.x, y.x, y.y * y.y);
+          v[3] = fma(z.x, z.x, z.y * z.y);
+        }
+        for (int o = 16; o > 0; o >>= 1)
+          for (int c = 0; c < 4; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        if (lane == 0)
+          for (int c = 0; c < 4; ++c) rsum[r][c] = v[c];
+      }
+      __syncthreads();
+      if (warp == 0) {
+        T v[4];
+        for (int c = 0; c < 4; ++c) v[c] = lane < rows ? rsum[lane][c] : (T)0;
+        for (int o = 16; o > 0; o >>= 1)
+          for (int c = 0; c < 4; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+        if (lane == 0)
+          for (int c = 0; c < 4; ++c) stot[c] += v[c];
+        if (obs)
+          for (int l = 0; l < p.n_levels; ++l) {
+            T w = (lane < rows && slev[lane] == l) ? rsum[lane][3] : (T)0;
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+            if (lane == 0) stot[4 + l] += w;
+          }
+      }
+    }
+  }
+  double* out = d.part + ((size_t)tj * p.nblk + b) * p.ps;
+  if (solve) {
+#pragma unroll
+    for (int q = 0; q < NACC; ++q) {
+      const int e = tid + q * SP_T;
+      if (e < n_ent) {
+        const double2 v = e < MM ? acc[q].g() : acc[q].t();
+        out[2 * e] = v.x;
+        out[2 * e + 1] = v.y;
+      }
+    }
+  }
+  const size_t o2 = (size_t)2 * n_ent;   // beta re, im, nphot, trace, pops[n_levels]
+  if ((beta || obs) && tid == 0) {   // stot was last written by this thread
+    for (int c = 0; c < 4; ++c) out[o2 + c] = (double)stot[c];
+    if (obs)
+      for (int l = 0; l < p.n_levels; ++l) out[o2 + 4 + l] = (double)stot[4 + l];
   }
 }
 
+// Dynamic shared memory: L [M][M+1] then B [K M][M+1] (column c of the right-hand
+// sides T_k, c = k M + j, stored as row B[c]), complex128.
 __global__ void __launch_bounds__(SP_T) sp_solve(SpDev d, SpParams p, long step, int mode) {
-  __shared__ double2 L[LR_MAX_RANK][LR_MAX_RANK + 1];
-  __shared__ double2 B[LR_MAX_RANK][LR_MAX_RANK + 1];   // right-hand sides of one T_k, B[column][row]
+  extern __shared__ double2 smem[];
   __shared__ int bad;
-  const int tj = blockIdx.x, M = p.M, K = p.K, MM = M * M, tid = threadIdx.x;
+  const int tj = blockIdx.x, M = p.M, K = p.K, MM = M * M, tid = threadIdx.x, ld = M + 1;
+  double2* L = smem;
+  double2* B = smem + (size_t)M * ld;
   const double* P = d.part + (size_t)tj * p.nblk * p.ps;
   const size_t o2 = (size_t)2 * (1 + K) * MM;
   if (tid == 0) bad = 0;
@@ -289,38 +340,39 @@ __global__ void __launch_bounds__(SP_T) sp_solve(SpDev d, SpParams p, long step,
     }
   }
   if (!(mode & MODE_SOLVE)) return;
-  for (int e = tid; e < MM; e += SP_T) {   // G, upper triangle, into the lower triangle of L
-    const int i = e / M, j = e - (e / M) * M;
-    if (i > j) continue;
+  for (int e = tid; e < (1 + K) * MM; e += SP_T) {   // block partials in block order
+    const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
+    if (mat == 0 && i > j) continue;
     double re = 0.0, im = 0.0;
     for (int b = 0; b < p.nblk; ++b) {
       re += P[b * p.ps + 2 * e];
       im += P[b * p.ps + 2 * e + 1];
     }
-    L[j][i] = i == j ? mk(re, 0.0) : mk(re, -im);   // G_ji = conj(G_ij)
+    if (mat == 0) L[j * ld + i] = i == j ? mk(re, 0.0) : mk(re, -im);   // lower: G_ji = conj(G_ij)
+    else B[((mat - 1) * M + j) * ld + i] = mk(re, im);                   // T_k (i, j)
   }
   __syncthreads();
   // right-looking Cholesky G = L L^dag on the lower triangle
   for (int k = 0; k < M; ++k) {
     if (tid == 0) {
-      const double piv = L[k][k].x;
+      const double piv = L[k * ld + k].x;
       if (!(piv > 0.0) || !isfinite(piv)) {
         bad = 1;
-        L[k][k] = mk(1.0, 0.0);
+        L[k * ld + k] = mk(1.0, 0.0);
       } else {
-        L[k][k] = mk(sqrt(piv), 0.0);
+        L[k * ld + k] = mk(sqrt(piv), 0.0);
       }
     }
     __syncthreads();
-    const double inv = 1.0 / L[k][k].x;
-    for (int i = k + 1 + tid; i < M; i += SP_T) L[i][k] = mk(L[i][k].x * inv, L[i][k].y * inv);
+    const double inv = 1.0 / L[k * ld + k].x;
+    for (int i = k + 1 + tid; i < M; i += SP_T) L[i * ld + k] = mk(L[i * ld + k].x * inv, L[i * ld + k].y * inv);
     __syncthreads();
     const int rem = M - k - 1;
     for (int e = tid; e < rem * rem; e += SP_T) {
       const int i = k + 1 + e / rem, j = k + 1 + e % rem;
       if (j > i) continue;
-      const double2 a = L[i][k], c = L[j][k];   // L_ij -= L_ik conj(L_jk)
-      L[i][j] = mk(L[i][j].x - (a.x * c.x + a.y * c.y), L[i][j].y - (a.y * c.x - a.x * c.y));
+      const double2 a = L[i * ld + k], c = L[j * ld + k];   // L_ij -= L_ik conj(L_jk)
+      L[i * ld + j] = mk(L[i * ld + j].x - (a.x * c.x + a.y * c.y), L[i * ld + j].y - (a.y * c.x - a.x * c.y));
     }
     __syncthreads();
   }
@@ -328,46 +380,44 @@ __global__ void __launch_bounds__(SP_T) sp_solve(SpDev d, SpParams p, long step,
     if (tid == 0) set_error(d.err, DEV_NOT_PD);
     return;
   }
-  double2* X = d.X + (size_t)tj * K * MM;
-  for (int k = 0; k < K; ++k) {
-    for (int e = tid; e < MM; e += SP_T) {   // T_k entry (i, j) -> B[j][i]
-      const int i = e / M, j = e - (e / M) * M;
-      const size_t q = (size_t)2 * ((1 + k) * MM + e);
-      double re = 0.0, im = 0.0;
-      for (int b = 0; b < p.nblk; ++b) {
-        re += P[b * p.ps + q];
-        im += P[b * p.ps + q + 1];
-      }
-      B[j][i] = mk(re, im);
-    }
+  const int nc = K * M;
+  // forward L y = t, right-looking: y_j = t_j / L_jj, then t_i -= L_ij y_j (i > j), all columns at once
+  for (int j = 0; j < M; ++j) {
+    const double dinv = 1.0 / L[j * ld + j].x;
+    for (int c = tid; c < nc; c += SP_T) B[c * ld + j] = mk(B[c * ld + j].x * dinv, B[c * ld + j].y * dinv);
     __syncthreads();
-    // X_k = G^-1 T_k: forward L y = t, then back L^dag x = y, one thread per column
-    for (int c = tid; c < M; c += SP_T) {
-      for (int i = 0; i < M; ++i) {
-        double2 s = B[c][i];
-        for (int j = 0; j < i; ++j)
-          s = mk(s.x - (L[i][j].x * B[c][j].x - L[i][j].y * B[c][j].y),
-                 s.y - (L[i][j].x * B[c][j].y + L[i][j].y * B[c][j].x));
-        const double dinv = 1.0 / L[i][i].x;
-        B[c][i] = mk(s.x * dinv, s.y * dinv);
-      }
-      for (int i = M - 1; i >= 0; --i) {
-        double2 s = B[c][i];
-        for (int j = i + 1; j < M; ++j)
-          s = mk(s.x - (L[j][i].x * B[c][j].x + L[j][i].y * B[c][j].y),
-                 s.y - (L[j][i].x * B[c][j].y - L[j][i].y * B[c][j].x));
-        const double dinv = 1.0 / L[i][i].x;
-        B[c][i] = mk(s.x * dinv, s.y * dinv);
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < MM; e += SP_T) {   // X[k][i][j] = (X_k)_ij = B[j][i]
-      const int i = e / M, j = e - (e / M) * M;
-      X[(size_t)k * MM + e] = B[j][i];
+    const int rem = M - j - 1;
+    for (int e = tid; e < nc * rem; e += SP_T) {
+      const int c = e / rem, i = j + 1 + e % rem;
+      const double2 l = L[i * ld + j], y = B[c * ld + j];
+      B[c * ld + i] = mk(B[c * ld + i].x - (l.x * y.x - l.y * y.y), B[c * ld + i].y - (l.x * y.y + l.y * y.x));
     }
     __syncthreads();
   }
+  // back L^dag x = y: x_j = y_j / L_jj, then y_i -= conj(L_ji) x_j (i < j)
+  for (int j = M - 1; j >= 0; --j) {
+    const double dinv = 1.0 / L[j * ld + j].x;
+    for (int c = tid; c < nc; c += SP_T) B[c * ld + j] = mk(B[c * ld + j].x * dinv, B[c * ld + j].y * dinv);
+    __syncthreads();
+    for (int e = tid; e < nc * j; e += SP_T) {
+      const int c = e / j, i = e % j;
+      const double2 l = L[j * ld + i], x = B[c * ld + j];
+      B[c * ld + i] = mk(B[c * ld + i].x - (l.x * x.x + l.y * x.y), B[c * ld + i].y - (l.x * x.y - l.y * x.x));
+    }
+    __syncthreads();
+  }
+  double2* X = d.X + (size_t)tj * K * MM;
+  float2* Xf = d.Xf + (size_t)tj * K * MM;
+  for (int e = tid; e < K * MM; e += SP_T) {   // X[k][i][j] = (X_k)_ij = B[(k M + j)][i]
+    const int k = e / MM, ij = e - k * MM, i = ij / M, j = ij - (ij / M) * M;
+    const double2 v = B[(k * M + j) * ld + i];
+    X[e] = v;
+    Xf[e] = make_float2((float)v.x, (float)v.y);
+  }
 }
+
+__device__ __forceinline__ double2 load_x(const SpDev& d, size_t i, double2) { return d.X[i]; }
+__device__ __forceinline__ float2 load_x(const SpDev& d, size_t i, float2) { return d.Xf[i]; }
 
 template <typename T2>
 __global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage, double dt_) {
@@ -386,7 +436,7 @@ __global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage
   const T half = (T)0.5;
   for (int k = 0; k < p.K; ++k) {
     __syncthreads();
-    for (int i = threadIdx.x; i < MM; i += SP_T) sX[i] = from_d<T2>(d.X[((size_t)tj * p.K + k) * MM + i]);
+    for (int i = threadIdx.x; i < MM; i += SP_T) sX[i] = load_x(d, ((size_t)tj * p.K + k) * MM + i, T2());
     __syncthreads();
     if (live) {   // F += 1/2 sum_j Y_k[n][j] conj(X_k[m][j])
       const T2* y = Yk + ((size_t)k * p.T + tj) * p.NM + (size_t)n * M;
@@ -425,7 +475,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 using namespace lr;
 
 struct lr_sparse {
-  int N, M, K, T, n_levels, nblk;
+  int N, M, K, T, n_levels, nblk, ntile;
   int fp32;   // 1: FP32_G64 state arithmetic
   long nnz, max_steps, n_rec, step;
   int pop_every;
@@ -437,7 +487,7 @@ struct lr_sparse {
   char* ws;
   size_t ws_bytes;
   // offsets into the workspace
-  size_t o_rowptr, o_col, o_val, o_valf, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X, o_chi,
+  size_t o_rowptr, o_col, o_val, o_valf, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X, o_chi, o_Xf,
       o_part, o_beta, o_pops, o_nphot, o_trace, total;
   std::string msg;
 };
@@ -480,6 +530,7 @@ void layout(lr_sparse* s) {
   s->o_Yr = take(state);
   s->o_X = take((size_t)s->T * s->K * s->M * s->M * sizeof(double2));
   s->o_chi = take((size_t)s->T * 4 * NCH * sizeof(double2));
+  s->o_Xf = take((size_t)s->T * s->K * s->M * s->M * sizeof(float2));
   const size_t ps = (size_t)2 * (1 + s->K) * s->M * s->M + 4 + s->n_levels;
   s->o_part = take((size_t)s->T * s->nblk * ps * sizeof(double));
   s->o_beta = take((size_t)s->T * (s->max_steps + 1) * sizeof(double2));
@@ -508,6 +559,7 @@ SpDev dev(const lr_sparse* s) {
   d.Yr = w + s->o_Yr;
   d.X = reinterpret_cast<double2*>(w + s->o_X);
   d.chi = reinterpret_cast<double2*>(w + s->o_chi);
+  d.Xf = reinterpret_cast<float2*>(w + s->o_Xf);
   d.part = reinterpret_cast<double*>(w + s->o_part);
   d.beta = reinterpret_cast<double2*>(w + s->o_beta);
   d.pops = reinterpret_cast<double*>(w + s->o_pops);
@@ -520,10 +572,24 @@ size_t state_bytes(const lr_sparse* s) {
   return (size_t)s->T * s->N * s->M * (s->fp32 ? sizeof(float2) : sizeof(double2));
 }
 
+size_t solve_smem(const lr_sparse* s) { return (size_t)(1 + s->K) * s->M * (s->M + 1) * sizeof(double2); }
+
+template <typename T2>
+void launch_gram(const lr_sparse* s, const SpDev& d, const SpParams& p, int mode, cudaStream_t st) {
+  const dim3 gg((unsigned)s->nblk, (unsigned)s->T);
+  const int per = ((1 + s->K) * s->M * s->M + SP_T - 1) / SP_T;
+  if (per <= 4)
+    sp_gram<T2, 4><<<gg, SP_T, 0, st>>>(d, p, mode);
+  else if (per <= 8)
+    sp_gram<T2, 8><<<gg, SP_T, 0, st>>>(d, p, mode);
+  else
+    sp_gram<T2, ACC_MAX><<<gg, SP_T, 0, st>>>(d, p, mode);
+}
+
 template <typename T2>
 void launch_step_kernels(const lr_sparse* s, const SpDev& d, const SpParams& p, long step0, long n_steps, double dt,
                          cudaStream_t st) {
-  const dim3 ge((unsigned)((p.NM + SP_T - 1) / SP_T), (unsigned)s->T), gg((unsigned)s->nblk, (unsigned)s->T);
+  const dim3 ge((unsigned)((p.NM + SP_T - 1) / SP_T), (unsigned)s->T);
   for (long i = 0; i <= n_steps; ++i) {
     const long step = step0 + i;
     const double t = (double)step * dt;
@@ -532,15 +598,15 @@ void launch_step_kernels(const lr_sparse* s, const SpDev& d, const SpParams& p, 
     if (i == n_steps) {   // observation of the final state
       const int mode = MODE_BETA | (rec ? MODE_OBS : 0);
       sp_apply<T2><<<ge, SP_T, 0, st>>>(d, p, 0, 1, 1);
-      sp_gram<T2><<<gg, SP_T, 0, st>>>(d, p, mode);
-      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
+      launch_gram<T2>(s, d, p, mode, st);
+      sp_solve<<<s->T, SP_T, solve_smem(s), st>>>(d, p, step, mode);
       break;
     }
     for (int stg = 0; stg < 4; ++stg) {
       const int mode = MODE_SOLVE | (stg == 0 ? MODE_BETA | (rec ? MODE_OBS : 0) : 0);
       sp_apply<T2><<<ge, SP_T, 0, st>>>(d, p, stg, stg == 0, 0);
-      sp_gram<T2><<<gg, SP_T, 0, st>>>(d, p, mode);
-      sp_solve<<<s->T, SP_T, 0, st>>>(d, p, step, mode);
+      launch_gram<T2>(s, d, p, mode, st);
+      sp_solve<<<s->T, SP_T, solve_smem(s), st>>>(d, p, step, mode);
       sp_update<T2><<<ge, SP_T, 0, st>>>(d, p, stg, dt);
     }
   }
@@ -554,6 +620,7 @@ SpParams params(const lr_sparse* s) {
   p.T = s->T;
   p.n_levels = s->n_levels;
   p.nblk = s->nblk;
+  p.ntile = s->ntile;
   p.NM = (long long)s->N * s->M;
   p.ps = (long long)2 * (1 + s->K) * s->M * s->M + 4 + s->n_levels;
   p.wd = s->wd;
@@ -629,7 +696,11 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   s->T = n_traj;
   s->n_levels = m->n_levels;
   const int R = s->fp32 ? rows_per_block<float2>() : rows_per_block<double2>();
-  s->nblk = (N + R - 1) / R;
+  s->ntile = (N + R - 1) / R;
+  // Gram blocks per trajectory: enough blocks for ~8 per SM over the batch, each
+  // looping over ntile / nblk row tiles (fewer partial sums for the solve)
+  const int want = (8 * 152 + n_traj - 1) / n_traj;
+  s->nblk = std::min(s->ntile, std::max(8, want));
   s->nnz = m->nnz;
   s->max_steps = max_steps;
   s->pop_every = pop_every;
@@ -692,6 +763,9 @@ extern "C" lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, siz
     if (u.bytes && (e = cudaMemcpyAsync(s->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(s, e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
+  if ((e = cudaFuncSetAttribute(sp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(s))) !=
+      cudaSuccess)
+    return cuda_fail(s, e);
   s->step = 0;
   return LR_OK;
 }

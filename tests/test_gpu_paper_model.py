@@ -85,12 +85,23 @@ def test_ragged_blocks_and_split_integrate(precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32_g64"])
 def test_full_size_sampled(precision):
     """The paper's Hilbert-space size N = 2000 (N_l = 100, N_u = 4, N_t = 5)
-    at M = 20, eight trajectories, 40 steps; trajectories 0 and 7 against the oracle."""
+    at M = 20, 32 trajectories, 40 steps; trajectories 0 and 31 against the
+    oracle. With 32 trajectories each Gram block sums 1 or 2 row tiles (63
+    tiles of 32 rows in FP32, 125 of 16 in FP64, over 38 blocks)."""
     P = _params()
     wd = P["wd"]
     tau = 40.0
-    pulses = [(0, [TP * (0.10 + 0.01 * (i // 2)), wd, 2.5, 0.0]) for i in range(8)]
-    _run((100, 4, 5), 20, pulses, tau, 5e-4, 40, 10, [0, 7], P, precision=precision)
+    pulses = [(0, [TP * (0.10 + 0.01 * (i // 2)), wd, 2.5, 0.0]) for i in range(32)]
+    _run((100, 4, 5), 20, pulses, tau, 5e-4, 40, 10, [0, 31], P, precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_g64"])
+def test_large_rank(precision):
+    """M = 28 (K = 2: 2352 partial sums per row tile, 10 per thread) on N = 150."""
+    P = _params(kappa=2.0, gamma=0.1)
+    wd = P["wd"]
+    pulses = [(0, [TP * 0.8, wd, 0.05, 0.0])] * 2
+    _run((10, 3, 5), 28, pulses, 0.3, 5e-4, 120, 40, [0, 1], P, precision=precision)
 
 
 def test_capacity_and_errors():
