@@ -559,10 +559,12 @@ def run_paper(args):
     sampler.start()
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kap, gam = wl.params["kappa"], wl.params["gamma"]
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
         b.integrate(wl.dt, chunk)
+        b.loss(kap, gam)                    # eps_a, T, Lambda over the run so far (syncs)
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -577,7 +579,9 @@ def run_paper(args):
                 "traffic": None, "kernel": "integrate (sparse engine, 4 launches per RK4 stage)",
                 "peak_source": "%s FMA pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
                                % ("FP64" if prec == "fp64" else "FP32", fma_clk, mhz), "flops_per_step": fl}
-    launches = (16 * chunk + 3) * args.steps
+    # per RK4 step sp_chi + 4 x (apply, gram, solve, update); the closing observation
+    # pass sp_chi, apply, gram, solve; then sp_loss
+    launches = (17 * chunk + 4 + 1) * args.steps
 
     e2e = None
     if not args.no_e2e:
@@ -591,6 +595,7 @@ def run_paper(args):
             b.set_state(Zh, step=step0)
             b.integrate(wl.dt, chunk)
             obs = b.observables()
+            obs.update(b.loss(kap, gam))
         te = time.perf_counter() - t0
         e2e = {"value": world * T * chunk * reps / te, "unit": "traj*steps/s", "h2d_bytes_per_step": int(Zh.nbytes),
                "d2h_bytes_per_step": int(sum(v.nbytes for v in obs.values()))}

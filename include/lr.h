@@ -358,8 +358,8 @@ typedef struct {
  * rowptr[o (N+1)] .. rowptr[o (N+1) + N] of the entry arrays:
  *   o = 0        A(t) = -i H_eff(t) = -i H(t) - 1/2 sum_k L_k(t)^dag L_k(t),
  *   o = 1 .. K   the jump operators L_k(t),
- *   o = K + 1    the readout operator r (static: every entry in channel 2),
- *                beta(t) = tr(rho r).
+ *   o = K + 1    the readout operator r(t), beta(t) = tr(rho r(t)) and the
+ *                photon number tr(rho r^dag r).
  * Within a row the entries may come in any order; every row's entries of an
  * operator are contiguous. Arrays are host memory owned by the caller and read
  * only during lr_sparse_create. */
@@ -380,7 +380,7 @@ typedef struct lr_sparse lr_sparse;
 
 /* Sizes of the paper's model for `p`: N = Nl Nu Nt and the total entry count
  * of its four operators (A, L_1 = sqrt(kappa) f in the rotated frame,
- * L_2 = sqrt(gamma) b, r = c_l). LR_ERR_ARG for cutoffs out of range. Host only. */
+ * L_2 = sqrt(gamma) b, r = f). LR_ERR_ARG for cutoffs out of range. Host only. */
 lr_status lr_paper_model_size(const lr_paper_params* p, int* N, long* nnz);
 
 /* Builds the operator set of the paper's model into caller-allocated host
@@ -396,7 +396,8 @@ lr_status lr_paper_model_size(const lr_paper_params* p, int* N, long* nnz);
  *    a = sum_i (alpha_i c_i - gamma_i c_i^dag), f = sum_i (beta_i c_i - delta_i c_i^dag);
  *  - A(t) from Eq. S(hamiltonian_rotated) and
  *    L_1(t) = sqrt(kappa) (s23 c_l + s24 c_u + e^{2i w_d t} (s21 c_u^dag + s22 c_l^dag)),
- *    L_2 = sqrt(gamma) sum_j sqrt(j) |j-1><j|, r = c_l.
+ *    L_2 = sqrt(gamma) sum_j sqrt(j) |j-1><j|, and the readout r(t) = L_1(t) / sqrt(kappa):
+ *    the filter field of Fig. 2, beta_rot(t) = e^{i w_d t} tr(rho_lab f).
  * Products of truncated operators are truncated products (an intermediate
  * state outside the cutoffs contributes zero). Entries with the same row,
  * column and channel are merged; each row is sorted by (column, channel).
@@ -437,7 +438,8 @@ lr_status lr_sparse_set_state(lr_sparse* s, const double* Z, long step, void* st
 lr_status lr_sparse_get_state(const lr_sparse* s, double* Z, void* stream);
 /* n_steps RK4 steps of size dt [ns] from the current step; records beta at
  * every step and populations, photons and trace every pop_every steps.
- * LR_ERR_STATE past max_steps. Async. */
+ * LR_ERR_STATE past max_steps; LR_ERR_ARG for a dt other than the one the
+ * pulse run has used so far. Async. */
 lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, void* stream);
 /* Copies the records to host arrays (any may be NULL): beta [n_traj][max_steps+1]
  * complex128, pops [n_traj][n_rec][n_levels], nphot and trace [n_traj][n_rec]
@@ -445,6 +447,17 @@ lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, void* strea
  * error status (LR_ERR_NOT_PD, LR_ERR_NONFINITE). */
 lr_status lr_sparse_observables(lr_sparse* s, double* beta, double* pops, double* nphot, double* trace,
                                 void* stream);
+/* Assignment error and loss of Sec. S3.A / S3.B for candidate c = trajectories
+ * (2c, 2c+1), started from |g> and |e>, over the steps integrated so far
+ * (tau = step dt): SNR = sqrt(2 eta kappa int |beta_e - beta_g|^2 dt) (trapezoid
+ * on the step grid), eps_a = erfc(SNR/2)/2 + tau gamma/2, the ionization penalty
+ * T = (1/tau) sum_{g,e} sum_{k>=2} int P_k dt (trapezoid on the record grid, bins
+ * k >= 2 of the population levels) and Lambda = log10(eps_a + T). kappa is the
+ * decay rate of the read-out mode (the filter for the paper's model), gamma the
+ * transmon's. Host outputs of n_traj / 2 doubles each (any may be NULL).
+ * LR_ERR_ARG for an odd n_traj; LR_ERR_STATE before the first step. Sync. */
+lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, double gamma, double* eps_a, double* ion,
+                         double* loss, void* stream);
 const char* lr_sparse_last_error(const lr_sparse* s);
 void lr_sparse_destroy(lr_sparse* s);
 

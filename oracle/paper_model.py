@@ -48,8 +48,11 @@ global phase removed (D[L] and the low-rank O[m] do not see it)
 kept exactly (no secular approximation). L_2 = sqrt(gamma) b with the
 transmon lowering operator b = sum_j sqrt(j) |j-1><j| in the eigenbasis (a
 reading: the paper names b without a matrix form); V only multiplies it by a
-phase. The readout observable is beta = tr(rho c_l) (Sec. S2.A: the lower
-normal mode is read out).
+phase. The readout signal is the filter field, beta = tr(rho f) (the caption of
+Fig. 2; the SNR of Sec. S3.A uses the filter rate kappa). In the rotated frame
+the operator is f(t) = A + e^{2i w_d t} B, the lab-frame f seen from the frame
+times e^{i w_d t}: beta_rot(t) = e^{i w_d t} beta_lab(t), so |beta_e - beta_g|
+and the photon number tr(rho f^dag f) are those of the lab frame.
 
 Every operator is stored as a sum over time channels (a, q):
 X(t) = sum Omega(t)^a e^{i q w_d t} X_{a,q}, a in {0, 1}, q in {-2..2}.
@@ -187,6 +190,7 @@ class PaperModel:
             B = s21 * dag(cu) + s22 * dag(cl)
             self.jump_terms = [{channel_index(0, 0): np.sqrt(kappa) * A, channel_index(0, 2): np.sqrt(kappa) * B},
                                {channel_index(0, 0): np.sqrt(gamma) * b}]
+            self.r_terms = {channel_index(0, 0): A.tocsr(), channel_index(0, 2): B.tocsr()}
         elif frame == "lab":
             add(0, 0, _kron3(I(Nl), I(Nu), sp.diags(self.eps - self.eps[0]).astype(complex)))
             nt = npl + nmi
@@ -199,12 +203,11 @@ class PaperModel:
             f = s21 * dag(cu) + s22 * dag(cl) + s23 * cl + s24 * cu
             self.jump_terms = [{channel_index(0, 0): np.sqrt(kappa) * f},
                                {channel_index(0, 0): np.sqrt(gamma) * b}]
+            self.r_terms = {channel_index(0, 0): f.tocsr()}
         else:
             raise ValueError("frame must be 'rot' or 'lab'")
         self.frame = frame
         self.h_terms = {k: v.tocsr() for k, v in terms.items()}
-        self.r = cl
-        self.n_r = (dag(cl) @ cl).tocsr()
         self.level = np.tile(np.arange(Nt), Nl * Nu)
         self.n_exc = np.array([jl + ju + j for jl in range(Nl) for ju in range(Nu) for j in range(Nt)], dtype=float)
 
@@ -220,6 +223,10 @@ class PaperModel:
 
     def jumps(self, t: float, omega: float):
         return [self._at(jt, t, omega) for jt in self.jump_terms]
+
+    def readout(self, t: float, omega: float):
+        """The readout operator f (lab frame) or f(t) (rotated frame)."""
+        return self._at(self.r_terms, t, omega)
 
     def heff_terms(self):
         """Channel terms of -i H_eff = -i H - 1/2 sum_k L_k^dag L_k: the channel of
@@ -264,14 +271,16 @@ def lindblad_rhs(rho, t, model, envelope):
     return out
 
 
-def _obs(y, model, low_rank):
+def _obs(y, model, low_rank, t, omega):
+    """beta = tr(rho r(t)), level populations, photons tr(rho r^dag r), trace."""
+    r = model.readout(t, omega)
     if low_rank:
-        rm = model.r @ y
+        rm = r @ y
         w = np.sum(np.abs(y) ** 2, axis=1)
         return np.trace(y.conj().T @ rm), np.bincount(model.level, w, model.dims[2]), np.vdot(rm, rm).real, w.sum()
     d = np.real(np.diag(y))
-    return (np.trace(model.r @ y), np.bincount(model.level, d, model.dims[2]),
-            np.trace(model.n_r @ y).real, d.sum())
+    return (np.trace(r @ y), np.bincount(model.level, d, model.dims[2]),
+            np.trace(r.conj().T @ (r @ y)).real, d.sum())
 
 
 def integrate(y0, model, envelope, dt, n_steps, pop_every=1, low_rank=True, return_state=False):
@@ -283,7 +292,8 @@ def integrate(y0, model, envelope, dt, n_steps, pop_every=1, low_rank=True, retu
     for n in range(n_steps + 1):
         if n > 0:
             y = rk4_step(lambda x, t: rhs(x, t, model, envelope), y, (n - 1) * dt, dt)
-        b, p, nr, tr = _obs(y, model, low_rank)
+        t = n * dt
+        b, p, nr, tr = _obs(y, model, low_rank, t, envelope(t))
         beta[n] = b
         if n % pop_every == 0:
             pops.append(p)

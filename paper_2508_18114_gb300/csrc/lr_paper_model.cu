@@ -17,7 +17,10 @@
 //     f = sum_i (beta_i c_i - delta_i c_i^dag) (from [a, c_i^dag] = alpha_i,
 //     [a, c_i] = gamma_i), so s13 = alpha_l, s12 = -gamma_l, s14 = alpha_u,
 //     s11 = -gamma_u, s23 = beta_l, s22 = -delta_l, s24 = beta_u, s21 = -delta_u.
-//  3. Operators as sums of "ladder words": a coefficient, a time channel and a
+//  3. Readout: the filter field, beta = tr(rho f) (Fig. 2), as
+//     f(t) = s23 c_l + s24 c_u + e^{2i w_d t} (s21 c_u^dag + s22 c_l^dag) in the
+//     frame of the drive (e^{i w_d t} times the lab-frame operator).
+//  4. Operators as sums of "ladder words": a coefficient, a time channel and a
 //     product of elementary operators applied right to left to a basis state;
 //     an intermediate state outside the cutoffs ends the word (truncated
 //     products, as matrix products of the truncated operators give).
@@ -242,7 +245,11 @@ std::vector<std::vector<Word>> words(const lr_paper_params& p, const Derived& D)
   w1(L1, sk * D.s21, chan(0, 2), UP);
   w1(L1, sk * D.s22, chan(0, 2), LP);
   w1(L2, sqrt(p.gamma), chan(0, 0), BL);
-  w1(R, 1.0, chan(0, 0), LM);
+  // readout: the filter field f in the frame of the drive, e^{i w_d t} times the lab-frame f
+  w1(R, D.s23, chan(0, 0), LM);
+  w1(R, D.s24, chan(0, 0), UM);
+  w1(R, D.s21, chan(0, 2), UP);
+  w1(R, D.s22, chan(0, 2), LP);
   return {A, L1, L2, R};
 }
 

@@ -467,6 +467,54 @@ __global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage
   }
 }
 
+// Sec. S3.A / S3.B for candidate c = trajectories (2c, 2c+1) = (g, e), over the
+// steps [0, step]: S = trapezoid of |beta_e - beta_g|^2 (step dt),
+// SNR = sqrt(2 eta kappa S), eps_a = erfc(SNR/2)/2 + tau gamma/2, tau = step dt;
+// T = (1/tau) sum_{g,e} sum_{k>=2} trapezoid of P_k over the records
+// [0, step / pop_every]; Lambda = log10(eps_a + T). out[c] = (eps_a, T, Lambda).
+__global__ void __launch_bounds__(SP_T) sp_loss(SpDev d, SpParams p, long step, double dt, double eta, double kappa,
+                                                double gamma, double* out) {
+  __shared__ double red[SP_T / 32];
+  const int c = blockIdx.x, tid = threadIdx.x;
+  const double2* bg = d.beta + (size_t)(2 * c) * (p.max_steps + 1);
+  const double2* be = d.beta + (size_t)(2 * c + 1) * (p.max_steps + 1);
+  double acc = 0.0, ion = 0.0;
+  for (long i = tid; i <= step; i += SP_T) {
+    const double dx = be[i].x - bg[i].x, dy = be[i].y - bg[i].y;
+    acc += (i == 0 || i == step ? 0.5 : 1.0) * (dx * dx + dy * dy);
+  }
+  const long last = step / p.pop_every;
+  for (long r = tid; r <= last; r += SP_T) {
+    double sum = 0.0;
+    for (int tj = 2 * c; tj <= 2 * c + 1; ++tj)
+      for (int k = 2; k < p.n_levels; ++k) sum += d.pops[((size_t)tj * p.n_rec + r) * p.n_levels + k];
+    ion += (r == 0 || r == last ? 0.5 : 1.0) * sum;
+  }
+  double v[2] = {acc, ion};
+  for (int q = 0; q < 2; ++q) {   // fixed-order block sum
+    double x = v[q];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = x;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < SP_T / 32; ++w) t += red[w];
+      v[q] = t;
+    }
+  }
+  if (tid == 0) {
+    const double tau = (double)step * dt;
+    const double S = step > 0 ? dt * v[0] : 0.0;
+    const double snr = sqrt(2.0 * eta * kappa * S);
+    const double e = 0.5 * erfc(0.5 * snr) + 0.5 * tau * gamma;
+    const double T = (step > 0 && last > 0) ? v[1] * p.pop_every * dt / tau : 0.0;
+    out[3 * c] = e;
+    out[3 * c + 1] = T;
+    out[3 * c + 2] = log10(e + T);
+  }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -478,6 +526,7 @@ struct lr_sparse {
   int N, M, K, T, n_levels, nblk, ntile;
   int fp32;   // 1: FP32_G64 state arithmetic
   long nnz, max_steps, n_rec, step;
+  double dt;   // RK4 step of the run (0 before the first integrate)
   int pop_every;
   double wd, tau;
   std::vector<int> rowptr, col, level;
@@ -487,7 +536,7 @@ struct lr_sparse {
   char* ws;
   size_t ws_bytes;
   // offsets into the workspace
-  size_t o_rowptr, o_col, o_val, o_valf, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X, o_chi, o_Xf,
+  size_t o_rowptr, o_col, o_val, o_valf, o_chan, o_level, o_pulse, o_traj, o_err, o_Z, o_Zs, o_acc, o_W, o_Y, o_Yr, o_X, o_chi, o_Xf, o_loss,
       o_part, o_beta, o_pops, o_nphot, o_trace, total;
   std::string msg;
 };
@@ -531,6 +580,7 @@ void layout(lr_sparse* s) {
   s->o_X = take((size_t)s->T * s->K * s->M * s->M * sizeof(double2));
   s->o_chi = take((size_t)s->T * 4 * NCH * sizeof(double2));
   s->o_Xf = take((size_t)s->T * s->K * s->M * s->M * sizeof(float2));
+  s->o_loss = take((size_t)(s->T / 2 + 1) * 3 * sizeof(double));
   const size_t ps = (size_t)2 * (1 + s->K) * s->M * s->M + 4 + s->n_levels;
   s->o_part = take((size_t)s->T * s->nblk * ps * sizeof(double));
   s->o_beta = take((size_t)s->T * (s->max_steps + 1) * sizeof(double2));
@@ -671,8 +721,6 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
     const int* rp = m->rowptr + (size_t)o * (N + 1);
     for (int n = 0; n < N; ++n)
       if (rp[n] < 0 || rp[n] > rp[n + 1] || rp[n + 1] > m->nnz) return LR_ERR_ARG;
-    for (int e = rp[0]; e < rp[N]; ++e)
-      if (o == K + 1 && m->chan[e] != 2) return LR_ERR_ARG;   // static readout operator
   }
   for (long e = 0; e < m->nnz; ++e)
     if (m->col[e] < 0 || m->col[e] >= N || m->chan[e] >= NCH || !isfinite(m->val[2 * e]) || !isfinite(m->val[2 * e + 1]))
@@ -796,6 +844,7 @@ extern "C" lr_status lr_sparse_set_initial(lr_sparse* s, const int* psi, uint64_
     return cuda_fail(s, e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
   s->step = 0;
+  s->dt = 0.0;
   return LR_OK;
 }
 
@@ -841,6 +890,8 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
   if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
   if (!(dt > 0.0) || !isfinite(dt) || n_steps < 0) return fail(s, LR_ERR_ARG, "bad dt or n_steps");
   if (s->step + n_steps > s->max_steps) return fail(s, LR_ERR_STATE, "integration past max_steps");
+  if (s->step > 0 && s->dt > 0.0 && dt != s->dt) return fail(s, LR_ERR_ARG, "dt differs within one pulse run");
+  s->dt = dt;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const SpDev d = dev(s);
   const SpParams p = params(s);
@@ -877,6 +928,32 @@ extern "C" lr_status lr_sparse_observables(lr_sparse* s, double* beta, double* p
   if (err == DEV_NOT_PD) return fail(s, LR_ERR_NOT_PD, "Gram matrix not positive definite");
   if (err == DEV_NONFINITE) return fail(s, LR_ERR_NONFINITE, "non-finite state or signal");
   if (err) return fail(s, LR_ERR_CUDA, "device error");
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, double gamma, double* eps_a, double* ion,
+                                    double* loss, void* stream) {
+  if (!s) return LR_ERR_ARG;
+  if (!s->ws) return fail(s, LR_ERR_WORKSPACE, "no workspace bound");
+  if (s->T % 2) return fail(s, LR_ERR_ARG, "trajectories must come in (g, e) pairs");
+  if (!(eta > 0.0) || !(kappa >= 0.0) || !(gamma >= 0.0) || !isfinite(eta + kappa + gamma))
+    return fail(s, LR_ERR_ARG, "bad eta, kappa or gamma");
+  if (s->step < 1 || !(s->dt > 0.0)) return fail(s, LR_ERR_STATE, "no integrated steps");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nc = s->T / 2;
+  double* dout = reinterpret_cast<double*>(s->ws + s->o_loss);
+  sp_loss<<<nc, SP_T, 0, st>>>(dev(s), params(s), s->step, s->dt, eta, kappa, gamma, dout);
+  cudaError_t e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(s, e);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
+  std::vector<double> h((size_t)nc * 3);
+  if ((e = cudaMemcpy(h.data(), dout, h.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(s, e);
+  for (int c = 0; c < nc; ++c) {
+    if (eps_a) eps_a[c] = h[3 * c];
+    if (ion) ion[c] = h[3 * c + 1];
+    if (loss) loss[c] = h[3 * c + 2];
+  }
   return LR_OK;
 }
 

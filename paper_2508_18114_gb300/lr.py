@@ -38,7 +38,8 @@ EXPORTS = (
     "lr_backward_workspace_size", "lr_backward", "lr_loss", "lr_diagnostics",
     "lr_paper_model_size", "lr_paper_model_build", "lr_sparse_create", "lr_sparse_workspace_size",
     "lr_sparse_bind_workspace", "lr_sparse_set_initial", "lr_sparse_set_state", "lr_sparse_get_state",
-    "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_last_error", "lr_sparse_destroy",
+    "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_loss", "lr_sparse_last_error",
+    "lr_sparse_destroy",
 )
 
 
@@ -118,6 +119,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_sparse_get_state.argtypes = [vp, vp, vp]
     lib.lr_sparse_integrate.argtypes = [vp, d, l, vp]
     lib.lr_sparse_observables.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.lr_sparse_loss.argtypes = [vp, d, d, d, vp, vp, vp, vp]
     lib.lr_sparse_last_error.argtypes = [vp]
     lib.lr_sparse_last_error.restype = C.c_char_p
     lib.lr_sparse_destroy.argtypes = [vp]

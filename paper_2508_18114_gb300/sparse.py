@@ -129,6 +129,15 @@ class SparseBatch:
                                                     C.c_void_p(_stream_ptr(stream))))
         return dict(beta=beta, pops=pops, nphot=nphot, trace=trace)
 
+    def loss(self, kappa: float, gamma: float, eta: float = 0.6, stream=None) -> dict:
+        """eps_a, ionization T and Lambda per candidate (trajectories 2c, 2c+1 =
+        |g>, |e>) over the steps integrated so far (Sec. S3.A, S3.B)."""
+        nc = self.n_traj // 2
+        out = {k: np.zeros(nc) for k in ("eps_a", "ion", "loss")}
+        self._check(self._lib.lr_sparse_loss(self._h, float(eta), float(kappa), float(gamma), _ptr(out["eps_a"]),
+                                             _ptr(out["ion"]), _ptr(out["loss"]), C.c_void_p(_stream_ptr(stream))))
+        return out
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and self._lib is not None:

@@ -104,6 +104,44 @@ def test_large_rank(precision):
     _run((10, 3, 5), 28, pulses, 0.3, 5e-4, 120, 40, [0, 1], P, precision=precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_g64"])
+def test_assignment_error_and_loss(precision):
+    """eps_a, T and Lambda (Sec. S3.A, S3.B) from the device records against the
+    oracle's signal functions on the oracle's beta and populations."""
+    from oracle import signal
+    from paper_2508_18114_gb300 import sparse
+    P = _params(g=TP * 0.3, kappa=1.0, gamma=0.05)
+    wd, tau, dt, n, pe = P["wd"], 0.4, 5e-4, 800, 100
+    dims, M = (6, 3, 4), 4
+    pulses = [(0, [TP * 1.0, wd, 0.05, 0.0])] * 2 + [(0, [TP * 0.6, wd, 0.08, 0.0])] * 2
+    model = sparse.paper_model(*dims, **P)
+    b = sparse.SparseBatch(model, M, pulses, tau, n, pop_every=pe, precision=precision)
+    b.set_initial([0, 1, 0, 1], SEED, EPS)
+    b.integrate(dt, n)
+    got = b.loss(P["kappa"], P["gamma"], eta=0.6)
+    ora_model = pm.PaperModel(*dims, frame="rot", **P)
+    # FP64: rounding order only. FP32_G64: eps_a relative 5e-5 (beta carries
+    # ~1e-6 relative error); T is a sum of populations, absolute 5e-5 as the
+    # populations; Lambda = log10(eps_a + T) then moves by at most ~5e-4.
+    tol = 1e-10 if precision == "fp64" else 5e-5
+    tol_T = (lambda T: 1e-10 * max(T, 1e-12)) if precision == "fp64" else (lambda T: 5e-5)
+    tol_L = 1e-10 if precision == "fp64" else 5e-4
+    for c in range(2):
+        outs = []
+        for tj in (2 * c, 2 * c + 1):
+            kind, p = pulses[tj]
+            env = lambda t, kind=kind, p=p: opulse.envelope(kind, p, t, tau)  # noqa: E731
+            m0 = init_state.initial_state(ora_model.N, M, tj % 2, EPS, SEED, tj)
+            outs.append(pm.integrate(m0, ora_model, env, dt, n, pop_every=pe, low_rank=True))
+        ea = signal.assignment_error(outs[0]["beta"], outs[1]["beta"], dt, P["kappa"], P["gamma"], 0.6)
+        T = signal.ionization(outs[0]["pops"], outs[1]["pops"], pe * dt, n * dt)
+        assert abs(got["eps_a"][c] - ea) <= tol * ea, c
+        assert abs(got["ion"][c] - T) <= tol_T(T) + 1e-15, c
+        assert abs(got["loss"][c] - signal.loss(ea, T)) <= tol_L, c
+    eps_sep = got["eps_a"] - 0.5 * n * dt * P["gamma"]   # minus eps_decay = tau gamma / 2
+    assert np.all(eps_sep < 0.5) and np.all(eps_sep > 0.0)  # SNR > 0: the signals do separate
+
+
 def test_capacity_and_errors():
     from paper_2508_18114_gb300 import lr, sparse
     P = _params()

@@ -171,6 +171,11 @@ def test_rotated_frame_equals_lab_frame():
     assert np.abs(out_r["state"] - want).max() < 2e-7
     assert np.abs(out_r["state"] - out_l["state"]).max() > 1e-2    # the frames do differ
     assert np.allclose(out_r["pops"], out_l["pops"], atol=2e-7)
+    # the filter field: beta_rot(t) = e^{i w_d t} tr(rho_lab f), photons equal
+    tt = dt * np.arange(n + 1)
+    assert np.abs(out_r["beta"] - np.exp(1j * lab.wd * tt) * out_l["beta"]).max() < 2e-7
+    assert np.abs(out_l["beta"]).max() > 1e-2
+    assert np.allclose(out_r["nr"], out_l["nr"], atol=2e-7)
 
 
 def test_lowrank_at_full_rank_is_the_master_equation():

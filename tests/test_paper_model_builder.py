@@ -67,7 +67,7 @@ def test_builder_matches_oracle(sparse_mod, dims, over):
     _close(ops[0], ora.heff_terms(), scale)
     _close(ops[1], ora.jump_terms[0], 1.0)
     _close(ops[2], ora.jump_terms[1], 1.0)
-    _close(ops[3], {pm.channel_index(0, 0): ora.r}, 1.0)
+    _close(ops[3], ora.r_terms, 1.0)
     assert np.array_equal(m["level"], ora.level)
     q = m["params"]
     assert abs(q["w_l"] - ora.wl) < 1e-12 * ora.wl and abs(q["w_u"] - ora.wu) < 1e-12 * ora.wu
@@ -125,7 +125,7 @@ def test_sparse_create_validates_arguments(sparse_mod):
         a[1][0] = N
 
     def bad_chan(a):
-        a[3][a[0][3 * (N + 1)]] = 3                               # readout operator must be static
+        a[3][0] = 10                                               # channels are 0 .. 9
 
     def bad_level(a):
         a[4][0] = 7
