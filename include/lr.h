@@ -199,6 +199,22 @@ lr_status lr_set_state(lr_ctx* ctx, int traj, const double* host_Z, long step, v
  * Synchronous. */
 lr_status lr_get_state(lr_ctx* ctx, int traj, double* host_Z, void* stream);
 
+/* Adaptive rank (Sec. S1.B: the rank is raised when the smallest eigenvalue
+ * of rho = Z Z^dag is no longer small against the largest). Continues the pulse
+ * run of `src` in `dst`, a context created with the same models, options and
+ * workspace kind but ranks M_dst >= M_src per candidate: every trajectory's
+ * state becomes Z_dst = [Z_src, sqrt(eps) q_{M_src}, ..., sqrt(eps) q_{M_dst-1}],
+ * with q_j the normalised component of a complex Gaussian vector (the
+ * generator of lr_set_initial, trajectory seed = output `traj` of `seed`,
+ * pair index (j - M_src) N + n) orthogonal to span(Z_src) and to the q before
+ * it; rho gains eps (M_dst - M_src) of trace. Copies the pulses, the step
+ * counter and the records (beta, populations, photons, trace, eps_a, T,
+ * Lambda); Gram snapshots are not copied, and lr_backward of dst is
+ * unavailable (no state at step 0). Both contexts must have workspaces bound;
+ * src is only read. LR_ERR_ARG when the contexts differ, LR_ERR_NOT_PD when a
+ * source Gram matrix is singular. Sync. */
+lr_status lr_grow_rank(lr_ctx* dst, const lr_ctx* src, uint64_t seed, double eps, void* stream);
+
 /* Advance every trajectory by n_steps RK4 steps of size dt from the current
  * step counter (t = step * dt), recording beta at every step and the other
  * observables every pop_every steps, then recompute eps_a of every candidate

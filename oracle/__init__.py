@@ -24,6 +24,8 @@ their printed order:
 * ``gradient``   - central finite-difference gradient of the assignment error
                    with respect to the pulse parameters.
 * ``diagnostics`` - spectrum of rho = m m^dag and purity tr(rho^2) (Sec. S1.B).
+* ``adaptive``   - rank control: spectrum test after each segment and rank
+                   growth by orthonormal padding columns (Sec. S1.B).
 * ``paper_model`` - the paper's own model: charge-basis transmon, normal modes
                    of the resonator-filter pair, the Hamiltonian in the frame of
                    the drive with its e^{+-2i w_d t} terms (Sec. S2.A, S2.D,
@@ -32,4 +34,4 @@ their printed order:
 
 Parity status of each function is stated in its module docstring.
 """
-from . import model, pulse, lowrank, lindblad, signal, init_state, gradient, diagnostics, paper_model  # noqa: F401
+from . import model, pulse, lowrank, lindblad, signal, init_state, gradient, diagnostics, paper_model, adaptive  # noqa: F401

@@ -368,6 +368,55 @@ lr_status lr_set_state(lr_ctx* c, int traj, const double* host_Z, long step, voi
   return LR_OK;
 }
 
+lr_status lr_grow_rank(lr_ctx* dst, const lr_ctx* src, uint64_t seed, double eps, void* stream) {
+  if (!dst || !src || dst == src) return LR_ERR_ARG;
+  if (!ready(dst) || !src->ws) return fail(dst, LR_ERR_WORKSPACE, "no workspace bound");
+  if (!src->have_state || !src->have_pulse) return fail(dst, LR_ERR_STATE, "the source has no pulse run");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(dst, LR_ERR_ARG, "need eps > 0");
+  if (dst->n_cand != src->n_cand || dst->n_traj != src->n_traj || dst->opt.precision != src->opt.precision ||
+      dst->opt.max_steps != src->opt.max_steps || dst->opt.pop_every != src->opt.pop_every ||
+      dst->opt.frame != src->opt.frame || dst->nt_max != src->nt_max)
+    return fail(dst, LR_ERR_ARG, "the contexts differ in batch, precision, capacity, records or frame");
+  for (int t = 0; t < dst->n_traj; ++t) {
+    const TrajDev &a = dst->traj[t], &b = src->traj[t];
+    if (a.N != b.N || a.Nt != b.Nt || a.Nr != b.Nr || a.Nf != b.Nf || a.n_modes != b.n_modes || a.wq != b.wq ||
+        a.alpha != b.alpha || a.wr != b.wr || a.wf != b.wf || a.g != b.g || a.J != b.J || a.kappa != b.kappa ||
+        a.gamma != b.gamma)
+      return fail(dst, LR_ERR_ARG, "the contexts hold different models");
+    if (a.M < b.M) return fail(dst, LR_ERR_ARG, "the destination rank is below the source rank");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dst->pulses = src->pulses;
+  cudaError_t e = cudaMemcpyAsync(dst->ws + dst->o_pulse, dst->pulses.data(), sizeof(PulseDev) * dst->n_cand,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dst->ws + dst->o_err, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess)
+    e = lr::launch_grow(dev_ptrs(dst), dev_ptrs(src), dst->n_traj, dst->opt.precision != LR_PREC_FP64, seed, eps, s);
+  // the records of the run so far, and the step counter
+  const size_t nt = dst->n_traj, nr = dst->n_rec;
+  const struct {
+    size_t d, s, bytes;
+  } cp[] = {{dst->o_beta, src->o_beta, sizeof(double2) * nt * (dst->opt.max_steps + 1)},
+            {dst->o_pops, src->o_pops, sizeof(double) * nt * nr * dst->nt_max},
+            {dst->o_nphot, src->o_nphot, sizeof(double) * nt * nr},
+            {dst->o_trace, src->o_trace, sizeof(double) * nt * nr},
+            {dst->o_eps, src->o_eps, sizeof(double) * dst->n_cand},
+            {dst->o_ion, src->o_ion, sizeof(double) * dst->n_cand},
+            {dst->o_loss, src->o_loss, sizeof(double) * dst->n_cand},
+            {dst->o_dstep, src->o_dstep, sizeof(long long)}};
+  for (const auto& x : cp)
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst->ws + x.d, src->ws + x.s, x.bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(dst, e, "growing the rank");
+  dst->tau = src->tau;
+  dst->dt = src->dt;
+  dst->step = src->step;
+  dst->have_pulse = true;
+  dst->have_state = true;
+  dst->z0_valid = false;
+  return check_device_error(dst);
+}
+
 lr_status lr_get_state(lr_ctx* c, int traj, double* host_Z, void* stream) {
   if (!c || !host_Z || traj < 0 || traj >= c->n_traj) return LR_ERR_ARG;
   if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");

@@ -113,6 +113,172 @@ __global__ void __launch_bounds__(IT) initial_state_kernel(const TrajDev* __rest
   }
 }
 
+// Rank growth (adaptive rank): one block per trajectory. The source state's
+// columns are kept; columns M_src .. M_dst-1 are sqrt(eps) q_j with q_j the
+// normalised component of a complex Gaussian vector xi_j (same generator as the
+// initial state, pair index (j - M_src) N + n) orthogonal to span(Z_src) and to
+// q_{M_src} .. q_{j-1}. The projection onto span(Z_src) is Z G^-1 Z^dag with
+// G = Z^dag Z (Cholesky, FP64), applied twice (reorthogonalisation).
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+
+template <typename T2>
+__global__ void __launch_bounds__(IT) grow_kernel(const TrajDev* __restrict__ dtraj, const TrajDev* __restrict__ straj,
+                                                  const T2* __restrict__ Zsrc, double2* __restrict__ Wbase,
+                                                  T2* __restrict__ Zdst, unsigned long long seed, double eps,
+                                                  unsigned* err) {
+  __shared__ double sh[33];
+  __shared__ double2 L[LR_MAX_RANK][LR_MAX_RANK + 1];
+  __shared__ double2 y[LR_MAX_RANK];
+  __shared__ int bad;
+  const int tj = blockIdx.x;
+  const TrajDev d = dtraj[tj], sr = straj[tj];
+  const int N = d.N, Ms = sr.M, Md = d.M, lds = sr.ld, ldd = d.ld;
+  double2* W = Wbase + d.z_off;
+  const T2* Zs = Zsrc + sr.z_off;
+  T2* Z = Zdst + d.z_off;
+  const unsigned long long ts = splitmix64(seed, (unsigned long long)tj);
+  if (threadIdx.x == 0) bad = 0;
+  for (int n = threadIdx.x; n < N; n += IT) {
+    for (int j = 0; j < Ms; ++j) W[(size_t)n * ldd + j] = to_d2(Zs[(size_t)n * lds + j]);
+    for (int j = Ms; j < Md; ++j) {
+      const unsigned long long pidx = (unsigned long long)(j - Ms) * N + n;
+      const double u1 = uniform_open0(ts, 2ull * pidx), u2 = uniform_open0(ts, 2ull * pidx + 1ull);
+      const double r = sqrt(-2.0 * log(u1));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      W[(size_t)n * ldd + j] = mk(r * cs, r * sn);
+    }
+  }
+  __syncthreads();
+  // inner product <W_i, W_j> = sum_n conj(W_ni) W_nj (fixed-order block sums)
+  auto dot = [&](int i, int j) {
+    double re = 0.0, im = 0.0;
+    for (int n = threadIdx.x; n < N; n += IT) {
+      const double2 a = W[(size_t)n * ldd + i], b = W[(size_t)n * ldd + j];
+      re += a.x * b.x + a.y * b.y;
+      im += a.x * b.y - a.y * b.x;
+    }
+    re = block_sum<IT>(re, sh);
+    im = block_sum<IT>(im, sh);
+    return mk(re, im);
+  };
+  // G = Z^dag Z, lower triangle: G_ij = <W_i, W_j> for i >= j
+  for (int i = 0; i < Ms; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double2 g = dot(i, j);
+      if (threadIdx.x == 0) L[i][j] = g;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // Cholesky G = L L^dag (serial, M <= 32)
+    for (int k = 0; k < Ms && !bad; ++k) {
+      double piv = L[k][k].x;
+      for (int q = 0; q < k; ++q) piv -= L[k][q].x * L[k][q].x + L[k][q].y * L[k][q].y;
+      if (!(piv > 0.0)) {
+        bad = 1;
+        break;
+      }
+      const double lkk = sqrt(piv);
+      L[k][k] = mk(lkk, 0.0);
+      for (int i = k + 1; i < Ms; ++i) {
+        double re = L[i][k].x, im = L[i][k].y;   // G_ik - sum_q L_iq conj(L_kq)
+        for (int q = 0; q < k; ++q) {
+          re -= L[i][q].x * L[k][q].x + L[i][q].y * L[k][q].y;
+          im -= L[i][q].y * L[k][q].x - L[i][q].x * L[k][q].y;
+        }
+        L[i][k] = mk(re / lkk, im / lkk);
+      }
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) set_error(err, DEV_NOT_PD);
+    return;
+  }
+  for (int j = Ms; j < Md; ++j) {
+    for (int pass = 0; pass < 2; ++pass) {
+      // remove the span(Z) component: c = Z^dag w, G y = c, w -= Z y
+      for (int i = 0; i < Ms; ++i) {
+        const double2 c = dot(i, j);
+        if (threadIdx.x == 0) y[i] = c;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < Ms; ++i) {   // L u = c
+          double re = y[i].x, im = y[i].y;
+          for (int q = 0; q < i; ++q) {
+            re -= L[i][q].x * y[q].x - L[i][q].y * y[q].y;
+            im -= L[i][q].x * y[q].y + L[i][q].y * y[q].x;
+          }
+          y[i] = mk(re / L[i][i].x, im / L[i][i].x);
+        }
+        for (int i = Ms - 1; i >= 0; --i) {   // L^dag y = u
+          double re = y[i].x, im = y[i].y;
+          for (int q = i + 1; q < Ms; ++q) {
+            re -= L[q][i].x * y[q].x + L[q][i].y * y[q].y;
+            im -= L[q][i].x * y[q].y - L[q][i].y * y[q].x;
+          }
+          y[i] = mk(re / L[i][i].x, im / L[i][i].x);
+        }
+      }
+      __syncthreads();
+      for (int n = threadIdx.x; n < N; n += IT) {
+        double2 w = W[(size_t)n * ldd + j];
+        for (int i = 0; i < Ms; ++i) {
+          const double2 a = W[(size_t)n * ldd + i], c = y[i];
+          w = mk(w.x - (a.x * c.x - a.y * c.y), w.y - (a.x * c.y + a.y * c.x));
+        }
+        W[(size_t)n * ldd + j] = w;
+      }
+      __syncthreads();
+      // and the components along the new orthonormal columns so far
+      for (int k = Ms; k < j; ++k) {
+        const double2 r = dot(k, j);
+        for (int n = threadIdx.x; n < N; n += IT) {
+          const double2 a = W[(size_t)n * ldd + k], b = W[(size_t)n * ldd + j];
+          W[(size_t)n * ldd + j] = mk(b.x - (r.x * a.x - r.y * a.y), b.y - (r.x * a.y + r.y * a.x));
+        }
+        __syncthreads();
+      }
+    }
+    const double nn = dot(j, j).x;
+    const double inv = 1.0 / sqrt(nn);
+    for (int n = threadIdx.x; n < N; n += IT) {
+      const double2 b = W[(size_t)n * ldd + j];
+      W[(size_t)n * ldd + j] = mk(b.x * inv, b.y * inv);
+    }
+    __syncthreads();
+  }
+  const double we = sqrt(eps);
+  for (int n = threadIdx.x; n < N; n += IT)
+    for (int j = 0; j < ldd; ++j) {
+      T2 v;
+      if (j < Ms) {
+        v = Zs[(size_t)n * lds + j];   // the kept columns, unchanged
+      } else if (j < Md) {
+        const double2 q = W[(size_t)n * ldd + j];
+        v.x = q.x * we;
+        v.y = q.y * we;
+      } else {
+        v.x = 0;
+        v.y = 0;
+      }
+      Z[(size_t)n * ldd + j] = v;
+    }
+}
+
+cudaError_t launch_grow(const DevPtrs& dst, const DevPtrs& src, int n_traj, int prec_fp32, uint64_t seed, double eps,
+                        cudaStream_t s) {
+  double2* W = reinterpret_cast<double2*>(dst.Za);
+  if (prec_fp32)
+    grow_kernel<float2><<<n_traj, IT, 0, s>>>(dst.traj, src.traj, reinterpret_cast<const float2*>(src.Zn), W,
+                                              reinterpret_cast<float2*>(dst.Zn), seed, eps, dst.err);
+  else
+    grow_kernel<double2><<<n_traj, IT, 0, s>>>(dst.traj, src.traj, reinterpret_cast<const double2*>(src.Zn), W,
+                                               reinterpret_cast<double2*>(dst.Zn), seed, eps, dst.err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_initial_state(const DevPtrs& p, const RunParams& rp, int /*max_N*/, int prec_fp32,
                                  uint64_t seed, double eps, cudaStream_t s) {
   double2* W = reinterpret_cast<double2*>(p.Za);

@@ -212,6 +212,10 @@ struct RunParams {
 // lr_common.cu
 cudaError_t launch_initial_state(const DevPtrs& p, const RunParams& rp, int max_N, int prec_fp32,
                                  uint64_t seed, double eps, cudaStream_t s);
+// Rank growth: dst's states = src's columns plus orthonormal padding columns of
+// weight eps, one block per trajectory (both contexts hold the same trajectories).
+cudaError_t launch_grow(const DevPtrs& dst, const DevPtrs& src, int n_traj, int prec_fp32, uint64_t seed, double eps,
+                        cudaStream_t s);
 // eps_a, T(tau) and Lambda at step *p.dstep + n_added (the integrate that
 // precedes it in the stream took n_added steps), then *p.dstep += n_added.
 cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long n_added, cudaStream_t s);

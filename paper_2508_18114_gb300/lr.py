@@ -39,7 +39,7 @@ EXPORTS = (
     "lr_paper_model_size", "lr_paper_model_build", "lr_sparse_create", "lr_sparse_workspace_size",
     "lr_sparse_bind_workspace", "lr_sparse_set_initial", "lr_sparse_set_state", "lr_sparse_get_state",
     "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_loss", "lr_sparse_last_error",
-    "lr_sparse_destroy",
+    "lr_sparse_destroy", "lr_grow_rank",
 )
 
 
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_sparse_integrate.argtypes = [vp, d, l, vp]
     lib.lr_sparse_observables.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.lr_sparse_loss.argtypes = [vp, d, d, d, vp, vp, vp, vp]
+    lib.lr_grow_rank.argtypes = [vp, vp, C.c_uint64, d, vp]
     lib.lr_sparse_last_error.argtypes = [vp]
     lib.lr_sparse_last_error.restype = C.c_char_p
     lib.lr_sparse_destroy.argtypes = [vp]
@@ -203,6 +204,8 @@ class LowRankBatch:
         self.models = list(models)
         self.ranks = [int(r) for r in ranks]
         self.precision = precision
+        self.options = dict(precision=precision, engine=engine, max_steps=int(max_steps), pop_every=int(pop_every),
+                            eta=float(eta), record_gram=bool(record_gram), frame=frame)
         self.device = torch.device(device)
         sz = C.c_size_t()
         self._check(self._lib.lr_workspace_size(h, C.byref(sz)))
@@ -314,6 +317,16 @@ class LowRankBatch:
         self._check(self._lib.lr_loss(self._h, ion.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
                                       C.c_void_p(_stream_ptr(stream))))
         return ion, loss
+
+    def grown(self, ranks, seed: int, eps: float = 1e-5, stream=None) -> "LowRankBatch":
+        """A new batch with ranks >= the current ones that continues this pulse
+        run (lr_grow_rank): the states keep their columns and gain orthonormal
+        padding columns of weight eps; pulses, step and records are copied."""
+        dst = LowRankBatch(self.models, ranks, device=self.device, **self.options)
+        dst._check(self._lib.lr_grow_rank(dst._h, self._h, C.c_uint64(seed), float(eps),
+                                          C.c_void_p(_stream_ptr(stream))))
+        dst.info = dst.query()
+        return dst
 
     def diagnostics(self, stream=None):
         """(purity [n_traj, n_rec], eigenvalues [n_traj, n_rec, max_M] descending)
