@@ -17,7 +17,8 @@
 //               record beta and the observables, Cholesky G = L L^dag and
 //               X_k = G^-1 T_k (the Moore-Penrose projection Zs^+ L_k Zs) by
 //               right-looking substitutions over all K M columns at once;
-//   sp_update - F = W + 1/2 sum_k Y_k X_k^dag, then the classical RK4 stage.
+//   sp_update - whole rows per block (Y_k rows staged in shared memory):
+//               F = W + 1/2 sum_k Y_k X_k^dag, then the classical RK4 stage.
 // After the last step an observation pass (apply r, Gram, solve without
 // Cholesky) records beta and the observables of the final state.
 //
@@ -419,30 +420,35 @@ __global__ void __launch_bounds__(SP_T) sp_solve(SpDev d, SpParams p, long step,
 __device__ __forceinline__ double2 load_x(const SpDev& d, size_t i, double2) { return d.X[i]; }
 __device__ __forceinline__ float2 load_x(const SpDev& d, size_t i, float2) { return d.Xf[i]; }
 
+// Whole rows per block: rb = SP_T / M rows; thread e < rb M owns element
+// (n0 + e / M, e % M). The block's rows of Y_k are contiguous in memory and are
+// staged in shared memory with coalesced loads.
 template <typename T2>
 __global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage, double dt_) {
   using T = typename Scalar<T2>::type;
   __shared__ T2 sX[LR_MAX_RANK * LR_MAX_RANK];
-  const int tj = blockIdx.y, M = p.M, MM = M * M;
-  const long long e = (long long)blockIdx.x * SP_T + threadIdx.x;
-  const bool live = e < p.NM;
-  const int n = live ? (int)(e / M) : 0, m = live ? (int)(e - (long long)n * M) : 0;
-  const size_t off = (size_t)tj * p.NM;
+  __shared__ T2 sY[SP_T];
+  const int tj = blockIdx.y, M = p.M, MM = M * M, e = threadIdx.x;
+  const int rb = SP_T / M, n0 = blockIdx.x * rb;
+  const int n = n0 + e / M, m = e - (e / M) * M;
+  const bool live = e < rb * M && n < p.N;
+  const size_t off = (size_t)tj * p.NM, idx = (size_t)n * M + m;
   T2* Z = static_cast<T2*>(d.Z);
   T2* Zs = static_cast<T2*>(d.Zs);
   T2* acc = static_cast<T2*>(d.acc);
   const T2* Yk = static_cast<const T2*>(d.Y);
-  T2 F = live ? static_cast<const T2*>(d.W)[off + e] : mk2<T2>(0, 0);
+  T2 F = live ? static_cast<const T2*>(d.W)[off + idx] : mk2<T2>(0, 0);
   const T half = (T)0.5;
+  const int rbase = (e / M) * M;   // this row's first element in sY
   for (int k = 0; k < p.K; ++k) {
     __syncthreads();
     for (int i = threadIdx.x; i < MM; i += SP_T) sX[i] = load_x(d, ((size_t)tj * p.K + k) * MM + i, T2());
+    if (live) sY[e] = Yk[((size_t)k * p.T + tj) * p.NM + idx];
     __syncthreads();
     if (live) {   // F += 1/2 sum_j Y_k[n][j] conj(X_k[m][j])
-      const T2* y = Yk + ((size_t)k * p.T + tj) * p.NM + (size_t)n * M;
       T2 s = mk2<T2>(0, 0);
-      for (int j = 0; j < M; ++j) {
-        const T2 a = y[j], x = sX[m * M + j];
+      for (int jj = 0; jj < M; ++jj) {
+        const T2 a = sY[rbase + jj], x = sX[m * M + jj];
         s = mk2<T2>(fma(a.x, x.x, fma(a.y, x.y, s.x)), fma(a.y, x.x, fma(-a.x, x.y, s.y)));
       }
       F = mk2<T2>(fma(half, s.x, F.x), fma(half, s.y, F.y));
@@ -451,19 +457,19 @@ __global__ void __launch_bounds__(SP_T) sp_update(SpDev d, SpParams p, int stage
   if (!live) return;
   const T dt = (T)dt_;
   const T w = (stage == 0 || stage == 3) ? (T)1 : (T)2;
-  const T2 a0 = stage == 0 ? mk2<T2>(0, 0) : acc[off + e];
+  const T2 a0 = stage == 0 ? mk2<T2>(0, 0) : acc[off + idx];
   const T2 a = mk2<T2>(fma(w, F.x, a0.x), fma(w, F.y, a0.y));
-  const T2 z = Z[off + e];
+  const T2 z = Z[off + idx];
   if (stage < 3) {
     const T c = stage == 2 ? dt : (T)0.5 * dt;
-    acc[off + e] = a;
-    Zs[off + e] = mk2<T2>(fma(c, F.x, z.x), fma(c, F.y, z.y));
+    acc[off + idx] = a;
+    Zs[off + idx] = mk2<T2>(fma(c, F.x, z.x), fma(c, F.y, z.y));
   } else {
     const T c = dt / (T)6;
     const T2 zn = mk2<T2>(fma(c, a.x, z.x), fma(c, a.y, z.y));
     if (!isfinite(zn.x) || !isfinite(zn.y)) set_error(d.err, DEV_NONFINITE);
-    Z[off + e] = zn;
-    Zs[off + e] = zn;
+    Z[off + idx] = zn;
+    Zs[off + idx] = zn;
   }
 }
 
@@ -640,6 +646,8 @@ template <typename T2>
 void launch_step_kernels(const lr_sparse* s, const SpDev& d, const SpParams& p, long step0, long n_steps, double dt,
                          cudaStream_t st) {
   const dim3 ge((unsigned)((p.NM + SP_T - 1) / SP_T), (unsigned)s->T);
+  const int rb = SP_T / s->M;
+  const dim3 gu((unsigned)((s->N + rb - 1) / rb), (unsigned)s->T);
   for (long i = 0; i <= n_steps; ++i) {
     const long step = step0 + i;
     const double t = (double)step * dt;
@@ -657,7 +665,7 @@ void launch_step_kernels(const lr_sparse* s, const SpDev& d, const SpParams& p, 
       sp_apply<T2><<<ge, SP_T, 0, st>>>(d, p, stg, stg == 0, 0);
       launch_gram<T2>(s, d, p, mode, st);
       sp_solve<<<s->T, SP_T, solve_smem(s), st>>>(d, p, step, mode);
-      sp_update<T2><<<ge, SP_T, 0, st>>>(d, p, stg, dt);
+      sp_update<T2><<<gu, SP_T, 0, st>>>(d, p, stg, dt);
     }
   }
 }
