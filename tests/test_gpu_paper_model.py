@@ -169,3 +169,77 @@ def test_fp32_state_round_trip():
     b.set_state(Z, step=2)
     back = b.get_state()
     assert np.abs(back - Z.astype(np.complex64)).max() == 0.0
+
+
+def _add_dephasing(model, gphi):
+    """The builder's operator set plus a third jump operator sqrt(gphi) n_t
+    (transmon dephasing, diagonal): the row entries of L_3 and -gphi/2 n_t^2 on
+    the diagonal of A = -i H_eff."""
+    N, K = model["N"], model["n_jumps"]
+    Nt = model["dims"][2]
+    rp, col, val, ch = model["rowptr"], model["col"], model["val"], model["chan"]
+    jt = np.arange(N) % Nt
+    ops = []
+    for o in range(K + 2):
+        r = rp[o * (N + 1):(o + 1) * (N + 1)]
+        rows = []
+        for n in range(N):
+            sl = slice(r[n], r[n + 1])
+            rows.append((col[sl].copy(), val[2 * r[n]:2 * r[n + 1]].copy(), ch[sl].copy()))
+        ops.append(rows)
+    for n in range(N):   # diagonal of A, channel 2 (static)
+        c, v, h = ops[0][n]
+        k = np.nonzero((c == n) & (h == 2))[0]
+        assert k.size == 1
+        v[2 * k[0]] += -0.5 * gphi * jt[n] ** 2
+    l3 = [(np.array([n], np.int32), np.array([np.sqrt(gphi) * jt[n], 0.0]), np.array([2], np.uint8))
+          for n in range(N)]
+    ops = ops[:K + 1] + [l3] + ops[K + 1:]
+    rowptr, cols, vals, chans, pos = [], [], [], [], 0
+    for rows in ops:
+        rowptr.append(pos)
+        for c, v, h in rows:
+            cols.append(c)
+            vals.append(v)
+            chans.append(h)
+            pos += c.size
+            rowptr.append(pos)
+        rowptr.pop()
+        rowptr.append(pos)
+    out = dict(model)
+    out.update(n_jumps=K + 1, nnz=pos, rowptr=np.array(rowptr, np.int32), col=np.concatenate(cols).astype(np.int32),
+               val=np.concatenate(vals), chan=np.concatenate(chans).astype(np.uint8))
+    assert out["rowptr"].size == (K + 3) * (N + 1)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_g64"])
+def test_three_jump_operators(precision):
+    """K = 3 (the engine's maximum): the paper model plus transmon dephasing."""
+    import scipy.sparse as sp
+    import torch
+    from paper_2508_18114_gb300 import sparse
+    P = _params(g=TP * 0.3, kappa=1.0, gamma=0.05)
+    gphi = 0.7
+    dims, M, dt, n, pe, tau = (6, 3, 4), 5, 5e-4, 400, 100, 0.2
+    wd = P["wd"]
+    pulses = [(0, [TP * 1.0, wd, 0.05, 0.0])] * 2
+    model = _add_dephasing(sparse.paper_model(*dims, **P), gphi)
+    b = sparse.SparseBatch(model, M, pulses, tau, n, pop_every=pe, precision=precision)
+    b.set_initial([0, 1], SEED, EPS)
+    b.integrate(dt, n)
+    got = b.observables()
+    torch.cuda.synchronize()
+    ora = pm.PaperModel(*dims, frame="rot", **P)
+    Nl, Nu, Nt = dims
+    nt_op = sp.kron(sp.identity(Nl * Nu), sp.diags(np.arange(Nt, dtype=float)), format="csr").astype(complex)
+    ora.jump_terms.append({pm.channel_index(0, 0): np.sqrt(gphi) * nt_op})
+    tol = TOL[precision]
+    for tj in (0, 1):
+        env = lambda t: opulse.envelope(0, pulses[tj][1], t, tau)  # noqa: E731
+        m0 = init_state.initial_state(ora.N, M, tj, EPS, SEED, tj)
+        want = pm.integrate(m0, ora, env, dt, n, pop_every=pe, low_rank=True)
+        bs = np.abs(want["beta"]).max()
+        assert np.abs(got["beta"][tj] - want["beta"]).max() <= tol["beta"] * max(bs, 1e-3), tj
+        assert np.abs(got["pops"][tj] - want["pops"]).max() <= tol["pops"], tj
+        assert np.abs(got["trace"][tj] - want["trace"]).max() <= tol["trace"], tj
