@@ -31,6 +31,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -630,6 +631,19 @@ size_t state_bytes(const lr_sparse* s) {
 
 size_t solve_smem(const lr_sparse* s) { return (size_t)(1 + s->K) * s->M * (s->M + 1) * sizeof(double2); }
 
+// The dynamic shared-memory limit of sp_solve is a property of the function, not
+// of a context: it only ever grows, so that a context bound later with a smaller
+// rank does not lower it under one bound earlier.
+cudaError_t raise_solve_smem(int bytes) {
+  static std::mutex mu;
+  static int current = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (bytes <= current) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(sp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) current = bytes;
+  return e;
+}
+
 template <typename T2>
 void launch_gram(const lr_sparse* s, const SpDev& d, const SpParams& p, int mode, cudaStream_t st) {
   const dim3 gg((unsigned)s->nblk, (unsigned)s->T);
@@ -819,9 +833,7 @@ extern "C" lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, siz
     if (u.bytes && (e = cudaMemcpyAsync(s->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(s, e);
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
-  if ((e = cudaFuncSetAttribute(sp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(s))) !=
-      cudaSuccess)
-    return cuda_fail(s, e);
+  if ((e = raise_solve_smem((int)solve_smem(s))) != cudaSuccess) return cuda_fail(s, e);
   s->step = 0;
   return LR_OK;
 }

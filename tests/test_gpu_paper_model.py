@@ -243,3 +243,22 @@ def test_three_jump_operators(precision):
         assert np.abs(got["beta"][tj] - want["beta"]).max() <= tol["beta"] * max(bs, 1e-3), tj
         assert np.abs(got["pops"][tj] - want["pops"]).max() <= tol["pops"], tj
         assert np.abs(got["trace"][tj] - want["trace"]).max() <= tol["trace"], tj
+
+
+def test_two_contexts_keep_their_solve_memory():
+    """A rank-32 context (solve shared memory above 48 KB) still integrates
+    after a rank-4 context is bound: the kernel's limit only grows."""
+    from paper_2508_18114_gb300 import sparse
+    P = _params(kappa=2.0, gamma=0.1)
+    wd = P["wd"]
+    pulses = [(0, [TP * 0.8, wd, 0.05, 0.0])] * 2
+    model = sparse.paper_model(10, 3, 5, **P)
+    big = sparse.SparseBatch(model, 32, pulses, 0.1, 20, pop_every=10)
+    small = sparse.SparseBatch(model, 4, pulses, 0.1, 20, pop_every=10)
+    for b in (big, small):
+        b.set_initial([0, 1], SEED, EPS)
+    small.integrate(5e-4, 20)
+    big.integrate(5e-4, 20)
+    for b in (big, small):
+        o = b.observables()
+        assert np.all(np.isfinite(o["beta"])) and np.abs(o["trace"][:, -1] - 1.0).max() < 1e-3
