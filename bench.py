@@ -37,6 +37,18 @@ FP32_FMA_PER_CLK = 128
 FP64_FMA_PER_CLK = 2
 
 
+# What each precision computes in (fused engine): the bulk state, operator
+# apply, projections and RK4 in FP32; the Gram matrix as a double-word FP32
+# sum of exact products and the M x M factorisation in double-word FP32
+# (both ~2^-48 relative, FP64-class); the readout signal and eps_a in FP64.
+DTYPE_LABEL = {
+    "fp64": "f64",
+    "fp32_g64": "f32 bulk; double-word f32 (~2^-48) Gram and LDL^dag/G^-1; f64 signal",
+    "fp32": "f32 bulk and Gram; double-word f32 (~2^-48) LDL^dag/G^-1; f64 signal",
+    "tf32_g64": "f32 bulk, tf32 projection; double-word f32 (~2^-48) Gram and LDL^dag/G^-1; f64 signal",
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,8 +455,7 @@ def run_ours(args):
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "tf32_g64": "f32 (tf32 projection; f64 Gram/Cholesky/signal)",
-                      "fp32": "f32 (f64 Cholesky/signal)"}.get(prec, "f32 (f64 Gram/Cholesky/signal)"),
+            "dtype": DTYPE_LABEL[prec],
             "data": "synthetic (seeded pulses and initial states)", "config": desc,
             "pulse_evals_per_s": value / (2 * spp),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -623,7 +634,8 @@ def run_paper(args):
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == "fp64" else "f32 (f64 Gram/Cholesky/signal)",
+            "dtype": "f64" if prec == "fp64" else ("f32 bulk; double-word f32 (~2^-48) Gram; "
+                                                   "f64 Cholesky, solves and signal"),
             "data": "synthetic (seeded flat-top pulses, seeded initial states)",
             "config": {"workload": "paper: %d candidates x {g,e} = %d trajectories, normal-mode model of Sec. S2 "
                                    "(rotated frame, counter-rotating terms kept), N=%d (%s), M=%d, dt=%g ns, "

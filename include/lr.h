@@ -84,20 +84,27 @@ typedef enum {
 } lr_status;
 
 /* Arithmetic of the bulk state. FP64: complex128 everywhere.
- * FP32: as FP32_G64 but with the Gram matrix accumulated in FP32 (Cholesky,
- * inverse and signal stay FP64); FUSED engine only.
- * FP32_G64: Z, the operator apply, the projection term and the RK4 stages in
- * complex64; the Gram matrix Z^dag Z (exact FP32 products, FP64-class
- * double-word accumulation), its Cholesky factor, the solves and the readout
- * signal in FP64. Where the fused engine keeps the stage state in L2 it may
- * run the projection term (the Y_k X_k^dag product of Eq. S5) on the tensor
- * cores as three TF32 passes of a two-term split (FP32-class products,
- * lr_info.tensor_passes = 3).
- * TF32_G64: as FP32_G64 with the projection term in ONE TF32 tensor-core pass
- * (operands rounded to 10-bit mantissas, FP32 accumulation): the reduced-
- * precision variant, for measuring its error; FUSED engine only, and only
- * for batches whose operand tiles fit in shared memory (else
- * LR_ERR_UNSUPPORTED). */
+ * FP32_G64 (FUSED engine): Z, the operator apply, the projections
+ * T_k = Z^dag L_k Z, the projection term and the RK4 stages in complex64.
+ * The Gram matrix Z^dag Z is accumulated from exact FP32 products in a
+ * double-word FP32 sum (hi + lo floats, about 2^-48 relative: FP64-class,
+ * not IEEE FP64). Its LDL^dag factorisation, L^-1 and G^-1 run in the same
+ * double-word FP32 arithmetic (Dekker products, Knuth sums, a Newton
+ * reciprocal; about 2^-48 relative); G^-1 is then rounded to FP32 and
+ * X_k = G^-1 T_k is formed in FP32. The readout signal beta, the populations,
+ * photons and trace are summed in FP64 from the FP32 state, and eps_a, T and
+ * Lambda are computed in FP64. Where the fused engine keeps the stage state
+ * in L2 it may run the projection term (the Y_k X_k^dag product of Eq. S5)
+ * on the tensor cores as three TF32 passes of a two-term split (FP32-class
+ * products, lr_info.tensor_passes = 3).
+ * FP32 (FUSED engine): as FP32_G64 but with the Gram matrix accumulated in
+ * plain FP32.
+ * TF32_G64 (FUSED engine): as FP32_G64 with the projection term in ONE TF32
+ * tensor-core pass (operands rounded to 10-bit mantissas, FP32
+ * accumulation): the reduced-precision variant, for measuring its error;
+ * only for batches whose operand tiles fit in shared memory (else
+ * LR_ERR_UNSUPPORTED).
+ * The PLAIN engine runs FP64 only. */
 typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1, LR_PREC_FP32 = 2, LR_PREC_TF32_G64 = 3 } lr_precision;
 
 /* PLAIN: straightforward HBM-resident kernels, several launches per RK4
@@ -324,9 +331,12 @@ lr_status lr_query(const lr_ctx* ctx, lr_info* info);
  * Results equal those of lr_integrate with the plain FP64 engine for the
  * same state.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the one array, which keeps the
+ * Every call made outside stream capture looks up the array's device
+ * address (cudaGetSymbolAddress) with the current device, so a device reset
+ * that moves the array is picked up by the next call; a call made during
+ * capture reuses the address found by the last call outside capture. So the
+ * first call on a device must come before any stream capture (a captured
+ * first call returns LR_ERR_STATE). All calls share the one array, which keeps the
  * previous call's contents (everything a call reads is rewritten or cleared
  * by that call first); calls that overlap on the GPU (other streams, other
  * host threads) race on it and must be serialised by the caller. */

@@ -1,6 +1,7 @@
 // FUSED engine, host side: launch planning (variants, team size, cost
 // model), workspace layout and launches. The kernel is in lr_fused_kernel.cuh;
 // its rotating-frame instantiations are compiled in lr_fused_rwa.cu.
+#include <mutex>
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -82,6 +83,10 @@ const void* kernel_ptr(lr_precision prec, int zs_smem, int tc, int frame) {
 // planned later cannot shrink it under a context (or a captured graph) that
 // needs more.
 cudaError_t raise_smem_limit(const void* kern, int bytes) {
+  // one lock around the read and the write: two host threads planning at
+  // once must not let the smaller request land last
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
   cudaFuncAttributes fa{};
   cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
@@ -290,6 +295,8 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
     off += ((2 * (size_t)plan.R * (plan.Mp + 1) * es * plan.C * plan.n_clusters + 255) / 256) * 256;
   }
   a.acc_glob = sc + off;
+  // test hook of the device-wait timeout path (see Args::debug_wait)
+  if (const char* e = getenv("LR_DEBUG_WAIT_CYCLES")) a.debug_wait = atoll(e);
   // the trajectory order is in the scratch since fused_prepare; the kernel's
   // attributes are raised here only outside a stream capture
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

@@ -58,6 +58,7 @@ struct Args {
   const int* order;
   void* zs_glob;      // global stage buffers, per cluster [C][2][R][Mp+1]
   void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
+  long long debug_wait;   // > 0: test hook, a wait of this many SM cycles that must run out
 };
 
 // ----------------------------------------------------------------- complex
@@ -279,9 +280,10 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// wait (at most ~1 s of SM clock) for the phase with the given parity;
-// false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// wait (at most `budget` SM cycles; ~1 s at the default) for the phase with
+// the given parity; false on timeout
+constexpr long long WAIT_BUDGET = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long budget = WAIT_BUDGET) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -291,7 +293,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 2000000000LL) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -334,6 +336,20 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   // steps, [140] phase-P task counter, [141] tensor-core timeout flag, [142]
   // tensor-core mbarrier, [143] TMEM base address
   double* misc = reinterpret_cast<double*>(smem + a.o_misc);
+  if (a.debug_wait > 0) {
+    // Test hook for the timeout path: thread 0 waits on an mbarrier that
+    // nothing arrives on, with a budget of debug_wait cycles. The wait runs
+    // out, the error word gets DEV_TIMEOUT, and the launch then carries on
+    // as usual (nothing asynchronous is in flight), so the context stays usable.
+    __shared__ __align__(8) unsigned long long dbg_bar;
+    if (tid == 0) {
+      const uint32_t mb = smem_u32(&dbg_bar);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(1) : "memory");
+      if (!mbar_wait(mb, 0u, a.debug_wait)) set_error(a.p.err, DEV_TIMEOUT);
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
+    }
+    __syncthreads();
+  }
   // row-ordered lower-triangle index table: entry e = i(i+1)/2 + j -> (i, j)
   __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
   for (int i = tid; i < LR_MAX_RANK; i += NT)

@@ -2,6 +2,7 @@
 // its scratch memory in a fixed, file-scope device array instead of a
 // caller-bound workspace, for callers that cannot allocate device memory.
 #include <climits>
+#include <mutex>
 
 #include "lr_internal.cuh"
 
@@ -37,7 +38,13 @@ constexpr size_t NA_BYTES = align256(NA_OFF_PART + sizeof(double) * NA_PART_BLOC
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 constexpr int NA_MAX_DEVICES = 64;
+// Device address of the array per device, guarded by g_scratch_mu. Outside
+// stream capture every call looks the address up again (cheap, and not a
+// stream operation), so a device reset or context teardown that reloads the
+// module and moves the array cannot leave a stale pointer; inside a capture
+// the address of the last call made outside capture is used.
 static void* g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
+static std::mutex g_scratch_mu;
 
 // Write the one-trajectory tables into the scratch and clear the error word
 // (no host-to-device copy is needed: the tables travel as kernel arguments).
@@ -68,13 +75,21 @@ extern "C" lr_status lr_integrate_plain_noalloc(const lr_model* m, int M, const 
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return LR_ERR_CUDA;
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LR_ERR_CUDA;
-    g_scratch_ptr[dev] = ptr;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return LR_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (cs == cudaStreamCaptureStatusNone) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LR_ERR_CUDA;
+      g_scratch_ptr[dev] = ptr;
+    } else if (!g_scratch_ptr[dev]) {
+      return LR_ERR_STATE;   // the first call on a device must come before any capture
+    }
+    base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  }
 
   TrajDev d{};
   d.N = (int)N;

@@ -631,17 +631,19 @@ size_t state_bytes(const lr_sparse* s) {
 
 size_t solve_smem(const lr_sparse* s) { return (size_t)(1 + s->K) * s->M * (s->M + 1) * sizeof(double2); }
 
-// The dynamic shared-memory limit of sp_solve is a property of the function, not
-// of a context: it only ever grows, so that a context bound later with a smaller
-// rank does not lower it under one bound earlier.
+// The dynamic shared-memory limit of sp_solve is a property of the function in
+// the current device's context, not of a lr_sparse context: it only ever grows,
+// so that a context bound later with a smaller rank does not lower it under one
+// bound earlier. The current limit is read from the device each time (it is
+// per device, and a device reset restores the default).
 cudaError_t raise_solve_smem(int bytes) {
   static std::mutex mu;
-  static int current = 0;
   std::lock_guard<std::mutex> lock(mu);
-  if (bytes <= current) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(sp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) current = bytes;
-  return e;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, sp_solve);
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(sp_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <typename T2>

@@ -1,0 +1,120 @@
+"""Whole-pulse parity at the benchmark's size: N = 2000, M = 20, tau = 40 ns,
+dt = 0.5 ps, 80,000 RK4 steps, against FP64 oracle values written by
+tests/golden/make_full_pulse.py (oracle only).
+
+* The bare-mode workload (candidates 0-2 of the N = 2000, M = 20 batch) on the
+  fused engine in FP32 bulk, in the launch plan the benchmark times: teams of
+  two CTAs, stage state in L2, projection on the CUDA cores. The per-
+  trajectory arithmetic of that plan does not depend on how many other
+  trajectories share the launch (checked bitwise against the whole 512-
+  trajectory batch over a short slice).
+* The paper's normal-mode model (candidate 0) on the sparse engine, FP32_G64
+  and FP64.
+
+Tolerances. FP64 paths: rounding only, ~1e-16 per step over 8e4 steps:
+relative 1e-10 is ample. FP32 bulk: every RK4 step rounds the state to FP32
+(u = 2^-24 = 6e-8); the errors of successive steps add like a random walk, so
+after n = 8e4 steps the state carries about sqrt(n) u = 1.7e-5 relative error
+in its leading column. The small columns (weight eps = 1e-5) carry relative
+errors up to 1/sqrt(p_M) ~ 300 times larger, but they enter beta, the
+populations and the photons only through their weight eps, so they add
+~u sqrt(n) 300 eps = 5e-8. The bound 1e-4 on beta, photons and
+populations is the random-walk estimate with a factor 6 of margin. eps_a =
+erfc(SNR/2)/2 + tau gamma/2 moves by (SNR^2/2) dSNR/SNR relative for large SNR
+(d ln erfc(x)/dx ~ -2x); with dSNR/SNR ~ dbeta/beta and SNR <= 6 here that
+is at most 18 dbeta/beta: bound 2e-3.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import lr_inputs as li
+from golden import full_pulse
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = dict(beta_rel=1e-4, pops_abs=1e-4, nphot_rel=1e-4, trace_abs=1e-4, eps_a_rel=2e-3, T_rel=2e-3)
+FP64_TOL = dict(beta_rel=1e-10, pops_abs=1e-10, nphot_rel=1e-10, trace_abs=1e-10, eps_a_rel=1e-9, T_rel=1e-9)
+TIMED_PLAN = {"LR_FUSED_C": "2", "LR_FUSED_ZS": "global", "LR_FUSED_TC": "0"}
+
+
+def _check(err, tol, what):
+    print(what, err)
+    for k, v in tol.items():
+        assert err[k] <= v, (what, k, err[k], v)
+
+
+def _timed_plan_batch(wl, monkeypatch, max_steps, pop_every):
+    from paper_2508_18114_gb300 import runner
+    for k, v in TIMED_PLAN.items():
+        monkeypatch.setenv(k, v)
+    b = runner.make_batch(wl, precision="fp32_g64", engine="fused", pop_every=pop_every, max_steps=max_steps)
+    info = b.query()
+    assert (info.team_size, info.stage_in_smem, info.tensor_passes) == (2, 0, 0)
+    return b
+
+
+@pytest.mark.skipif(not full_pulse.available("c4"), reason="full-pulse values not generated")
+def test_c4_full_pulse_fused_fp32_timed_plan(monkeypatch):
+    gold = full_pulse.load("c4")
+    cands = sorted(gold["cands"])
+    wl = li.c4(n_candidates=max(cands) + 1)
+    assert wl.dt == gold["dt"] and wl.n_steps == gold["n_steps"]
+    b = _timed_plan_batch(wl, monkeypatch, wl.n_steps, gold["rec_every"])
+    b.set_initial(wl.init_seed, wl.eps)
+    b.integrate(wl.dt, wl.n_steps)
+    obs = b.observables()
+    ion, _ = b.loss()
+    b.close()
+    obs["pop_every"] = gold["rec_every"]
+    err = full_pulse.errors(gold, obs, cands, eps_a=obs["eps_a"], ion=ion)
+    print("eps_a gpu", obs["eps_a"], "oracle", [gold["cands"][c]["eps_a"] for c in cands])
+    _check(err, FP32_TOL, "c4 fused fp32_g64 (team 2, L2), 80,000 steps")
+
+
+def test_timed_plan_small_batch_equals_full_batch(monkeypatch):
+    """The first three candidates run alone in the timed plan give bitwise the
+    results they get inside the whole 512-trajectory batch."""
+    wl = li.c4()
+    small = li.c4(n_candidates=3)
+    n = 60
+    out = []
+    for w in (wl, small):
+        b = _timed_plan_batch(w, monkeypatch, n, 20)
+        b.set_initial(w.init_seed, w.eps)
+        b.integrate(w.dt, n)
+        o = b.observables()
+        out.append((o, b.get_state(5)))
+        b.close()
+    (full, zf), (part, zp) = out
+    assert np.array_equal(full["beta"][:6], part["beta"])
+    assert np.array_equal(full["pops"][:6], part["pops"])
+    assert np.array_equal(zf, zp)
+
+
+def _paper_run(precision, gold):
+    from paper_2508_18114_gb300 import sparse
+    cands = sorted(gold["cands"])
+    wl = li.paper(max(cands) + 1)
+    n = int(round(wl.tau / wl.dt))
+    assert wl.dt == gold["dt"] and n == gold["n_steps"]
+    model = sparse.paper_model(*wl.dims, **wl.params)
+    pulses = [wl.pulses[c] for c in cands for _ in (0, 1)]
+    b = sparse.SparseBatch(model, wl.M, pulses, wl.tau, n, pop_every=gold["rec_every"], precision=precision)
+    b.set_initial([j % 2 for j in range(len(pulses))], wl.init_seed, wl.eps)
+    b.integrate(wl.dt, n)
+    obs = b.observables()
+    loss = b.loss(wl.params["kappa"], wl.params["gamma"])
+    del b
+    obs["pop_every"] = gold["rec_every"]
+    return full_pulse.errors(gold, obs, cands, eps_a=loss["eps_a"], ion=loss["ion"]), loss
+
+
+@pytest.mark.skipif(not full_pulse.available("paper"), reason="full-pulse values not generated")
+@pytest.mark.parametrize("precision", ["fp32_g64", "fp64"])
+def test_paper_model_full_pulse_sparse(precision):
+    gold = full_pulse.load("paper")
+    err, loss = _paper_run(precision, gold)
+    print("eps_a gpu", loss["eps_a"], "oracle", [gold["cands"][c]["eps_a"] for c in sorted(gold["cands"])])
+    _check(err, FP32_TOL if precision == "fp32_g64" else FP64_TOL, "paper model sparse %s, 80,000 steps" % precision)

@@ -383,6 +383,59 @@ def _tiny_workload(n_steps=1500, dt=2e-3):
                        n_steps * dt, init_seed=11, eps=1e-3)
 
 
+def test_fd_gradient_exact_on_polynomial_stand_in(monkeypatch):
+    """fd_gradient against the exact central difference of a known polynomial.
+
+    The workload runner is replaced by a stand-in whose eps_a is
+        e(theta) = sum_i c_i theta_i + sum_i d_i theta_i^2 + e01 theta_0 theta_1
+                   + sum_i k_i theta_i^3,
+    for which the central difference with step h_i = rel |theta_i| is exactly
+        c_i + 2 d_i theta_i + e01 theta_(1-i) [i < 2] + k_i (3 theta_i^2 + h_i^2).
+    Perturbing the wrong component, a one-sided step (error d_i h_i ~ 1e-4
+    relative), a step of h instead of 2h in the denominator, or an absolute
+    instead of a relative step each miss this by far more than rounding.
+    A zero parameter uses the absolute step rel."""
+    th0 = np.array([1.3, -0.7, 2.9, 0.0, 4.1, 0.55, 47.0, 1.9])
+    c = np.array([0.3, -1.1, 0.25, 0.8, -0.4, 1.7, 0.02, -0.6])
+    d = np.array([0.9, 0.2, -0.35, 1.4, 0.15, -0.8, 0.003, 0.45])
+    k = np.array([0.05, -0.02, 0.01, 0.3, 0.004, 0.07, 1e-5, -0.03])
+    e01 = 0.37
+
+    def e_of(th):
+        th = np.asarray(th, dtype=float)
+        return float(c @ th + d @ th ** 2 + e01 * th[0] * th[1] + k @ th ** 3)
+
+    import lr_inputs as li
+    m = li.ModelParams(dims=(2, 3), wq=2.0, alpha=-0.4, wr=3.0, g=0.3, kappa=0.5, gamma=0.1)
+    wl = li.Workload("stand-in", [li.Candidate(m, 2, li.PulseParams(1, tuple(th0)))], 1e-3, 1, 1e-3,
+                     init_seed=1)
+    calls = []
+
+    def fake_run(wl_, cand_index, n_steps=None, pop_every=1, theta=None, model=None):
+        assert cand_index == 0
+        th = wl_.candidates[0].pulse.p if theta is None else theta
+        calls.append(np.array(th, dtype=float))
+        return {"eps_a": e_of(th)}
+
+    monkeypatch.setattr(gradient, "run_candidate", fake_run)
+    rel = 1e-4
+    got = gradient.fd_gradient(wl, 0, rel=rel)
+    h = np.where(th0 != 0.0, rel * np.abs(th0), rel)
+    want = c + 2.0 * d * th0 + k * (3.0 * th0 ** 2 + h ** 2)
+    want[0] += e01 * th0[1]
+    want[1] += e01 * th0[0]
+    assert len(calls) == 2 * th0.size
+    # every call moves exactly one component, by +h_i then -h_i
+    for i in range(th0.size):
+        dp, dm = calls[2 * i] - th0, calls[2 * i + 1] - th0
+        assert np.count_nonzero(dp) == 1 and np.count_nonzero(dm) == 1
+        assert dp[i] == pytest.approx(h[i], rel=1e-9) and dm[i] == pytest.approx(-h[i], rel=1e-9)
+    # rounding: eps_a values of size ~1e2 differenced over h ~ 1e-4: ~1e-10
+    assert np.abs(got - want).max() <= 1e-8 * max(1.0, np.abs(want).max())
+    # the one-sided difference would be off by d_i h_i: far above the bound
+    assert np.abs(d * h).max() > 1e3 * 1e-8 * max(1.0, np.abs(want).max())
+
+
 def test_fd_gradient_richardson_consistent():
     """Central differences at h and h/2 agree to O(h^2) (smooth eps_a)."""
     wl = _tiny_workload()
