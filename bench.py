@@ -188,6 +188,17 @@ class ClockSampler:
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
 
 
+def pipe_peak_measured(kind, stream):
+    """FP32/FP64 FMA or TF32 MMA peak from the library's microbenchmark
+    (lr_measure_peak), in TFLOP/s, or None."""
+    try:
+        from paper_2508_18114_gb300 import lr as lrmod
+        f, _ = lrmod.measure_peak(kind, stream)
+        return f / 1e12
+    except Exception:
+        return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -251,20 +262,23 @@ def run_reference_paper(args):
     import lr_inputs as li
     from oracle import paper_model as pm
     wl = li.paper(args.candidates if args.candidates is not None else 256)
-    model_o = pm.PaperModel(*wl.dims, frame="rot", **wl.params)
+    frame = "rwa" if args.frame == "rwa" else "rot"
+    dt = args.dt or (2.5e-3 if frame == "rwa" else wl.dt)
+    model_o = pm.PaperModel(*wl.dims, frame=frame, **wl.params)
     ns = args.cpu_steps or 400
     for _ in range(args.warmup):
-        paper_oracle_sample(wl, model_o, max(2, ns // 10))
+        paper_oracle_sample(wl, model_o, max(2, ns // 10), dt=dt)
     tt = 0.0
     for _ in range(args.steps):
-        tt += paper_oracle_sample(wl, model_o, ns)[1]
+        tt += paper_oracle_sample(wl, model_o, ns, dt=dt)[1]
     value = ns * args.steps / tt
     line = {
         "impl": "reference", "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "paper: normal-mode model of Sec. S2, N=%d, M=%d, dt=%g ns"
-                               % (model_o.N, wl.M, wl.dt), "parallelism": "cpu oracle, one trajectory"},
+        "config": {"workload": "paper: normal-mode model of Sec. S2 (%s), N=%d, M=%d, dt=%g ns"
+                               % ("RWA, Eq. S(hamiltonian_rwa)" if frame == "rwa" else "frame of the drive",
+                                  model_o.N, wl.M, dt), "parallelism": "cpu oracle, one trajectory"},
         "cpu_baseline": {"value": value, "unit": "traj*steps/s", "cores": 1, "kind": "oracle",
                          "sample": "%d RK4 steps of trajectory 0 per step" % ns},
         "e2e": {"value": value, "unit": "traj*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -364,6 +378,11 @@ def run_ours(args):
                 "peak_source": "%s pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
                                % (pipe, FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK, mhz),
                 "flops_per_step": fl}
+    pm = pipe_peak_measured("fp64_fma" if prec == "fp64" else "fp32_fma", stream)
+    roofline["peak_measured"] = pm
+    roofline["frac_of_measured"] = achieved / pm if pm else None
+    roofline["peak_measured_source"] = ("lr_measure_peak: %s chains, 8 CTAs x 256 threads per SM, CUDA events, "
+                                        "after the timed region" % ("DFMA" if prec == "fp64" else "FFMA"))
     # kernels per bench step: the integrator's (plain: 3 per RK4 stage pair and
     # records; fused: one persistent launch), the eps_a epilogue and the step advance
     if engine == "plain":
@@ -517,8 +536,9 @@ def paper_flops_per_stage(model, M):
     return 8 * entries * M + 8 * N * (M * (M + 1) // 2 + K * M * M) + 8 * K * N * M * M + 12 * N * M
 
 
-def paper_oracle_sample(wl, model_o, n_steps, traj=0):
+def paper_oracle_sample(wl, model_o, n_steps, traj=0, dt=None):
     """FP64 oracle on one trajectory of the paper's model: (traj-steps/s, seconds, result)."""
+    dt = dt or wl.dt
     from oracle import init_state
     from oracle import paper_model as pm
     from oracle import pulse as opulse
@@ -526,9 +546,9 @@ def paper_oracle_sample(wl, model_o, n_steps, traj=0):
     env = lambda t: opulse.envelope(kind, p, t, wl.tau)  # noqa: E731
     m0 = init_state.initial_state(model_o.N, wl.M, traj % 2, wl.eps, wl.init_seed, traj)
     t0 = time.perf_counter()
-    out = pm.integrate(m0, model_o, env, wl.dt, n_steps, pop_every=n_steps, low_rank=True)
-    dt = time.perf_counter() - t0
-    return n_steps / dt, dt, out
+    out = pm.integrate(m0, model_o, env, dt, n_steps, pop_every=n_steps, low_rank=True)
+    sec = time.perf_counter() - t0
+    return n_steps / sec, sec, out
 
 
 def run_paper(args):
@@ -549,10 +569,12 @@ def run_paper(args):
     dev = torch.device("cuda", local)
     n = args.candidates if args.candidates is not None else 256
     wl = li.paper(n, first=rank * n)
-    model = sparse.paper_model(*wl.dims, **wl.params)
+    frame = "rwa" if args.frame == "rwa" else "rot"
+    dt = args.dt or (2.5e-3 if frame == "rwa" else wl.dt)
+    model = sparse.paper_model(*wl.dims, frame=frame, **wl.params)
     T = 2 * n
     pulses = [q for q in wl.pulses for _ in (0, 1)]
-    spp = int(round(wl.tau / wl.dt))
+    spp = int(round(wl.tau / dt))
     chunk = args.chunk or 40
     total = chunk * (args.warmup + args.steps)
     prec = args.precision or "fp32_g64"
@@ -562,7 +584,7 @@ def run_paper(args):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
-        b.integrate(wl.dt, chunk)
+        b.integrate(dt, chunk)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(local)
     if dist:
@@ -574,7 +596,7 @@ def run_paper(args):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        b.integrate(wl.dt, chunk)
+        b.integrate(dt, chunk)
         b.loss(kap, gam)                    # eps_a, T, Lambda over the run so far (syncs)
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
@@ -590,6 +612,9 @@ def run_paper(args):
                 "traffic": None, "kernel": "integrate (sparse engine, 4 launches per RK4 stage)",
                 "peak_source": "%s FMA pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
                                % ("FP64" if prec == "fp64" else "FP32", fma_clk, mhz), "flops_per_step": fl}
+    pm = pipe_peak_measured("fp64_fma" if prec == "fp64" else "fp32_fma", stream)
+    roofline["peak_measured"] = pm
+    roofline["frac_of_measured"] = achieved / pm if pm else None
     # per RK4 step sp_chi + 4 x (apply, gram, solve, update); the closing observation
     # pass sp_chi, apply, gram, solve; then sp_loss
     launches = (17 * chunk + 4 + 1) * args.steps
@@ -604,7 +629,7 @@ def run_paper(args):
         obs = None
         for _ in range(reps):
             b.set_state(Zh, step=step0)
-            b.integrate(wl.dt, chunk)
+            b.integrate(dt, chunk)
             obs = b.observables()
             obs.update(b.loss(kap, gam))
         te = time.perf_counter() - t0
@@ -614,14 +639,14 @@ def run_paper(args):
     cpu = err = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import paper_model as pm
-        model_o = pm.PaperModel(*wl.dims, frame="rot", **wl.params)
+        model_o = pm.PaperModel(*wl.dims, frame=frame, **wl.params)
         ns = args.cpu_steps or 400
-        v, dt_cpu, ora = paper_oracle_sample(wl, model_o, ns, traj=1)
+        v, dt_cpu, ora = paper_oracle_sample(wl, model_o, ns, traj=1, dt=dt)
         cpu = {"value": v, "unit": "traj*steps/s", "cores": 1, "kind": "oracle",
                "sample": "%d RK4 steps of trajectory 1 (candidate 0, |e>) (%.1f s)" % (ns, dt_cpu)}
         bq = sparse.SparseBatch(model, wl.M, pulses[:2], wl.tau, ns, pop_every=ns, device=dev, precision=prec)
         bq.set_initial([0, 1], wl.init_seed, wl.eps)
-        bq.integrate(wl.dt, ns)
+        bq.integrate(dt, ns)
         og = bq.observables()
         bo = ora["beta"]
         err = {"sample": "candidate 0, |e>, %d RK4 steps" % ns,
@@ -638,9 +663,10 @@ def run_paper(args):
                                                    "f64 Cholesky, solves and signal"),
             "data": "synthetic (seeded flat-top pulses, seeded initial states)",
             "config": {"workload": "paper: %d candidates x {g,e} = %d trajectories, normal-mode model of Sec. S2 "
-                                   "(rotated frame, counter-rotating terms kept), N=%d (%s), M=%d, dt=%g ns, "
-                                   "tau=%g ns, %s" % (n, T, model["N"], "x".join(map(str, wl.dims)), wl.M,
-                                                      wl.dt, wl.tau, prec),
+                                   "(%s), N=%d (%s), M=%d, dt=%g ns, tau=%g ns, %s"
+                                   % (n, T, "rotating-wave approximation, Eq. S(hamiltonian_rwa)" if frame == "rwa"
+                                      else "frame of the drive, counter-rotating terms kept", model["N"],
+                                      "x".join(map(str, wl.dims)), wl.M, dt, wl.tau, prec),
                        "trajectories": T, "N": model["N"], "M": wl.M, "nnz": int(model["nnz"]),
                        "engine": "sparse", "chunk_rk4_steps": chunk,
                        "parallelism": "dp%d (independent replicas)" % world,

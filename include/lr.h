@@ -343,6 +343,20 @@ lr_status lr_query(const lr_ctx* ctx, lr_info* info);
 lr_status lr_integrate_plain_noalloc(const lr_model* model, int M, const lr_pulse* pulse, double tau,
                                      double* Z, double* beta, double dt, long step0, long n_steps,
                                      void* stream);
+/* Arithmetic-pipe peak of the current device, measured (the paper has no
+ * counterpart: these are the roofline denominators of the kernels above).
+ *   kind 0: FP32 FMA (every thread runs 8 independent FFMA chains);
+ *   kind 1: FP64 FMA (the same with DFMA);
+ *   kind 2: TF32 tensor cores (one thread per CTA issues back-to-back
+ *           tcgen05.mma.kind::tf32 128 x 256 x 8 into tensor memory).
+ * Grids are a multiple of the SM count; one warm-up launch, then one timed
+ * launch with CUDA events on `stream`. flops_per_s (host, out): counted flops
+ * (an FMA is 2) per second; seconds (host, out, may be NULL): the timed
+ * launch. Synchronous. Uses no workspace (a 4-byte static device word holds
+ * the timeout flag). LR_ERR_ARG for an unknown kind, LR_ERR_TIMEOUT when the
+ * tensor-core wait ran out of its budget. */
+lr_status lr_measure_peak(int kind, double* flops_per_s, double* seconds, void* stream);
+
 const char* lr_status_string(lr_status s);
 const char* lr_last_error(const lr_ctx* ctx);
 void lr_destroy(lr_ctx* ctx);
@@ -378,6 +392,13 @@ typedef struct {
   double g, J;          /* transmon-resonator and resonator-filter couplings */
   double kappa, gamma;  /* filter and transmon decay rates */
   double wd;            /* drive frequency = frame frequency */
+  int frame;            /* 0: the Hamiltonian in the frame of the drive with its counter-rotating
+                           e^{+-2i w_d t} terms, Eq. S(hamiltonian_rotated), and L_1(t), r(t) with
+                           their e^{2i w_d t} parts; 1: the rotating-wave approximation,
+                           Eq. S(hamiltonian_rwa): every explicitly time-dependent term dropped
+                           (the channels q != 0 of H), and L_1 = sqrt(kappa) (s23 c_l + s24 c_u),
+                           r = s23 c_l + s24 c_u (their slow parts), so that the generator is slow
+                           and a larger dt can be used */
 } lr_paper_params;
 
 /* Operator set of the sparse engine. K = n_jumps; operator o occupies rows

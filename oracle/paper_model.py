@@ -144,6 +144,9 @@ class PaperModel:
     """Operators of the paper's model on |j_l> (x) |j_u> (x) |j_t>.
 
     ``frame="rot"``: Eq. S(hamiltonian_rotated) with the dissipators above.
+    ``frame="rwa"``: Eq. S(hamiltonian_rwa), the rotated Hamiltonian without its
+    explicitly time-dependent terms, with L_1 = sqrt(kappa) A and r = A (the slow
+    parts of the rotated-frame f).
     ``frame="lab"``: the same model before the frame map (the nearest-neighbour
     n_t, H = H_t + w_l N_l + w_u N_u + i g n_t sum_x mu_x (c_x^dag - c_x)
     + i Omega(t) sin(w_d t) sum_x nu_x (c_x^dag - c_x), static f), for the frame pin.
@@ -176,21 +179,32 @@ class PaperModel:
             terms[k] = terms.get(k, sp.csr_matrix((self.N, self.N), dtype=complex)) + X
 
         modes = (("l", cl, self.mu_l, self.nu_l, self.wl), ("u", cu, self.mu_u, self.nu_u, self.wu))
-        if frame == "rot":
+        if frame in ("rot", "rwa"):
+            # "rwa": Eq. S(hamiltonian_rwa), the explicitly time-dependent terms of
+            # Eq. S(hamiltonian_rotated) dropped; the jump operator and the readout
+            # keep their slow part A (reading: a slow generator, as the RWA intends)
+            rot = frame == "rot"
             add(0, 0, _kron3(I(Nl), I(Nu), sp.diags(self.eps - self.eps[0] - jt * wd).astype(complex)))
             for _, c, mu, nu, w in modes:
                 add(0, 0, (w - wd) * (dag(c) @ c))
                 add(0, 0, 1j * g * mu * (npl @ dag(c) - nmi @ c))
-                add(0, -2, -1j * g * mu * (npl @ c))
-                add(0, 2, 1j * g * mu * (nmi @ dag(c)))
                 add(1, 0, -0.5 * nu * (dag(c) + c))
-                add(1, 2, 0.5 * nu * dag(c))
-                add(1, -2, 0.5 * nu * c)
+                if rot:
+                    add(0, -2, -1j * g * mu * (npl @ c))
+                    add(0, 2, 1j * g * mu * (nmi @ dag(c)))
+                    add(1, 2, 0.5 * nu * dag(c))
+                    add(1, -2, 0.5 * nu * c)
             A = s23 * cl + s24 * cu
             B = s21 * dag(cu) + s22 * dag(cl)
-            self.jump_terms = [{channel_index(0, 0): np.sqrt(kappa) * A, channel_index(0, 2): np.sqrt(kappa) * B},
-                               {channel_index(0, 0): np.sqrt(gamma) * b}]
-            self.r_terms = {channel_index(0, 0): A.tocsr(), channel_index(0, 2): B.tocsr()}
+            if rot:
+                self.jump_terms = [{channel_index(0, 0): np.sqrt(kappa) * A,
+                                    channel_index(0, 2): np.sqrt(kappa) * B},
+                                   {channel_index(0, 0): np.sqrt(gamma) * b}]
+                self.r_terms = {channel_index(0, 0): A.tocsr(), channel_index(0, 2): B.tocsr()}
+            else:
+                self.jump_terms = [{channel_index(0, 0): np.sqrt(kappa) * A},
+                                   {channel_index(0, 0): np.sqrt(gamma) * b}]
+                self.r_terms = {channel_index(0, 0): A.tocsr()}
         elif frame == "lab":
             add(0, 0, _kron3(I(Nl), I(Nu), sp.diags(self.eps - self.eps[0]).astype(complex)))
             nt = npl + nmi
@@ -205,7 +219,7 @@ class PaperModel:
                                {channel_index(0, 0): np.sqrt(gamma) * b}]
             self.r_terms = {channel_index(0, 0): f.tocsr()}
         else:
-            raise ValueError("frame must be 'rot' or 'lab'")
+            raise ValueError("frame must be 'rot', 'rwa' or 'lab'")
         self.frame = frame
         self.h_terms = {k: v.tocsr() for k, v in terms.items()}
         self.level = np.tile(np.arange(Nt), Nl * Nu)

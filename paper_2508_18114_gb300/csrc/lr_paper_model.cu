@@ -214,13 +214,17 @@ std::vector<std::vector<Word>> words(const lr_paper_params& p, const Derived& D)
   w1(H, D.wu - p.wd, chan(0, 0), NU);
   const int up[2] = {LP, UP}, dn[2] = {LM, UM};
   const double mu[2] = {D.mu_l, D.mu_u}, nu[2] = {D.nu_l, D.nu_u};
+  // frame 1, Eq. S(hamiltonian_rwa): the same terms without the explicitly
+  // time-dependent ones (channels q != 0)
+  const bool rwa = p.frame == 1;
   for (int x = 0; x < 2; ++x) {
     w2(H, I * p.g * mu[x], chan(0, 0), TM_, up[x]);     //  i g mu n^+ c^dag
     w2(H, -I * p.g * mu[x], chan(0, 0), TP_, dn[x]);    // -i g mu n^- c
-    w2(H, -I * p.g * mu[x], chan(0, -2), TM_, dn[x]);   // -i g mu n^+ c e^{-2i w_d t}
-    w2(H, I * p.g * mu[x], chan(0, 2), TP_, up[x]);     //  i g mu n^- c^dag e^{2i w_d t}
     w1(H, -0.5 * nu[x], chan(1, 0), up[x]);             // -(nu/2) Omega (c^dag + c)
     w1(H, -0.5 * nu[x], chan(1, 0), dn[x]);
+    if (rwa) continue;
+    w2(H, -I * p.g * mu[x], chan(0, -2), TM_, dn[x]);   // -i g mu n^+ c e^{-2i w_d t}
+    w2(H, I * p.g * mu[x], chan(0, 2), TP_, up[x]);     //  i g mu n^- c^dag e^{2i w_d t}
     w1(H, 0.5 * nu[x], chan(1, 2), up[x]);              // +(nu/2) Omega c^dag e^{2i w_d t}
     w1(H, 0.5 * nu[x], chan(1, -2), dn[x]);             // +(nu/2) Omega c e^{-2i w_d t}
   }
@@ -231,9 +235,11 @@ std::vector<std::vector<Word>> words(const lr_paper_params& p, const Derived& D)
   const int aop[2] = {LM, UM}, bop[2] = {UP, LP};
   const double ac[2] = {D.s23, D.s24}, bc[2] = {D.s21, D.s22};
   const int aopd[2] = {LP, UP}, bopd[2] = {UM, LM};   // adjoints
+  // (RWA: L_1 = sqrt(kappa) Aop, its slow part)
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
       w2(A, k2 * ac[i] * ac[j], chan(0, 0), aopd[i], aop[j]);   // Aop^dag Aop
+      if (rwa) continue;
       w2(A, k2 * bc[i] * bc[j], chan(0, 0), bopd[i], bop[j]);   // Bop^dag Bop
       w2(A, k2 * ac[i] * bc[j], chan(0, 2), aopd[i], bop[j]);   // Aop^dag Bop e^{2i w_d t}
       w2(A, k2 * bc[i] * ac[j], chan(0, -2), bopd[i], aop[j]);  // Bop^dag Aop e^{-2i w_d t}
@@ -242,14 +248,19 @@ std::vector<std::vector<Word>> words(const lr_paper_params& p, const Derived& D)
   const double sk = sqrt(p.kappa);
   w1(L1, sk * D.s23, chan(0, 0), LM);
   w1(L1, sk * D.s24, chan(0, 0), UM);
-  w1(L1, sk * D.s21, chan(0, 2), UP);
-  w1(L1, sk * D.s22, chan(0, 2), LP);
+  if (!rwa) {
+    w1(L1, sk * D.s21, chan(0, 2), UP);
+    w1(L1, sk * D.s22, chan(0, 2), LP);
+  }
   w1(L2, sqrt(p.gamma), chan(0, 0), BL);
-  // readout: the filter field f in the frame of the drive, e^{i w_d t} times the lab-frame f
+  // readout: the filter field f in the frame of the drive, e^{i w_d t} times the
+  // lab-frame f (RWA: its slow part)
   w1(R, D.s23, chan(0, 0), LM);
   w1(R, D.s24, chan(0, 0), UM);
-  w1(R, D.s21, chan(0, 2), UP);
-  w1(R, D.s22, chan(0, 2), LP);
+  if (!rwa) {
+    w1(R, D.s21, chan(0, 2), UP);
+    w1(R, D.s22, chan(0, 2), LP);
+  }
   return {A, L1, L2, R};
 }
 
@@ -267,6 +278,7 @@ bool params_ok(const lr_paper_params* p) {
   const double v[] = {p->Ec, p->Ej, p->wr, p->wf, p->g, p->J, p->kappa, p->gamma, p->wd};
   for (double x : v)
     if (!isfinite(x)) return false;
+  if (p->frame != 0 && p->frame != 1) return false;
   return p->Ec > 0.0 && p->Ej > 0.0 && p->wr > 0.0 && p->wf > 0.0 && p->kappa >= 0.0 && p->gamma >= 0.0;
 }
 

@@ -39,7 +39,7 @@ EXPORTS = (
     "lr_paper_model_size", "lr_paper_model_build", "lr_sparse_create", "lr_sparse_workspace_size",
     "lr_sparse_bind_workspace", "lr_sparse_set_initial", "lr_sparse_set_state", "lr_sparse_get_state",
     "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_loss", "lr_sparse_last_error",
-    "lr_sparse_destroy", "lr_grow_rank",
+    "lr_sparse_destroy", "lr_grow_rank", "lr_measure_peak",
 )
 
 
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_sparse_observables.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.lr_sparse_loss.argtypes = [vp, d, d, d, vp, vp, vp, vp]
     lib.lr_grow_rank.argtypes = [vp, vp, C.c_uint64, d, vp]
+    lib.lr_measure_peak.argtypes = [i, C.POINTER(d), C.POINTER(d), vp]
     lib.lr_sparse_last_error.argtypes = [vp]
     lib.lr_sparse_last_error.restype = C.c_char_p
     lib.lr_sparse_destroy.argtypes = [vp]
@@ -161,6 +162,19 @@ def make_pulse(kind: int, params: Sequence[float]) -> lr_pulse:
     for k, v in enumerate(params):
         q.p[k] = float(v)
     return q
+
+
+PEAK_KIND = {"fp32_fma": 0, "fp64_fma": 1, "tf32_mma": 2}
+
+
+def measure_peak(kind: str, stream=None):
+    """(flop/s, seconds) of the arithmetic-pipe microbenchmark lr_measure_peak."""
+    lib = load_library()
+    f, sec = C.c_double(), C.c_double()
+    st = lib.lr_measure_peak(PEAK_KIND[kind], C.byref(f), C.byref(sec), C.c_void_p(_stream_ptr(stream)))
+    if st != 0:
+        raise LrError(st, "lr_measure_peak(%s)" % kind)
+    return f.value, sec.value
 
 
 def integrate_plain_noalloc(model, M, pulse, tau, Z, beta, dt, step0, n_steps, stream=None):

@@ -25,7 +25,10 @@ class lr_paper_params(C.Structure):
     _fields_ = [("Nl", C.c_int), ("Nu", C.c_int), ("Nt", C.c_int), ("n_cut", C.c_int),
                 ("Ec", C.c_double), ("Ej", C.c_double), ("wr", C.c_double), ("wf", C.c_double),
                 ("g", C.c_double), ("J", C.c_double), ("kappa", C.c_double), ("gamma", C.c_double),
-                ("wd", C.c_double)]
+                ("wd", C.c_double), ("frame", C.c_int)]
+
+
+FRAME = {"rot": 0, "rwa": 1}
 
 
 class lr_sparse_model(C.Structure):
@@ -39,17 +42,19 @@ def _ptr(a: np.ndarray) -> C.c_void_p:
 
 
 def paper_model(Nl: int, Nu: int, Nt: int, Ec: float, Ej: float, wr: float, wf: float, g: float,
-                J: float, kappa: float, gamma: float, wd: float, n_cut: int = 20) -> dict:
-    """Operator set of the paper's model built by the library (host code)."""
+                J: float, kappa: float, gamma: float, wd: float, n_cut: int = 20, frame: str = "rot") -> dict:
+    """Operator set of the paper's model built by the library (host code).
+    frame "rot": Eq. S(hamiltonian_rotated) with its counter-rotating terms;
+    "rwa": the rotating-wave approximation, Eq. S(hamiltonian_rwa)."""
     lib = load_library()
     p = lr_paper_params(int(Nl), int(Nu), int(Nt), int(n_cut), float(Ec), float(Ej), float(wr), float(wf),
-                        float(g), float(J), float(kappa), float(gamma), float(wd))
+                        float(g), float(J), float(kappa), float(gamma), float(wd), FRAME[frame])
     N, nnz = C.c_int(), C.c_long()
     st = lib.lr_paper_model_size(C.byref(p), C.byref(N), C.byref(nnz))
     if st != 0:
         raise LrError(st, "lr_paper_model_size")
     n, z = N.value, nnz.value
-    out = dict(N=n, nnz=z, n_jumps=N_JUMPS_PAPER, n_levels=int(Nt), wd=float(wd), dims=(Nl, Nu, Nt),
+    out = dict(N=n, nnz=z, n_jumps=N_JUMPS_PAPER, n_levels=int(Nt), wd=float(wd), dims=(Nl, Nu, Nt), frame=frame,
                rowptr=np.zeros(4 * (n + 1), np.int32), col=np.zeros(z, np.int32), val=np.zeros(2 * z),
                chan=np.zeros(z, np.uint8), level=np.zeros(n, np.int32), derived=np.zeros(16))
     st = lib.lr_paper_model_build(C.byref(p), _ptr(out["rowptr"]), _ptr(out["col"]), _ptr(out["val"]),

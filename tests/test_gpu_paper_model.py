@@ -28,11 +28,12 @@ TOL = {"fp64": dict(beta=1e-10, pops=1e-10, nphot=1e-10, trace=1e-11),
        "fp32_g64": dict(beta=5e-5, pops=5e-5, nphot=5e-5, trace=2e-5)}
 
 
-def _run(dims, M, pulses, tau, dt, n_steps, pop_every, check_traj, params, split=None, precision="fp64"):
+def _run(dims, M, pulses, tau, dt, n_steps, pop_every, check_traj, params, split=None, precision="fp64",
+         frame="rot"):
     import torch
     from paper_2508_18114_gb300 import sparse
     Nl, Nu, Nt = dims
-    model = sparse.paper_model(Nl, Nu, Nt, **params)
+    model = sparse.paper_model(Nl, Nu, Nt, frame=frame, **params)
     T = len(pulses)
     psi = [i % 2 for i in range(T)]          # |0_l, 0_u, g> and |0_l, 0_u, e>
     b = sparse.SparseBatch(model, M, pulses, tau, n_steps, pop_every=pop_every, precision=precision)
@@ -44,7 +45,7 @@ def _run(dims, M, pulses, tau, dt, n_steps, pop_every, check_traj, params, split
         b.integrate(dt, n_steps)
     got = b.observables()
     torch.cuda.synchronize()
-    ora_model = pm.PaperModel(Nl, Nu, Nt, frame="rot", **params)
+    ora_model = pm.PaperModel(Nl, Nu, Nt, frame=frame, **params)
     for tj in check_traj:
         kind, p = pulses[tj]
         env = lambda t, kind=kind, p=p: opulse.envelope(kind, p, t, tau)  # noqa: E731
@@ -69,6 +70,19 @@ def test_small_model_parity(precision):
     pulses = [pulses[0], pulses[0], pulses[1], pulses[1]]
     got = _run((6, 3, 4), 4, pulses, tau, 5e-4, 800, 100, [0, 1, 3], P, precision=precision)
     assert np.abs(got["beta"][0]).max() > 1e-2           # the drive does displace the readout mode
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_g64"])
+def test_rwa_model_parity(precision):
+    """The rotating-wave approximation of Eq. S(hamiltonian_rwa) on the same
+    engine: N = 72 (6 x 3 x 4), M = 4, at a 5x larger step (2.5 ps) than the
+    rotated-frame runs, two candidates x {g, e}."""
+    P = _params(g=TP * 0.3, kappa=1.0, gamma=0.05)
+    wd = P["wd"]
+    tau = 2.0
+    pulses = [(0, [TP * 1.0, wd, 0.25, 0.0])] * 2 + [(0, [TP * 0.6, wd, 0.4, 0.0])] * 2
+    got = _run((6, 3, 4), 4, pulses, tau, 2.5e-3, 800, 100, [0, 1, 3], P, precision=precision, frame="rwa")
+    assert np.abs(got["beta"][0]).max() > 1e-2
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_g64"])

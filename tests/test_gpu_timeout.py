@@ -46,5 +46,6 @@ def test_wait_budget_runs_out_and_is_reported(monkeypatch):
     b.sync()
     got = b.observables()
     b.close()
-    assert np.array_equal(got["beta"], want["beta"])
-    assert np.array_equal(got["pops"], want["pops"])
+    # entries up to the current step (20 steps, records every 10) are the meaningful ones
+    assert np.array_equal(got["beta"][:, :21], want["beta"][:, :21])
+    assert np.array_equal(got["pops"][:, :3], want["pops"][:, :3])

@@ -210,3 +210,47 @@ def test_heff_channels_follow_the_jump_phases():
     got = T[pm.channel_index(0, 2)].toarray()[dst, 0]
     assert abs(got - (-0.5 * rot.kappa * s23 * s22 * np.sqrt(2.0))) < 1e-12
     assert abs(s22) > 1e-4                            # the counter-rotating part is not zero
+
+
+def test_rwa_operators_are_the_period_average_of_the_rotated_ones():
+    """Eq. S(hamiltonian_rwa) drops the explicitly time-dependent terms of Eq.
+    S(hamiltonian_rotated): at a fixed envelope, H_rwa is the average of
+    H_rot(t) over one period pi / w_d of the e^{+-2i w_d t} factors, and the RWA
+    jump operator and readout are the averages of L_1(t) and r(t). The average
+    is taken by the trapezoid rule on 16 equal steps (exact for trigonometric
+    polynomials of degree < 16)."""
+    rot, rwa = _small("rot"), _small("rwa")
+    T = np.pi / rot.wd
+    ts = 0.37 + T * np.arange(16) / 16.0
+    for om in (0.0, 1.3):
+        Hbar = sum(rot.hamiltonian(t, om) for t in ts) / 16.0
+        assert np.abs((Hbar - rwa.hamiltonian(0.37, om)).toarray()).max() < 1e-12
+        Lbar = sum(rot.jumps(t, om)[0] for t in ts) / 16.0
+        assert np.abs((Lbar - rwa.jumps(0.37, om)[0]).toarray()).max() < 1e-12
+        Rbar = sum(rot.readout(t, om) for t in ts) / 16.0
+        assert np.abs((Rbar - rwa.readout(0.37, om)).toarray()).max() < 1e-12
+    # the RWA generator is static in time at fixed envelope; the rotated one is not
+    assert np.abs((rwa.hamiltonian(0.1, 1.0) - rwa.hamiltonian(0.9, 1.0)).toarray()).max() == 0.0
+    assert np.abs((rot.hamiltonian(0.1, 1.0) - rot.hamiltonian(0.13, 1.0)).toarray()).max() > 1e-3
+    # and -i H_eff keeps only the slow part of L_1^dag L_1
+    assert all(k in (pm.channel_index(0, 0), pm.channel_index(1, 0)) for k in rwa.heff_terms())
+
+
+def test_rwa_tracks_the_rotated_frame():
+    """With g, Omega << w_d the RWA dynamics follows the rotated-frame dynamics
+    up to corrections of order (g, Omega) / w_d: populations and |beta| of a
+    resonantly driven run agree to a few percent, and differ (the dropped terms
+    are not zero)."""
+    rot, rwa = _small("rot", g=TP * 0.05), _small("rwa", g=TP * 0.05)
+    env = lambda t: TP * 0.2 * min(1.0, t / 0.5)  # noqa: E731
+    psi = np.zeros(rot.N, dtype=complex)
+    psi[1] = 1.0
+    rho0 = np.outer(psi, psi.conj())
+    dt, n = 2.5e-4, 8000
+    a = pm.integrate(rho0, rot, env, dt, n, pop_every=400, low_rank=False)
+    b = pm.integrate(rho0, rwa, env, dt, n, pop_every=400, low_rank=False)
+    bs = np.abs(a["beta"]).max()
+    assert bs > 1e-2
+    d = np.abs(a["beta"] - b["beta"]).max() / bs
+    assert 1e-4 < d < 0.1, d
+    assert np.abs(a["pops"] - b["pops"]).max() < 0.02

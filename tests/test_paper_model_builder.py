@@ -49,18 +49,19 @@ def _close(got, want, scale):
         assert np.abs(g - w).max() <= 1e-11 * scale, k
 
 
+@pytest.mark.parametrize("frame", ["rot", "rwa"])
 @pytest.mark.parametrize("dims,over", [
     ((6, 3, 4), {}),
     ((5, 4, 6), dict(g=TP * 0.4, J=TP * 0.2, kappa=2.0, gamma=0.3)),
     ((3, 2, 3), dict(wr=TP * 5.0, wf=TP * 6.5)),
 ])
-def test_builder_matches_oracle(sparse_mod, dims, over):
+def test_builder_matches_oracle(sparse_mod, dims, over, frame):
     P = dict(Ec=TP * 0.315, Ej=51 * TP * 0.315, wr=TP * 7.2, wf=TP * 7.21, g=TP * 0.15, J=TP * 0.03,
              kappa=TP * 0.03, gamma=TP * 8e-6, wd=TP * 7.18)
     P.update(over)
     Nl, Nu, Nt = dims
-    m = sparse_mod.paper_model(Nl, Nu, Nt, **P)
-    ora = pm.PaperModel(Nl, Nu, Nt, frame="rot", **P)
+    m = sparse_mod.paper_model(Nl, Nu, Nt, frame=frame, **P)
+    ora = pm.PaperModel(Nl, Nu, Nt, frame=frame, **P)
     assert m["N"] == ora.N
     ops = _ops(m)
     scale = max(abs(P["wd"]) * Nt, 1.0)
