@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=None, help="RK4 steps of the oracle sample")
     ap.add_argument("--no-plain-baseline", action="store_true")
+    ap.add_argument("--no-full-pulse", action="store_true", help="skip the full-pulse error check against the oracle")
     ap.add_argument("--plain-steps", type=int, default=8, help="RK4 steps timed on the plain FP64 engine")
     ap.add_argument("--no-graph", action="store_true", help="time direct lr_integrate calls instead of graph replays")
     ap.add_argument("--frame", default="lab", choices=["lab", "rwa"],
@@ -71,6 +72,7 @@ def parse():
     ap.add_argument("--dt", type=float, default=None, help="RK4 step [ns] (default: the workload's; 2.5e-3 with rwa)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the gradient (lr_backward) of a pulse slice of --chunk steps instead")
+    ap.add_argument("--ckpt", type=int, default=None, help="adjoint checkpoint spacing (default: --chunk)")
     return ap.parse_args()
 
 
@@ -218,6 +220,52 @@ def oracle_sample(wl, n_steps, candidates=(0,)):
     dt = time.perf_counter() - t0
     ntraj = 2 * len(candidates)
     return ntraj * n_steps / dt, dt, ntraj
+
+
+def full_pulse_error(wl, info, dev):
+    """Errors of the timed launch plan over the whole pulse against the FP64
+    oracle's full-pulse values (tests/golden/full_pulse_c4.txt, written by the
+    oracle-only script beside it): the golden candidates of this workload run
+    alone in the same plan (the per-trajectory arithmetic of a plan does not
+    depend on the other trajectories of the launch) for all tau / dt steps."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from golden import full_pulse
+    if not full_pulse.available("c4"):
+        return None
+    from paper_2508_18114_gb300 import LowRankBatch
+    gold = full_pulse.load("c4")
+    cands = sorted(gold["cands"])
+    sub = [wl.candidates[c] for c in cands]
+    saved = {k: os.environ.get(k) for k in ("LR_FUSED_C", "LR_FUSED_ZS", "LR_FUSED_TC")}
+    os.environ.update({"LR_FUSED_C": str(info.team_size), "LR_FUSED_ZS": "smem" if info.stage_in_smem else "global",
+                       "LR_FUSED_TC": str(info.tensor_passes)})
+    try:
+        b = LowRankBatch([c.model for c in sub], [c.M for c in sub], precision="fp32_g64", engine="fused",
+                         max_steps=wl.n_steps, pop_every=gold["rec_every"], eta=wl.eta, device=dev)
+        q = b.query()
+        b.set_pulse([(c.pulse.kind, c.pulse.p) for c in sub], wl.tau)
+        b.set_initial(wl.init_seed, wl.eps)
+        t0 = time.perf_counter()
+        b.integrate(wl.dt, wl.n_steps)
+        obs = b.observables()
+        ion, _ = b.loss()
+        sec = time.perf_counter() - t0
+        b.close()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    obs["pop_every"] = gold["rec_every"]
+    e = full_pulse.errors(gold, obs, cands, eps_a=obs["eps_a"], ion=ion)
+    e.update({"sample": "candidates %s of this workload, g and e, all %d RK4 steps (tau = %g ns), plan: team %d, "
+                        "stage state %s, tensor passes %d (%.1f s)"
+                        % (cands, wl.n_steps, wl.tau, q.team_size, "shared memory" if q.stage_in_smem else "L2",
+                           q.tensor_passes, sec),
+              "eps_a": [float(x) for x in obs["eps_a"]],
+              "eps_a_oracle": [gold["cands"][c]["eps_a"] for c in cands]})
+    return e
 
 
 def default_cpu_steps(wl):
@@ -437,6 +485,9 @@ def run_ours(args):
 
     cpu = None
     err = None
+    full = None
+    if rank == 0 and not args.no_full_pulse and wl.name == "c4" and prec == "fp32_g64" and engine == "fused":
+        full = full_pulse_error(wl, info, dev)
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import parallel
         ns = args.cpu_steps or default_cpu_steps(wl)
@@ -479,7 +530,7 @@ def run_ours(args):
             "pulse_evals_per_s": value / (2 * spp),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "peaks_source": peak_src,
-            "plain_fp64_baseline": plain, "error_vs_oracle": err,
+            "plain_fp64_baseline": plain, "error_vs_oracle": err, "error_vs_oracle_full_pulse": full,
         }
         print(json.dumps(line))
     b.close()
@@ -507,18 +558,23 @@ def run_adjoint(args):
         b.integrate(wl.dt, chunk)
         b.sync()
         t0 = time.perf_counter()
-        g = b.backward(np.ones(len(cands)), chunk)
+        g = b.backward(np.ones(len(cands)), args.ckpt or chunk)
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     tt = sum(times)
     value = b.n_traj * chunk * args.steps / tt
     desc = workload_desc(wl, prec)
+    ck = args.ckpt or chunk
     desc.update({"chunk_rk4_steps": chunk, "engine_forward": lrmod.ENGINE_NAME[b.query().engine],
-                 "adjoint": "lr_backward, FP64 plain-kernel recomputation, checkpoint every chunk"})
+                 "adjoint": "lr_backward, plain-kernel recomputation per checkpoint segment (%d steps), %s"
+                            % (ck, "FP64" if prec == "fp64" else
+                               "FP32 bulk with the Gram matrix summed in FP64 from exact products, FP64 "
+                               "Cholesky/G^-1/solves, FP64 signal and gradient sums")})
     print(json.dumps({"metric": "adjoint_traj_steps_per_s", "value": value, "unit": "traj*steps/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
-                      "higher_is_better": True, "dtype": "f64", "config": desc,
+                      "higher_is_better": True, "dtype": "f64" if prec == "fp64" else "f32 bulk (f64 Gram/solves)",
+                      "config": desc,
                       "grad_evals_per_s": value / (2 * desc["steps_per_pulse"]),
                       "grad_norm": float(np.abs(g).max())}))
     b.close()

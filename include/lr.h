@@ -505,8 +505,60 @@ lr_status lr_sparse_observables(lr_sparse* s, double* beta, double* pops, double
  * LR_ERR_ARG for an odd n_traj; LR_ERR_STATE before the first step. Sync. */
 lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, double gamma, double* eps_a, double* ion,
                          double* loss, void* stream);
+/* Which integrator the context runs (host only): *fused = 1 for the fused
+ * persistent kernel (FP32_G64 contexts by default: one launch per
+ * lr_sparse_integrate, one CTA per trajectory, the stage input, the operator
+ * images and the RK4 accumulator in a per-CTA L2-resident region, the Gram
+ * matrix in double-word FP32 and its LDL^dag factorisation, L^-1 and G^-1 in
+ * double-word FP32), 0 for the four launches per RK4 stage described at
+ * lr_sparse_create (FP64 contexts, or FP32_G64 with the environment variable
+ * LR_SPARSE_FUSED=0 at lr_sparse_create). */
+lr_status lr_sparse_query(const lr_sparse* s, int* fused);
 const char* lr_sparse_last_error(const lr_sparse* s);
 void lr_sparse_destroy(lr_sparse* s);
+
+/* ======================================================================
+ * The full master equation on the device (FP64), the reference that the
+ * low-rank runs of a model are compared with (Fig. 2) and timed against
+ * (Table 1): the N x N density matrix under Eq. 2 / Eq. S4,
+ *     d rho / dt = A rho + (A rho)^dag + sum_k L_k rho L_k^dag,
+ * A = -i H_eff, for one trajectory of an operator set in the lr_sparse_model
+ * layout (the paper's model from lr_paper_model_build, either frame), with the
+ * classical RK4 scheme of the low-rank engines. Per RK4 stage: the operator
+ * values at the stage time, B = A rho and Y_k = L_k rho (CSR row gathers, one
+ * thread per element), B^dag and Y_k^dag (tiled transposes), and the update
+ * F = B + B^dag + sum_k L_k Y_k^dag with the RK4 stage. Observables at the
+ * start of every step: beta = tr(rho r(t)); at recording steps the level
+ * populations, the photon number tr(r rho r^dag) and tr rho.
+ * Memory: (5 + 2K) N^2 complex128 in the caller's workspace (576 MB at
+ * N = 2000, K = 2), N <= 16384.
+ * ====================================================================== */
+typedef struct lr_full lr_full;
+/* Context for one trajectory driven by `pulse` (kinds as lr_pulse, phase 0 and
+ * w_d = model->wd as for lr_sparse_create); tau places the falling edge;
+ * max_steps and pop_every size the records. Copies the operator arrays. Host only. */
+lr_status lr_full_create(const lr_sparse_model* model, const lr_pulse* pulse, double tau, long max_steps,
+                         int pop_every, lr_full** out);
+lr_status lr_full_workspace_size(const lr_full* f, size_t* bytes);
+/* Binds a caller-owned device buffer (>= lr_full_workspace_size, 256-byte
+ * aligned) and uploads the operators (sync on `stream`). */
+lr_status lr_full_bind_workspace(lr_full* f, void* workspace, size_t bytes, void* stream);
+/* rho = |psi><psi| (a basis index), step counter reset. Async. */
+lr_status lr_full_set_initial(lr_full* f, int psi, void* stream);
+/* Host rho [N][N] complex128 (interleaved re, im) -> device; step counter set. Sync. */
+lr_status lr_full_set_state(lr_full* f, const double* rho, long step, void* stream);
+/* Device rho -> host [N][N] complex128. Sync. */
+lr_status lr_full_get_state(const lr_full* f, double* rho, void* stream);
+/* n_steps RK4 steps of size dt from the current step, recording beta at every
+ * step and the other observables every pop_every steps. LR_ERR_STATE past
+ * max_steps; LR_ERR_ARG for a dt other than the run's. Async. */
+lr_status lr_full_integrate(lr_full* f, double dt, long n_steps, void* stream);
+/* Records to host or device arrays (any may be NULL): beta [max_steps+1]
+ * complex128, pops [n_rec][n_levels], nphot and trace [n_rec]. Syncs and
+ * returns the device error status (LR_ERR_NONFINITE). */
+lr_status lr_full_observables(lr_full* f, double* beta, double* pops, double* nphot, double* trace, void* stream);
+const char* lr_full_last_error(const lr_full* f);
+void lr_full_destroy(lr_full* f);
 
 #ifdef __cplusplus
 }

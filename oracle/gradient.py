@@ -37,17 +37,31 @@ def run_candidate(wl, cand_index: int, n_steps=None, pop_every=1, theta=None,
     return res
 
 
-def fd_gradient(wl, cand_index: int, n_steps=None, rel=1e-4):
+def _eps_at(args):
+    wl, cand_index, n_steps, theta = args
+    return run_candidate(wl, cand_index, n_steps, theta=theta)["eps_a"]
+
+
+def fd_gradient(wl, cand_index: int, n_steps=None, rel=1e-4, pool_map=None):
+    """Central differences (eps_a(theta + h_i e_i) - eps_a(theta - h_i e_i)) / (2 h_i).
+    pool_map (optional, e.g. a process pool's map) evaluates the 2 n runs; by
+    default they run here, one after the other."""
     cand = wl.candidates[cand_index]
-    mdl = Model.from_params(cand.model)
     theta = np.array(cand.pulse.p, dtype=float)
     grad = np.zeros_like(theta)
+    hs, points = [], []
     for i in range(theta.size):
         h = rel * abs(theta[i]) if theta[i] != 0.0 else rel
         tp, tm = theta.copy(), theta.copy()
         tp[i] += h
         tm[i] -= h
-        ep = run_candidate(wl, cand_index, n_steps, theta=tp, model=mdl)["eps_a"]
-        em = run_candidate(wl, cand_index, n_steps, theta=tm, model=mdl)["eps_a"]
-        grad[i] = (ep - em) / (2.0 * h)
+        hs.append(h)
+        points += [tp, tm]
+    if pool_map is None:
+        mdl = Model.from_params(cand.model)
+        vals = [run_candidate(wl, cand_index, n_steps, theta=t, model=mdl)["eps_a"] for t in points]
+    else:
+        vals = list(pool_map(_eps_at, [(wl, cand_index, n_steps, tuple(t)) for t in points]))
+    for i in range(theta.size):
+        grad[i] = (vals[2 * i] - vals[2 * i + 1]) / (2.0 * hs[i])
     return grad

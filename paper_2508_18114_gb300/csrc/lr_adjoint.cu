@@ -27,8 +27,17 @@
 // The pulse enters only through c(t) (r + r^dag): theta_bar_i +=
 // Im tr(Fbar^dag (r + r^dag) U) dc/dtheta_i at the stage time.
 //
-// The forward recomputation uses the plain FP64 kernels; states are stored
+// The forward recomputation uses the plain engine's kernels; states are stored
 // every `ckpt_every` steps and each segment is recomputed step by step.
+//
+// Precision follows the context. FP64 context: everything in complex128 /
+// FP64. FP32-bulk context: the states, stage inputs, cotangents and every
+// per-element product (operator apply, projection terms, the VJP rows, the
+// partial sums of (l_k U)^dag Fbar and T_k) in complex64 / FP32; the Gram
+// matrix summed in FP64 from exact products of the FP32 entries; the Cholesky
+// factor, G^-1, X_k', E_k', P_k' (M x M) in FP64 (rounded once to FP32 for the
+// per-element kernels); the readout signal, the trapezoid weights and the
+// pulse-parameter gradient accumulated in FP64.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -52,6 +61,8 @@ struct Ptrs {
   double2* Xs;      // [4][n_traj][2][MR2]  X_k' of each stage (row-major M x M)
   double2* Gi;      // [4][n_traj][MR2]     G^-1 of each stage
   double2* EP;      // [n_traj][4][MR2]     E_r', E_b', P_r', P_b'
+  float2* Xs32;     // FP32-bulk adjoint: FP32 copies of Xs and EP (else null)
+  float2* EP32;
   const double* part;
   double* bpart;
   double* thbar;    // [n_traj][8]
@@ -148,45 +159,65 @@ __global__ void __launch_bounds__(AT) adj_factor(Ptrs a, int stage) {
   __syncthreads();
   // X_k' = G^-1 T_k
   double2* X = a.Xs + (((size_t)stage * a.n_traj + tj) * 2) * MR2;
+  float2* X32 = a.Xs32 ? a.Xs32 + (((size_t)stage * a.n_traj + tj) * 2) * MR2 : nullptr;
   for (int e = tid; e < 2 * MM; e += AT) {
     const int k = e / MM, ij = e - k * MM, i = ij / M, j = ij - (ij / M) * M;
     double2 s = mk(0.0, 0.0);
     for (int l = 0; l < M; ++l) s = cadd(s, cmul(Gi[i * M + l], T[k][l][j]));
     X[k * MR2 + ij] = s;
+    if (X32) X32[k * MR2 + ij] = make_float2((float)s.x, (float)s.y);
   }
 }
 
 // Partial sums of B_k' = (l_k U)^dag Fbar and w = tr(Fbar^dag (r + r^dag) U) per row block.
-// Fbar = ca lam + cb Un (cb == 0: Un unused).
-__global__ void __launch_bounds__(AT) adj_bpart(Ptrs a, const double2* __restrict__ U, const double2* __restrict__ lam,
-                                                const double2* __restrict__ Un, double ca, double cb) {
+// Fbar = ca lam + cb Un (cb == 0: Un unused). B_k' in the bulk arithmetic, w in FP64.
+template <typename T2>
+__global__ void __launch_bounds__(AT) adj_bpart(Ptrs a, const T2* __restrict__ U, const T2* __restrict__ lam,
+                                                const T2* __restrict__ Un, double ca_d, double cb_d) {
+  using T = typename real_of<T2>::type;
   const TrajDev d = a.traj[blockIdx.y];
   const int b = blockIdx.x;
   if (b >= d.nblk) return;
-  __shared__ double2 sF[AR][LR_MAX_RANK], sR[AR][LR_MAX_RANK], sB[AR][LR_MAX_RANK];
+  __shared__ T2 sF[AR][LR_MAX_RANK], sR[AR][LR_MAX_RANK], sB[AR][LR_MAX_RANK];
   __shared__ double2 wpart[AT];
   const int M = d.M, ld = d.ld, r0 = b * AR, rows = min(AR, d.N - r0);
   const size_t off = d.z_off;
   const int st = d.Nr * d.Nf;
+  const T ca = (T)ca_d, cb = (T)cb_d;
   double2 wsum = mk(0.0, 0.0);
   for (int e = threadIdx.x; e < AR * M; e += AT) {
     const int i = e / M, m = e - (e / M) * M;
-    double2 f = mk(0, 0), zr = mk(0, 0), zb = mk(0, 0);
+    T2 f = mkc<T2>(0, 0), zr = mkc<T2>(0, 0), zb = mkc<T2>(0, 0);
     if (i < rows) {
       const int n = r0 + i;
       const size_t o = off + (size_t)n * ld + m;
-      f = cscale(ca, lam[o]);
-      if (cb != 0.0) f = cadd(f, cscale(cb, Un[o]));
+      const T2 l0 = lam[o];
+      f = mkc<T2>(ca * l0.x, ca * l0.y);
+      if (cb_d != 0.0) {
+        const T2 u0 = Un[o];
+        f = mkc<T2>(f.x + cb * u0.x, f.y + cb * u0.y);
+      }
       const RowIdx ri = row_index(d, n);
       const int iro = readout_index(d, ri), dro = readout_dim(d);
-      double2 xd = mk(0, 0);
+      T2 xd = mkc<T2>(0, 0);
       if (iro + 1 < dro) {
-        zr = cscale(sqrt(iro + 1.0), U[o + ld]);
+        const T c = (T)sqrt(iro + 1.0);
+        const T2 v = U[o + ld];
+        zr = mkc<T2>(c * v.x, c * v.y);
         xd = zr;
       }
-      if (iro >= 1) xd = cadd(xd, cscale(sqrt((double)iro), U[o - ld]));
-      if (ri.it + 1 < d.Nt) zb = cscale(sqrt(ri.it + 1.0), U[o + (size_t)st * ld]);
-      wsum = cadd(wsum, cmulc(f, xd));
+      if (iro >= 1) {
+        const T c = (T)sqrt((double)iro);
+        const T2 v = U[o - ld];
+        xd = mkc<T2>(xd.x + c * v.x, xd.y + c * v.y);
+      }
+      if (ri.it + 1 < d.Nt) {
+        const T c = (T)sqrt(ri.it + 1.0);
+        const T2 v = U[o + (size_t)st * ld];
+        zb = mkc<T2>(c * v.x, c * v.y);
+      }
+      // conj(f) xd, summed in FP64
+      wsum = cadd(wsum, cmulc(mk((double)f.x, (double)f.y), mk((double)xd.x, (double)xd.y)));
     }
     sF[i][m] = f;
     sR[i][m] = zr;
@@ -198,10 +229,14 @@ __global__ void __launch_bounds__(AT) adj_bpart(Ptrs a, const double2* __restric
   const int MM = M * M;
   for (int e = threadIdx.x; e < 2 * MM; e += AT) {
     const int k = e / MM, ij = e - k * MM, i = ij / M, j = ij - (ij / M) * M;
-    double2 s = mk(0.0, 0.0);
-    for (int r = 0; r < rows; ++r) s = cadd(s, cmulc(k == 0 ? sR[r][i] : sB[r][i], sF[r][j]));
-    out[2 * e] = s.x;
-    out[2 * e + 1] = s.y;
+    T re = 0, im = 0;
+    for (int r = 0; r < rows; ++r) {
+      const T2 x = k == 0 ? sR[r][i] : sB[r][i], y = sF[r][j];   // conj(x) y
+      re = fma(x.x, y.x, fma(x.y, y.y, re));
+      im = fma(x.x, y.y, fma(-x.y, y.x, im));
+    }
+    out[2 * e] = (double)re;
+    out[2 * e + 1] = (double)im;
   }
   if (threadIdx.x == 0) {
     double2 w = mk(0.0, 0.0);
@@ -255,18 +290,28 @@ __global__ void __launch_bounds__(AT) adj_bsolve(Ptrs a, int stage, double t_sta
   }
   __syncthreads();
   double2* EP = a.EP + (size_t)tj * 4 * MR2;
+  float2* EP32 = a.EP32 ? a.EP32 + (size_t)tj * 4 * MR2 : nullptr;
   for (int e = tid; e < 2 * MM; e += AT) {
     const int k = e / MM, ij = e - k * MM, i = ij / M, j = ij - (ij / M) * M;
-    EP[k * MR2 + ij] = E[k][i][j];
+    const double2 ev = E[k][i][j];
+    EP[k * MR2 + ij] = ev;
     const double2 p = XE[k][i][j], q = XE[k][j][i];
-    EP[(2 + k) * MR2 + ij] = mk(p.x + q.x, p.y - q.y);
+    const double2 pv = mk(p.x + q.x, p.y - q.y);
+    EP[(2 + k) * MR2 + ij] = pv;
+    if (EP32) {
+      EP32[k * MR2 + ij] = make_float2((float)ev.x, (float)ev.y);
+      EP32[(2 + k) * MR2 + ij] = make_float2((float)pv.x, (float)pv.y);
+    }
   }
 }
 
 // Ubar_s per element (n, m) for the cotangent Fbar = ca lam + cb Un.
-__global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict__ U, const double2* __restrict__ lam,
-                                              const double2* __restrict__ Un, double ca, double cb, double t_stage,
-                                              double2* __restrict__ Ub) {
+template <typename T2>
+__global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const T2* __restrict__ U, const T2* __restrict__ lam,
+                                              const T2* __restrict__ Un, double ca_d, double cb_d, double t_stage,
+                                              T2* __restrict__ Ub) {
+  using T = typename real_of<T2>::type;
+  constexpr bool f32 = sizeof(T) == 4;
   const int tj = blockIdx.y;
   const TrajDev d = a.traj[tj];
   const int M = d.M, ld = d.ld;
@@ -275,23 +320,44 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict_
   __shared__ double coef;
   if (threadIdx.x == 0) coef = pulse_coefficient(a.pulse[d.cand], a.tau, t_stage);
   __syncthreads();
-  const double2* EP = a.EP + (size_t)tj * 4 * MR2;
+  // M x M factors of this trajectory and stage (FP64, or their FP32 copies)
+  const T2* EP;
+  const T2* Xt;
+  if constexpr (f32) {
+    EP = a.EP32 + (size_t)tj * 4 * MR2;
+    Xt = a.Xs32 + (size_t)tj * 2 * MR2;    // a.Xs32 points at this stage's [traj][2][MR2]
+  } else {
+    EP = a.EP + (size_t)tj * 4 * MR2;
+    Xt = a.Xs + (size_t)tj * 2 * MR2;
+  }
+  const T ca = (T)ca_d, cb = (T)cb_d, cf = (T)coef;
   const long total = (long)d.N * M;
   auto F = [&](size_t o) {
-    double2 f = cscale(ca, lam[o]);
-    if (cb != 0.0) f = cadd(f, cscale(cb, Un[o]));
+    const T2 l0 = lam[o];
+    T2 f = mkc<T2>(ca * l0.x, ca * l0.y);
+    if (cb_d != 0.0) {
+      const T2 u0 = Un[o];
+      f = mkc<T2>(f.x + cb * u0.x, f.y + cb * u0.y);
+    }
     return f;
   };
+  auto cmul_t = [](T2 x, T2 y) { return mkc<T2>(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); };
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int n = (int)(idx / M), m = (int)(idx - (long)n * M);
     const RowIdx ri = row_index(d, n);
     double dre, dim_;
     heff_diag(d, ri, 0.0, dre, dim_);   // the adjoint runs in the lab frame
     const size_t o = off + (size_t)n * ld + m;
-    const double2 f0 = F(o);
+    const T2 f0 = F(o);
     // i H_eff^dag Fbar: diagonal i conj(h) = i dre + dim
-    double2 acc = mk(-dre * f0.y + dim_ * f0.x, dre * f0.x + dim_ * f0.y);
-    double hr = 0.0, hi = 0.0;   // sum of real off-diagonal H entries times Fbar
+    T2 acc;
+    if constexpr (f32) {
+      const T dh = (T)dre, dl = (T)(dre - (double)dh), di = (T)dim_;
+      acc = mkc<T2>(fma(-dh, f0.y, fma(-dl, f0.y, di * f0.x)), fma(dh, f0.x, fma(dl, f0.x, di * f0.y)));
+    } else {
+      acc = mkc<T2>(-dre * f0.y + dim_ * f0.x, dre * f0.x + dim_ * f0.y);
+    }
+    T hr = 0, hi = 0;   // sum of real off-diagonal H entries times Fbar
     for (int sa = -1; sa <= 1; sa += 2) {
       const int it2 = ri.it + sa;
       if (it2 < 0 || it2 >= d.Nt) continue;
@@ -299,8 +365,8 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict_
       for (int sb = -1; sb <= 1; sb += 2) {
         const int ir2 = ri.ir + sb;
         if (ir2 < 0 || ir2 >= d.Nr) continue;
-        const double w = d.g * ct * sqrt((double)max(ri.ir, ir2));
-        const double2 v = F(off + (size_t)(n + sa * st + sb * sr) * ld + m);
+        const T w = (T)(d.g * ct * sqrt((double)max(ri.ir, ir2)));
+        const T2 v = F(off + (size_t)(n + sa * st + sb * sr) * ld + m);
         hr += w * v.x;
         hi += w * v.y;
       }
@@ -313,8 +379,8 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict_
         for (int sb = -1; sb <= 1; sb += 2) {
           const int if2 = ri.iff + sb;
           if (if2 < 0 || if2 >= d.Nf) continue;
-          const double w = d.J * cr * sqrt((double)max(ri.iff, if2));
-          const double2 v = F(off + (size_t)(n + sa * sr + sb) * ld + m);
+          const T w = (T)(d.J * cr * sqrt((double)max(ri.iff, if2)));
+          const T2 v = F(off + (size_t)(n + sa * sr + sb) * ld + m);
           hr += w * v.x;
           hi += w * v.y;
         }
@@ -324,12 +390,12 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict_
     for (int sa = -1; sa <= 1; sa += 2) {
       const int i2 = iro + sa;
       if (i2 < 0 || i2 >= dro) continue;
-      const double w = coef * sqrt((double)max(iro, i2));
-      const double2 v = F(off + (size_t)(n + sa) * ld + m);
+      const T w = cf * (T)sqrt((double)max(iro, i2));
+      const T2 v = F(off + (size_t)(n + sa) * ld + m);
       hr += w * v.x;
       hi += w * v.y;
     }
-    acc = cadd(acc, mk(-hi, hr));   // i * (H_off Fbar)
+    acc = mkc<T2>(acc.x - hi, acc.y + hr);   // i * (H_off Fbar)
     // projection terms, k = r (stride 1, readout index), k = b (stride st, transmon index)
     for (int k = 0; k < 2; ++k) {
       const double ak = k == 0 ? d.kappa : d.gamma;
@@ -337,43 +403,55 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const double2* __restrict_
       const int idx_k = k == 0 ? iro : ri.it;
       const int dim_k = k == 0 ? dro : d.Nt;
       const int s_k = k == 0 ? 1 : st;
-      const double2* Xk = a.Xs + (size_t)k * MR2;   // a.Xs points at this stage's [traj][2][MR2]
-      const double2* Ek = EP + (size_t)k * MR2;
-      const double2* Pk = EP + (size_t)(2 + k) * MR2;
-      double2 t = mk(0.0, 0.0);
+      const T2* Xk = Xt + (size_t)k * MR2;
+      const T2* Ek = EP + (size_t)k * MR2;
+      const T2* Pk = EP + (size_t)(2 + k) * MR2;
+      T2 t = mkc<T2>(0, 0);
       if (idx_k >= 1) {          // l_k^dag (Fbar X_k' + U E_k'^dag) at row n - s_k
         const size_t om = off + (size_t)(n - s_k) * ld;
-        double2 s1 = mk(0.0, 0.0);
+        T2 s1 = mkc<T2>(0, 0);
         for (int l = 0; l < M; ++l) {
-          s1 = cadd(s1, cmul(F(om + l), Xk[(size_t)tj * 2 * MR2 + l * M + m]));
-          const double2 e = Ek[m * M + l];
-          s1 = cadd(s1, cmul(U[om + l], mk(e.x, -e.y)));
+          const T2 p1 = cmul_t(F(om + l), Xk[l * M + m]);
+          const T2 e = Ek[m * M + l];
+          const T2 p2 = cmul_t(U[om + l], mkc<T2>(e.x, -e.y));
+          s1 = mkc<T2>(s1.x + p1.x + p2.x, s1.y + p1.y + p2.y);
         }
-        t = cadd(t, cscale(sqrt((double)idx_k), s1));
+        const T c = (T)sqrt((double)idx_k);
+        t = mkc<T2>(t.x + c * s1.x, t.y + c * s1.y);
       }
       if (idx_k + 1 < dim_k) {   // (l_k U) E_k'
         const size_t op = off + (size_t)(n + s_k) * ld;
-        double2 s2 = mk(0.0, 0.0);
-        for (int l = 0; l < M; ++l) s2 = cadd(s2, cmul(U[op + l], Ek[l * M + m]));
-        t = cadd(t, cscale(sqrt(idx_k + 1.0), s2));
+        T2 s2 = mkc<T2>(0, 0);
+        for (int l = 0; l < M; ++l) {
+          const T2 p = cmul_t(U[op + l], Ek[l * M + m]);
+          s2 = mkc<T2>(s2.x + p.x, s2.y + p.y);
+        }
+        const T c = (T)sqrt(idx_k + 1.0);
+        t = mkc<T2>(t.x + c * s2.x, t.y + c * s2.y);
       }
       {                          // - U P_k'
         const size_t on = off + (size_t)n * ld;
-        double2 s3 = mk(0.0, 0.0);
-        for (int l = 0; l < M; ++l) s3 = cadd(s3, cmul(U[on + l], Pk[l * M + m]));
-        t = mk(t.x - s3.x, t.y - s3.y);
+        T2 s3 = mkc<T2>(0, 0);
+        for (int l = 0; l < M; ++l) {
+          const T2 p = cmul_t(U[on + l], Pk[l * M + m]);
+          s3 = mkc<T2>(s3.x + p.x, s3.y + p.y);
+        }
+        t = mkc<T2>(t.x - s3.x, t.y - s3.y);
       }
-      acc = cadd(acc, cscale(0.5 * ak, t));
+      const T h = (T)(0.5 * ak);
+      acc = mkc<T2>(acc.x + h * t.x, acc.y + h * t.y);
     }
     Ub[o] = acc;
   }
 }
 
 // lam_new = lam + sum_s Ubar_s + conj(g) r Z + g r^dag Z (readout cotangent of step n).
-__global__ void __launch_bounds__(AT) adj_update(Ptrs a, const double2* __restrict__ Z, const double2* __restrict__ lam,
-                                                 const double2* __restrict__ U0, const double2* __restrict__ U1,
-                                                 const double2* __restrict__ U2, const double2* __restrict__ U3,
-                                                 double2* __restrict__ lam_new, long step, long S, int with_sum) {
+template <typename T2>
+__global__ void __launch_bounds__(AT) adj_update(Ptrs a, const T2* __restrict__ Z, const T2* __restrict__ lam,
+                                                 const T2* __restrict__ U0, const T2* __restrict__ U1,
+                                                 const T2* __restrict__ U2, const T2* __restrict__ U3,
+                                                 T2* __restrict__ lam_new, long step, long S, int with_sum) {
+  using T = typename real_of<T2>::type;
   const int tj = blockIdx.y;
   const TrajDev d = a.traj[tj];
   const int M = d.M, ld = d.ld;
@@ -384,17 +462,34 @@ __global__ void __launch_bounds__(AT) adj_update(Ptrs a, const double2* __restri
   const double w = (step == 0 || step == S) ? 0.5 : 1.0;
   const double sg = (tj & 1) ? 1.0 : -1.0;
   const double gs = sg * a.gcoef[c] * w;
-  const double2 g = mk(gs * (be.x - bg.x), gs * (be.y - bg.y));
+  const T gx = (T)(gs * (be.x - bg.x)), gy = (T)(gs * (be.y - bg.y));
   const long total = (long)d.N * M;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int n = (int)(idx / M), m = (int)(idx - (long)n * M);
     const size_t o = off + (size_t)n * ld + m;
-    double2 v = with_sum ? cadd(cadd(lam[o], cadd(U0[o], U1[o])), cadd(U2[o], U3[o])) : mk(0.0, 0.0);
+    T vx = 0, vy = 0;
+    if (with_sum) {
+      const T2 l0 = lam[o], a0 = U0[o], a1 = U1[o], a2 = U2[o], a3 = U3[o];
+      vx = l0.x + ((a0.x + a1.x) + (a2.x + a3.x));
+      vy = l0.y + ((a0.y + a1.y) + (a2.y + a3.y));
+    }
     const RowIdx ri = row_index(d, n);
     const int iro = readout_index(d, ri), dro = readout_dim(d);
-    if (iro + 1 < dro) v = cadd(v, cmulc(g, cscale(sqrt(iro + 1.0), Z[o + ld])));   // conj(g) r Z
-    if (iro >= 1) v = cadd(v, cmul(g, cscale(sqrt((double)iro), Z[o - ld])));        // g r^dag Z
-    lam_new[o] = v;
+    if (iro + 1 < dro) {   // conj(g) r Z
+      const T cc = (T)sqrt(iro + 1.0);
+      const T2 z = Z[o + ld];
+      const T zx = cc * z.x, zy = cc * z.y;
+      vx += gx * zx + gy * zy;
+      vy += gx * zy - gy * zx;
+    }
+    if (iro >= 1) {        // g r^dag Z
+      const T cc = (T)sqrt((double)iro);
+      const T2 z = Z[o - ld];
+      const T zx = cc * z.x, zy = cc * z.y;
+      vx += gx * zx - gy * zy;
+      vy += gx * zy + gy * zx;
+    }
+    lam_new[o] = mkc<T2>(vx, vy);
   }
 }
 
@@ -427,7 +522,7 @@ __global__ void adj_gcoef(Ptrs a, const double* __restrict__ deps, double eta, l
 
 // ------------------------------------------------------------------ driver
 
-BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t part_doubles, long S, int K) {
+BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t part_doubles, long S, int K, int fp32) {
   BwdLayout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -435,8 +530,9 @@ BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t p
     o = (o + bytes + 255) / 256 * 256;
     return at;
   };
-  const size_t T = sizeof(double2) * (size_t)tot;
+  const size_t T = (fp32 ? sizeof(float2) : sizeof(double2)) * (size_t)tot;
   L.K = K;
+  L.fp32 = fp32;
   L.n_seg = (S + K - 1) / K;
   L.ck = take(T * L.n_seg);
   L.seg = take(T * (K + 1));
@@ -453,6 +549,8 @@ BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t p
   L.Xs = take(sizeof(double2) * 4 * 2 * adj::MR2 * n_traj);
   L.Gi = take(sizeof(double2) * 4 * adj::MR2 * n_traj);
   L.EP = take(sizeof(double2) * 4 * adj::MR2 * n_traj);
+  L.Xs32 = fp32 ? take(sizeof(float2) * 4 * 2 * adj::MR2 * n_traj) : 0;
+  L.EP32 = fp32 ? take(sizeof(float2) * 4 * adj::MR2 * n_traj) : 0;
   L.bpart = take(sizeof(double) * part_doubles);
   L.beta = take(sizeof(double2) * n_traj * (size_t)(S + 1));
   L.pops = take(sizeof(double) * n_traj * nt_max);
@@ -465,11 +563,16 @@ BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t p
   return L;
 }
 
-cudaError_t backward_run(const DevPtrs& main, const RunParams& rp0, char* ws, const BwdLayout& L, long long tot,
-                         int max_nblk, int max_N, long S, const void* z0, int z0_fp32, const double* deps_host,
-                         double* dtheta_host, cudaStream_t s) {
-  const size_t T = sizeof(double2) * (size_t)tot;
+namespace {
+
+template <typename T2>
+cudaError_t backward_t(const DevPtrs& main, const RunParams& rp0, char* ws, const BwdLayout& L, long long tot,
+                       int max_nblk, int max_N, long S, const void* z0, int z0_fp32, const double* deps_host,
+                       double* dtheta_host, cudaStream_t s) {
+  constexpr bool f32 = sizeof(T2) == sizeof(float2);
+  const size_t T = sizeof(T2) * (size_t)tot;
   auto P2 = [&](size_t off) { return reinterpret_cast<double2*>(ws + off); };
+  auto PS = [&](size_t off) { return reinterpret_cast<T2*>(ws + off); };
   cudaError_t e;
   // plain-engine pointers for the forward recomputation
   DevPtrs p{};
@@ -497,6 +600,8 @@ cudaError_t backward_run(const DevPtrs& main, const RunParams& rp0, char* ws, co
   a.Xs = P2(L.Xs);
   a.Gi = P2(L.Gi);
   a.EP = P2(L.EP);
+  a.Xs32 = f32 ? reinterpret_cast<float2*>(ws + L.Xs32) : nullptr;
+  a.EP32 = f32 ? reinterpret_cast<float2*>(ws + L.EP32) : nullptr;
   a.part = p.part;
   a.bpart = reinterpret_cast<double*>(ws + L.bpart);
   a.thbar = reinterpret_cast<double*>(ws + L.thbar);
@@ -508,11 +613,11 @@ cudaError_t backward_run(const DevPtrs& main, const RunParams& rp0, char* ws, co
   a.dt = rp.dt;
   const double h = rp.dt;
 
-  // initial state into the first checkpoint (complex128)
-  if (z0_fp32)
-    e = launch_convert(z0, P2(L.ck), tot, 0, s);
+  // initial state into the first checkpoint (in the adjoint's state type)
+  if (z0_fp32 == (int)f32)
+    e = cudaMemcpyAsync(PS(L.ck), z0, T, cudaMemcpyDeviceToDevice, s);
   else
-    e = cudaMemcpyAsync(P2(L.ck), z0, T, cudaMemcpyDeviceToDevice, s);
+    e = launch_convert(z0, PS(L.ck), tot, f32 ? 1 : 0, s);
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws + L.thbar, 0, sizeof(double) * 8 * rp.n_traj, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(ws + L.deps, deps_host, sizeof(double) * rp.n_cand, cudaMemcpyHostToDevice, s)) !=
@@ -521,42 +626,42 @@ cudaError_t backward_run(const DevPtrs& main, const RunParams& rp0, char* ws, co
   // forward pass: checkpoints and the readout signal
   for (long sg = 0; sg < L.n_seg; ++sg) {
     const long s0 = sg * L.K, len = std::min<long>(L.K, S - s0);
-    if ((e = cudaMemcpyAsync(p.Zn, P2(L.ck) + (size_t)sg * tot, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(p.Zn, PS(L.ck) + (size_t)sg * tot, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return e;
-    if ((e = plain_integrate(p, rp, max_nblk, max_N, s0, len, s)) != cudaSuccess) return e;
+    if ((e = plain_integrate(p, rp, max_nblk, max_N, s0, len, s, f32)) != cudaSuccess) return e;
     if (sg + 1 < L.n_seg &&
-        (e = cudaMemcpyAsync(P2(L.ck) + (size_t)(sg + 1) * tot, p.Zn, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        (e = cudaMemcpyAsync(PS(L.ck) + (size_t)(sg + 1) * tot, p.Zn, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return e;
   }
   adj::adj_gcoef<<<rp.n_cand, adj::AT, 0, s>>>(a, reinterpret_cast<double*>(ws + L.deps), rp.eta, S,
                                                 reinterpret_cast<double*>(ws + L.gcoef));
   const dim3 egrid((unsigned)std::min<long>(((long)max_N * LR_MAX_RANK + adj::AT - 1) / adj::AT, 4096), rp.n_traj);
   const dim3 pgrid(max_nblk, rp.n_traj);
-  double2* lam = P2(L.lam);
-  double2* lamn = P2(L.lamn);
+  T2* lam = PS(L.lam);
+  T2* lamn = PS(L.lamn);
   // lambda_S: readout cotangent of the final state
-  adj::adj_update<<<egrid, adj::AT, 0, s>>>(a, reinterpret_cast<const double2*>(p.Zn), lam, lam, lam, lam, lam, lam,
-                                            S, S, 0);
-  double2* U[4] = {nullptr, P2(L.U) + tot, P2(L.U) + 2 * tot, P2(L.U) + 3 * tot};
-  double2* Ub[4] = {P2(L.Ub), P2(L.Ub) + tot, P2(L.Ub) + 2 * tot, P2(L.Ub) + 3 * tot};
+  adj::adj_update<T2><<<egrid, adj::AT, 0, s>>>(a, reinterpret_cast<const T2*>(p.Zn), lam, lam, lam, lam, lam, lam,
+                                                S, S, 0);
+  T2* U[4] = {nullptr, PS(L.U) + tot, PS(L.U) + 2 * tot, PS(L.U) + 3 * tot};
+  T2* Ub[4] = {PS(L.Ub), PS(L.Ub) + tot, PS(L.Ub) + 2 * tot, PS(L.Ub) + 3 * tot};
   const double ca[4] = {h / 6.0, h / 3.0, h / 3.0, h / 6.0};
   const double cb[4] = {h / 2.0, h / 2.0, h, 0.0};
   const double cs[4] = {0.0, 0.5, 0.5, 1.0};
   for (long sg = L.n_seg - 1; sg >= 0; --sg) {
     const long s0 = sg * L.K, len = std::min<long>(L.K, S - s0);
-    double2* seg = P2(L.seg);
-    if ((e = cudaMemcpyAsync(seg, P2(L.ck) + (size_t)sg * tot, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    T2* seg = PS(L.seg);
+    if ((e = cudaMemcpyAsync(seg, PS(L.ck) + (size_t)sg * tot, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
       return e;
     for (long i = 1; i < len; ++i) {
       if ((e = cudaMemcpyAsync(p.Zn, seg + (size_t)(i - 1) * tot, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return e;
-      if ((e = plain_integrate(p, rp, max_nblk, max_N, s0 + i - 1, 1, s)) != cudaSuccess) return e;
+      if ((e = plain_integrate(p, rp, max_nblk, max_N, s0 + i - 1, 1, s, f32)) != cudaSuccess) return e;
       if ((e = cudaMemcpyAsync(seg + (size_t)i * tot, p.Zn, T, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     }
     for (long i = len - 1; i >= 0; --i) {
       const long n = s0 + i;
       const double tn = (double)n * h;
-      double2* Z = seg + (size_t)i * tot;
+      T2* Z = seg + (size_t)i * tot;
       U[0] = Z;
       // forward stages: U_s, G^-1, X_k', next stage input
       DevPtrs q = p;
@@ -571,16 +676,17 @@ cudaError_t backward_run(const DevPtrs& main, const RunParams& rp0, char* ws, co
       }
       // reverse stages
       for (int st = 3; st >= 0; --st) {
-        const double2* un = st < 3 ? Ub[st + 1] : Ub[0];
+        const T2* un = st < 3 ? Ub[st + 1] : Ub[0];
         const double cbs = st < 3 ? cb[st] : 0.0;
         const double ts = tn + cs[st] * h;
-        adj::adj_bpart<<<pgrid, adj::AT, 0, s>>>(a, U[st], lam, un, ca[st], cbs);
+        adj::adj_bpart<T2><<<pgrid, adj::AT, 0, s>>>(a, U[st], lam, un, ca[st], cbs);
         adj::adj_bsolve<<<rp.n_traj, adj::AT, 0, s>>>(a, st, ts);
         adj::Ptrs as = a;
         as.Xs = a.Xs + (size_t)st * rp.n_traj * 2 * adj::MR2;
-        adj::adj_vjp<<<egrid, adj::AT, 0, s>>>(as, U[st], lam, un, ca[st], cbs, ts, Ub[st]);
+        if (f32) as.Xs32 = a.Xs32 + (size_t)st * rp.n_traj * 2 * adj::MR2;
+        adj::adj_vjp<T2><<<egrid, adj::AT, 0, s>>>(as, U[st], lam, un, ca[st], cbs, ts, Ub[st]);
       }
-      adj::adj_update<<<egrid, adj::AT, 0, s>>>(a, Z, lam, Ub[0], Ub[1], Ub[2], Ub[3], lamn, n, S, 1);
+      adj::adj_update<T2><<<egrid, adj::AT, 0, s>>>(a, Z, lam, Ub[0], Ub[1], Ub[2], Ub[3], lamn, n, S, 1);
       std::swap(lam, lamn);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -594,6 +700,16 @@ cudaError_t backward_run(const DevPtrs& main, const RunParams& rp0, char* ws, co
   for (int c = 0; c < rp.n_cand; ++c)
     for (int i = 0; i < 8; ++i) dtheta_host[8 * c + i] = th[8 * (2 * c) + i] + th[8 * (2 * c + 1) + i];
   return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t backward_run(const DevPtrs& main, const RunParams& rp, char* ws, const BwdLayout& L, long long tot,
+                         int max_nblk, int max_N, long S, const void* z0, int z0_fp32, const double* deps_host,
+                         double* dtheta_host, cudaStream_t s) {
+  if (L.fp32)
+    return backward_t<float2>(main, rp, ws, L, tot, max_nblk, max_N, S, z0, z0_fp32, deps_host, dtheta_host, s);
+  return backward_t<double2>(main, rp, ws, L, tot, max_nblk, max_N, S, z0, z0_fp32, deps_host, dtheta_host, s);
 }
 
 }  // namespace lr

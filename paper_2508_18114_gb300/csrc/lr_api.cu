@@ -542,7 +542,8 @@ lr_status lr_backward_workspace_size(const lr_ctx* c, int ckpt_every, size_t* by
   if (c->step < 1) return LR_ERR_STATE;
   size_t part = 0;
   for (const TrajDev& d : c->traj) part += (size_t)d.nblk * lr::plain_pstride(d.M);
-  const lr::BwdLayout L = lr::bwd_layout(c->tot_elems, c->n_traj, c->n_cand, c->nt_max, part, c->step, ckpt_every);
+  const lr::BwdLayout L = lr::bwd_layout(c->tot_elems, c->n_traj, c->n_cand, c->nt_max, part, c->step, ckpt_every,
+                                         c->opt.precision != LR_PREC_FP64);
   *bytes = L.total;
   return LR_OK;
 }
@@ -563,7 +564,8 @@ lr_status lr_backward(lr_ctx* c, void* dev_ws, size_t ws_bytes, const double* d_
     if (!std::isfinite(d_eps_a[k])) return fail(c, LR_ERR_ARG, "non-finite cotangent");
   size_t part = 0;
   for (const TrajDev& d : c->traj) part += (size_t)d.nblk * lr::plain_pstride(d.M);
-  const lr::BwdLayout L = lr::bwd_layout(c->tot_elems, c->n_traj, c->n_cand, c->nt_max, part, c->step, ckpt_every);
+  const lr::BwdLayout L = lr::bwd_layout(c->tot_elems, c->n_traj, c->n_cand, c->nt_max, part, c->step, ckpt_every,
+                                         c->opt.precision != LR_PREC_FP64);
   if (!dev_ws || ws_bytes < L.total) return fail(c, LR_ERR_WORKSPACE, "backward workspace missing or too small");
   if (reinterpret_cast<uintptr_t>(dev_ws) % 256 != 0) return fail(c, LR_ERR_WORKSPACE, "backward workspace misaligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -45,7 +45,7 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
   L.o_xs = o;
   o += al16(2 * Mp * Mp * (int)es);
   L.o_misc = o;
-  o += al16(160 * (int)sizeof(double));
+  o += al16(144 * (int)sizeof(double));
   L.o_tab = o;
   o += al16(fz::TAB * 7 * (int)(es / 2));
   L.o_ta = L.o_tb = o;

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
   // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
   // photons, [96..128) 1/L[k][k], [128..131) bulk-precision coefficient and
   // steps, [140] phase-P task counter, [141] tensor-core timeout flag, [142]
-  // tensor-core mbarrier, [143] TMEM base address, [144..160) diagonal of G (FP32)
+  // tensor-core mbarrier, [143] TMEM base address
   double* misc = reinterpret_cast<double*>(smem + a.o_misc);
   if (a.debug_wait > 0) {
     // Test hook for the timeout path: thread 0 waits on an mbarrier that
@@ -858,61 +858,29 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
           }
           if (last) break;
           T2* Gi = reinterpret_cast<T2*>(Gd);   // G^-1 reuses the storage of L once L is no longer needed
-          // X of the FP32 state, double-word, row-major [M][2 Mp]: columns k Mp + l
-          // hold X_k = G^-1 T_k. It spans the W and Tred regions (contiguous).
-          DWC* Bx = reinterpret_cast<DWC*>(W);
-          const int ldb = 2 * Mp;
           if constexpr (sizeof(T) == 4) {
-            // FP32 state: X_k = G^-1 T_k by an LDL^dag elimination of the augmented
-            // matrix [G | T_r | T_b] in double-word FP32 (~2^-48 relative, FP64-class
-            // like the Gram matrix), on the FP32 pipes: on this GPU an FP64 warp
-            // instruction holds its SMSP's FP64 pipe for ~60 cycles. The forward
-            // sweep factorises G = L D L^dag (unit lower L, right-looking, in place)
-            // and applies L^-1 to the 2M right-hand sides in the same elimination
-            // steps; then D^-1; then the back substitution with L^dag. One block
-            // barrier per elimination step; X is rounded to FP32 once, at the end.
+            // FP32 state: the same factorisation and inverse in double-word FP32
+            // (~2^-48 relative, FP64-class like the Gram matrix), on the FP32 pipes:
+            // on this GPU an FP64 warp instruction holds its SMSP's FP64 pipe for
+            // ~60 cycles, and G^-1 is rounded to FP32 at the end anyway. G, L and W
+            // use the storage of their FP64 counterparts (16 bytes per entry).
             DWC* Gw = reinterpret_cast<DWC*>(Gd);
+            DWC* Ww = reinterpret_cast<DWC*>(W);
             DW* dinv = reinterpret_cast<DW*>(misc + 96);   // [M] 1 / D[k]
-            float* diag0 = reinterpret_cast<float*>(misc + 144);   // [M] diagonal of G
-            const int nrhs = 2 * M;
-            // T (FP32, in Tred) into registers first: Bx overwrites Tred
-            constexpr int TPT = (2 * LR_MAX_RANK * LR_MAX_RANK + NT - 1) / NT;
-            T2 tv[TPT];
-#pragma unroll
-            for (int u = 0; u < TPT; ++u) {
-              const int e = tid + u * NT;
-              tv[u] = cm<T2>(0, 0);
-              if (e < M * nrhs) {
-                const int i = e / nrhs, c = e - i * nrhs, k2 = c >= M ? 1 : 0;
-                tv[u] = Tred[k2 * MM + i * Mp + (c - k2 * M)];
-              }
-            }
+            float* diag0 = reinterpret_cast<float*>(W);    // W[k][0] slot: the diagonal of G
             for (int e = tid; e < M * (M + 1) / 2; e += NT) {
               const int i = tri[e].x, j = tri[e].y;
               const double2 v = Gd[i * ldg + j];
               DWC g;
               g.re = dw_make(v.x);
               g.im = dw_make(v.y);
-              if (i == j) diag0[i] = (float)v.x;
+              if (i == j) diag0[i * ldg * 4] = (float)v.x;
               Gw[i * ldg + j] = g;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < TPT; ++u) {
-              const int e = tid + u * NT;
-              if (e < M * nrhs) {
-                const int i = e / nrhs, c = e - i * nrhs, k2 = c >= M ? 1 : 0;
-                DWC b;
-                b.re.hi = tv[u].x;
-                b.im.hi = tv[u].y;
-                b.re.lo = b.im.lo = 0.0f;
-                Bx[i * ldb + k2 * Mp + (c - k2 * M)] = b;
-              }
             }
             // pivot k: breakdown check against the original diagonal, then 1 / D[k]
             auto pivot = [&](int k) {
               const DW piv = Gw[k * ldg + k].re;
-              if (!(piv.hi > 1e-13f * diag0[k]) || !isfinite(piv.hi) || piv.hi < 1e-30f) {
+              if (!(piv.hi > 1e-13f * diag0[k * ldg * 4]) || !isfinite(piv.hi) || piv.hi < 1e-30f) {
                 misc[1] = 1.0;
                 dinv[k].hi = 1.0f;
                 dinv[k].lo = 0.0f;
@@ -920,52 +888,57 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
                 dinv[k] = dw_recip(piv);
               }
             };
+            __syncthreads();
             if (tid == 0) pivot(0);
             __syncthreads();
-            // forward sweep: step k updates the trailing lower triangle,
-            // G[i][j] -= G[i][k] conj(G[j][k]) / D[k] (i >= j > k), and the rows
-            // below k of the right-hand sides, B[i] -= (G[i][k] / D[k]) B[k];
-            // item 0 (the next pivot) belongs to thread 0, which forms 1 / D[k+1]
-            // before the barrier
             for (int k = 0; k < M; ++k) {
               const DW rk = dinv[k];
               const int w = M - k - 1;
-              const int n_tr = w * (w + 1) / 2;
-              for (int e = tid; e < n_tr + w * nrhs; e += NT) {
-                if (e < n_tr) {
-                  const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
-                  const DWC t = dwc_scale(dwc_mul_conj(Gw[i * ldg + k], Gw[j * ldg + k]), rk);
-                  Gw[i * ldg + j] = dwc_sub(Gw[i * ldg + j], t);
-                } else {
-                  const int e2 = e - n_tr, i = k + 1 + e2 / nrhs, c = e2 - (i - k - 1) * nrhs;
-                  const int col = c >= M ? c - M + Mp : c;
-                  const DWC t = dwc_mul(dwc_scale(Gw[i * ldg + k], rk), Bx[k * ldb + col]);
-                  Bx[i * ldb + col] = dwc_sub(Bx[i * ldb + col], t);
-                }
+              // trailing update G[i][j] -= G[i][k] conj(G[j][k]) / D[k], i >= j > k;
+              // entry 0 (the next pivot) belongs to thread 0, which then forms
+              // 1 / D[k+1] before the barrier: one barrier per elimination step
+              for (int e = tid; e < w * (w + 1) / 2; e += NT) {
+                const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
+                const DWC t = dwc_scale(dwc_mul_conj(Gw[i * ldg + k], Gw[j * ldg + k]), rk);
+                Gw[i * ldg + j] = dwc_sub(Gw[i * ldg + j], t);
               }
               if (tid == 0 && k + 1 < M) pivot(k + 1);
               __syncthreads();
             }
             if (tid == 0 && misc[1] != 0.0) set_error(a.p.err, DEV_NOT_PD);
-            // D^-1
-            for (int e = tid; e < M * nrhs; e += NT) {
-              const int i = e / nrhs, c = e - i * nrhs, col = c >= M ? c - M + Mp : c;
-              Bx[i * ldb + col] = dwc_scale(Bx[i * ldb + col], dinv[i]);
+            // W = L^-1 (unit lower, L[i][k] = G[i][k] / D[k]) by columns: column j
+            // by warp j mod NWARP, lane i = row i, forward substitution
+            // W[i][j] = delta_ij - sum_{j <= k < i} L[i][k] W[k][j] with W[k][j]
+            // broadcast from lane k (no block barrier)
+            for (int j = warp; j < M; j += NWARP) {
+              DWC wv;
+              wv.re.hi = lane == j ? 1.0f : 0.0f;
+              wv.re.lo = wv.im.hi = wv.im.lo = 0.0f;
+              for (int k = j; k < M - 1; ++k) {
+                DWC wk;
+                wk.re.hi = __shfl_sync(0xffffffffu, wv.re.hi, k);
+                wk.re.lo = __shfl_sync(0xffffffffu, wv.re.lo, k);
+                wk.im.hi = __shfl_sync(0xffffffffu, wv.im.hi, k);
+                wk.im.lo = __shfl_sync(0xffffffffu, wv.im.lo, k);
+                if (lane > k && lane < M) wv = dwc_sub(wv, dwc_mul(dwc_scale(Gw[lane * ldg + k], dinv[k]), wk));
+              }
+              if (lane < M) Ww[lane * ldg + j] = wv;
             }
             __syncthreads();
-            // back substitution with L^dag (L[k][j] = G[k][j] / D[j]): once row k
-            // is final, B[j] -= conj(L[k][j]) B[k] for every j < k
-            for (int k = M - 1; k > 0; --k) {
-              for (int e = tid; e < k * nrhs; e += NT) {
-                const int j = e / nrhs, c = e - j * nrhs, col = c >= M ? c - M + Mp : c;
-                const DWC l = dwc_scale(Gw[k * ldg + j], dinv[j]);
-                DWC lc;
-                lc.re = l.re;
-                lc.im = dw_neg(l.im);
-                Bx[j * ldb + col] = dwc_sub(Bx[j * ldb + col], dwc_mul(lc, Bx[k * ldb + col]));
-              }
-              __syncthreads();
+            // G^-1 = W^dag D^-1 W (Hermitian): entry (i, j), i <= j, is
+            // sum_{k >= j} conj(W[k][i]) W[k][j] / D[k], rounded once to FP32
+            for (int e = tid; e < M * M; e += NT) {
+              const int i = e / M, j = e - i * M;
+              if (i > j) continue;
+              DWC acc;
+              acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
+              for (int k = j; k < M; ++k)   // W[k][j] conj(W[k][i]) = conj of the term
+                acc = dwc_add(acc, dwc_scale(dwc_mul_conj(Ww[k * ldg + j], Ww[k * ldg + i]), dinv[k]));
+              const T re = acc.re.hi + acc.re.lo, im = acc.im.hi + acc.im.lo;
+              Gi[i * Mp + j] = cm<T2>(re, im);
+              if (i != j) Gi[j * Mp + i] = cm<T2>(re, -im);
             }
+            __syncthreads();
           } else {
             // FP64 G = L D L^dag (unit lower L, right-looking, in place in Gd), then
             // W = L^-1 (unit lower) and G^-1 = W^dag D^-1 W. One FP64 reciprocal per
@@ -1038,26 +1011,19 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
             __syncthreads();
           }
-          // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k: from the double-word
-          // solve (FP32 state), or as the product G^-1 T_k (FP64 state)
+          // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
           const double sk[2] = {0.5 * d.kappa, 0.5 * d.gamma};
           for (int e = tid; e < 2 * Mq * Mq; e += NT) {
             const int k = e / (Mq * Mq), lq = e - k * (Mq * Mq), l = lq / Mq, m = lq - l * Mq, lm = l * Mp + m;
             T xr = 0, xi = 0;
             if (l < M && m < M) {
-              if constexpr (sizeof(T) == 4) {
-                const DWC x = Bx[m * ldb + k * Mp + l];
-                xr = x.re.hi + x.re.lo;
-                xi = x.im.hi + x.im.lo;
-              } else {
-                const T2* Tk = Tred + k * MM;
-                for (int j = 0; j < M; ++j) {
-                  const T2 gv = Gi[m * Mp + j];
-                  const T gr = gv.x, gi = gv.y;
-                  const T2 t = Tk[j * Mp + l];
-                  xr = fma(gr, t.x, fma(-gi, t.y, xr));
-                  xi = fma(gr, t.y, fma(gi, t.x, xi));
-                }
+              const T2* Tk = Tred + k * MM;
+              for (int j = 0; j < M; ++j) {
+                const T2 gv = Gi[m * Mp + j];
+                const T gr = gv.x, gi = gv.y;
+                const T2 t = Tk[j * Mp + l];
+                xr = fma(gr, t.x, fma(-gi, t.y, xr));
+                xi = fma(gr, t.y, fma(gi, t.x, xi));
               }
             }
             const T s = (T)sk[k];

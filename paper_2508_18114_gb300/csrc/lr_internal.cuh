@@ -47,6 +47,18 @@ template <> struct cplx<float> { using type = float2; };
 __host__ __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
 __host__ __device__ __forceinline__ float2 mkf(float r, float i) { return make_float2(r, i); }
 
+// Real type of a complex storage type, and a constructor generic over both.
+template <typename T2> struct real_of;
+template <> struct real_of<double2> { using type = double; };
+template <> struct real_of<float2> { using type = float; };
+template <typename T2>
+__host__ __device__ __forceinline__ T2 mkc(typename real_of<T2>::type r, typename real_of<T2>::type i) {
+  T2 v;
+  v.x = r;
+  v.y = i;
+  return v;
+}
+
 // ------------------------------------------------------------------ pulse
 
 // Logistic step f(t, t0, s) of Sec. S2.C.
@@ -230,20 +242,28 @@ cudaError_t launch_diagnostics(const DevPtrs& p, const RunParams& rp, long n_val
 // lr_plain.cu
 int plain_rows_per_block();
 size_t plain_partial_doubles(int M);
+// The plain engine on complex128 state (the reference GPU path), or on
+// complex64 state (fp32 = 1: the adjoint's FP32-bulk recomputation; the Gram
+// matrix is summed in FP64 from exact products, Cholesky and solves in FP64,
+// the rest in FP32).
 cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0,
-                            long n_steps, cudaStream_t s);
+                            long n_steps, cudaStream_t s, int fp32 = 0);
 // single kernels of the plain engine (used by the adjoint's recomputation)
 void plain_gram_launch(const DevPtrs& p, const RunParams& rp, int max_nblk, const double2* zin, cudaStream_t s);
+void plain_gram_launch(const DevPtrs& p, const RunParams& rp, int max_nblk, const float2* zin, cudaStream_t s);
 void plain_rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const double2* zin, double2* zout, int stage,
+                      double t, cudaStream_t s);
+void plain_rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const float2* zin, float2* zout, int stage,
                       double t, cudaStream_t s);
 
 // lr_adjoint.cu
 struct BwdLayout {
-  size_t ck, seg, cur, za, zb, acc, U, Ub, lam, lamn, X, part, Xs, Gi, EP, bpart, beta, pops, nphot, trace, gcoef,
-      deps, thbar, total;
+  size_t ck, seg, cur, za, zb, acc, U, Ub, lam, lamn, X, part, Xs, Gi, EP, Xs32, EP32, bpart, beta, pops, nphot,
+      trace, gcoef, deps, thbar, total;
   long n_seg, K;
+  int fp32;   // 1: FP32-bulk adjoint (complex64 states and cotangents)
 };
-BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t part_doubles, long S, int K);
+BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t part_doubles, long S, int K, int fp32);
 cudaError_t backward_run(const DevPtrs& main, const RunParams& rp, char* ws, const BwdLayout& L, long long tot,
                          int max_nblk, int max_N, long S, const void* z0, int z0_fp32, const double* deps_host,
                          double* dtheta_host, cudaStream_t s);

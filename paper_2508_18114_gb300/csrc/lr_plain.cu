@@ -12,6 +12,14 @@
 // With Y_k = L_k Z the projection term of Eq. S5 is 1/2 sum_k Y_k (Z^+ Y_k)^dag
 // = 1/2 kappa (rZ)(G^-1 Z^dag r Z)^dag + 1/2 gamma (bZ)(G^-1 Z^dag b Z)^dag,
 // and -1/2 sum_k L_k^dag L_k Z is folded into the diagonal of H_eff.
+//
+// The state type is a template parameter: complex128 (the reference path), or
+// complex64 for the FP32-bulk recomputation inside the adjoint. With complex64
+// the Gram matrix is summed in FP64 from the exact products of the FP32
+// entries (FP64-class), the Cholesky factor and the solves are FP64 as always,
+// and the operator apply, T_k, the projection term and the RK4 update run in
+// FP32 (the diagonal energies and the step sizes split into hi + lo floats so
+// that FP32 does not round the mode frequencies or dt).
 #include "lr_internal.cuh"
 
 namespace lr {
@@ -24,36 +32,38 @@ __host__ __device__ inline size_t pstride(int M) { return plain_pstride(M); }
 int plain_rows_per_block() { return PR; }
 size_t plain_partial_doubles(int M) { return pstride(M); }
 
-__global__ void __launch_bounds__(PT) plain_gram(const TrajDev* __restrict__ traj, const double2* __restrict__ Zin,
+template <typename T2>
+__global__ void __launch_bounds__(PT) plain_gram(const TrajDev* __restrict__ traj, const T2* __restrict__ Zin,
                                                  double* __restrict__ part, int with_obs) {
+  using T = typename real_of<T2>::type;
   const TrajDev d = traj[blockIdx.y];
   const int b = blockIdx.x;
   if (b >= d.nblk) return;
-  __shared__ double2 sZ[PR][LR_MAX_RANK], sR[PR][LR_MAX_RANK], sB[PR][LR_MAX_RANK];
+  __shared__ T2 sZ[PR][LR_MAX_RANK], sR[PR][LR_MAX_RANK], sB[PR][LR_MAX_RANK];
   __shared__ double sw[PR];
   __shared__ int slev[PR], sro[PR];
   const int M = d.M, ld = d.ld;
   const int r0 = b * PR;
   const int rows = min(PR, d.N - r0);
-  const double2* Z = Zin + d.z_off;
+  const T2* Z = Zin + d.z_off;
   const int st = d.Nr * d.Nf;
   for (int e = threadIdx.x; e < PR * M; e += blockDim.x) {
     const int i = e / M, m = e - (e / M) * M;
-    double2 z = mk(0, 0), zr = mk(0, 0), zb = mk(0, 0);
+    T2 z = mkc<T2>(0, 0), zr = mkc<T2>(0, 0), zb = mkc<T2>(0, 0);
     if (i < rows) {
       const int n = r0 + i;
       z = Z[(size_t)n * ld + m];
       const RowIdx ri = row_index(d, n);
       const int iro = readout_index(d, ri);
       if (iro + 1 < readout_dim(d)) {
-        const double c = sqrt(iro + 1.0);
-        const double2 v = Z[(size_t)(n + 1) * ld + m];
-        zr = mk(c * v.x, c * v.y);
+        const T c = (T)sqrt(iro + 1.0);
+        const T2 v = Z[(size_t)(n + 1) * ld + m];
+        zr = mkc<T2>(c * v.x, c * v.y);
       }
       if (ri.it + 1 < d.Nt) {
-        const double c = sqrt(ri.it + 1.0);
-        const double2 v = Z[(size_t)(n + st) * ld + m];
-        zb = mk(c * v.x, c * v.y);
+        const T c = (T)sqrt(ri.it + 1.0);
+        const T2 v = Z[(size_t)(n + st) * ld + m];
+        zb = mkc<T2>(c * v.x, c * v.y);
       }
       if (m == 0) {
         slev[i] = ri.it;
@@ -70,21 +80,38 @@ __global__ void __launch_bounds__(PT) plain_gram(const TrajDev* __restrict__ tra
   for (int e = threadIdx.x; e < 3 * MM; e += blockDim.x) {
     const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
     if (mat == 0 && i > j) continue;
-    double re = 0.0, im = 0.0;
-    for (int r = 0; r < rows; ++r) {
-      const double2 a = sZ[r][i];
-      const double2 c = mat == 0 ? sZ[r][j] : (mat == 1 ? sR[r][j] : sB[r][j]);
-      re = fma(a.x, c.x, fma(a.y, c.y, re));      // conj(a) * c
-      im = fma(a.x, c.y, fma(-a.y, c.x, im));
+    if (sizeof(T) == 8 || mat == 0) {
+      // FP64 sums (of exact products when the state is FP32)
+      double re = 0.0, im = 0.0;
+      for (int r = 0; r < rows; ++r) {
+        const T2 a = sZ[r][i];
+        const T2 c = mat == 0 ? sZ[r][j] : (mat == 1 ? sR[r][j] : sB[r][j]);
+        const double ax = a.x, ay = a.y, cx = c.x, cy = c.y;
+        re = fma(ax, cx, fma(ay, cy, re));      // conj(a) * c
+        im = fma(ax, cy, fma(-ay, cx, im));
+      }
+      out[2 * e] = re;
+      out[2 * e + 1] = im;
+    } else {
+      T re = 0, im = 0;
+      for (int r = 0; r < rows; ++r) {
+        const T2 a = sZ[r][i];
+        const T2 c = mat == 1 ? sR[r][j] : sB[r][j];
+        re = fma(a.x, c.x, fma(a.y, c.y, re));
+        im = fma(a.x, c.y, fma(-a.y, c.x, im));
+      }
+      out[2 * e] = (double)re;
+      out[2 * e + 1] = (double)im;
     }
-    out[2 * e] = re;
-    out[2 * e + 1] = im;
   }
   if (with_obs) {
     for (int i = threadIdx.x; i < PR; i += blockDim.x) {
       double w = 0.0;
       if (i < rows)
-        for (int m = 0; m < M; ++m) w += sZ[i][m].x * sZ[i][m].x + sZ[i][m].y * sZ[i][m].y;
+        for (int m = 0; m < M; ++m) {
+          const double x = sZ[i][m].x, y = sZ[i][m].y;
+          w += x * x + y * y;
+        }
       sw[i] = w;
     }
     __syncthreads();
@@ -216,17 +243,21 @@ __global__ void __launch_bounds__(PT) plain_solve(DevPtrs p, RunParams rp, long 
   }
 }
 
-__global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const double2* __restrict__ Zin,
-                                                double2* __restrict__ Zout, int stage, double t) {
+template <typename T2>
+__global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const T2* __restrict__ Zin,
+                                                T2* __restrict__ Zout, int stage, double t) {
+  using T = typename real_of<T2>::type;
+  constexpr bool f32 = sizeof(T) == 4;
   const int tj = blockIdx.y;
   const TrajDev d = p.traj[tj];
-  __shared__ double2 sX[2][LR_MAX_RANK * LR_MAX_RANK];
+  __shared__ T2 sX[2][LR_MAX_RANK * LR_MAX_RANK];
   __shared__ double coef, coef_i, wfr;
   const int M = d.M, MM = M * M, ld = d.ld;
   const double2* X = p.X + (size_t)tj * 2 * LR_MAX_RANK * LR_MAX_RANK;
   for (int e = threadIdx.x; e < 2 * MM; e += blockDim.x) {
     const int k = e / MM, ij = e - k * MM;
-    sX[k][ij] = X[k * LR_MAX_RANK * LR_MAX_RANK + ij];
+    const double2 x = X[k * LR_MAX_RANK * LR_MAX_RANK + ij];
+    sX[k][ij] = mkc<T2>((T)x.x, (T)x.y);
   }
   if (threadIdx.x == 0) {
     const PulseDev P = p.pulse[d.cand];
@@ -242,12 +273,16 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
     }
   }
   __syncthreads();
-  const double2* Z = Zin + d.z_off;
-  double2* Zn = reinterpret_cast<double2*>(p.Zn) + d.z_off;
-  double2* acc = reinterpret_cast<double2*>(p.acc) + d.z_off;
-  double2* Zo = Zout ? Zout + d.z_off : nullptr;
+  const T2* Z = Zin + d.z_off;
+  T2* Zn = reinterpret_cast<T2*>(p.Zn) + d.z_off;
+  T2* acc = reinterpret_cast<T2*>(p.acc) + d.z_off;
+  T2* Zo = Zout ? Zout + d.z_off : nullptr;
   const int st = d.Nr * d.Nf, sr = d.Nf;
-  const double c = coef, ci = coef_i, dt = rp.dt;
+  const T c = (T)coef, ci = (T)coef_i;
+  const double dt = rp.dt;
+  // FP32 state: step sizes as hi + lo floats
+  const double hsd = stage == 2 ? dt : 0.5 * dt, h6d = dt / 6.0;
+  const T hs_hi = (T)hsd, hs_lo = (T)(hsd - (double)hs_hi), h6_hi = (T)h6d, h6_lo = (T)(h6d - (double)h6_hi);
   const bool rwa = rp.frame != 0;
   const long total = (long)d.N * M;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
@@ -255,8 +290,17 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
     const RowIdx ri = row_index(d, n);
     double dre, dim_;
     heff_diag(d, ri, wfr, dre, dim_);
-    const double2 z = Z[(size_t)n * ld + m];
-    double hr = dre * z.x - dim_ * z.y, hi = dre * z.y + dim_ * z.x;
+    const T2 z = Z[(size_t)n * ld + m];
+    T hr, hi;
+    if constexpr (f32) {
+      // diagonal energy as hi + lo floats: FP32 does not round the mode frequencies
+      const T dh = (T)dre, dl = (T)(dre - (double)dh), di = (T)dim_;
+      hr = fma(dh, z.x, fma(dl, z.x, -di * z.y));
+      hi = fma(dh, z.y, fma(dl, z.y, di * z.x));
+    } else {
+      hr = dre * z.x - dim_ * z.y;
+      hi = dre * z.y + dim_ * z.x;
+    }
     // g (b + b^dag)(a + a^dag)
     for (int a = -1; a <= 1; a += 2) {
       const int it2 = ri.it + a;
@@ -266,8 +310,8 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
         const int ir2 = ri.ir + bb;
         if (ir2 < 0 || ir2 >= d.Nr) continue;
         if (rwa && a == bb) continue;   // RWA keeps g (b^dag a + b a^dag) only
-        const double w = d.g * ct * sqrt((double)max(ri.ir, ir2));
-        const double2 v = Z[(size_t)(n + a * st + bb * sr) * ld + m];
+        const T w = (T)(d.g * ct * sqrt((double)max(ri.ir, ir2)));
+        const T2 v = Z[(size_t)(n + a * st + bb * sr) * ld + m];
         hr += w * v.x;
         hi += w * v.y;
       }
@@ -282,8 +326,8 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
           const int if2 = ri.iff + bb;
           if (if2 < 0 || if2 >= d.Nf) continue;
           if (rwa && a == bb) continue;   // RWA keeps J (a^dag f + a f^dag) only
-          const double w = d.J * cr * sqrt((double)max(ri.iff, if2));
-          const double2 v = Z[(size_t)(n + a * sr + bb) * ld + m];
+          const T w = (T)(d.J * cr * sqrt((double)max(ri.iff, if2)));
+          const T2 v = Z[(size_t)(n + a * sr + bb) * ld + m];
           hr += w * v.x;
           hi += w * v.y;
         }
@@ -295,21 +339,21 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
     for (int a = -1; a <= 1; a += 2) {
       const int i2 = iro + a;
       if (i2 < 0 || i2 >= dro) continue;
-      const double s = sqrt((double)max(iro, i2));
-      const double wr = c * s, wi = (a > 0 ? ci : -ci) * s;
-      const double2 v = Z[(size_t)(n + a) * ld + m];
+      const T s = (T)sqrt((double)max(iro, i2));
+      const T wr = c * s, wi = (a > 0 ? ci : -ci) * s;
+      const T2 v = Z[(size_t)(n + a) * ld + m];
       hr += wr * v.x - wi * v.y;
       hi += wr * v.y + wi * v.x;
     }
     // F = -i H_eff Z
-    double fr = hi, fi = -hr;
+    T fr = hi, fi = -hr;
     // + 1/2 kappa (rZ) X_r^dag + 1/2 gamma (bZ) X_b^dag
     if (iro + 1 < dro) {
-      const double s = 0.5 * d.kappa * sqrt(iro + 1.0);
-      const double2* zr = Z + (size_t)(n + 1) * ld;
-      double sr_ = 0.0, si_ = 0.0;
+      const T s = (T)(0.5 * d.kappa * sqrt(iro + 1.0));
+      const T2* zr = Z + (size_t)(n + 1) * ld;
+      T sr_ = 0, si_ = 0;
       for (int l = 0; l < M; ++l) {
-        const double2 y = zr[l], x = sX[0][m * M + l];   // y * conj(x)
+        const T2 y = zr[l], x = sX[0][m * M + l];   // y * conj(x)
         sr_ += y.x * x.x + y.y * x.y;
         si_ += y.y * x.x - y.x * x.y;
       }
@@ -317,11 +361,11 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
       fi += s * si_;
     }
     if (ri.it + 1 < d.Nt) {
-      const double s = 0.5 * d.gamma * sqrt(ri.it + 1.0);
-      const double2* zb = Z + (size_t)(n + st) * ld;
-      double sr_ = 0.0, si_ = 0.0;
+      const T s = (T)(0.5 * d.gamma * sqrt(ri.it + 1.0));
+      const T2* zb = Z + (size_t)(n + st) * ld;
+      T sr_ = 0, si_ = 0;
       for (int l = 0; l < M; ++l) {
-        const double2 y = zb[l], x = sX[1][m * M + l];
+        const T2 y = zb[l], x = sX[1][m * M + l];
         sr_ += y.x * x.x + y.y * x.y;
         si_ += y.y * x.x - y.x * x.y;
       }
@@ -330,41 +374,70 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const d
     }
     // RK4 (weights 1/6, 1/3, 1/3, 1/6)
     const size_t o = (size_t)n * ld + m;
-    const double2 zn = Zn[o];
-    if (stage == 0) {
-      acc[o] = mk(fr, fi);
-      Zo[o] = mk(zn.x + 0.5 * dt * fr, zn.y + 0.5 * dt * fi);
-    } else if (stage == 1) {
-      const double2 a = acc[o];
-      acc[o] = mk(a.x + 2.0 * fr, a.y + 2.0 * fi);
-      Zo[o] = mk(zn.x + 0.5 * dt * fr, zn.y + 0.5 * dt * fi);
-    } else if (stage == 2) {
-      const double2 a = acc[o];
-      acc[o] = mk(a.x + 2.0 * fr, a.y + 2.0 * fi);
-      Zo[o] = mk(zn.x + dt * fr, zn.y + dt * fi);
+    const T2 zn = Zn[o];
+    if constexpr (f32) {
+      if (stage < 3) {
+        if (stage == 0) {
+          acc[o] = mkc<T2>(fr, fi);
+        } else {
+          const T2 a = acc[o];
+          acc[o] = mkc<T2>(fma((T)2, fr, a.x), fma((T)2, fi, a.y));
+        }
+        Zo[o] = mkc<T2>(zn.x + fma(hs_lo, fr, hs_hi * fr), zn.y + fma(hs_lo, fi, hs_hi * fi));
+      } else {
+        const T2 a = acc[o];
+        const T s_r = a.x + fr, s_i = a.y + fi;
+        Zn[o] = mkc<T2>(zn.x + fma(h6_lo, s_r, h6_hi * s_r), zn.y + fma(h6_lo, s_i, h6_hi * s_i));
+      }
     } else {
-      const double2 a = acc[o];
-      const double h = dt / 6.0;
-      Zn[o] = mk(zn.x + h * (a.x + fr), zn.y + h * (a.y + fi));
+      if (stage == 0) {
+        acc[o] = mkc<T2>(fr, fi);
+        Zo[o] = mkc<T2>(zn.x + 0.5 * dt * fr, zn.y + 0.5 * dt * fi);
+      } else if (stage == 1) {
+        const T2 a = acc[o];
+        acc[o] = mkc<T2>(a.x + 2.0 * fr, a.y + 2.0 * fi);
+        Zo[o] = mkc<T2>(zn.x + 0.5 * dt * fr, zn.y + 0.5 * dt * fi);
+      } else if (stage == 2) {
+        const T2 a = acc[o];
+        acc[o] = mkc<T2>(a.x + 2.0 * fr, a.y + 2.0 * fi);
+        Zo[o] = mkc<T2>(zn.x + dt * fr, zn.y + dt * fi);
+      } else {
+        const T2 a = acc[o];
+        const double h = dt / 6.0;
+        Zn[o] = mkc<T2>(zn.x + h * (a.x + fr), zn.y + h * (a.y + fi));
+      }
     }
   }
 }
 
 void plain_gram_launch(const DevPtrs& p, const RunParams& rp, int max_nblk, const double2* zin, cudaStream_t s) {
-  plain_gram<<<dim3(max_nblk, rp.n_traj), PT, 0, s>>>(p.traj, zin, p.part, 0);
+  plain_gram<double2><<<dim3(max_nblk, rp.n_traj), PT, 0, s>>>(p.traj, zin, p.part, 0);
+}
+void plain_gram_launch(const DevPtrs& p, const RunParams& rp, int max_nblk, const float2* zin, cudaStream_t s) {
+  plain_gram<float2><<<dim3(max_nblk, rp.n_traj), PT, 0, s>>>(p.traj, zin, p.part, 0);
 }
 
+template <typename T2>
+void rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const T2* zin, T2* zout, int stage, double t,
+                cudaStream_t s) {
+  const int rhs_blocks = (int)((long)max_N * LR_MAX_RANK / PT / 2 + 1);
+  plain_rhs<T2><<<dim3(rhs_blocks, rp.n_traj), PT, 0, s>>>(p, rp, zin, zout, stage, t);
+}
 void plain_rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const double2* zin, double2* zout, int stage,
                       double t, cudaStream_t s) {
-  const int rhs_blocks = (int)((long)max_N * LR_MAX_RANK / PT / 2 + 1);
-  plain_rhs<<<dim3(rhs_blocks, rp.n_traj), PT, 0, s>>>(p, rp, zin, zout, stage, t);
+  rhs_launch(p, rp, max_N, zin, zout, stage, t, s);
+}
+void plain_rhs_launch(const DevPtrs& p, const RunParams& rp, int max_N, const float2* zin, float2* zout, int stage,
+                      double t, cudaStream_t s) {
+  rhs_launch(p, rp, max_N, zin, zout, stage, t, s);
 }
 
-cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0,
-                            long n_steps, cudaStream_t s) {
-  double2* Zn = reinterpret_cast<double2*>(p.Zn);
-  double2* Za = reinterpret_cast<double2*>(p.Za);
-  double2* Zb = reinterpret_cast<double2*>(p.Zb);
+template <typename T2>
+cudaError_t integrate_t(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0, long n_steps,
+                        cudaStream_t s) {
+  T2* Zn = reinterpret_cast<T2*>(p.Zn);
+  T2* Za = reinterpret_cast<T2*>(p.Za);
+  T2* Zb = reinterpret_cast<T2*>(p.Zb);
   const dim3 ggrid(max_nblk, rp.n_traj);
   const int rhs_blocks = (int)((long)max_N * LR_MAX_RANK / PT / 2 + 1);
   const dim3 rgrid(rhs_blocks < 1 ? 1 : rhs_blocks, rp.n_traj);
@@ -372,12 +445,12 @@ cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk,
     const double tn = (double)st * rp.dt;
     const int record = (st % rp.pop_every) == 0;
     for (int stage = 0; stage < 4; ++stage) {
-      const double2* zin = stage == 0 ? Zn : (stage == 2 ? Zb : Za);
-      double2* zout = stage == 1 ? Zb : (stage == 3 ? nullptr : Za);
+      const T2* zin = stage == 0 ? Zn : (stage == 2 ? Zb : Za);
+      T2* zout = stage == 1 ? Zb : (stage == 3 ? nullptr : Za);
       const double ts = tn + (stage == 0 ? 0.0 : (stage == 3 ? rp.dt : 0.5 * rp.dt));
-      plain_gram<<<ggrid, PT, 0, s>>>(p.traj, zin, p.part, stage == 0 && record);
+      plain_gram<T2><<<ggrid, PT, 0, s>>>(p.traj, zin, p.part, stage == 0 && record);
       plain_solve<<<rp.n_traj, PT, 0, s>>>(p, rp, st, stage, stage == 0 && record, 1);
-      plain_rhs<<<rgrid, PT, 0, s>>>(p, rp, zin, zout, stage, ts);
+      plain_rhs<T2><<<rgrid, PT, 0, s>>>(p, rp, zin, zout, stage, ts);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -385,9 +458,15 @@ cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk,
   // observables of the final state
   const long se = step0 + n_steps;
   const int record = (se % rp.pop_every) == 0;
-  plain_gram<<<ggrid, PT, 0, s>>>(p.traj, Zn, p.part, record);
+  plain_gram<T2><<<ggrid, PT, 0, s>>>(p.traj, Zn, p.part, record);
   plain_solve<<<rp.n_traj, PT, 0, s>>>(p, rp, se, 0, record, 0);
   return cudaGetLastError();
+}
+
+cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0,
+                            long n_steps, cudaStream_t s, int fp32) {
+  return fp32 ? integrate_t<float2>(p, rp, max_nblk, max_N, step0, n_steps, s)
+              : integrate_t<double2>(p, rp, max_nblk, max_N, step0, n_steps, s);
 }
 
 }  // namespace lr

@@ -22,6 +22,11 @@
 // After the last step an observation pass (apply r, Gram, solve without
 // Cholesky) records beta and the observables of the final state.
 //
+// FP32_G64 contexts run, by default, the fused persistent kernel of
+// lr_sparse_fused.cuh instead: one launch per integrate call, one CTA per
+// trajectory, all four phases of a stage inside the CTA (the four-launch path
+// stays selectable with LR_SPARSE_FUSED=0 and is the FP64 path).
+//
 // Precisions: FP64 throughout, or FP32_G64 - the state, the operator apply,
 // T_k, the projection term and the RK4 update in FP32, the Gram matrix
 // accumulated in FP64 from the exact products of FP32 entries (an FP32
@@ -37,6 +42,7 @@
 #include <vector>
 
 #include "lr_internal.cuh"
+#include "lr_sparse_fused.cuh"
 
 namespace lr {
 namespace {
@@ -532,6 +538,9 @@ using namespace lr;
 struct lr_sparse {
   int N, M, K, T, n_levels, nblk, ntile;
   int fp32;   // 1: FP32_G64 state arithmetic
+  int fused;  // 1: the fused persistent kernel (FP32_G64), 0: four launches per RK4 stage
+  int n_cta;  // fused: persistent CTAs (one trajectory at a time each)
+  size_t o_fsc;   // fused: per-CTA stage buffers
   long nnz, max_steps, n_rec, step;
   double dt;   // RK4 step of the run (0 before the first integrate)
   int pop_every;
@@ -594,7 +603,44 @@ void layout(lr_sparse* s) {
   s->o_pops = take((size_t)s->T * s->n_rec * s->n_levels * sizeof(double));
   s->o_nphot = take((size_t)s->T * s->n_rec * sizeof(double));
   s->o_trace = take((size_t)s->T * s->n_rec * sizeof(double));
+  if (s->fused) {
+    const size_t Mp = (size_t)(s->M + 3) / 4 * 4;
+    s->o_fsc = take((size_t)s->n_cta * (3 + s->K + 1) * s->N * Mp * sizeof(float2));
+  }
   s->total = o;
+}
+
+// Dynamic shared memory of the fused kernel: G and L^-1 (FP64-sized complex
+// [Mp][Mp+1]), T_k and XT_k (FP32 complex [K][Mp][Mp]), scalars.
+struct SfSmem {
+  int o_gd, o_w, o_tred, o_xt, o_misc, total;
+};
+SfSmem sf_smem(int M, int K) {
+  const int Mp = (M + 3) / 4 * 4;
+  SfSmem L;
+  int o = 0;
+  L.o_gd = o;
+  o += Mp * (Mp + 1) * (int)sizeof(double2);
+  L.o_w = o;
+  o += Mp * (Mp + 1) * (int)sizeof(double2);
+  L.o_tred = o;
+  o += K * Mp * Mp * (int)sizeof(float2);
+  L.o_xt = o;
+  o += K * Mp * Mp * (int)sizeof(float2);
+  L.o_misc = o;
+  o += 96 * (int)sizeof(double);
+  L.total = o;
+  return L;
+}
+
+cudaError_t raise_fused_smem(int bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, sfz::sf_kernel);
+  if (e != cudaSuccess) return e;
+  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(sfz::sf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 SpDev dev(const lr_sparse* s) {
@@ -792,6 +838,21 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   }
   s->ws = nullptr;
   s->ws_bytes = 0;
+  // the fused kernel: FP32_G64, unless LR_SPARSE_FUSED=0 selects the four-launch path;
+  // one persistent CTA per SM (fewer when the batch is smaller)
+  s->fused = 0;
+  s->n_cta = 0;
+  const char* fz_env = getenv("LR_SPARSE_FUSED");
+  if (s->fp32 && !(fz_env && strcmp(fz_env, "0") == 0)) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                   cudaSuccess && sms > 0) {
+      s->fused = 1;
+      s->n_cta = std::min(n_traj, sms);
+    } else {
+      cudaGetLastError();
+    }
+  }
   layout(s);
   *out = s;
   return LR_OK;
@@ -917,10 +978,49 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const SpDev d = dev(s);
   const SpParams p = params(s);
-  if (s->fp32)
+  if (s->fused) {
+    const SfSmem L = sf_smem(s->M, s->K);
+    cudaError_t e0 = raise_fused_smem(L.total);
+    if (e0 != cudaSuccess) return cuda_fail(s, e0);
+    sfz::Args a{};
+    a.rowptr = d.rowptr;
+    a.col = d.col;
+    a.valf = d.valf;
+    a.chan = d.chan;
+    a.level = d.level;
+    a.pulse = d.pulse;
+    a.err = d.err;
+    a.Z = static_cast<float2*>(d.Z);
+    a.scratch = reinterpret_cast<float2*>(s->ws + s->o_fsc);
+    a.beta = d.beta;
+    a.pops = d.pops;
+    a.nphot = d.nphot;
+    a.trace = d.trace;
+    a.N = s->N;
+    a.M = s->M;
+    a.Mp = (s->M + 3) / 4 * 4;
+    a.K = s->K;
+    a.T = s->T;
+    a.n_levels = s->n_levels;
+    a.wd = s->wd;
+    a.tau = s->tau;
+    a.dt = dt;
+    a.max_steps = s->max_steps;
+    a.n_rec = s->n_rec;
+    a.pop_every = s->pop_every;
+    a.step0 = s->step;
+    a.n_steps = n_steps;
+    a.o_gd = L.o_gd;
+    a.o_w = L.o_w;
+    a.o_tred = L.o_tred;
+    a.o_xt = L.o_xt;
+    a.o_misc = L.o_misc;
+    sfz::sf_kernel<<<s->n_cta, sfz::NT, L.total, st>>>(a);
+  } else if (s->fp32) {
     launch_step_kernels<float2>(s, d, p, s->step, n_steps, dt, st);
-  else
+  } else {
     launch_step_kernels<double2>(s, d, p, s->step, n_steps, dt, st);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e);
   s->step += n_steps;
@@ -976,6 +1076,12 @@ extern "C" lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, doub
     if (ion) ion[c] = h[3 * c + 1];
     if (loss) loss[c] = h[3 * c + 2];
   }
+  return LR_OK;
+}
+
+extern "C" lr_status lr_sparse_query(const lr_sparse* s, int* fused) {
+  if (!s || !fused) return LR_ERR_ARG;
+  *fused = s->fused;
   return LR_OK;
 }
 

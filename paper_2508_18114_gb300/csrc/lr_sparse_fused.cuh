@@ -1,0 +1,613 @@
+#pragma once
+// Fused persistent kernel of the sparse-operator engine (FP32 state with the
+// FP64-class Gram matrix): the paper's normal-mode model of Sec. S2, or any
+// operator set given as CSR rows with time channels, integrated by one launch
+// per lr_sparse_integrate call.
+//
+// One CTA integrates one trajectory at a time (persistent over the batch).
+// The stage input Z_s, the operator images Y_k = L_k(t) Z_s (and r(t) Z_s at
+// the first stage of a step) and the RK4 accumulator live in a per-CTA global
+// region that stays L2-resident; every phase of a stage runs inside the CTA,
+// separated by block barriers only:
+//   C  channel factors Omega(t)^a e^{i q w_d t} of the stage time (FP64,
+//      rounded once to FP32);
+//   Y  Y_k = L_k(t) Z_s by CSR gathers; at the first stage of every step also
+//      r(t) Z_s, the readout signal beta = tr(Z_s^dag r Z_s) and, at recording
+//      steps, the photon number |r Z_s|^2 (FP64 sums in a fixed order);
+//   P  warp tasks over 4 x 4 tiles: G = Z_s^dag Z_s (upper tiles, exact FP32
+//      products in double-word sums) and T_k = Z_s^dag Y_k (FP32), each tile
+//      summed over all rows and reduced over the warp by recursive halving;
+//   R  G = L D L^dag, L^-1 and G^-1 in double-word FP32 (~2^-48 relative),
+//      X_k = G^-1 T_k and XT_k[l][m] = 1/2 conj(X_k[m][l]) in FP32;
+//   F  F = A(t) Z_s (A = -i H_eff, CSR gathers) + sum_k Y_k XT_k and the
+//      classical RK4 stage update; the next stage input goes to the other
+//      Z_s buffer, the accumulator and Z_n are updated in place.
+#include "lr_internal.cuh"
+
+namespace lr {
+namespace sfz {
+
+constexpr int NT = 384;
+constexpr int NWARP = NT / 32;
+constexpr int NCH = 10;   // time channels
+constexpr int TP = 4;     // phase-P tile edge
+constexpr int TR = 4;     // phase-F rows per thread tile
+
+struct Args {
+  const int* rowptr;   // [(K + 2) (N + 1)]
+  const int* col;
+  const float2* valf;
+  const unsigned char* chan;
+  const int* level;
+  const PulseDev* pulse;   // per trajectory
+  unsigned* err;
+  float2* Z;               // state [T][N][M]
+  float2* scratch;         // per CTA: Z_s [2][N][Mp], Y [K + 1][N][Mp], accumulator [N][Mp]
+  double2* beta;           // [T][max_steps + 1]
+  double *pops, *nphot, *trace;
+  int N, M, Mp, K, T, n_levels;
+  double wd, tau, dt;
+  long max_steps, n_rec;
+  int pop_every;
+  long step0, n_steps;
+  // byte offsets in dynamic shared memory
+  int o_gd, o_w, o_tred, o_xt, o_misc;
+};
+
+struct DW {
+  float hi, lo;
+};
+__device__ __forceinline__ void dw_add_prod(DW& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+__device__ __forceinline__ void dw_add(DW& s, const DW& o) {
+  const float t = s.hi + o.hi;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (o.hi - bp);
+  s.hi = t;
+  s.lo += err + o.lo;
+}
+__device__ __forceinline__ DW dw_make(double x) {
+  DW r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ DW dw_sum(DW a, DW b) {
+  const float s = a.hi + b.hi, bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  DW r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+__device__ __forceinline__ DW dw_neg(DW a) {
+  a.hi = -a.hi;
+  a.lo = -a.lo;
+  return a;
+}
+__device__ __forceinline__ DW dw_mul(DW a, DW b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  DW r;
+  r.hi = p + e;
+  r.lo = e - (r.hi - p);
+  return r;
+}
+// 1/p for p > 0: one Newton step r + r (1 - p r) in double-word from the FP32 quotient
+__device__ __forceinline__ DW dw_recip(DW p) {
+  DW r0{1.0f / p.hi, 0.0f};
+  const DW one{1.0f, 0.0f};
+  const DW e = dw_sum(one, dw_neg(dw_mul(p, r0)));
+  return dw_sum(r0, dw_mul(r0, e));
+}
+struct DWC {
+  DW re, im;
+};
+__device__ __forceinline__ DWC dwc_mul_conj(const DWC& x, const DWC& y) {   // x conj(y)
+  DWC r;
+  r.re = dw_sum(dw_mul(x.re, y.re), dw_mul(x.im, y.im));
+  r.im = dw_sum(dw_mul(x.im, y.re), dw_neg(dw_mul(x.re, y.im)));
+  return r;
+}
+__device__ __forceinline__ DWC dwc_mul(const DWC& x, const DWC& y) {
+  DWC r;
+  r.re = dw_sum(dw_mul(x.re, y.re), dw_neg(dw_mul(x.im, y.im)));
+  r.im = dw_sum(dw_mul(x.re, y.im), dw_mul(x.im, y.re));
+  return r;
+}
+__device__ __forceinline__ DWC dwc_sub(const DWC& a, const DWC& b) {
+  DWC r;
+  r.re = dw_sum(a.re, dw_neg(b.re));
+  r.im = dw_sum(a.im, dw_neg(b.im));
+  return r;
+}
+__device__ __forceinline__ DWC dwc_add(const DWC& a, const DWC& b) {
+  DWC r;
+  r.re = dw_sum(a.re, b.re);
+  r.im = dw_sum(a.im, b.im);
+  return r;
+}
+__device__ __forceinline__ DWC dwc_scale(const DWC& a, DW s) {
+  DWC r;
+  r.re = dw_mul(a.re, s);
+  r.im = dw_mul(a.im, s);
+  return r;
+}
+
+__device__ __forceinline__ void load4(const float2* p, float2 (&v)[4]) {
+  const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
+  v[0] = make_float2(x.x, x.y);
+  v[1] = make_float2(x.z, x.w);
+  v[2] = make_float2(y.x, y.y);
+  v[3] = make_float2(y.z, y.w);
+}
+__device__ __forceinline__ void store4(float2* p, const float2 (&v)[4]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+
+// Reduce-scatter of 32 values over the warp (recursive halving, fixed order):
+// lane L ends with the total of value L in v[0].
+template <typename V, typename Add>
+__device__ __forceinline__ void reduce_scatter32(V (&v)[32], int lane, Add add) {
+#pragma unroll
+  for (int lev = 0; lev < 5; ++lev) {
+    const int o = 16 >> lev;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < (16 >> lev); ++k) {
+      V keep = up ? v[k + (16 >> lev)] : v[k];
+      const V send = up ? v[k] : v[k + (16 >> lev)];
+      add(keep, send, o);
+      v[k] = keep;
+    }
+  }
+}
+
+// acc[u] += sum over the CSR row n of operator `op` of chi[ch] val * Z[col][m0 + u]
+__device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0, const float2* __restrict__ zs,
+                                            const float2* chi, float2 (&acc)[4]) {
+  const int* rp = a.rowptr + (size_t)op * (a.N + 1);
+  const int e1 = rp[n + 1];
+  for (int e = rp[n]; e < e1; ++e) {
+    const float2 c = chi[a.chan[e]], v = a.valf[e];
+    const float wr = c.x * v.x - c.y * v.y, wi = c.x * v.y + c.y * v.x;
+    float2 z[4];
+    load4(zs + (size_t)a.col[e] * a.Mp + m0, z);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[u].x = fmaf(wr, z[u].x, fmaf(-wi, z[u].y, acc[u].x));
+      acc[u].y = fmaf(wr, z[u].y, fmaf(wi, z[u].x, acc[u].y));
+    }
+  }
+}
+
+// Fixed-order block sum of NV doubles per thread; the totals are returned to
+// every thread. red: NWARP * NV doubles of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int tid) {
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) red[warp * NV + c] = v[c];
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    double s = 0.0;
+    for (int w = 0; w < NWARP; ++w) s += red[w * NV + c];
+    v[c] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
+  __shared__ float2 chi[NCH];
+  __shared__ double red[NWARP * 4];
+  __shared__ int task_ctr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = a.N, M = a.M, Mp = a.Mp, K = a.K, MM = Mp * Mp;
+  const int Mq = (M + 3) / 4 * 4;
+  const int ldg = Mp + 1;
+  for (int i = tid; i < LR_MAX_RANK; i += NT)
+    for (int j = 0; j <= i; ++j) tri[i * (i + 1) / 2 + j] = make_short2((short)i, (short)j);
+  double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);   // [Mp][Mp+1]  G -> L -> G^-1
+  double2* W = reinterpret_cast<double2*>(smem + a.o_w);     // [Mp][Mp+1]  L^-1
+  float2* Tred = reinterpret_cast<float2*>(smem + a.o_tred);  // [K][Mp*Mp]  T_k
+  float2* XT = reinterpret_cast<float2*>(smem + a.o_xt);      // [K][Mp][Mp] (l, m)
+  double* misc = reinterpret_cast<double*>(smem + a.o_misc);  // [0] not-PD flag, [32..64) 1/D, [64..] populations
+  const size_t zsb = (size_t)N * Mp;
+  float2* zs0 = a.scratch + (size_t)blockIdx.x * (size_t)(3 + K + 1) * zsb;
+  float2* ybuf = zs0 + 2 * zsb;              // Y_1 .. Y_K, then r Z_s
+  float2* accg = zs0 + (2 + K + 1) * zsb;
+  const double dt = a.dt;
+  const int pe = a.pop_every;
+
+  for (int tj = blockIdx.x; tj < a.T; tj += gridDim.x) {
+    const PulseDev pulse = a.pulse[tj];
+    float2* Zn = a.Z + (size_t)tj * N * M;
+    for (long long e = tid; e < (long long)N * Mp; e += NT) {
+      const int n = (int)(e / Mp), m = (int)(e - (long long)n * Mp);
+      zs0[e] = m < M ? Zn[(size_t)n * M + m] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    int cur = 0;
+    const long s_end = a.step0 + a.n_steps;
+    for (long step = a.step0;; ++step) {
+      const bool last = step == s_end;
+      for (int stage = 0; stage < 4; ++stage) {
+        const bool record = stage == 0 && (step % pe) == 0;
+        const float2* zc = zs0 + (size_t)cur * zsb;
+        // ================= C: channel factors of the stage time
+        if (tid < NCH) {
+          const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
+          const int ach = tid / 5, q = tid % 5 - 2;
+          const double om = ach ? pulse_envelope(pulse, a.tau, ts) : 1.0;
+          double sn, cs;
+          sincos((double)q * a.wd * ts, &sn, &cs);
+          chi[tid] = make_float2((float)(om * cs), (float)(om * sn));
+        }
+        if (tid == 0) task_ctr = 0;
+        __syncthreads();
+        // ================= Y: operator images, readout signal
+        {
+          const int nk = stage == 0 ? K + 1 : K;
+          const int mq = Mq / 4;
+          double acc3[3] = {0.0, 0.0, 0.0};   // Re, Im tr(Z^dag r Z), |r Z|^2
+          for (long long t = tid; t < (long long)N * mq * nk; t += NT) {
+            const int k = (int)(t / ((long long)N * mq));
+            const int rem = (int)(t - (long long)k * N * mq), n = rem / mq, m0 = (rem - n * mq) * 4;
+            float2 y[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                           make_float2(0.f, 0.f)};
+            row_gather4(a, 1 + k, n, m0, zc, chi, y);
+            store4(ybuf + (size_t)k * zsb + (size_t)n * Mp + m0, y);
+            if (k == K) {
+              float2 z[4];
+              load4(zc + (size_t)n * Mp + m0, z);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {   // padding columns are zero
+                const double zx = z[u].x, zy = z[u].y, yx = y[u].x, yy = y[u].y;
+                acc3[0] += zx * yx + zy * yy;
+                acc3[1] += zx * yy - zy * yx;
+                acc3[2] += yx * yx + yy * yy;
+              }
+            }
+          }
+          if (stage == 0) {
+            block_sum<3>(acc3, red, tid);
+            if (tid == 0) {
+              a.beta[(size_t)tj * (a.max_steps + 1) + step] = mk(acc3[0], acc3[1]);
+              if (!isfinite(acc3[0]) || !isfinite(acc3[1])) set_error(a.err, DEV_NONFINITE);
+              if (record) a.nphot[(size_t)tj * a.n_rec + step / pe] = acc3[2];
+            }
+          }
+          if (record) {
+            // level populations: warp per level, fixed order over the rows
+            for (int lv = warp; lv < a.n_levels; lv += NWARP) {
+              double s = 0.0;
+              for (int n = lane; n < N; n += 32) {
+                if (a.level[n] != lv) continue;
+                const float2* z = zc + (size_t)n * Mp;
+                for (int m = 0; m < M; ++m) s += (double)z[m].x * z[m].x + (double)z[m].y * z[m].y;
+              }
+              for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+              if (lane == 0) misc[64 + lv] = s;
+            }
+          }
+          __syncthreads();
+          if (record && tid == 0) {
+            const long rec = step / pe;
+            double tr = 0.0;
+            for (int lv = 0; lv < a.n_levels; ++lv) {
+              a.pops[((size_t)tj * a.n_rec + rec) * a.n_levels + lv] = misc[64 + lv];
+              tr += misc[64 + lv];
+            }
+            a.trace[(size_t)tj * a.n_rec + rec] = tr;
+          }
+        }
+        if (last) break;
+        // ================= P: Gram and T_k tiles over all rows
+        {
+          const int nt_ = Mq / TP;
+          const int n_g = nt_ * (nt_ + 1) / 2, n_t = K * nt_ * nt_;
+          for (;;) {
+            int task = 0;
+            if (lane == 0) task = atomicAdd(&task_ctr, 1);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (task >= n_g + n_t) break;
+            if (task < n_g) {
+              int ti = 0, rem = task;
+              while (rem >= nt_ - ti) {
+                rem -= nt_ - ti;
+                ++ti;
+              }
+              const int tj2 = ti + rem, i0 = ti * TP, j0 = tj2 * TP;
+              DW acc[TP][TP][2];
+#pragma unroll
+              for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TP; ++j) acc[i][j][0] = acc[i][j][1] = DW{0.f, 0.f};
+              for (int n = lane; n < N; n += 32) {
+                float2 zi[4], zj[4];
+                load4(zc + (size_t)n * Mp + i0, zi);
+                load4(zc + (size_t)n * Mp + j0, zj);
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) {   // conj(zi) zj
+                    if (ti == tj2 && j < i) continue;
+                    dw_add_prod(acc[i][j][0], zi[i].x, zj[j].x);
+                    dw_add_prod(acc[i][j][0], zi[i].y, zj[j].y);
+                    dw_add_prod(acc[i][j][1], zi[i].x, zj[j].y);
+                    dw_add_prod(acc[i][j][1], -zi[i].y, zj[j].x);
+                  }
+              }
+              DW v[32];
+#pragma unroll
+              for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TP; ++j)
+#pragma unroll
+                  for (int c = 0; c < 2; ++c) v[(i * 4 + j) * 2 + c] = acc[i][j][c];
+              reduce_scatter32(v, lane, [](DW& keep, const DW& send, int o) {
+                DW t;
+                t.hi = __shfl_xor_sync(0xffffffffu, send.hi, o);
+                t.lo = __shfl_xor_sync(0xffffffffu, send.lo, o);
+                dw_add(keep, t);
+              });
+              const int i = i0 + (lane >> 3), j = j0 + ((lane >> 1) & 3), c = lane & 1;
+              const double val = (double)v[0].hi + (double)v[0].lo;
+              if (i <= j) {   // G[i][j] and its conjugate G[j][i]
+                reinterpret_cast<double*>(Gd)[2 * (i * ldg + j) + c] = val;
+                reinterpret_cast<double*>(Gd)[2 * (j * ldg + i) + c] = c ? -val : val;
+              }
+            } else {
+              const int t2 = task - n_g, k = t2 / (nt_ * nt_), r2 = t2 - k * nt_ * nt_, ti = r2 / nt_,
+                        tj2 = r2 - ti * nt_;
+              const int i0 = ti * TP, j0 = tj2 * TP;
+              const float2* yk = ybuf + (size_t)k * zsb;
+              float tr_[TP][TP], ti_[TP][TP];
+#pragma unroll
+              for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TP; ++j) tr_[i][j] = ti_[i][j] = 0.f;
+              for (int n = lane; n < N; n += 32) {
+                float2 z[4], y[4];
+                load4(zc + (size_t)n * Mp + i0, z);
+                load4(yk + (size_t)n * Mp + j0, y);
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                  for (int j = 0; j < TP; ++j) {   // conj(z_i) y_j
+                    tr_[i][j] = fmaf(z[i].x, y[j].x, fmaf(z[i].y, y[j].y, tr_[i][j]));
+                    ti_[i][j] = fmaf(z[i].x, y[j].y, fmaf(-z[i].y, y[j].x, ti_[i][j]));
+                  }
+              }
+              float v[32];
+#pragma unroll
+              for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TP; ++j) {
+                  v[(i * 4 + j) * 2] = tr_[i][j];
+                  v[(i * 4 + j) * 2 + 1] = ti_[i][j];
+                }
+              reduce_scatter32(v, lane, [](float& keep, const float& send, int o) {
+                keep += __shfl_xor_sync(0xffffffffu, send, o);
+              });
+              const int i = i0 + (lane >> 3), j = j0 + ((lane >> 1) & 3), c = lane & 1;
+              reinterpret_cast<float*>(Tred)[2 * (k * MM + i * Mp + j) + c] = v[0];
+            }
+          }
+        }
+        __syncthreads();
+        // ================= R: G = L D L^dag, L^-1, G^-1 (double-word FP32), XT_k
+        {
+          DWC* Gw = reinterpret_cast<DWC*>(Gd);
+          DWC* Ww = reinterpret_cast<DWC*>(W);
+          DW* dinv = reinterpret_cast<DW*>(misc + 32);   // [M] 1 / D[k]
+          float* diag0 = reinterpret_cast<float*>(W);    // W[k][0] slot: the diagonal of G
+          if (tid == 0) misc[0] = 0.0;
+          for (int e = tid; e < M * (M + 1) / 2; e += NT) {
+            const int i = tri[e].x, j = tri[e].y;
+            const double2 v = Gd[i * ldg + j];
+            DWC g;
+            g.re = dw_make(v.x);
+            g.im = dw_make(v.y);
+            if (i == j) diag0[i * ldg * 4] = (float)v.x;
+            Gw[i * ldg + j] = g;
+          }
+          auto pivot = [&](int k) {
+            const DW piv = Gw[k * ldg + k].re;
+            if (!(piv.hi > 1e-13f * diag0[k * ldg * 4]) || !isfinite(piv.hi) || piv.hi < 1e-30f) {
+              misc[0] = 1.0;
+              dinv[k] = DW{1.0f, 0.0f};
+            } else {
+              dinv[k] = dw_recip(piv);
+            }
+          };
+          __syncthreads();
+          if (tid == 0) pivot(0);
+          __syncthreads();
+          for (int k = 0; k < M; ++k) {
+            const DW rk = dinv[k];
+            const int w = M - k - 1;
+            for (int e = tid; e < w * (w + 1) / 2; e += NT) {
+              const int i = k + 1 + tri[e].x, j = k + 1 + tri[e].y;
+              const DWC t = dwc_scale(dwc_mul_conj(Gw[i * ldg + k], Gw[j * ldg + k]), rk);
+              Gw[i * ldg + j] = dwc_sub(Gw[i * ldg + j], t);
+            }
+            if (tid == 0 && k + 1 < M) pivot(k + 1);
+            __syncthreads();
+          }
+          if (tid == 0 && misc[0] != 0.0) set_error(a.err, DEV_NOT_PD);
+          // W = L^-1 by columns (warp j mod NWARP, lane i = row i)
+          for (int j = warp; j < M; j += NWARP) {
+            DWC wv;
+            wv.re.hi = lane == j ? 1.0f : 0.0f;
+            wv.re.lo = wv.im.hi = wv.im.lo = 0.0f;
+            for (int k = j; k < M - 1; ++k) {
+              DWC wk;
+              wk.re.hi = __shfl_sync(0xffffffffu, wv.re.hi, k);
+              wk.re.lo = __shfl_sync(0xffffffffu, wv.re.lo, k);
+              wk.im.hi = __shfl_sync(0xffffffffu, wv.im.hi, k);
+              wk.im.lo = __shfl_sync(0xffffffffu, wv.im.lo, k);
+              if (lane > k && lane < M) wv = dwc_sub(wv, dwc_mul(dwc_scale(Gw[lane * ldg + k], dinv[k]), wk));
+            }
+            if (lane < M) Ww[lane * ldg + j] = wv;
+          }
+          __syncthreads();
+          // G^-1 = W^dag D^-1 W, rounded once to FP32 (into the storage of L)
+          float2* Gi = reinterpret_cast<float2*>(Gd);
+          for (int e = tid; e < M * M; e += NT) {
+            const int i = e / M, j = e - i * M;
+            if (i > j) continue;
+            DWC acc;
+            acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
+            for (int k = j; k < M; ++k)
+              acc = dwc_add(acc, dwc_scale(dwc_mul_conj(Ww[k * ldg + j], Ww[k * ldg + i]), dinv[k]));
+            const float re = acc.re.hi + acc.re.lo, im = acc.im.hi + acc.im.lo;
+            Gi[i * Mp + j] = make_float2(re, im);
+            if (i != j) Gi[j * Mp + i] = make_float2(re, -im);
+          }
+          __syncthreads();
+          // XT_k[l][m] = 1/2 conj(X_k[m][l]), X_k = G^-1 T_k (the 1/2 of Eq. S5)
+          for (int e = tid; e < K * Mq * Mq; e += NT) {
+            const int k = e / (Mq * Mq), lq = e - k * (Mq * Mq), l = lq / Mq, m = lq - l * Mq;
+            float xr = 0.f, xi = 0.f;
+            if (l < M && m < M) {
+              const float2* Tk = Tred + k * MM;
+              for (int j = 0; j < M; ++j) {
+                const float2 g = Gi[m * Mp + j], t = Tk[j * Mp + l];
+                xr = fmaf(g.x, t.x, fmaf(-g.y, t.y, xr));
+                xi = fmaf(g.x, t.y, fmaf(g.y, t.x, xi));
+              }
+            }
+            XT[k * MM + l * Mp + m] = make_float2(0.5f * xr, -0.5f * xi);
+          }
+          __syncthreads();
+        }
+        // ================= F: A Z_s + projection, RK4 stage update
+        {
+          const double hsd = stage == 2 ? dt : 0.5 * dt, h6d = dt / 6.0;
+          const float hs_hi = (float)hsd, hs_lo = (float)(hsd - (double)hs_hi);
+          const float h6_hi = (float)h6d, h6_lo = (float)(h6d - (double)h6_hi);
+          const bool zn_vec = (M % 2) == 0;
+          float2* zo_buf = zs0 + (size_t)(cur ^ 1) * zsb;
+          const int mq = Mq / 4, nrt = (N + TR - 1) / TR;
+          for (int tile = tid; tile < nrt * mq; tile += NT) {
+            const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = rt * TR;
+            float2 f[TR][4];
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) f[r][u] = make_float2(0.f, 0.f);
+              if (l0 + r < N) row_gather4(a, 0, l0 + r, m0, zc, chi, f[r]);
+            }
+            // + sum_k Y_k XT_k: l in pairs, 16-byte loads of the Y rows
+            for (int k = 0; k < K; ++k) {
+              const float2* yk = ybuf + (size_t)k * zsb;
+              const float2* xk = XT + k * MM;
+              for (int l = 0; l < Mq; l += 2) {
+                float4 y2[TR];
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+                  y2[r] = l0 + r < N ? *reinterpret_cast<const float4*>(yk + (size_t)(l0 + r) * Mp + l)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int ll = 0; ll < 2; ++ll) {
+                  const float4 xa = reinterpret_cast<const float4*>(xk + (l + ll) * Mp + m0)[0];
+                  const float4 xb = reinterpret_cast<const float4*>(xk + (l + ll) * Mp + m0)[1];
+                  const float2 x[4] = {make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xb.x, xb.y),
+                                       make_float2(xb.z, xb.w)};
+#pragma unroll
+                  for (int r = 0; r < TR; ++r) {
+                    const float yx = ll ? y2[r].z : y2[r].x, yy = ll ? y2[r].w : y2[r].y;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                      f[r][u].x = fmaf(yx, x[u].x, fmaf(-yy, x[u].y, f[r][u].x));
+                      f[r][u].y = fmaf(yx, x[u].y, fmaf(yy, x[u].x, f[r][u].y));
+                    }
+                  }
+                }
+              }
+            }
+            // RK4 (weights 1/6, 1/3, 1/3, 1/6), step sizes as hi + lo floats
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+              const int n = l0 + r;
+              if (n >= N) continue;
+              float2 zo[4];
+#pragma unroll
+              for (int pr = 0; pr < 2; ++pr) {
+                const int u0 = 2 * pr, m = m0 + u0;
+                if (m >= M) {
+                  zo[u0] = zo[u0 + 1] = make_float2(0.f, 0.f);
+                  continue;
+                }
+                const bool two = m + 1 < M;
+                const size_t oz = (size_t)n * M + m, oa = (size_t)n * Mp + m;
+                float2 zn0, zn1 = make_float2(0.f, 0.f);
+                if (zn_vec) {
+                  const float4 v = *reinterpret_cast<const float4*>(Zn + oz);
+                  zn0 = make_float2(v.x, v.y);
+                  zn1 = make_float2(v.z, v.w);
+                } else {
+                  zn0 = Zn[oz];
+                  if (two) zn1 = Zn[oz + 1];
+                }
+                float4* ap = reinterpret_cast<float4*>(accg + oa);
+                const float f0r = f[r][u0].x, f0i = f[r][u0].y, f1r = f[r][u0 + 1].x, f1i = f[r][u0 + 1].y;
+                if (stage < 3) {
+                  if (stage == 0) {
+                    *ap = make_float4(f0r, f0i, f1r, f1i);
+                  } else {
+                    const float4 ac = *ap;
+                    *ap = make_float4(fmaf(2.f, f0r, ac.x), fmaf(2.f, f0i, ac.y), fmaf(2.f, f1r, ac.z),
+                                      fmaf(2.f, f1i, ac.w));
+                  }
+                  zo[u0] = make_float2(zn0.x + fmaf(hs_lo, f0r, hs_hi * f0r), zn0.y + fmaf(hs_lo, f0i, hs_hi * f0i));
+                  zo[u0 + 1] = two ? make_float2(zn1.x + fmaf(hs_lo, f1r, hs_hi * f1r),
+                                                 zn1.y + fmaf(hs_lo, f1i, hs_hi * f1i))
+                                   : make_float2(0.f, 0.f);
+                } else {
+                  const float4 ac = *ap;
+                  const float s0r = ac.x + f0r, s0i = ac.y + f0i, s1r = ac.z + f1r, s1i = ac.w + f1i;
+                  zo[u0] = make_float2(zn0.x + fmaf(h6_lo, s0r, h6_hi * s0r), zn0.y + fmaf(h6_lo, s0i, h6_hi * s0i));
+                  zo[u0 + 1] = two ? make_float2(zn1.x + fmaf(h6_lo, s1r, h6_hi * s1r),
+                                                 zn1.y + fmaf(h6_lo, s1i, h6_hi * s1i))
+                                   : make_float2(0.f, 0.f);
+                  if (zn_vec) {
+                    *reinterpret_cast<float4*>(Zn + oz) = make_float4(zo[u0].x, zo[u0].y, zo[u0 + 1].x, zo[u0 + 1].y);
+                  } else {
+                    Zn[oz] = zo[u0];
+                    if (two) Zn[oz + 1] = zo[u0 + 1];
+                  }
+                }
+              }
+              store4(zo_buf + (size_t)n * Mp + m0, zo);
+            }
+          }
+          cur ^= 1;
+          __syncthreads();
+        }
+      }
+      if (last) break;
+    }
+  }
+}
+
+}  // namespace sfz
+}  // namespace lr

@@ -1,0 +1,136 @@
+"""The readout of Fig. 2 and the timing of Table 1 on this GPU: the paper's
+normal-mode model (Sec. S2, N = N_l N_u N_t = 100 x 4 x 5 = 2000) driven by the
+square pulse of the paper's figure (|Omega_d| / 2 pi = 150 MHz, logistic edges
+with sigma = 0.5 ns, tau = 40 ns), from |g> and |e>, integrated
+
+* by the full master equation (lr_full_*, FP64, the N x N density matrix), and
+* by the low-rank ansatz of rank M (lr_sparse_*, FP64 on the four-launch
+  path, and FP32 bulk with the FP64-class Gram matrix on the fused kernel),
+
+with RK4 at dt = 0.5 ps. Output (JSON): the readout signals beta_g(t), beta_e(t)
+and photon numbers n(t) of both methods every `--every` steps, the relative
+deviation delta = |y_full - y_LRA| / |y_full| of beta and n, the assignment
+error of each method (Sec. S3.A), and the wall time of each run.
+
+    python -m paper_2508_18114_gb300.fig2 --out fig2.json [--steps 80000]
+
+Argument marshalling and bookkeeping only: every step runs in liblr.so.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+TWO_PI = 2.0 * math.pi
+
+
+def paper_params():
+    """Sec. S2.B (rad/ns, 1/ns)."""
+    Ec = TWO_PI * 0.315
+    return dict(Ec=Ec, Ej=51.0 * Ec, wr=TWO_PI * 7.2, wf=TWO_PI * 7.21, g=TWO_PI * 0.15, J=TWO_PI * 0.03,
+                kappa=TWO_PI * 0.03, gamma=TWO_PI * 8e-6, wd=TWO_PI * 7.18)
+
+
+def assignment_error(beta_g, beta_e, dt, kappa, gamma, eta=0.6):
+    """Sec. S3.A: SNR = sqrt(2 eta kappa int |beta_e - beta_g|^2), trapezoid on the step grid."""
+    d2 = np.abs(np.asarray(beta_e) - np.asarray(beta_g)) ** 2
+    s = dt * (0.5 * d2[0] + d2[1:-1].sum() + 0.5 * d2[-1])
+    snr = math.sqrt(2.0 * eta * kappa * s)
+    return 0.5 * math.erfc(0.5 * snr) + 0.5 * (len(d2) - 1) * dt * gamma
+
+
+def run(steps=80000, dt=5e-4, M=20, every=100, amp_mhz=150.0, dims=(100, 4, 5), eps=1e-5, seed=1008,
+        fp32=True, device="cuda:0"):
+    import torch
+    from . import sparse
+    P = paper_params()
+    model = sparse.paper_model(*dims, **P)
+    tau = steps * dt
+    pulse = (0, [TWO_PI * amp_mhz * 1e-3, P["wd"], 2.5, 0.0])
+    out = {"model": "paper's normal-mode model, %s (N=%d), frame of the drive" % ("x".join(map(str, dims)),
+                                                                                  model["N"]),
+           "pulse": "flat-top %.0f MHz, sigma 0.5 ns, tau %.3g ns" % (amp_mhz, tau),
+           "dt_ns": dt, "steps": steps, "M": M, "every": every, "runs": {}}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    # full master equation, one trajectory at a time
+    full = {}
+    for lv, tag in ((0, "g"), (1, "e")):
+        f = sparse.FullME(model, pulse, tau, steps, pop_every=every, device=device)
+        f.set_initial(lv)
+        _, sec = timed(lambda: f.integrate(dt, steps))
+        full[tag] = dict(f.observables(), seconds=sec)
+        del f
+    out["runs"]["full_fp64"] = {"seconds_per_trajectory": [full["g"]["seconds"], full["e"]["seconds"]],
+                                "eps_a": assignment_error(full["g"]["beta"], full["e"]["beta"], dt, P["kappa"],
+                                                          P["gamma"])}
+    precs = ["fp64"] + (["fp32_g64"] if fp32 else [])
+    lra = {}
+    for prec in precs:
+        b = sparse.SparseBatch(model, M, [pulse, pulse], tau, steps, pop_every=every, precision=prec,
+                               device=device)
+        b.set_initial([0, 1], seed, eps)
+        _, sec = timed(lambda: b.integrate(dt, steps))
+        o = b.observables()
+        lra[prec] = o
+        out["runs"]["lra_%s" % prec] = {
+            "engine": "fused" if b.fused else "four launches per stage",
+            "seconds_g_and_e_together": sec,
+            "eps_a": assignment_error(o["beta"][0], o["beta"][1], dt, P["kappa"], P["gamma"])}
+        del b
+    ef = out["runs"]["full_fp64"]["eps_a"]
+    for prec in precs:
+        r = out["runs"]["lra_%s" % prec]
+        r["eps_a_rel_dev"] = abs(r["eps_a"] - ef) / ef
+        dev = {}
+        for j, tag in ((0, "g"), (1, "e")):
+            bf = full[tag]["beta"][::every]
+            bl = lra[prec]["beta"][j][::every]
+            nf, nl = full[tag]["nphot"], lra[prec]["nphot"][j]
+            dev[tag] = {"delta_beta_max": float(np.max(np.abs(bf - bl)[1:] / np.abs(bf)[1:])),
+                        "delta_beta_end": float(abs(bf[-1] - bl[-1]) / abs(bf[-1])),
+                        "delta_n_max": float(np.max(np.abs(nf - nl)[1:] / np.abs(nf)[1:])),
+                        "delta_n_end": float(abs(nf[-1] - nl[-1]) / abs(nf[-1]))}
+        r["deviation_from_full"] = dev
+    curves = {"t_ns": (np.arange(0, steps + 1, every) * dt).tolist()}
+    for tag in ("g", "e"):
+        b = full[tag]["beta"][::every]
+        curves["full_beta_%s" % tag] = [[float(z.real), float(z.imag)] for z in b]
+        curves["full_n_%s" % tag] = full[tag]["nphot"].tolist()
+    for prec in precs:
+        for j, tag in ((0, "g"), (1, "e")):
+            b = lra[prec]["beta"][j][::every]
+            curves["lra_%s_beta_%s" % (prec, tag)] = [[float(z.real), float(z.imag)] for z in b]
+            curves["lra_%s_n_%s" % (prec, tag)] = lra[prec]["nphot"][j].tolist()
+    out["curves"] = curves
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--steps", type=int, default=80000)
+    ap.add_argument("--dt", type=float, default=5e-4)
+    ap.add_argument("--M", type=int, default=20)
+    ap.add_argument("--every", type=int, default=100)
+    ap.add_argument("--no-fp32", action="store_true")
+    a = ap.parse_args()
+    res = run(steps=a.steps, dt=a.dt, M=a.M, every=a.every, fp32=not a.no_fp32)
+    with open(a.out, "w") as fh:
+        json.dump(res, fh)
+    summary = {k: v for k, v in res.items() if k != "curves"}
+    print(json.dumps(summary, indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -39,7 +39,10 @@ EXPORTS = (
     "lr_paper_model_size", "lr_paper_model_build", "lr_sparse_create", "lr_sparse_workspace_size",
     "lr_sparse_bind_workspace", "lr_sparse_set_initial", "lr_sparse_set_state", "lr_sparse_get_state",
     "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_loss", "lr_sparse_last_error",
-    "lr_sparse_destroy", "lr_grow_rank", "lr_measure_peak",
+    "lr_sparse_destroy", "lr_grow_rank", "lr_measure_peak", "lr_sparse_query",
+    "lr_full_create", "lr_full_workspace_size", "lr_full_bind_workspace", "lr_full_set_initial",
+    "lr_full_set_state", "lr_full_get_state", "lr_full_integrate", "lr_full_observables", "lr_full_last_error",
+    "lr_full_destroy",
 )
 
 
@@ -122,13 +125,26 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_sparse_loss.argtypes = [vp, d, d, d, vp, vp, vp, vp]
     lib.lr_grow_rank.argtypes = [vp, vp, C.c_uint64, d, vp]
     lib.lr_measure_peak.argtypes = [i, C.POINTER(d), C.POINTER(d), vp]
+    lib.lr_sparse_query.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.lr_full_create.argtypes = [vp, C.POINTER(lr_pulse), d, l, i, C.POINTER(vp)]
+    lib.lr_full_workspace_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+    lib.lr_full_bind_workspace.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.lr_full_set_initial.argtypes = [vp, i, vp]
+    lib.lr_full_set_state.argtypes = [vp, vp, l, vp]
+    lib.lr_full_get_state.argtypes = [vp, vp, vp]
+    lib.lr_full_integrate.argtypes = [vp, d, l, vp]
+    lib.lr_full_observables.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.lr_full_last_error.argtypes = [vp]
+    lib.lr_full_last_error.restype = C.c_char_p
+    lib.lr_full_destroy.argtypes = [vp]
+    lib.lr_full_destroy.restype = None
     lib.lr_sparse_last_error.argtypes = [vp]
     lib.lr_sparse_last_error.restype = C.c_char_p
     lib.lr_sparse_destroy.argtypes = [vp]
     lib.lr_sparse_destroy.restype = None
     for name in EXPORTS:
         if name not in ("lr_status_string", "lr_last_error", "lr_destroy", "lr_sparse_last_error",
-                        "lr_sparse_destroy"):
+                        "lr_sparse_destroy", "lr_full_last_error", "lr_full_destroy"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

@@ -103,6 +103,13 @@ class SparseBatch:
         self._check(self._lib.lr_sparse_bind_workspace(h, C.c_void_p(self._ws_ptr), C.c_size_t(self.workspace_bytes),
                                                        C.c_void_p(_stream_ptr(None))))
 
+    @property
+    def fused(self) -> bool:
+        """True when the context runs the fused persistent kernel."""
+        f = C.c_int()
+        self._check(self._lib.lr_sparse_query(self._h, C.byref(f)))
+        return bool(f.value)
+
     def _check(self, st: int):
         if st != 0:
             msg = self._lib.lr_sparse_last_error(self._h)
@@ -147,4 +154,70 @@ class SparseBatch:
         h = getattr(self, "_h", None)
         if h is not None and self._lib is not None:
             self._lib.lr_sparse_destroy(h)
+            self._h = None
+
+
+class FullME:
+    """One trajectory of the full master equation (FP64, N x N density matrix)
+    for an operator set from ``paper_model`` (lr_full_*): the reference run that
+    low-rank batches of the same model are compared with and timed against."""
+
+    def __init__(self, model: dict, pulse, tau: float, max_steps: int, pop_every: int = 1, device="cuda:0"):
+        import torch
+        self._lib = load_library()
+        self.model = model
+        self._arrays = [np.ascontiguousarray(model[k], dtype=t) for k, t in
+                        (("rowptr", np.int32), ("col", np.int32), ("val", np.float64), ("chan", np.uint8),
+                         ("level", np.int32))]
+        rp, col, val, ch, lev = self._arrays
+        m = lr_sparse_model(int(model["N"]), int(model["n_jumps"]), int(model["n_levels"]), int(model["nnz"]),
+                            float(model["wd"]), _ptr(rp), _ptr(col), _ptr(val), _ptr(ch), _ptr(lev))
+        pl = pulse if isinstance(pulse, lr_pulse) else make_pulse(*pulse)
+        h = C.c_void_p()
+        st = self._lib.lr_full_create(C.byref(m), C.byref(pl), float(tau), int(max_steps), int(pop_every),
+                                      C.byref(h))
+        if st != 0:
+            raise LrError(st, "lr_full_create")
+        self._h = h
+        self.N, self.max_steps, self.pop_every = int(model["N"]), int(max_steps), int(pop_every)
+        self.n_rec = self.max_steps // self.pop_every + 1
+        sz = C.c_size_t()
+        self._check(self._lib.lr_full_workspace_size(h, C.byref(sz)))
+        self.workspace = torch.empty(int(sz.value) + 256, dtype=torch.uint8, device=torch.device(device))
+        ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        self._check(self._lib.lr_full_bind_workspace(h, C.c_void_p(ptr), sz, C.c_void_p(_stream_ptr(None))))
+
+    def _check(self, st: int):
+        if st != 0:
+            msg = self._lib.lr_full_last_error(self._h)
+            raise LrError(st, msg.decode() if msg else "")
+
+    def set_initial(self, psi: int, stream=None):
+        self._check(self._lib.lr_full_set_initial(self._h, int(psi), C.c_void_p(_stream_ptr(stream))))
+
+    def set_state(self, rho: np.ndarray, step: int = 0, stream=None):
+        r = np.ascontiguousarray(rho, dtype=np.complex128).reshape(self.N, self.N)
+        self._check(self._lib.lr_full_set_state(self._h, _ptr(r), int(step), C.c_void_p(_stream_ptr(stream))))
+
+    def get_state(self, stream=None) -> np.ndarray:
+        r = np.zeros((self.N, self.N), np.complex128)
+        self._check(self._lib.lr_full_get_state(self._h, _ptr(r), C.c_void_p(_stream_ptr(stream))))
+        return r
+
+    def integrate(self, dt: float, n_steps: int, stream=None):
+        self._check(self._lib.lr_full_integrate(self._h, float(dt), int(n_steps), C.c_void_p(_stream_ptr(stream))))
+
+    def observables(self, stream=None) -> dict:
+        beta = np.zeros(self.max_steps + 1, np.complex128)
+        pops = np.zeros((self.n_rec, int(self.model["n_levels"])))
+        nphot = np.zeros(self.n_rec)
+        trace = np.zeros(self.n_rec)
+        self._check(self._lib.lr_full_observables(self._h, _ptr(beta), _ptr(pops), _ptr(nphot), _ptr(trace),
+                                                  C.c_void_p(_stream_ptr(stream))))
+        return dict(beta=beta, pops=pops, nphot=nphot, trace=trace)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and self._lib is not None:
+            self._lib.lr_full_destroy(h)
             self._h = None

@@ -276,3 +276,33 @@ def test_two_contexts_keep_their_solve_memory():
     for b in (big, small):
         o = b.observables()
         assert np.all(np.isfinite(o["beta"])) and np.abs(o["trace"][:, -1] - 1.0).max() < 1e-3
+
+
+def test_fused_kernel_runs_fp32_and_matches_the_launch_path(monkeypatch):
+    """FP32_G64 contexts run the fused persistent kernel; it agrees with the
+    four-launch path (same precision split, different summation order) within
+    the FP32 rounding of a few hundred steps, on a batch with a ragged row
+    count (N = 150) and three trajectories."""
+    from paper_2508_18114_gb300 import sparse
+    P = _params(kappa=2.0, gamma=0.1)
+    wd = P["wd"]
+    model = sparse.paper_model(10, 3, 5, **P)
+    pulses = [(0, [TP * 0.8, wd, 0.05, 0.0]), (0, [TP * 0.5, wd, 0.05, 0.0]), (0, [TP * 0.3, wd, 0.05, 0.0])]
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("LR_SPARSE_FUSED", mode)
+        b = sparse.SparseBatch(model, 6, pulses, 0.3, 600, pop_every=50, precision="fp32_g64")
+        assert b.fused == (mode == "1")
+        b.set_initial([0, 1, 0], SEED, EPS)
+        b.integrate(5e-4, 257)
+        b.integrate(5e-4, 343)
+        out[mode] = b.observables()
+        del b
+    f, l = out["1"], out["0"]
+    assert np.abs(f["beta"] - l["beta"]).max() <= 5e-5 * np.abs(l["beta"]).max()
+    assert np.abs(f["pops"] - l["pops"]).max() <= 5e-5
+    assert np.abs(f["trace"] - l["trace"]).max() <= 5e-5
+    # FP64 contexts keep the four-launch path
+    monkeypatch.delenv("LR_SPARSE_FUSED")
+    b = sparse.SparseBatch(model, 6, pulses[:2], 0.3, 10, precision="fp64")
+    assert not b.fused
