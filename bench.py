@@ -664,16 +664,19 @@ def run_paper(args):
     fma_clk = FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK
     peak = SMS * fma_clk * 2 * mhz * 1e6 / 1e12
     achieved = fl / (ms * 1e-3 / args.steps) / 1e12
+    kname = ("sf_kernel (fused persistent sparse kernel, one launch per integrate)" if b.fused
+             else "integrate (sparse engine, 4 launches per RK4 stage)")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "integrate (sparse engine, 4 launches per RK4 stage)",
+                "traffic": None, "kernel": kname,
                 "peak_source": "%s FMA pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
                                % ("FP64" if prec == "fp64" else "FP32", fma_clk, mhz), "flops_per_step": fl}
     pm = pipe_peak_measured("fp64_fma" if prec == "fp64" else "fp32_fma", stream)
     roofline["peak_measured"] = pm
     roofline["frac_of_measured"] = achieved / pm if pm else None
-    # per RK4 step sp_chi + 4 x (apply, gram, solve, update); the closing observation
-    # pass sp_chi, apply, gram, solve; then sp_loss
-    launches = (17 * chunk + 4 + 1) * args.steps
+    # fused: one integrate launch and sp_loss per bench step; four-launch path: per RK4
+    # step sp_chi + 4 x (apply, gram, solve, update), the closing observation pass
+    # sp_chi, apply, gram, solve, then sp_loss
+    launches = (2 if b.fused else 17 * chunk + 4 + 1) * args.steps
 
     e2e = None
     if not args.no_e2e:
@@ -724,7 +727,8 @@ def run_paper(args):
                                       else "frame of the drive, counter-rotating terms kept", model["N"],
                                       "x".join(map(str, wl.dims)), wl.M, dt, wl.tau, prec),
                        "trajectories": T, "N": model["N"], "M": wl.M, "nnz": int(model["nnz"]),
-                       "engine": "sparse", "chunk_rk4_steps": chunk,
+                       "engine": "sparse (fused persistent kernel)" if b.fused else "sparse (four launches per stage)",
+                       "chunk_rk4_steps": chunk,
                        "parallelism": "dp%d (independent replicas)" % world,
                        "l2": "flushed (256 MiB write) between timed steps"},
             "pulse_evals_per_s": value / (2 * spp),

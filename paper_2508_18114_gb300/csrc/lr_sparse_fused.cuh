@@ -173,14 +173,37 @@ __device__ __forceinline__ void reduce_scatter32(V (&v)[32], int lane, Add add) 
   }
 }
 
-// acc[u] += sum over the CSR row n of operator `op` of chi[ch] val * Z[col][m0 + u]
+// acc[u] += sum over the CSR row n of operator `op` of chi[ch] val * Z[col][m0 + u].
+// Entries go in groups of four: their indices and weights first, then the four
+// row loads, then the products, so that four gathers are in flight at once
+// (the order of the additions is the entry order either way).
 __device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0, const float2* __restrict__ zs,
                                             const float2* chi, float2 (&acc)[4]) {
   const int* rp = a.rowptr + (size_t)op * (a.N + 1);
+  int e = rp[n];
   const int e1 = rp[n + 1];
-  for (int e = rp[n]; e < e1; ++e) {
-    const float2 c = chi[a.chan[e]], v = a.valf[e];
-    const float wr = c.x * v.x - c.y * v.y, wi = c.x * v.y + c.y * v.x;
+  for (; e + 4 <= e1; e += 4) {
+    int c[4];
+    float2 w[4], z[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      c[q] = a.col[e + q];
+      const float2 ch = chi[a.chan[e + q]], v = a.valf[e + q];
+      w[q] = make_float2(ch.x * v.x - ch.y * v.y, ch.x * v.y + ch.y * v.x);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load4(zs + (size_t)c[q] * a.Mp + m0, z[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc[u].x = fmaf(w[q].x, z[q][u].x, fmaf(-w[q].y, z[q][u].y, acc[u].x));
+        acc[u].y = fmaf(w[q].x, z[q][u].y, fmaf(w[q].y, z[q][u].x, acc[u].y));
+      }
+  }
+  for (; e < e1; ++e) {
+    const float2 ch = chi[a.chan[e]], v = a.valf[e];
+    const float wr = ch.x * v.x - ch.y * v.y, wi = ch.x * v.y + ch.y * v.x;
     float2 z[4];
     load4(zs + (size_t)a.col[e] * a.Mp + m0, z);
 #pragma unroll
