@@ -39,13 +39,14 @@ FP64_FMA_PER_CLK = 2
 
 # What each precision computes in (fused engine): the bulk state, operator
 # apply, projections and RK4 in FP32; the Gram matrix as a double-word FP32
-# sum of exact products and the M x M factorisation in double-word FP32
-# (both ~2^-48 relative, FP64-class); the readout signal and eps_a in FP64.
+# sum of exact products, and the M x M factorisation, G^-1 and X_k = G^-1 T_k
+# in double-word FP32 (all ~2^-48 relative, FP64-class); the readout signal
+# and eps_a in FP64.
 DTYPE_LABEL = {
     "fp64": "f64",
-    "fp32_g64": "f32 bulk; double-word f32 (~2^-48) Gram and LDL^dag/G^-1; f64 signal",
-    "fp32": "f32 bulk and Gram; double-word f32 (~2^-48) LDL^dag/G^-1; f64 signal",
-    "tf32_g64": "f32 bulk, tf32 projection; double-word f32 (~2^-48) Gram and LDL^dag/G^-1; f64 signal",
+    "fp32_g64": "f32 bulk; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 and X_k; f64 signal",
+    "fp32": "f32 bulk and Gram; double-word f32 (~2^-48) LDL^dag, G^-1 and X_k; f64 signal",
+    "tf32_g64": "f32 bulk, tf32 projection; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 and X_k; f64 signal",
 }
 
 
@@ -569,7 +570,7 @@ def run_adjoint(args):
     desc.update({"chunk_rk4_steps": chunk, "engine_forward": lrmod.ENGINE_NAME[b.query().engine],
                  "adjoint": "lr_backward, plain-kernel recomputation per checkpoint segment (%d steps), %s"
                             % (ck, "FP64" if prec == "fp64" else
-                               "FP32 bulk with the Gram matrix summed in FP64 from exact products, FP64 "
+                               "FP32 bulk with the Gram matrix summed from exact products in double-word FP32, FP64 "
                                "Cholesky/G^-1/solves, FP64 signal and gradient sums")})
     print(json.dumps({"metric": "adjoint_traj_steps_per_s", "value": value, "unit": "traj*steps/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
@@ -718,8 +719,10 @@ def run_paper(args):
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == "fp64" else ("f32 bulk; double-word f32 (~2^-48) Gram; "
-                                                   "f64 Cholesky, solves and signal"),
+            "dtype": "f64" if prec == "fp64" else (("f32 bulk; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 "
+                                                    "and X_k; f64 signal") if b.fused else
+                                                   "f32 bulk; double-word f32 (~2^-48) Gram; f64 Cholesky, "
+                                                   "solves and signal"),
             "data": "synthetic (seeded flat-top pulses, seeded initial states)",
             "config": {"workload": "paper: %d candidates x {g,e} = %d trajectories, normal-mode model of Sec. S2 "
                                    "(%s), N=%d (%s), M=%d, dt=%g ns, tau=%g ns, %s"

@@ -90,8 +90,8 @@ typedef enum {
  * double-word FP32 sum (hi + lo floats, about 2^-48 relative: FP64-class,
  * not IEEE FP64). Its LDL^dag factorisation, L^-1 and G^-1 run in the same
  * double-word FP32 arithmetic (Dekker products, Knuth sums, a Newton
- * reciprocal; about 2^-48 relative); G^-1 is then rounded to FP32 and
- * X_k = G^-1 T_k is formed in FP32. The readout signal beta, the populations,
+ * reciprocal; about 2^-48 relative), and so is X_k = G^-1 T_k (from the FP32
+ * T_k), which is rounded to FP32 once. The readout signal beta, the populations,
  * photons and trace are summed in FP64 from the FP32 state, and eps_a, T and
  * Lambda are computed in FP64. Where the fused engine keeps the stage state
  * in L2 it may run the projection term (the Y_k X_k^dag product of Eq. S5)
@@ -294,10 +294,17 @@ lr_status lr_sync(lr_ctx* ctx, void* stream);
  *   parameter count (4 for flat-top) are zero.
  * ckpt_every: states are kept every ckpt_every steps and each segment is
  *   recomputed; memory is (ceil(S/ckpt_every) + ckpt_every + 15) copies of all
- *   states in complex128 plus small tables, in the caller's workspace `dev_ws`
+ *   states (complex128, or complex64 for an FP32-bulk context) plus small
+ *   tables, in the caller's workspace `dev_ws`
  *   (lr_backward_workspace_size bytes, 256-byte aligned).
- * Arithmetic: FP64 throughout (for an FP32 context the kept initial state is
- * widened), forward recomputation with the PLAIN engine's kernels.
+ * Arithmetic follows the context's precision. FP64 context: FP64 throughout.
+ * FP32-bulk context (FP32_G64, FP32, TF32_G64): the checkpoints, stage
+ * inputs, cotangents and every per-element product in complex64 / FP32; the
+ * Gram matrix summed from exact FP32 products in double-word FP32 (~2^-48,
+ * FP64-class); the Cholesky factor, G^-1 and the M x M adjoint factors in
+ * FP64; the readout signal and the gradient sums in FP64. The checkpoint
+ * segments are recomputed with the PLAIN engine's kernels in that arithmetic
+ * (the copies in the workspace are complex64 then: half the memory).
  * Synchronous; returns the device error status. */
 lr_status lr_backward_workspace_size(const lr_ctx* ctx, int ckpt_every, size_t* bytes);
 lr_status lr_backward(lr_ctx* ctx, void* dev_ws, size_t ws_bytes, const double* d_eps_a, double* d_theta,
@@ -547,6 +554,10 @@ lr_status lr_full_bind_workspace(lr_full* f, void* workspace, size_t bytes, void
 lr_status lr_full_set_initial(lr_full* f, int psi, void* stream);
 /* Host rho [N][N] complex128 (interleaved re, im) -> device; step counter set. Sync. */
 lr_status lr_full_set_state(lr_full* f, const double* rho, long step, void* stream);
+/* rho = Z Z^dag from a host low-rank factor Z [N][M] complex128 (e.g. the
+ * initial state of a low-rank run, so that both start from the same rho);
+ * step counter set. Sync. */
+lr_status lr_full_set_state_lowrank(lr_full* f, const double* Z, int M, long step, void* stream);
 /* Device rho -> host [N][N] complex128. Sync. */
 lr_status lr_full_get_state(const lr_full* f, double* rho, void* stream);
 /* n_steps RK4 steps of size dt from the current step, recording beta at every

@@ -34,8 +34,8 @@
 // FP64. FP32-bulk context: the states, stage inputs, cotangents and every
 // per-element product (operator apply, projection terms, the VJP rows, the
 // partial sums of (l_k U)^dag Fbar and T_k) in complex64 / FP32; the Gram
-// matrix summed in FP64 from exact products of the FP32 entries; the Cholesky
-// factor, G^-1, X_k', E_k', P_k' (M x M) in FP64 (rounded once to FP32 for the
+// matrix summed from exact products of the FP32 entries in double-word FP32;
+// the Cholesky factor, G^-1, X_k', E_k', P_k' (M x M) in FP64 (rounded once to FP32 for the
 // per-element kernels); the readout signal, the trapezoid weights and the
 // pulse-parameter gradient accumulated in FP64.
 #include <algorithm>
@@ -61,8 +61,8 @@ struct Ptrs {
   double2* Xs;      // [4][n_traj][2][MR2]  X_k' of each stage (row-major M x M)
   double2* Gi;      // [4][n_traj][MR2]     G^-1 of each stage
   double2* EP;      // [n_traj][4][MR2]     E_r', E_b', P_r', P_b'
-  float2* Xs32;     // FP32-bulk adjoint: FP32 copies of Xs and EP (else null)
-  float2* EP32;
+  float2* Xs32;     // FP32-bulk adjoint: FP32 copies of Xs and EP (else null);
+  float2* EP32;     // EP32 [n_traj][6][MR2] also holds E_r', E_b' transposed
   const double* part;
   double* bpart;
   double* thbar;    // [n_traj][8]
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(AT) adj_bsolve(Ptrs a, int stage, double t_sta
   }
   __syncthreads();
   double2* EP = a.EP + (size_t)tj * 4 * MR2;
-  float2* EP32 = a.EP32 ? a.EP32 + (size_t)tj * 4 * MR2 : nullptr;
+  float2* EP32 = a.EP32 ? a.EP32 + (size_t)tj * 6 * MR2 : nullptr;
   for (int e = tid; e < 2 * MM; e += AT) {
     const int k = e / MM, ij = e - k * MM, i = ij / M, j = ij - (ij / M) * M;
     const double2 ev = E[k][i][j];
@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(AT) adj_bsolve(Ptrs a, int stage, double t_sta
     if (EP32) {
       EP32[k * MR2 + ij] = make_float2((float)ev.x, (float)ev.y);
       EP32[(2 + k) * MR2 + ij] = make_float2((float)pv.x, (float)pv.y);
+      EP32[(4 + k) * MR2 + j * M + i] = make_float2((float)ev.x, (float)ev.y);   // E_k' transposed
     }
   }
 }
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const T2* __restrict__ U, 
   const T2* EP;
   const T2* Xt;
   if constexpr (f32) {
-    EP = a.EP32 + (size_t)tj * 4 * MR2;
+    EP = a.EP32 + (size_t)tj * 6 * MR2;    // E_r', E_b', P_r', P_b', then E_r', E_b' transposed
     Xt = a.Xs32 + (size_t)tj * 2 * MR2;    // a.Xs32 points at this stage's [traj][2][MR2]
   } else {
     EP = a.EP + (size_t)tj * 4 * MR2;
@@ -406,13 +407,16 @@ __global__ void __launch_bounds__(AT) adj_vjp(Ptrs a, const T2* __restrict__ U, 
       const T2* Xk = Xt + (size_t)k * MR2;
       const T2* Ek = EP + (size_t)k * MR2;
       const T2* Pk = EP + (size_t)(2 + k) * MR2;
+      // E_k'[m][l] for the lanes' consecutive m: the transposed copy (FP32) keeps
+      // the loads of a warp contiguous
+      const T2* EkT = f32 ? EP + (size_t)(4 + k) * MR2 : nullptr;
       T2 t = mkc<T2>(0, 0);
       if (idx_k >= 1) {          // l_k^dag (Fbar X_k' + U E_k'^dag) at row n - s_k
         const size_t om = off + (size_t)(n - s_k) * ld;
         T2 s1 = mkc<T2>(0, 0);
         for (int l = 0; l < M; ++l) {
           const T2 p1 = cmul_t(F(om + l), Xk[l * M + m]);
-          const T2 e = Ek[m * M + l];
+          const T2 e = f32 ? EkT[l * M + m] : Ek[m * M + l];
           const T2 p2 = cmul_t(U[om + l], mkc<T2>(e.x, -e.y));
           s1 = mkc<T2>(s1.x + p1.x + p2.x, s1.y + p1.y + p2.y);
         }
@@ -550,7 +554,7 @@ BwdLayout bwd_layout(long long tot, int n_traj, int n_cand, int nt_max, size_t p
   L.Gi = take(sizeof(double2) * 4 * adj::MR2 * n_traj);
   L.EP = take(sizeof(double2) * 4 * adj::MR2 * n_traj);
   L.Xs32 = fp32 ? take(sizeof(float2) * 4 * 2 * adj::MR2 * n_traj) : 0;
-  L.EP32 = fp32 ? take(sizeof(float2) * 4 * adj::MR2 * n_traj) : 0;
+  L.EP32 = fp32 ? take(sizeof(float2) * 6 * adj::MR2 * n_traj) : 0;
   L.bpart = take(sizeof(double) * part_doubles);
   L.beta = take(sizeof(double2) * n_traj * (size_t)(S + 1));
   L.pops = take(sizeof(double) * n_traj * nt_max);

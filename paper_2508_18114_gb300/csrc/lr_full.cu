@@ -209,6 +209,19 @@ __global__ void fm_pure(double2* rho, int N, int psi) {
     rho[e] = mk(e == (long long)psi * N + psi ? 1.0 : 0.0, 0.0);
 }
 
+// rho = Z Z^dag for a low-rank factor Z [N][M] (the initial state of a low-rank run)
+__global__ void __launch_bounds__(FT) fm_from_lowrank(double2* rho, const double2* __restrict__ Z, int N, int M) {
+  const int j = blockIdx.x * FT + threadIdx.x, i = blockIdx.y;
+  if (j >= N) return;
+  double2 s = mk(0.0, 0.0);
+  for (int m = 0; m < M; ++m) {
+    const double2 a = Z[(size_t)i * M + m], b = Z[(size_t)j * M + m];   // a conj(b)
+    s.x = fma(a.x, b.x, fma(a.y, b.y, s.x));
+    s.y = fma(a.y, b.x, fma(-a.x, b.y, s.y));
+  }
+  rho[(size_t)i * N + j] = s;
+}
+
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
@@ -414,6 +427,23 @@ extern "C" lr_status lr_full_set_state(lr_full* f, const double* rho, long step,
   cudaError_t e = cudaMemcpyAsync(f->ws + f->o_rho, rho, (size_t)f->N * f->N * sizeof(double2),
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(f->ws + f->o_err, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fcuda(f, e);
+  f->step = step;
+  return LR_OK;
+}
+
+extern "C" lr_status lr_full_set_state_lowrank(lr_full* f, const double* Z, int M, long step, void* stream) {
+  if (!f || !Z) return LR_ERR_ARG;
+  if (!f->ws) return ffail(f, LR_ERR_WORKSPACE, "no workspace bound");
+  if (M < 1 || M > f->N || step < 0 || step > f->max_steps) return ffail(f, LR_ERR_ARG, "bad rank or step");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double2* zdev = reinterpret_cast<double2*>(f->ws + f->o_B);   // scratch: B holds N^2 >= N M entries
+  cudaError_t e = cudaMemcpyAsync(zdev, Z, (size_t)f->N * M * sizeof(double2), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fcuda(f, e);
+  fm_from_lowrank<<<dim3((f->N + FT - 1) / FT, f->N), FT, 0, st>>>(reinterpret_cast<double2*>(f->ws + f->o_rho), zdev,
+                                                                  f->N, M);
+  if ((e = cudaGetLastError()) == cudaSuccess) e = cudaMemsetAsync(f->ws + f->o_err, 0, sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fcuda(f, e);
   f->step = step;

@@ -171,7 +171,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
       }
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(C * 32);
-      cfg.blockDim = dim3(fz::NT);
+      cfg.blockDim = dim3(fz::threads_for(tc));
       cfg.dynamicSmemBytes = L.total;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -212,7 +212,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
         plan->ok = 1;
         plan->C = C;
         plan->n_clusters = used;
-        plan->threads = fz::NT;
+        plan->threads = fz::threads_for(tc);
         plan->smem = L.total;
         plan->zs_smem = zs_smem;
         plan->tc = tc;
@@ -311,7 +311,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.C * plan.n_clusters);
-  cfg.blockDim = dim3(fz::NT);
+  cfg.blockDim = dim3(plan.threads);
   cfg.dynamicSmemBytes = L.total;
   cfg.stream = s;
   cudaLaunchAttribute at[1];

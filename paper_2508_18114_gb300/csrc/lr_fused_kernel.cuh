@@ -7,9 +7,10 @@
 //               (+ level populations and readout photons at recording steps);
 //   B1          one cluster barrier: partials and the new Z_s are visible;
 //   R  (every CTA, redundantly) reduce the C partial slots in rank order,
-//               Cholesky G = L L^dag, L^-1, G^-1 = L^-dag L^-1 (all FP64),
-//               X_k = G^-1 T_k (bulk precision), pre-scaled and conjugate-
-//               transposed: XT_r = kappa/2 X_r^dag, XT_b = gamma/2 X_b^dag;
+//               G = L D L^dag, L^-1, G^-1 = L^-dag D^-1 L^-1 and X_k = G^-1 T_k
+//               (FP64 for the FP64 state; double-word FP32, ~2^-48, for the FP32
+//               state), pre-scaled, conjugate-transposed and rounded to the bulk
+//               precision: XT_r = kappa/2 X_r^dag, XT_b = gamma/2 X_b^dag;
 //   F  (local + DSMEM halo) F = -i H_eff Z_s + (rZ_s) XT_r + (bZ_s) XT_b and the
 //               RK4 stage update; the next stage input goes to the other Z_s
 //               buffer, the accumulator and Z_n are updated in L2.
@@ -41,8 +42,10 @@ namespace cg = cooperative_groups;
 namespace lr {
 namespace fz {
 
-constexpr int NT = 384;
+constexpr int NT = 384;       // threads of the tensor-core variants (12 warps: 4 TMEM lane groups x 3)
 constexpr int NWARP = NT / 32;
+constexpr int NT_CC = 512;    // threads of the CUDA-core variants (16 warps at <= 128 registers)
+__host__ __device__ constexpr int threads_for(int tc) { return tc > 0 ? NT : NT_CC; }
 constexpr int TAB = 64;   // mode truncations handled by the fused engine: N_t, N_r, N_f < 64
 
 struct Args {
@@ -192,6 +195,23 @@ __device__ __forceinline__ DWC dwc_scale(const DWC& a, DW s) {
   r.im = dw_mul(a.im, s);
   return r;
 }
+// double-word times float (the float exact as a double-word with lo = 0)
+__device__ __forceinline__ DW dw_mul_f(DW a, float b) {
+  const float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  DW r;
+  r.hi = p + e;
+  r.lo = e - (r.hi - p);
+  return r;
+}
+// g t for a double-word complex g and an FP32 complex t
+__device__ __forceinline__ DWC dwc_mul_f(const DWC& g, float tx, float ty) {
+  DWC r;
+  r.re = dw_sum(dw_mul_f(g.re, tx), dw_neg(dw_mul_f(g.im, ty)));
+  r.im = dw_sum(dw_mul_f(g.re, ty), dw_mul_f(g.im, tx));
+  return r;
+}
 
 // Reduce-scatter of NV = 2^p partial sums over a warp (recursive halving): at
 // offset o each lane keeps the half of its values named by bit o of its lane
@@ -297,8 +317,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
   }
 }
 
-template <typename T2, int GRAM_DW, int ZSM, int TC, int FRAME>
-__global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
+template <typename T2, int GRAM_DW, int ZSM, int TC, int FRAME, int NTH = threads_for(TC)>
+__global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
+  constexpr int NT = NTH, NWARP = NTH / 32;
   static_assert(TC == 0 || (ZSM == 0 && sizeof(T2) == 8), "tensor-core projection: FP32 state in L2 only");
   using T = typename Real<T2>::t;
   constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
@@ -926,7 +947,10 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
             __syncthreads();
             // G^-1 = W^dag D^-1 W (Hermitian): entry (i, j), i <= j, is
-            // sum_{k >= j} conj(W[k][i]) W[k][j] / D[k], rounded once to FP32
+            // sum_{k >= j} conj(W[k][i]) W[k][j] / D[k], kept in double-word (in the
+            // storage of G, no longer needed): X_k = G^-1 T_k is formed from it in
+            // double-word below, because G^-1 has entries up to 1 / p_M and a product
+            // rounded to FP32 first would lose the small columns to cancellation
             for (int e = tid; e < M * M; e += NT) {
               const int i = e / M, j = e - i * M;
               if (i > j) continue;
@@ -934,9 +958,11 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
               acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
               for (int k = j; k < M; ++k)   // W[k][j] conj(W[k][i]) = conj of the term
                 acc = dwc_add(acc, dwc_scale(dwc_mul_conj(Ww[k * ldg + j], Ww[k * ldg + i]), dinv[k]));
-              const T re = acc.re.hi + acc.re.lo, im = acc.im.hi + acc.im.lo;
-              Gi[i * Mp + j] = cm<T2>(re, im);
-              if (i != j) Gi[j * Mp + i] = cm<T2>(re, -im);
+              Gw[i * ldg + j] = acc;
+              if (i != j) {
+                acc.im = dw_neg(acc.im);
+                Gw[j * ldg + i] = acc;
+              }
             }
             __syncthreads();
           } else {
@@ -1011,19 +1037,32 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Args a) {
             }
             __syncthreads();
           }
-          // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k  (bulk precision)
+          // XT_k[l][m] = s_k conj(X_k[m][l]), X_k = G^-1 T_k
           const double sk[2] = {0.5 * d.kappa, 0.5 * d.gamma};
           for (int e = tid; e < 2 * Mq * Mq; e += NT) {
             const int k = e / (Mq * Mq), lq = e - k * (Mq * Mq), l = lq / Mq, m = lq - l * Mq, lm = l * Mp + m;
             T xr = 0, xi = 0;
             if (l < M && m < M) {
               const T2* Tk = Tred + k * MM;
-              for (int j = 0; j < M; ++j) {
-                const T2 gv = Gi[m * Mp + j];
-                const T gr = gv.x, gi = gv.y;
-                const T2 t = Tk[j * Mp + l];
-                xr = fma(gr, t.x, fma(-gi, t.y, xr));
-                xi = fma(gr, t.y, fma(gi, t.x, xi));
+              if constexpr (sizeof(T) == 4) {
+                // FP32 state: double-word sums of G^-1 (double-word) times T_k (exact)
+                const DWC* Giw = reinterpret_cast<const DWC*>(Gd);
+                DWC acc;
+                acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
+                for (int j = 0; j < M; ++j) {
+                  const T2 t = Tk[j * Mp + l];
+                  acc = dwc_add(acc, dwc_mul_f(Giw[m * ldg + j], t.x, t.y));
+                }
+                xr = acc.re.hi + acc.re.lo;
+                xi = acc.im.hi + acc.im.lo;
+              } else {
+                for (int j = 0; j < M; ++j) {
+                  const T2 gv = Gi[m * Mp + j];
+                  const T gr = gv.x, gi = gv.y;
+                  const T2 t = Tk[j * Mp + l];
+                  xr = fma(gr, t.x, fma(-gi, t.y, xr));
+                  xi = fma(gr, t.y, fma(gi, t.x, xi));
+                }
               }
             }
             const T s = (T)sk[k];

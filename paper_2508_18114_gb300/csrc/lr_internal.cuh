@@ -244,8 +244,8 @@ int plain_rows_per_block();
 size_t plain_partial_doubles(int M);
 // The plain engine on complex128 state (the reference GPU path), or on
 // complex64 state (fp32 = 1: the adjoint's FP32-bulk recomputation; the Gram
-// matrix is summed in FP64 from exact products, Cholesky and solves in FP64,
-// the rest in FP32).
+// matrix is summed from exact products in double-word FP32, Cholesky and solves
+// in FP64, the rest in FP32).
 cudaError_t plain_integrate(const DevPtrs& p, const RunParams& rp, int max_nblk, int max_N, long step0,
                             long n_steps, cudaStream_t s, int fp32 = 0);
 // single kernels of the plain engine (used by the adjoint's recomputation)

@@ -15,8 +15,8 @@
 //
 // The state type is a template parameter: complex128 (the reference path), or
 // complex64 for the FP32-bulk recomputation inside the adjoint. With complex64
-// the Gram matrix is summed in FP64 from the exact products of the FP32
-// entries (FP64-class), the Cholesky factor and the solves are FP64 as always,
+// the Gram matrix is summed from the exact products of the FP32 entries in
+// double-word FP32 (FP64-class), the Cholesky factor and the solves are FP64,
 // and the operator apply, T_k, the projection term and the RK4 update run in
 // FP32 (the diagonal energies and the step sizes split into hi + lo floats so
 // that FP32 does not round the mode frequencies or dt).
@@ -80,8 +80,26 @@ __global__ void __launch_bounds__(PT) plain_gram(const TrajDev* __restrict__ tra
   for (int e = threadIdx.x; e < 3 * MM; e += blockDim.x) {
     const int mat = e / MM, ij = e - mat * MM, i = ij / M, j = ij - (ij / M) * M;
     if (mat == 0 && i > j) continue;
-    if (sizeof(T) == 8 || mat == 0) {
-      // FP64 sums (of exact products when the state is FP32)
+    if (sizeof(T) == 4 && mat == 0) {
+      // FP32 state: exact FP32 products (FMA TwoProduct) in double-word sums
+      // (Knuth TwoSum), ~2^-48 relative: the FP64-class Gram on the FP32 pipes
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      auto acc2 = [](float& hi, float& lo, float a, float b) {
+        const float p = a * b, e = fmaf(a, b, -p), t = hi + p, bp = t - hi;
+        lo += ((hi - (t - bp)) + (p - bp)) + e;
+        hi = t;
+      };
+      for (int r = 0; r < rows; ++r) {
+        const T2 a = sZ[r][i], c = sZ[r][j];
+        acc2(rh, rl, (float)a.x, (float)c.x);      // conj(a) * c
+        acc2(rh, rl, (float)a.y, (float)c.y);
+        acc2(ih, il, (float)a.x, (float)c.y);
+        acc2(ih, il, -(float)a.y, (float)c.x);
+      }
+      out[2 * e] = (double)rh + (double)rl;
+      out[2 * e + 1] = (double)ih + (double)il;
+    } else if (sizeof(T) == 8 || mat == 0) {
+      // FP64 sums
       double re = 0.0, im = 0.0;
       for (int r = 0; r < rows; ++r) {
         const T2 a = sZ[r][i];
@@ -254,10 +272,12 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const T
   __shared__ double coef, coef_i, wfr;
   const int M = d.M, MM = M * M, ld = d.ld;
   const double2* X = p.X + (size_t)tj * 2 * LR_MAX_RANK * LR_MAX_RANK;
+  // transposed in shared memory, sX[k][l * M + m] = X_k[m][l]: the threads of a
+  // warp (consecutive m) then read consecutive words (no bank conflicts)
   for (int e = threadIdx.x; e < 2 * MM; e += blockDim.x) {
-    const int k = e / MM, ij = e - k * MM;
+    const int k = e / MM, ij = e - k * MM, i = ij / M, j = ij - i * M;
     const double2 x = X[k * LR_MAX_RANK * LR_MAX_RANK + ij];
-    sX[k][ij] = mkc<T2>((T)x.x, (T)x.y);
+    sX[k][j * M + i] = mkc<T2>((T)x.x, (T)x.y);
   }
   if (threadIdx.x == 0) {
     const PulseDev P = p.pulse[d.cand];
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const T
       const T2* zr = Z + (size_t)(n + 1) * ld;
       T sr_ = 0, si_ = 0;
       for (int l = 0; l < M; ++l) {
-        const T2 y = zr[l], x = sX[0][m * M + l];   // y * conj(x)
+        const T2 y = zr[l], x = sX[0][l * M + m];   // y * conj(x)
         sr_ += y.x * x.x + y.y * x.y;
         si_ += y.y * x.x - y.x * x.y;
       }
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(PT) plain_rhs(DevPtrs p, RunParams rp, const T
       const T2* zb = Z + (size_t)(n + st) * ld;
       T sr_ = 0, si_ = 0;
       for (int l = 0; l < M; ++l) {
-        const T2 y = zb[l], x = sX[1][m * M + l];
+        const T2 y = zb[l], x = sX[1][l * M + m];
         sr_ += y.x * x.x + y.y * x.y;
         si_ += y.y * x.x - y.x * x.y;
       }

@@ -541,6 +541,7 @@ struct lr_sparse {
   int fused;  // 1: the fused persistent kernel (FP32_G64), 0: four launches per RK4 stage
   int n_cta;  // fused: persistent CTAs (one trajectory at a time each)
   size_t o_fsc;   // fused: per-CTA stage buffers
+  size_t o_fvala, o_fdiag;   // fused: values of A without its static diagonal, and that diagonal (hi + lo)
   long nnz, max_steps, n_rec, step;
   double dt;   // RK4 step of the run (0 before the first integrate)
   int pop_every;
@@ -606,6 +607,8 @@ void layout(lr_sparse* s) {
   if (s->fused) {
     const size_t Mp = (size_t)(s->M + 3) / 4 * 4;
     s->o_fsc = take((size_t)s->n_cta * (3 + s->K + 1) * s->N * Mp * sizeof(float2));
+    s->o_fvala = take((size_t)s->nnz * sizeof(float2));
+    s->o_fdiag = take((size_t)s->N * sizeof(float4));
   }
   s->total = o;
 }
@@ -895,6 +898,31 @@ extern "C" lr_status lr_sparse_bind_workspace(lr_sparse* s, void* workspace, siz
   for (const Up& u : ups)
     if (u.bytes && (e = cudaMemcpyAsync(s->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(s, e);
+  std::vector<float2> vala;
+  std::vector<float4> diag;
+  if (s->fused) {
+    // A's static (channel a = 0, q = 0) diagonal entries leave the gathered values
+    // and go, summed per row in FP64, into hi + lo floats
+    vala = valf;
+    diag.assign(s->N, make_float4(0.f, 0.f, 0.f, 0.f));
+    const int static_ch = 2;
+    for (int n = 0; n < s->N; ++n) {
+      double dr = 0.0, di = 0.0;
+      for (int k = s->rowptr[n]; k < s->rowptr[n + 1]; ++k)
+        if (s->col[k] == n && s->chan[k] == static_ch) {
+          dr += s->val[2 * k];
+          di += s->val[2 * k + 1];
+          vala[k] = make_float2(0.f, 0.f);
+        }
+      const float hr = (float)dr, hi = (float)di;
+      diag[n] = make_float4(hr, hi, (float)(dr - (double)hr), (float)(di - (double)hi));
+    }
+    if ((e = cudaMemcpyAsync(s->ws + s->o_fvala, vala.data(), vala.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->ws + s->o_fdiag, diag.data(), diag.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+      return cuda_fail(s, e);
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(s, e);
   if ((e = raise_solve_smem((int)solve_smem(s))) != cudaSuccess) return cuda_fail(s, e);
   s->step = 0;
@@ -986,6 +1014,8 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
     a.rowptr = d.rowptr;
     a.col = d.col;
     a.valf = d.valf;
+    a.valf_a = reinterpret_cast<const float2*>(s->ws + s->o_fvala);
+    a.diag_a = reinterpret_cast<const float4*>(s->ws + s->o_fdiag);
     a.chan = d.chan;
     a.level = d.level;
     a.pulse = d.pulse;

@@ -17,17 +17,18 @@
 //   P  warp tasks over 4 x 4 tiles: G = Z_s^dag Z_s (upper tiles, exact FP32
 //      products in double-word sums) and T_k = Z_s^dag Y_k (FP32), each tile
 //      summed over all rows and reduced over the warp by recursive halving;
-//   R  G = L D L^dag, L^-1 and G^-1 in double-word FP32 (~2^-48 relative),
-//      X_k = G^-1 T_k and XT_k[l][m] = 1/2 conj(X_k[m][l]) in FP32;
-//   F  F = A(t) Z_s (A = -i H_eff, CSR gathers) + sum_k Y_k XT_k and the
-//      classical RK4 stage update; the next stage input goes to the other
+//   R  G = L D L^dag, L^-1, G^-1 and X_k = G^-1 T_k in double-word FP32
+//      (~2^-48 relative), XT_k[l][m] = 1/2 conj(X_k[m][l]) rounded to FP32;
+//   F  F = A(t) Z_s (A = -i H_eff: its static diagonal as hi + lo floats, the
+//      other entries by CSR gathers) + sum_k Y_k XT_k and the classical RK4
+//      stage update; the next stage input goes to the other
 //      Z_s buffer, the accumulator and Z_n are updated in place.
 #include "lr_internal.cuh"
 
 namespace lr {
 namespace sfz {
 
-constexpr int NT = 384;
+constexpr int NT = 512;       // 16 warps at <= 128 registers
 constexpr int NWARP = NT / 32;
 constexpr int NCH = 10;   // time channels
 constexpr int TP = 4;     // phase-P tile edge
@@ -37,6 +38,8 @@ struct Args {
   const int* rowptr;   // [(K + 2) (N + 1)]
   const int* col;
   const float2* valf;
+  const float2* valf_a;    // valf with the static diagonal of A (operator 0) set to zero
+  const float4* diag_a;    // that diagonal per row as hi + lo floats (re_hi, im_hi, re_lo, im_lo)
   const unsigned char* chan;
   const int* level;
   const PulseDev* pulse;   // per trajectory
@@ -142,6 +145,21 @@ __device__ __forceinline__ DWC dwc_scale(const DWC& a, DW s) {
   r.im = dw_mul(a.im, s);
   return r;
 }
+__device__ __forceinline__ DW dw_mul_f(DW a, float b) {   // b exact as a double-word
+  const float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  DW r;
+  r.hi = p + e;
+  r.lo = e - (r.hi - p);
+  return r;
+}
+__device__ __forceinline__ DWC dwc_mul_f(const DWC& g, float tx, float ty) {
+  DWC r;
+  r.re = dw_sum(dw_mul_f(g.re, tx), dw_neg(dw_mul_f(g.im, ty)));
+  r.im = dw_sum(dw_mul_f(g.re, ty), dw_mul_f(g.im, tx));
+  return r;
+}
 
 __device__ __forceinline__ void load4(const float2* p, float2 (&v)[4]) {
   const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
@@ -180,6 +198,7 @@ __device__ __forceinline__ void reduce_scatter32(V (&v)[32], int lane, Add add) 
 __device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0, const float2* __restrict__ zs,
                                             const float2* chi, float2 (&acc)[4]) {
   const int* rp = a.rowptr + (size_t)op * (a.N + 1);
+  const float2* __restrict__ vals = op == 0 ? a.valf_a : a.valf;
   int e = rp[n];
   const int e1 = rp[n + 1];
   for (; e + 4 <= e1; e += 4) {
@@ -188,7 +207,7 @@ __device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       c[q] = a.col[e + q];
-      const float2 ch = chi[a.chan[e + q]], v = a.valf[e + q];
+      const float2 ch = chi[a.chan[e + q]], v = vals[e + q];
       w[q] = make_float2(ch.x * v.x - ch.y * v.y, ch.x * v.y + ch.y * v.x);
     }
 #pragma unroll
@@ -202,7 +221,7 @@ __device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0
       }
   }
   for (; e < e1; ++e) {
-    const float2 ch = chi[a.chan[e]], v = a.valf[e];
+    const float2 ch = chi[a.chan[e]], v = vals[e];
     const float wr = ch.x * v.x - ch.y * v.y, wi = ch.x * v.y + ch.y * v.x;
     float2 z[4];
     load4(zs + (size_t)a.col[e] * a.Mp + m0, z);
@@ -492,8 +511,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             if (lane < M) Ww[lane * ldg + j] = wv;
           }
           __syncthreads();
-          // G^-1 = W^dag D^-1 W, rounded once to FP32 (into the storage of L)
-          float2* Gi = reinterpret_cast<float2*>(Gd);
+          // G^-1 = W^dag D^-1 W in double-word, into the storage of L (no longer needed)
           for (int e = tid; e < M * M; e += NT) {
             const int i = e / M, j = e - i * M;
             if (i > j) continue;
@@ -501,22 +519,29 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
             for (int k = j; k < M; ++k)
               acc = dwc_add(acc, dwc_scale(dwc_mul_conj(Ww[k * ldg + j], Ww[k * ldg + i]), dinv[k]));
-            const float re = acc.re.hi + acc.re.lo, im = acc.im.hi + acc.im.lo;
-            Gi[i * Mp + j] = make_float2(re, im);
-            if (i != j) Gi[j * Mp + i] = make_float2(re, -im);
+            Gw[i * ldg + j] = acc;
+            if (i != j) {
+              acc.im = dw_neg(acc.im);
+              Gw[j * ldg + i] = acc;
+            }
           }
           __syncthreads();
-          // XT_k[l][m] = 1/2 conj(X_k[m][l]), X_k = G^-1 T_k (the 1/2 of Eq. S5)
+          // XT_k[l][m] = 1/2 conj(X_k[m][l]), X_k = G^-1 T_k (the 1/2 of Eq. S5), in
+          // double-word sums: G^-1 has entries up to 1 / p_M, and a product rounded
+          // to FP32 first would lose the small columns to cancellation
           for (int e = tid; e < K * Mq * Mq; e += NT) {
             const int k = e / (Mq * Mq), lq = e - k * (Mq * Mq), l = lq / Mq, m = lq - l * Mq;
             float xr = 0.f, xi = 0.f;
             if (l < M && m < M) {
               const float2* Tk = Tred + k * MM;
+              DWC acc;
+              acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
               for (int j = 0; j < M; ++j) {
-                const float2 g = Gi[m * Mp + j], t = Tk[j * Mp + l];
-                xr = fmaf(g.x, t.x, fmaf(-g.y, t.y, xr));
-                xi = fmaf(g.x, t.y, fmaf(g.y, t.x, xi));
+                const float2 t = Tk[j * Mp + l];
+                acc = dwc_add(acc, dwc_mul_f(Gw[m * ldg + j], t.x, t.y));
               }
+              xr = acc.re.hi + acc.re.lo;
+              xi = acc.im.hi + acc.im.lo;
             }
             XT[k * MM + l * Mp + m] = make_float2(0.5f * xr, -0.5f * xi);
           }
@@ -537,7 +562,19 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             for (int r = 0; r < TR; ++r) {
 #pragma unroll
               for (int u = 0; u < 4; ++u) f[r][u] = make_float2(0.f, 0.f);
-              if (l0 + r < N) row_gather4(a, 0, l0 + r, m0, zc, chi, f[r]);
+              if (l0 + r < N) {
+                // the static diagonal of A as hi + lo floats (FP32 does not round the
+                // detunings), then the other entries of the row
+                const float4 dg = a.diag_a[l0 + r];
+                float2 z[4];
+                load4(zc + (size_t)(l0 + r) * Mp + m0, z);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  f[r][u].x = fmaf(dg.x, z[u].x, fmaf(-dg.y, z[u].y, fmaf(dg.z, z[u].x, -dg.w * z[u].y)));
+                  f[r][u].y = fmaf(dg.x, z[u].y, fmaf(dg.y, z[u].x, fmaf(dg.z, z[u].y, dg.w * z[u].x)));
+                }
+                row_gather4(a, 0, l0 + r, m0, zc, chi, f[r]);
+              }
             }
             // + sum_k Y_k XT_k: l in pairs, 16-byte loads of the Y rows
             for (int k = 0; k < K; ++k) {

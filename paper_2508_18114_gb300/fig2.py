@@ -7,7 +7,8 @@ with sigma = 0.5 ns, tau = 40 ns), from |g> and |e>, integrated
 * by the low-rank ansatz of rank M (lr_sparse_*, FP64 on the four-launch
   path, and FP32 bulk with the FP64-class Gram matrix on the fused kernel),
 
-with RK4 at dt = 0.5 ps. Output (JSON): the readout signals beta_g(t), beta_e(t)
+with RK4 at dt = 0.5 ps, both from the same initial density matrix (the
+low-rank initial state of Sec. S1.A, rho(0) = Z(0) Z(0)^dag). Output (JSON): the readout signals beta_g(t), beta_e(t)
 and photon numbers n(t) of both methods every `--every` steps, the relative
 deviation delta = |y_full - y_LRA| / |y_full| of beta and n, the assignment
 error of each method (Sec. S3.A), and the wall time of each run.
@@ -63,11 +64,18 @@ def run(steps=80000, dt=5e-4, M=20, every=100, amp_mhz=150.0, dims=(100, 4, 5), 
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
+    # the low-rank initial states (Sec. S1.A: |g> or |e> plus padding of weight eps);
+    # the full master equation starts from the same rho(0) = Z(0) Z(0)^dag, so that
+    # the deviation is the rank truncation alone
+    b0 = sparse.SparseBatch(model, M, [pulse, pulse], tau, 1, precision="fp64", device=device)
+    b0.set_initial([0, 1], seed, eps)
+    z0 = b0.get_state()
+    del b0
     # full master equation, one trajectory at a time
     full = {}
     for lv, tag in ((0, "g"), (1, "e")):
         f = sparse.FullME(model, pulse, tau, steps, pop_every=every, device=device)
-        f.set_initial(lv)
+        f.set_state_lowrank(z0[lv])
         _, sec = timed(lambda: f.integrate(dt, steps))
         full[tag] = dict(f.observables(), seconds=sec)
         del f

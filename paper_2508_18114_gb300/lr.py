@@ -41,7 +41,7 @@ EXPORTS = (
     "lr_sparse_integrate", "lr_sparse_observables", "lr_sparse_loss", "lr_sparse_last_error",
     "lr_sparse_destroy", "lr_grow_rank", "lr_measure_peak", "lr_sparse_query",
     "lr_full_create", "lr_full_workspace_size", "lr_full_bind_workspace", "lr_full_set_initial",
-    "lr_full_set_state", "lr_full_get_state", "lr_full_integrate", "lr_full_observables", "lr_full_last_error",
+    "lr_full_set_state", "lr_full_set_state_lowrank", "lr_full_get_state", "lr_full_integrate", "lr_full_observables", "lr_full_last_error",
     "lr_full_destroy",
 )
 
@@ -132,6 +132,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_full_set_initial.argtypes = [vp, i, vp]
     lib.lr_full_set_state.argtypes = [vp, vp, l, vp]
     lib.lr_full_get_state.argtypes = [vp, vp, vp]
+    lib.lr_full_set_state_lowrank.argtypes = [vp, vp, i, l, vp]
     lib.lr_full_integrate.argtypes = [vp, d, l, vp]
     lib.lr_full_observables.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.lr_full_last_error.argtypes = [vp]

@@ -199,6 +199,12 @@ class FullME:
         r = np.ascontiguousarray(rho, dtype=np.complex128).reshape(self.N, self.N)
         self._check(self._lib.lr_full_set_state(self._h, _ptr(r), int(step), C.c_void_p(_stream_ptr(stream))))
 
+    def set_state_lowrank(self, Z: np.ndarray, step: int = 0, stream=None):
+        """rho = Z Z^dag from a low-rank factor Z [N][M] (computed on the device)."""
+        z = np.ascontiguousarray(Z, dtype=np.complex128)
+        self._check(self._lib.lr_full_set_state_lowrank(self._h, _ptr(z), int(z.shape[1]), int(step),
+                                                        C.c_void_p(_stream_ptr(stream))))
+
     def get_state(self, stream=None) -> np.ndarray:
         r = np.zeros((self.N, self.N), np.complex128)
         self._check(self._lib.lr_full_get_state(self._h, _ptr(r), C.c_void_p(_stream_ptr(stream))))

@@ -71,3 +71,26 @@ def test_full_me_paper_size_first_steps():
     assert np.abs(rho - want["state"]).max() <= 1e-12
     assert np.abs(got["pops"] - want["pops"]).max() <= 1e-12
     assert np.abs(got["beta"] - want["beta"]).max() <= 1e-12
+
+
+def test_full_me_from_a_low_rank_factor_equals_the_low_rank_run_at_full_rank():
+    """rho(0) = Z Z^dag on the device (lr_full_set_state_lowrank); with M = N the
+    low-rank equation is the master equation (Eq. S5 vs Eq. S4), so the two GPU
+    engines agree to the RK4 discretisation gap (O(dt^4) per unit time)."""
+    from paper_2508_18114_gb300 import sparse
+    P = _params(g=TP * 0.3, kappa=1.0, gamma=0.05)
+    dims, dt, n, tau = (3, 2, 3), 5e-4, 400, 0.2
+    pulse = (0, [TP * 1.0, P["wd"], 0.03, 0.0])
+    model = sparse.paper_model(*dims, **P)
+    N = model["N"]
+    b = sparse.SparseBatch(model, N, [pulse], tau, n, pop_every=100, precision="fp64")
+    b.set_initial([1], 5, 1e-3)
+    z0 = b.get_state()[0]
+    f = sparse.FullME(model, pulse, tau, n, pop_every=100)
+    f.set_state_lowrank(z0)
+    assert np.abs(f.get_state() - z0 @ z0.conj().T).max() < 1e-15
+    b.integrate(dt, n)
+    f.integrate(dt, n)
+    lo, fo = b.observables(), f.observables()
+    assert np.abs(lo["beta"][0] - fo["beta"]).max() < 1e-8 * max(np.abs(fo["beta"]).max(), 1.0)
+    assert np.abs(lo["pops"][0] - fo["pops"]).max() < 1e-8
