@@ -12,17 +12,22 @@ tests/golden/make_full_pulse.py (oracle only).
   and FP64.
 
 Tolerances. FP64 paths: rounding only, ~1e-16 per step over 8e4 steps:
-relative 1e-10 is ample. FP32 bulk: every RK4 step rounds the state to FP32
-(u = 2^-24 = 6e-8); the errors of successive steps add like a random walk, so
-after n = 8e4 steps the state carries about sqrt(n) u = 1.7e-5 relative error
-in its leading column. The small columns (weight eps = 1e-5) carry relative
-errors up to 1/sqrt(p_M) ~ 300 times larger, but they enter beta, the
-populations and the photons only through their weight eps, so they add
-~u sqrt(n) 300 eps = 5e-8. The bound 1e-4 on beta, photons and
-populations is the random-walk estimate with a factor 6 of margin. eps_a =
-erfc(SNR/2)/2 + tau gamma/2 moves by (SNR^2/2) dSNR/SNR relative for large SNR
-(d ln erfc(x)/dx ~ -2x); with dSNR/SNR ~ dbeta/beta and SNR <= 6 here that
-is at most 18 dbeta/beta: bound 2e-3.
+relative 1e-10 is ample (measured: 2e-13 on the paper's model). FP32 bulk:
+every RK4 step rounds the state at its four stage inputs and its update, and
+the stage arithmetic adds a few roundings of the same size; with ~16 roundings
+of u = 2^-24 = 6e-8 per step adding like a random walk, after n = 8e4 steps an
+amplitude carries ~u sqrt(16 n) = 6.7e-5 relative error and the |Z|^2 sums
+(populations, photons, tr rho) about twice that, 1.4e-4. The bound is 2e-4 for
+beta, the populations, photons, tr rho and the ionization penalty T. In the lab
+frame of the bare-mode workload the state's phases turn by up to 0.8 rad per
+step, the roundings are uncorrelated and the walk is reached (measured 1.0e-4);
+in the frame of the drive (the paper's model) the errors stay at 2-5e-6
+(measured). The small columns (weight eps = 1e-5) reach the observables only
+through that weight, and G^-1 T_k is formed in double-word (its FP32 rounding
+before the product cost 3.5e-4 on the paper's model). eps_a = erfc(SNR/2)/2 +
+tau gamma/2 moves by (SNR^2/2) dSNR/SNR relative for large SNR (d ln erfc(x)/dx
+~ -2x); with dSNR/SNR ~ dbeta/beta and SNR <= 6 that is at most 18 dbeta/beta:
+bound 4e-3.
 """
 import os
 
@@ -34,7 +39,7 @@ from golden import full_pulse
 
 pytestmark = pytest.mark.gpu
 
-FP32_TOL = dict(beta_rel=1e-4, pops_abs=1e-4, nphot_rel=1e-4, trace_abs=1e-4, eps_a_rel=2e-3, T_rel=2e-3)
+FP32_TOL = dict(beta_rel=2e-4, pops_abs=2e-4, nphot_rel=2e-4, trace_abs=2e-4, eps_a_rel=4e-3, T_rel=2e-4)
 FP64_TOL = dict(beta_rel=1e-10, pops_abs=1e-10, nphot_rel=1e-10, trace_abs=1e-10, eps_a_rel=1e-9, T_rel=1e-9)
 TIMED_PLAN = {"LR_FUSED_C": "2", "LR_FUSED_ZS": "global", "LR_FUSED_TC": "0"}
 
