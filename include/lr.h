@@ -514,13 +514,18 @@ lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, double gamma, d
                          double* loss, void* stream);
 /* Which integrator the context runs (host only): *fused = 1 for the fused
  * persistent kernel (FP32_G64 contexts by default: one launch per
- * lr_sparse_integrate, one CTA per trajectory, the stage input, the operator
- * images and the RK4 accumulator in a per-CTA L2-resident region, the Gram
- * matrix in double-word FP32 and its LDL^dag factorisation, L^-1 and G^-1 in
+ * lr_sparse_integrate; the stage input, the operator images and the RK4
+ * accumulator in a per-team L2-resident region; the Gram matrix in
+ * double-word FP32 and its LDL^dag factorisation, L^-1 and G^-1 in
  * double-word FP32), 0 for the four launches per RK4 stage described at
  * lr_sparse_create (FP64 contexts, or FP32_G64 with the environment variable
- * LR_SPARSE_FUSED=0 at lr_sparse_create). */
-lr_status lr_sparse_query(const lr_sparse* s, int* fused);
+ * LR_SPARSE_FUSED=0 at lr_sparse_create). *team (may be NULL) = the CTAs
+ * (one thread-block cluster) that share each trajectory's rows: 1 when the
+ * batch has at least as many trajectories as the GPU has SMs (each CTA then
+ * takes an equal span of the batch's trajectory-steps, unless
+ * LR_SPARSE_SPLIT=0 at lr_sparse_integrate), else up to 16 (LR_SPARSE_C at
+ * lr_sparse_create forces it); 0 for the four-launch path. */
+lr_status lr_sparse_query(const lr_sparse* s, int* fused, int* team);
 const char* lr_sparse_last_error(const lr_sparse* s);
 void lr_sparse_destroy(lr_sparse* s);
 
@@ -552,7 +557,9 @@ lr_status lr_full_workspace_size(const lr_full* f, size_t* bytes);
 lr_status lr_full_bind_workspace(lr_full* f, void* workspace, size_t bytes, void* stream);
 /* rho = |psi><psi| (a basis index), step counter reset. Async. */
 lr_status lr_full_set_initial(lr_full* f, int psi, void* stream);
-/* Host rho [N][N] complex128 (interleaved re, im) -> device; step counter set. Sync. */
+/* Host rho [N][N] complex128 (interleaved re, im) -> device; step counter set.
+ * Only the upper triangle is read: rho is made exactly Hermitian from it (the
+ * integrator keeps it so). Sync. */
 lr_status lr_full_set_state(lr_full* f, const double* rho, long step, void* stream);
 /* rho = Z Z^dag from a host low-rank factor Z [N][M] complex128 (e.g. the
  * initial state of a low-rank run, so that both start from the same rho);

@@ -13,7 +13,8 @@
 //               gathering rows rho[col][j] over the CSR entries of row i;
 //   fm_transp   Bt = B^dag, Yt_k = Y_k^dag (32 x 32 shared-memory tiles);
 //   fm_update   F = B + Bt + sum_k L_k Yt_k (gathers of rows of Yt_k), and the
-//               RK4 stage update of the accumulator and the next stage input.
+//               RK4 stage update of the accumulator and the next stage input,
+//               from the upper triangle, mirrored: rho stays exactly Hermitian.
 // Observables at the start of every step (fm_obs, one block, fixed order):
 // beta = tr(rho r), and at recording steps the level populations, the photon
 // number tr(r rho r^dag) and tr rho.
@@ -114,10 +115,15 @@ __global__ void __launch_bounds__(FT) fm_transp(FmDev d, FmParams p) {
 }
 
 // F = B + Bt + sum_k L_k Yt_k, then the RK4 stage (weights 1/6, 1/3, 1/3, 1/6).
+// The thread of (i, j), i <= j, writes entry (i, j) and its conjugate at (j, i):
+// rho, the accumulator and the stage inputs stay exactly Hermitian. (The form
+// A rho + (A rho)^dag + L (L rho)^dag equals the generator only for Hermitian
+// rho; a rounding-level anti-Hermitian part would evolve under -sum_k L_k K
+// L_k^dag and grow exponentially.)
 __global__ void __launch_bounds__(FT) fm_update(FmDev d, FmParams p, int stage, double dt) {
   const int j = blockIdx.x * FT + threadIdx.x, i = blockIdx.y;
-  if (j >= p.N) return;
-  const size_t ij = (size_t)i * p.N + j;
+  if (j >= p.N || j < i) return;
+  const size_t ij = (size_t)i * p.N + j, ji = (size_t)j * p.N + i;
   const double2 b = d.B[ij], bt = d.Bt[ij];
   double2 f = mk(b.x + bt.x, b.y + bt.y);
   for (int k = 0; k < p.K; ++k) {
@@ -129,24 +135,40 @@ __global__ void __launch_bounds__(FT) fm_update(FmDev d, FmParams p, int stage, 
       f.y = fma(v.x, z.y, fma(v.y, z.x, f.y));
     }
   }
+  if (i == j) f.y = 0.0;
   const double2 r0 = d.rho[ij];
+  auto put = [&](double2* a, double2 v) {
+    a[ij] = v;
+    if (i != j) a[ji] = mk(v.x, -v.y);
+  };
   if (stage == 0) {
-    d.acc[ij] = f;
+    put(d.acc, f);
   } else if (stage < 3) {
     const double2 a = d.acc[ij];
-    d.acc[ij] = mk(a.x + 2.0 * f.x, a.y + 2.0 * f.y);
+    put(d.acc, mk(a.x + 2.0 * f.x, a.y + 2.0 * f.y));
   }
   if (stage < 3) {
     const double c = stage == 2 ? dt : 0.5 * dt;
-    d.rs[ij] = mk(r0.x + c * f.x, r0.y + c * f.y);
+    put(d.rs, mk(r0.x + c * f.x, r0.y + c * f.y));
   } else {
     const double2 a = d.acc[ij];
     const double h = dt / 6.0;
     const double2 rn = mk(r0.x + h * (a.x + f.x), r0.y + h * (a.y + f.y));
     if (!isfinite(rn.x) || !isfinite(rn.y)) set_error(d.err, DEV_NONFINITE);
-    d.rho[ij] = rn;
-    d.rs[ij] = rn;
+    put(d.rho, rn);
+    put(d.rs, rn);
   }
+}
+
+// rho = (rho + rho^dag) / 2 from its upper triangle (entries (i, j), i <= j, kept,
+// the lower triangle their conjugates, the diagonal real).
+__global__ void __launch_bounds__(FT) fm_hermitian(double2* rho, int N) {
+  const int j = blockIdx.x * FT + threadIdx.x, i = blockIdx.y;
+  if (j >= N || j < i) return;
+  double2 v = rho[(size_t)i * N + j];
+  if (i == j) v.y = 0.0;
+  rho[(size_t)i * N + j] = v;
+  rho[(size_t)j * N + i] = mk(v.x, -v.y);
 }
 
 // beta = tr(rho r) = sum_j sum_e r[j][c] rho[c][j]; at recording steps also the
@@ -426,6 +448,10 @@ extern "C" lr_status lr_full_set_state(lr_full* f, const double* rho, long step,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(f->ws + f->o_rho, rho, (size_t)f->N * f->N * sizeof(double2),
                                   cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    fm_hermitian<<<dim3((f->N + FT - 1) / FT, f->N), FT, 0, st>>>(reinterpret_cast<double2*>(f->ws + f->o_rho), f->N);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(f->ws + f->o_err, 0, sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fcuda(f, e);
@@ -443,6 +469,7 @@ extern "C" lr_status lr_full_set_state_lowrank(lr_full* f, const double* Z, int 
   if (e != cudaSuccess) return fcuda(f, e);
   fm_from_lowrank<<<dim3((f->N + FT - 1) / FT, f->N), FT, 0, st>>>(reinterpret_cast<double2*>(f->ws + f->o_rho), zdev,
                                                                   f->N, M);
+  fm_hermitian<<<dim3((f->N + FT - 1) / FT, f->N), FT, 0, st>>>(reinterpret_cast<double2*>(f->ws + f->o_rho), f->N);
   if ((e = cudaGetLastError()) == cudaSuccess) e = cudaMemsetAsync(f->ws + f->o_err, 0, sizeof(unsigned), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fcuda(f, e);

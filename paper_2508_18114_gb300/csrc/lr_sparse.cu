@@ -24,13 +24,16 @@
 //
 // FP32_G64 contexts run, by default, the fused persistent kernel of
 // lr_sparse_fused.cuh instead: one launch per integrate call, one CTA per
-// trajectory, all four phases of a stage inside the CTA (the four-launch path
-// stays selectable with LR_SPARSE_FUSED=0 and is the FP64 path).
+// trajectory (or, for batches larger than the grid, an equal span of the
+// batch's trajectory-steps per CTA), all phases of a stage inside the CTA
+// (the four-launch path stays selectable with LR_SPARSE_FUSED=0 and is the
+// FP64 path).
 //
 // Precisions: FP64 throughout, or FP32_G64 - the state, the operator apply,
 // T_k, the projection term and the RK4 update in FP32, the Gram matrix
-// accumulated in FP64 from the exact products of FP32 entries (an FP32
-// product has 48 significant bits), Cholesky, solves and the signal in FP64.
+// summed in double-word FP32 (~2^-48) from the exact products of FP32
+// entries (TwoProduct by one FMA), the M x M solves (FP64 here, double-word
+// in the fused kernel) and the signal in FP64.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -539,9 +542,11 @@ struct lr_sparse {
   int N, M, K, T, n_levels, nblk, ntile;
   int fp32;   // 1: FP32_G64 state arithmetic
   int fused;  // 1: the fused persistent kernel (FP32_G64), 0: four launches per RK4 stage
-  int n_cta;  // fused: persistent CTAs (one trajectory at a time each)
+  int n_cta;   // fused: persistent CTAs (n_team teams of team_c)
+  int n_team, team_c;   // fused: teams (one trajectory at a time each), CTAs per team
   size_t o_fsc;   // fused: per-CTA stage buffers
   size_t o_fvala, o_fdiag;   // fused: values of A without its static diagonal, and that diagonal (hi + lo)
+  size_t o_fflag;   // fused: [T] hand-over flags of the split schedule
   long nnz, max_steps, n_rec, step;
   double dt;   // RK4 step of the run (0 before the first integrate)
   int pop_every;
@@ -606,17 +611,19 @@ void layout(lr_sparse* s) {
   s->o_trace = take((size_t)s->T * s->n_rec * sizeof(double));
   if (s->fused) {
     const size_t Mp = (size_t)(s->M + 3) / 4 * 4;
-    s->o_fsc = take((size_t)s->n_cta * (3 + s->K + 1) * s->N * Mp * sizeof(float2));
+    s->o_fsc = take((size_t)s->n_team * (3 + s->K + 1) * s->N * Mp * sizeof(float2));
     s->o_fvala = take((size_t)s->nnz * sizeof(float2));
     s->o_fdiag = take((size_t)s->N * sizeof(float4));
+    s->o_fflag = take((size_t)s->T * sizeof(int));
   }
   s->total = o;
 }
 
 // Dynamic shared memory of the fused kernel: G and L^-1 (FP64-sized complex
-// [Mp][Mp+1]), T_k and XT_k (FP32 complex [K][Mp][Mp]), scalars.
+// [Mp][Mp+1]), T_k and XT_k (FP32 complex [K][Mp][Mp]), scalars, and the
+// partials of G (FP64 complex [Mp][Mp]) and the team's T_k ([K][Mp][Mp]).
 struct SfSmem {
-  int o_gd, o_w, o_tred, o_xt, o_misc, total;
+  int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum, total;
 };
 SfSmem sf_smem(int M, int K) {
   const int Mp = (M + 3) / 4 * 4;
@@ -632,6 +639,10 @@ SfSmem sf_smem(int M, int K) {
   o += K * Mp * Mp * (int)sizeof(float2);
   L.o_misc = o;
   o += 96 * (int)sizeof(double);
+  L.o_gpart = o;
+  o += Mp * Mp * (int)sizeof(double2);
+  L.o_tsum = o;
+  o += K * Mp * Mp * (int)sizeof(float2);
   L.total = o;
   return L;
 }
@@ -639,11 +650,54 @@ SfSmem sf_smem(int M, int K) {
 cudaError_t raise_fused_smem(int bytes) {
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, sfz::sf_kernel);
-  if (e != cudaSuccess) return e;
-  if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
-  return cudaFuncSetAttribute(sfz::sf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for (const void* k : {(const void*)sfz::sf_kernel<false>, (const void*)sfz::sf_kernel<true>}) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    if (fa.maxDynamicSharedSizeBytes >= bytes && fa.nonPortableClusterSizeAllowed) continue;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < bytes)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Team size of the fused kernel for a batch of T trajectories on `sms` SMs:
+// one CTA per trajectory when the batch fills the grid, else the largest team
+// (<= 16 CTAs, >= 64 rows per CTA) that keeps the teams within the SMs and
+// that the GPU can hold as resident clusters. LR_SPARSE_C forces a size.
+void fused_teams(lr_sparse* s, int sms) {
+  int C = 1;
+  if (s->T < sms) C = std::max(1, std::min({16, sms / s->T, s->N / 64}));
+  if (const char* e = getenv("LR_SPARSE_C")) C = std::max(1, std::min(16, atoi(e)));
+  C = std::min(C, s->N);
+  const SfSmem L = sf_smem(s->M, s->K);
+  for (; C > 1; --C) {   // the largest team that fits as a cluster
+    if (raise_fused_smem(L.total) != cudaSuccess) break;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C * std::max(1, std::min(s->T, sms / C)));
+    cfg.blockDim = dim3(sfz::NT);
+    cfg.dynamicSmemBytes = L.total;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, sfz::sf_kernel<true>, &cfg) == cudaSuccess && ncl > 0) {
+      s->team_c = C;
+      s->n_team = std::min(s->T, ncl);
+      s->n_cta = C * s->n_team;
+      return;
+    }
+  }
+  cudaGetLastError();
+  s->team_c = 1;
+  s->n_team = std::min(s->T, sms);
+  s->n_cta = s->n_team;
 }
 
 SpDev dev(const lr_sparse* s) {
@@ -844,14 +898,14 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   // the fused kernel: FP32_G64, unless LR_SPARSE_FUSED=0 selects the four-launch path;
   // one persistent CTA per SM (fewer when the batch is smaller)
   s->fused = 0;
-  s->n_cta = 0;
+  s->n_cta = s->n_team = s->team_c = 0;
   const char* fz_env = getenv("LR_SPARSE_FUSED");
   if (s->fp32 && !(fz_env && strcmp(fz_env, "0") == 0)) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
                                                    cudaSuccess && sms > 0) {
       s->fused = 1;
-      s->n_cta = std::min(n_traj, sms);
+      fused_teams(s, sms);
     } else {
       cudaGetLastError();
     }
@@ -1021,6 +1075,12 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
     a.pulse = d.pulse;
     a.err = d.err;
     a.Z = static_cast<float2*>(d.Z);
+    a.flag = reinterpret_cast<int*>(s->ws + s->o_fflag);
+    // equal spans of trajectory-steps per CTA when the batch has more
+    // trajectories than CTAs (LR_SPARSE_SPLIT=0: whole trajectories per CTA)
+    const char* sp_env = getenv("LR_SPARSE_SPLIT");
+    a.split = s->team_c == 1 && s->T > s->n_cta && n_steps > 0 && !(sp_env && strcmp(sp_env, "0") == 0);
+    a.C = a.split ? 1 : s->team_c;
     a.scratch = reinterpret_cast<float2*>(s->ws + s->o_fsc);
     a.beta = d.beta;
     a.pops = d.pops;
@@ -1045,7 +1105,48 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
     a.o_tred = L.o_tred;
     a.o_xt = L.o_xt;
     a.o_misc = L.o_misc;
-    sfz::sf_kernel<<<s->n_cta, sfz::NT, L.total, st>>>(a);
+    a.o_gpart = L.o_gpart;
+    a.o_tsum = L.o_tsum;
+    if (a.split) {
+      // the hand-over waits need every CTA resident: a cooperative launch
+      // (refused, rather than run, when the grid does not fit)
+      int per_sm = 0, dev = 0, sms = 0;
+      cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sfz::sf_kernel<false>, sfz::NT, L.total);
+      if (e1 == cudaSuccess) e1 = cudaGetDevice(&dev);
+      if (e1 == cudaSuccess) e1 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e1 != cudaSuccess) return cuda_fail(s, e1);
+      if (per_sm * sms < s->n_cta) return fail(s, LR_ERR_CUDA, "split schedule: CTAs do not fit at once");
+      e1 = cudaMemsetAsync(a.flag, 0, (size_t)s->T * sizeof(int), st);
+      if (e1 != cudaSuccess) return cuda_fail(s, e1);
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(s->n_cta);
+      cfg.blockDim = dim3(sfz::NT);
+      cfg.dynamicSmemBytes = L.total;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      e1 = cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false>, a);
+      if (e1 != cudaSuccess) return cuda_fail(s, e1);
+    } else {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(s->n_cta);
+      cfg.blockDim = dim3(sfz::NT);
+      cfg.dynamicSmemBytes = L.total;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = a.C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e1 =
+          a.C > 1 ? cudaLaunchKernelEx(&cfg, sfz::sf_kernel<true>, a) : cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false>, a);
+      if (e1 != cudaSuccess) return cuda_fail(s, e1);
+    }
   } else if (s->fp32) {
     launch_step_kernels<float2>(s, d, p, s->step, n_steps, dt, st);
   } else {
@@ -1109,9 +1210,10 @@ extern "C" lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, doub
   return LR_OK;
 }
 
-extern "C" lr_status lr_sparse_query(const lr_sparse* s, int* fused) {
+extern "C" lr_status lr_sparse_query(const lr_sparse* s, int* fused, int* team) {
   if (!s || !fused) return LR_ERR_ARG;
   *fused = s->fused;
+  if (team) *team = s->fused ? s->team_c : 0;
   return LR_OK;
 }
 

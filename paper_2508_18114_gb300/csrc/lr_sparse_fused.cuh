@@ -4,11 +4,21 @@
 // operator set given as CSR rows with time channels, integrated by one launch
 // per lr_sparse_integrate call.
 //
-// One CTA integrates one trajectory at a time (persistent over the batch).
+// A team of C CTAs (a thread-block cluster, C = 1 .. 16) integrates one
+// trajectory at a time (persistent over the batch); CTA q of the team owns the
+// rows [N q / C, N (q + 1) / C). When the batch has more trajectories than the
+// grid has CTAs, teams are single CTAs and each takes an equal span of the
+// batch's trajectory-steps instead: a trajectory cut between two CTAs passes
+// its state Z_n from one to the other through global memory (release /
+// acquire on a per-trajectory flag).
 // The stage input Z_s, the operator images Y_k = L_k(t) Z_s (and r(t) Z_s at
-// the first stage of a step) and the RK4 accumulator live in a per-CTA global
-// region that stays L2-resident; every phase of a stage runs inside the CTA,
-// separated by block barriers only:
+// the first stage of a step) and the RK4 accumulator live in a per-team
+// global region that stays L2-resident. Per stage, each CTA works on its own
+// rows (the operator gathers read any row), with two team barriers: B1 after
+// the partial sums of G, T_k and the signal over its rows (every CTA then adds
+// the team's partials in rank order from distributed shared memory and runs
+// the M x M phase itself), B2 after the RK4 update (the new Z_s is visible).
+// The phases:
 //   C  channel factors Omega(t)^a e^{i q w_d t} of the stage time (FP64,
 //      rounded once to FP32);
 //   Y  Y_k = L_k(t) Z_s by CSR gathers; at the first stage of every step also
@@ -23,16 +33,23 @@
 //      other entries by CSR gathers) + sum_k Y_k XT_k and the classical RK4
 //      stage update; the next stage input goes to the other
 //      Z_s buffer, the accumulator and Z_n are updated in place.
+#include <cooperative_groups.h>
+
 #include "lr_internal.cuh"
 
 namespace lr {
 namespace sfz {
+
+namespace cg = cooperative_groups;
 
 constexpr int NT = 512;       // 16 warps at <= 128 registers
 constexpr int NWARP = NT / 32;
 constexpr int NCH = 10;   // time channels
 constexpr int TP = 4;     // phase-P tile edge
 constexpr int TR = 4;     // phase-F rows per thread tile
+// bound of the wait for a head piece (~10 s at 2 GHz); the wait normally ends
+// at once, since the previous CTA runs that head first
+constexpr long long SPLIT_WAIT_BUDGET = 20000000000LL;
 
 struct Args {
   const int* rowptr;   // [(K + 2) (N + 1)]
@@ -45,16 +62,19 @@ struct Args {
   const PulseDev* pulse;   // per trajectory
   unsigned* err;
   float2* Z;               // state [T][N][M]
-  float2* scratch;         // per CTA: Z_s [2][N][Mp], Y [K + 1][N][Mp], accumulator [N][Mp]
+  int* flag;               // [T] split schedule: 1 once the head of trajectory t is written
+  int split;               // 1: equal spans of trajectory-steps per CTA (cooperative launch)
+  float2* scratch;         // per team: Z_s [2][N][Mp], Y [K + 1][N][Mp], accumulator [N][Mp]
   double2* beta;           // [T][max_steps + 1]
   double *pops, *nphot, *trace;
   int N, M, Mp, K, T, n_levels;
+  int C;                   // CTAs per team (cluster size; 1 with the split schedule)
   double wd, tau, dt;
   long max_steps, n_rec;
   int pop_every;
   long step0, n_steps;
   // byte offsets in dynamic shared memory
-  int o_gd, o_w, o_tred, o_xt, o_misc;
+  int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum;
 };
 
 struct DW {
@@ -254,6 +274,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int tid)
   __syncthreads();
 }
 
+// TEAM = false: teams of one CTA (C = 1 known at compile time; the equal-span
+// schedule); TEAM = true: clusters of a.C CTAs.
+template <bool TEAM>
 __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
@@ -268,28 +291,88 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
     for (int j = 0; j <= i; ++j) tri[i * (i + 1) / 2 + j] = make_short2((short)i, (short)j);
   double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);   // [Mp][Mp+1]  G -> L -> G^-1
   double2* W = reinterpret_cast<double2*>(smem + a.o_w);     // [Mp][Mp+1]  L^-1
-  float2* Tred = reinterpret_cast<float2*>(smem + a.o_tred);  // [K][Mp*Mp]  T_k
+  float2* Tred = reinterpret_cast<float2*>(smem + a.o_tred);  // [K][Mp*Mp]  T_k over this CTA's rows
   float2* XT = reinterpret_cast<float2*>(smem + a.o_xt);      // [K][Mp][Mp] (l, m)
-  double* misc = reinterpret_cast<double*>(smem + a.o_misc);  // [0] not-PD flag, [32..64) 1/D, [64..] populations
+  // [0] not-PD flag, [8..11) signal partials (Re, Im beta, photons), [32..64) 1/D,
+  // [64..96) population partials
+  double* misc = reinterpret_cast<double*>(smem + a.o_misc);
+  double2* gpart = reinterpret_cast<double2*>(smem + a.o_gpart);   // [Mp][Mp]  G over this CTA's rows
+  float2* tsum = reinterpret_cast<float2*>(smem + a.o_tsum);       // [K][Mp*Mp]  T_k of the team
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = TEAM ? a.C : 1;
+  const int q = C > 1 ? (int)cluster.block_rank() : 0;
+  const int team = blockIdx.x / C, n_teams = gridDim.x / C;
+  const int r_lo = (int)((long long)N * q / C), r_hi = (int)((long long)N * (q + 1) / C), NR = r_hi - r_lo;
+  auto team_sync = [&]() {
+    if (C > 1)
+      cluster.sync();
+    else
+      __syncthreads();
+  };
+  // rank r's copy of a shared-memory object of this CTA
+  auto at_rank = [&](auto* p, int r) { return r == q ? p : cluster.map_shared_rank(p, r); };
   const size_t zsb = (size_t)N * Mp;
-  float2* zs0 = a.scratch + (size_t)blockIdx.x * (size_t)(3 + K + 1) * zsb;
+  float2* zs0 = a.scratch + (size_t)team * (size_t)(3 + K + 1) * zsb;
   float2* ybuf = zs0 + 2 * zsb;              // Y_1 .. Y_K, then r Z_s
   float2* accg = zs0 + (2 + K + 1) * zsb;
   const double dt = a.dt;
   const int pe = a.pop_every;
 
-  for (int tj = blockIdx.x; tj < a.T; tj += gridDim.x) {
+  // Steps [s_a, s_b) (relative to step0) of trajectory tj, and the signal at
+  // s_b unless the piece is a head (its continuation evaluates it). A tail
+  // piece first waits for the head's state; a head piece publishes it.
+  auto piece = [&](int tj, long s_a, long s_b, bool head, bool tail) {
     const PulseDev pulse = a.pulse[tj];
     float2* Zn = a.Z + (size_t)tj * N * M;
-    for (long long e = tid; e < (long long)N * Mp; e += NT) {
-      const int n = (int)(e / Mp), m = (int)(e - (long long)n * Mp);
-      zs0[e] = m < M ? Zn[(size_t)n * M + m] : make_float2(0.f, 0.f);
+    if (tail) {
+      if (tid == 0) {
+        const long long t0 = clock64();
+        volatile int* f = a.flag + tj;
+        while (*f == 0) {
+          if (clock64() - t0 > SPLIT_WAIT_BUDGET) {
+            set_error(a.err, DEV_TIMEOUT);
+            break;
+          }
+        }
+        __threadfence();
+        *f = 0;   // consumed: ready for the next launch
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    if (C > 1) cluster.sync();   // the team is done with the previous trajectory's rows
+    for (long long e = (long long)r_lo * Mp + tid; e < (long long)r_hi * Mp; e += NT) {
+      const int n = (int)(e / Mp), m = (int)(e - (long long)n * Mp);
+      zs0[e] = m < M ? __ldcg(Zn + (size_t)n * M + m) : make_float2(0.f, 0.f);
+    }
+    team_sync();
     int cur = 0;
-    const long s_end = a.step0 + a.n_steps;
-    for (long step = a.step0;; ++step) {
+    // rank 0 adds the team's signal and population partials (after a team
+    // barrier) and writes the step's records
+    auto publish = [&](long step, bool record) {
+      if (q != 0 || tid != 0) return;
+      double sg[3] = {0.0, 0.0, 0.0};
+      for (int r = 0; r < C; ++r) {
+        const double* mr = at_rank(misc, r);
+        for (int c = 0; c < 3; ++c) sg[c] += mr[8 + c];
+      }
+      a.beta[(size_t)tj * (a.max_steps + 1) + step] = mk(sg[0], sg[1]);
+      if (!isfinite(sg[0]) || !isfinite(sg[1])) set_error(a.err, DEV_NONFINITE);
+      if (!record) return;
+      const long rec = step / pe;
+      a.nphot[(size_t)tj * a.n_rec + rec] = sg[2];
+      double tr = 0.0;
+      for (int lv = 0; lv < a.n_levels; ++lv) {
+        double v = 0.0;
+        for (int r = 0; r < C; ++r) v += at_rank(misc, r)[64 + lv];
+        a.pops[((size_t)tj * a.n_rec + rec) * a.n_levels + lv] = v;
+        tr += v;
+      }
+      a.trace[(size_t)tj * a.n_rec + rec] = tr;
+    };
+    const long s_end = a.step0 + s_b;
+    for (long step = a.step0 + s_a;; ++step) {
       const bool last = step == s_end;
+      if (last && head) break;
       for (int stage = 0; stage < 4; ++stage) {
         const bool record = stage == 0 && (step % pe) == 0;
         const float2* zc = zs0 + (size_t)cur * zsb;
@@ -309,9 +392,9 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           const int nk = stage == 0 ? K + 1 : K;
           const int mq = Mq / 4;
           double acc3[3] = {0.0, 0.0, 0.0};   // Re, Im tr(Z^dag r Z), |r Z|^2
-          for (long long t = tid; t < (long long)N * mq * nk; t += NT) {
-            const int k = (int)(t / ((long long)N * mq));
-            const int rem = (int)(t - (long long)k * N * mq), n = rem / mq, m0 = (rem - n * mq) * 4;
+          for (long long t = tid; t < (long long)NR * mq * nk; t += NT) {
+            const int k = (int)(t / ((long long)NR * mq));
+            const int rem = (int)(t - (long long)k * NR * mq), nl = rem / mq, m0 = (rem - nl * mq) * 4, n = r_lo + nl;
             float2 y[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
                            make_float2(0.f, 0.f)};
             row_gather4(a, 1 + k, n, m0, zc, chi, y);
@@ -330,17 +413,14 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           }
           if (stage == 0) {
             block_sum<3>(acc3, red, tid);
-            if (tid == 0) {
-              a.beta[(size_t)tj * (a.max_steps + 1) + step] = mk(acc3[0], acc3[1]);
-              if (!isfinite(acc3[0]) || !isfinite(acc3[1])) set_error(a.err, DEV_NONFINITE);
-              if (record) a.nphot[(size_t)tj * a.n_rec + step / pe] = acc3[2];
-            }
+            if (tid == 0)
+              for (int c = 0; c < 3; ++c) misc[8 + c] = acc3[c];
           }
           if (record) {
             // level populations: warp per level, fixed order over the rows
             for (int lv = warp; lv < a.n_levels; lv += NWARP) {
               double s = 0.0;
-              for (int n = lane; n < N; n += 32) {
+              for (int n = r_lo + lane; n < r_hi; n += 32) {
                 if (a.level[n] != lv) continue;
                 const float2* z = zc + (size_t)n * Mp;
                 for (int m = 0; m < M; ++m) s += (double)z[m].x * z[m].x + (double)z[m].y * z[m].y;
@@ -350,17 +430,12 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             }
           }
           __syncthreads();
-          if (record && tid == 0) {
-            const long rec = step / pe;
-            double tr = 0.0;
-            for (int lv = 0; lv < a.n_levels; ++lv) {
-              a.pops[((size_t)tj * a.n_rec + rec) * a.n_levels + lv] = misc[64 + lv];
-              tr += misc[64 + lv];
-            }
-            a.trace[(size_t)tj * a.n_rec + rec] = tr;
-          }
         }
-        if (last) break;
+        if (last) {
+          team_sync();
+          publish(step, record);
+          break;
+        }
         // ================= P: Gram and T_k tiles over all rows
         {
           const int nt_ = Mq / TP;
@@ -382,7 +457,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               for (int i = 0; i < TP; ++i)
 #pragma unroll
                 for (int j = 0; j < TP; ++j) acc[i][j][0] = acc[i][j][1] = DW{0.f, 0.f};
-              for (int n = lane; n < N; n += 32) {
+              for (int n = r_lo + lane; n < r_hi; n += 32) {
                 float2 zi[4], zj[4];
                 load4(zc + (size_t)n * Mp + i0, zi);
                 load4(zc + (size_t)n * Mp + j0, zj);
@@ -412,9 +487,9 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               });
               const int i = i0 + (lane >> 3), j = j0 + ((lane >> 1) & 3), c = lane & 1;
               const double val = (double)v[0].hi + (double)v[0].lo;
-              if (i <= j) {   // G[i][j] and its conjugate G[j][i]
-                reinterpret_cast<double*>(Gd)[2 * (i * ldg + j) + c] = val;
-                reinterpret_cast<double*>(Gd)[2 * (j * ldg + i) + c] = c ? -val : val;
+              if (i <= j) {   // G[i][j] and its conjugate G[j][i] over this CTA's rows
+                reinterpret_cast<double*>(gpart)[2 * (i * Mp + j) + c] = val;
+                reinterpret_cast<double*>(gpart)[2 * (j * Mp + i) + c] = c ? -val : val;
               }
             } else {
               const int t2 = task - n_g, k = t2 / (nt_ * nt_), r2 = t2 - k * nt_ * nt_, ti = r2 / nt_,
@@ -426,7 +501,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               for (int i = 0; i < TP; ++i)
 #pragma unroll
                 for (int j = 0; j < TP; ++j) tr_[i][j] = ti_[i][j] = 0.f;
-              for (int n = lane; n < N; n += 32) {
+              for (int n = r_lo + lane; n < r_hi; n += 32) {
                 float2 z[4], y[4];
                 load4(zc + (size_t)n * Mp + i0, z);
                 load4(yk + (size_t)n * Mp + j0, y);
@@ -454,7 +529,9 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             }
           }
         }
-        __syncthreads();
+        // ================= B1: the team's partials are visible
+        team_sync();
+        if (stage == 0) publish(step, record);
         // ================= R: G = L D L^dag, L^-1, G^-1 (double-word FP32), XT_k
         {
           DWC* Gw = reinterpret_cast<DWC*>(Gd);
@@ -462,9 +539,24 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           DW* dinv = reinterpret_cast<DW*>(misc + 32);   // [M] 1 / D[k]
           float* diag0 = reinterpret_cast<float*>(W);    // W[k][0] slot: the diagonal of G
           if (tid == 0) misc[0] = 0.0;
+          // T_k of the team: the partials added in rank order (the same in every CTA)
+          for (int e = tid; e < K * MM; e += NT) {
+            float2 v = at_rank(Tred, 0)[e];
+            for (int r = 1; r < C; ++r) {
+              const float2 u = at_rank(Tred, r)[e];
+              v.x += u.x;
+              v.y += u.y;
+            }
+            tsum[e] = v;
+          }
           for (int e = tid; e < M * (M + 1) / 2; e += NT) {
             const int i = tri[e].x, j = tri[e].y;
-            const double2 v = Gd[i * ldg + j];
+            double2 v = at_rank(gpart, 0)[i * Mp + j];
+            for (int r = 1; r < C; ++r) {
+              const double2 u = at_rank(gpart, r)[i * Mp + j];
+              v.x += u.x;
+              v.y += u.y;
+            }
             DWC g;
             g.re = dw_make(v.x);
             g.im = dw_make(v.y);
@@ -533,7 +625,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             const int k = e / (Mq * Mq), lq = e - k * (Mq * Mq), l = lq / Mq, m = lq - l * Mq;
             float xr = 0.f, xi = 0.f;
             if (l < M && m < M) {
-              const float2* Tk = Tred + k * MM;
+              const float2* Tk = tsum + k * MM;
               DWC acc;
               acc.re.hi = acc.re.lo = acc.im.hi = acc.im.lo = 0.0f;
               for (int j = 0; j < M; ++j) {
@@ -554,15 +646,15 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           const float h6_hi = (float)h6d, h6_lo = (float)(h6d - (double)h6_hi);
           const bool zn_vec = (M % 2) == 0;
           float2* zo_buf = zs0 + (size_t)(cur ^ 1) * zsb;
-          const int mq = Mq / 4, nrt = (N + TR - 1) / TR;
+          const int mq = Mq / 4, nrt = (NR + TR - 1) / TR;
           for (int tile = tid; tile < nrt * mq; tile += NT) {
-            const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = rt * TR;
+            const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = r_lo + rt * TR;
             float2 f[TR][4];
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
 #pragma unroll
               for (int u = 0; u < 4; ++u) f[r][u] = make_float2(0.f, 0.f);
-              if (l0 + r < N) {
+              if (l0 + r < r_hi) {
                 // the static diagonal of A as hi + lo floats (FP32 does not round the
                 // detunings), then the other entries of the row
                 const float4 dg = a.diag_a[l0 + r];
@@ -584,7 +676,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 float4 y2[TR];
 #pragma unroll
                 for (int r = 0; r < TR; ++r)
-                  y2[r] = l0 + r < N ? *reinterpret_cast<const float4*>(yk + (size_t)(l0 + r) * Mp + l)
+                  y2[r] = l0 + r < r_hi ? *reinterpret_cast<const float4*>(yk + (size_t)(l0 + r) * Mp + l)
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int ll = 0; ll < 2; ++ll) {
@@ -608,7 +700,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
               const int n = l0 + r;
-              if (n >= N) continue;
+              if (n >= r_hi) continue;
               float2 zo[4];
 #pragma unroll
               for (int pr = 0; pr < 2; ++pr) {
@@ -661,12 +753,35 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             }
           }
           cur ^= 1;
-          __syncthreads();
+          team_sync();   // B2: the next stage input is visible to the team
         }
       }
       if (last) break;
     }
+    if (head && tid == 0) {   // every thread's Z_n rows are written (barrier above)
+      __threadfence();
+      atomicExch(a.flag + tj, 1);
+    }
+  };
+
+  if (!a.split) {
+    for (int tj = team; tj < a.T; tj += n_teams) piece(tj, 0, a.n_steps, false, false);
+    if (C > 1) cluster.sync();   // no CTA leaves while the team may read its shared memory
+    return;
   }
+  // Equal spans of the T x n_steps trajectory-steps, in trajectory-major
+  // order, one per CTA (T >= gridDim.x, so a span covers at least one whole
+  // trajectory's steps and cuts at most two trajectories): the head of the
+  // trajectory cut at the span's end runs first, then the whole trajectories,
+  // then the tail of the trajectory cut at its start, whose head the previous
+  // CTA ran first. (The launch is cooperative: every CTA is resident.)
+  const long long nts = (long long)a.T * a.n_steps;
+  const long long lo = nts * blockIdx.x / gridDim.x, hi = nts * (blockIdx.x + 1) / gridDim.x;
+  const int ta = (int)(lo / a.n_steps), tb = (int)((hi - 1) / a.n_steps);
+  const long sa = (long)(lo - (long long)ta * a.n_steps), sb = (long)(hi - (long long)tb * a.n_steps);
+  if (sb < a.n_steps) piece(tb, 0, sb, true, false);
+  for (int tj = sa > 0 ? ta + 1 : ta; tj <= (sb < a.n_steps ? tb - 1 : tb); ++tj) piece(tj, 0, a.n_steps, false, false);
+  if (sa > 0) piece(ta, sa, a.n_steps, false, true);
 }
 
 }  // namespace sfz

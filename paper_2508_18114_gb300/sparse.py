@@ -107,8 +107,15 @@ class SparseBatch:
     def fused(self) -> bool:
         """True when the context runs the fused persistent kernel."""
         f = C.c_int()
-        self._check(self._lib.lr_sparse_query(self._h, C.byref(f)))
+        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), None))
         return bool(f.value)
+
+    @property
+    def team(self) -> int:
+        """CTAs per trajectory of the fused kernel (0: the four-launch path)."""
+        f, t = C.c_int(), C.c_int()
+        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), C.byref(t)))
+        return t.value
 
     def _check(self, st: int):
         if st != 0:

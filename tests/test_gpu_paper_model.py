@@ -29,7 +29,7 @@ TOL = {"fp64": dict(beta=1e-10, pops=1e-10, nphot=1e-10, trace=1e-11),
 
 
 def _run(dims, M, pulses, tau, dt, n_steps, pop_every, check_traj, params, split=None, precision="fp64",
-         frame="rot"):
+         frame="rot", team=None):
     import torch
     from paper_2508_18114_gb300 import sparse
     Nl, Nu, Nt = dims
@@ -37,6 +37,8 @@ def _run(dims, M, pulses, tau, dt, n_steps, pop_every, check_traj, params, split
     T = len(pulses)
     psi = [i % 2 for i in range(T)]          # |0_l, 0_u, g> and |0_l, 0_u, e>
     b = sparse.SparseBatch(model, M, pulses, tau, n_steps, pop_every=pop_every, precision=precision)
+    if team is not None:
+        assert b.team == team
     b.set_initial(psi, SEED, EPS)
     if split:
         b.integrate(dt, split)
@@ -306,3 +308,68 @@ def test_fused_kernel_runs_fp32_and_matches_the_launch_path(monkeypatch):
     monkeypatch.delenv("LR_SPARSE_FUSED")
     b = sparse.SparseBatch(model, 6, pulses[:2], 0.3, 10, precision="fp64")
     assert not b.fused
+
+
+def test_fused_split_schedule_is_bitwise(monkeypatch):
+    """A batch with more trajectories than the grid has CTAs runs the equal-span
+    schedule (trajectories cut between two CTAs hand their state over through
+    global memory); every trajectory's arithmetic is unchanged, so the results
+    equal bitwise those of the whole-trajectory schedule, over two calls whose
+    spans cut trajectories at different steps."""
+    import torch
+    from paper_2508_18114_gb300 import sparse
+    P = _params(kappa=2.0, gamma=0.1)
+    wd = P["wd"]
+    model = sparse.paper_model(10, 3, 5, **P)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    T = 2 * n_sm + 36
+    pulses = [(0, [TP * (0.2 + 0.6 * ((7 * j) % 11) / 10.0), wd, 0.05, 0.0]) for j in range(T)]
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("LR_SPARSE_SPLIT", mode)
+        b = sparse.SparseBatch(model, 6, pulses, 0.3, 100, pop_every=10, precision="fp32_g64")
+        assert b.fused
+        b.set_initial([j % 2 for j in range(T)], SEED, EPS)
+        b.integrate(5e-4, 37)
+        b.integrate(5e-4, 23)
+        out[mode] = (b.observables(), b.get_state())
+        del b
+    (o1, z1), (o0, z0) = out["1"], out["0"]
+    assert np.array_equal(o1["beta"][:, :61], o0["beta"][:, :61])
+    for k in ("pops", "nphot", "trace"):   # records at steps 0, 10, ..., 60
+        assert np.array_equal(o1[k][:, :7], o0[k][:, :7]), k
+    assert np.array_equal(z1, z0)
+    assert np.all(np.isfinite(o1["beta"][:, :61])) and np.abs(o1["trace"][:, 6] - 1.0).max() < 1e-3
+
+
+@pytest.mark.parametrize("team", [2, 3, 7, 16])
+def test_fused_teams_parity(monkeypatch, team):
+    """Small batches run the fused kernel on teams of C CTAs (a cluster; each
+    CTA owns N/C rows, the team adds its partial G, T_k and signal sums in
+    rank order through distributed shared memory): parity with the oracle at
+    the FP32_G64 bounds, N = 150 (ragged row ranges for C = 7 and 16), two
+    integrate calls."""
+    monkeypatch.setenv("LR_SPARSE_C", str(team))
+    P = _params(g=TP * 0.3, kappa=1.0, gamma=0.05)
+    wd = P["wd"]
+    pulses = [(0, [TP * 0.9, wd, 0.05, 0.0]), (0, [TP * 0.9, wd, 0.05, 0.0]), (0, [TP * 0.5, wd, 0.08, 0.0]),
+              (0, [TP * 0.5, wd, 0.08, 0.0])]
+    got = _run((10, 3, 5), 6, pulses, 0.3, 5e-4, 600, 50, [0, 3], P, split=233, precision="fp32_g64", team=team)
+    assert np.abs(got["beta"][0]).max() > 1e-2
+
+
+def test_fused_team_default_for_small_batches():
+    """Without an override, a two-trajectory batch of the N = 2000 model runs
+    on teams of several CTAs, and a batch as large as the grid on one CTA per
+    trajectory."""
+    import torch
+    from paper_2508_18114_gb300 import sparse
+    P = _params()
+    model = sparse.paper_model(100, 4, 5, **P)
+    p = (0, [TP * 0.15, P["wd"], 2.5, 0.0])
+    b = sparse.SparseBatch(model, 20, [p, p], 40.0, 10, precision="fp32_g64")
+    assert b.team > 1
+    del b
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    b = sparse.SparseBatch(model, 20, [p] * n_sm, 40.0, 10, precision="fp32_g64")
+    assert b.team == 1
