@@ -415,12 +415,13 @@ def run_ours(args):
         pipe = "FP32 FMA"
     achieved = fl / (ms * 1e-3 / args.steps) / 1e12
     # DRAM bytes per launch from one ncu capture of this kernel on a 76-trajectory, 10-step case
-    # of the same workload (2.462 MB per trajectory-step at the same number of resident teams),
-    # scaled by the trajectory-steps of one launch; only for the kernel that capture measured
+    # of the same workload (0.338 GB read + 1.586 GB written for 760 trajectory-steps: 2.532 MB
+    # per trajectory-step at the same number of resident teams), scaled by the trajectory-steps
+    # of one launch; only for the kernel that capture measured
     traffic = None
     if (wl.name == "c4" and prec == "fp32_g64" and engine == "fused" and info.team_size == 2
             and not info.stage_in_smem and info.tensor_passes == 0):
-        traffic = 2.462e6 * ntraj * chunk
+        traffic = 2.532e6 * ntraj * chunk
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "kernel": "integrate (%s engine)" % engine,
@@ -665,8 +666,12 @@ def run_paper(args):
     fma_clk = FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK
     peak = SMS * fma_clk * 2 * mhz * 1e6 / 1e12
     achieved = fl / (ms * 1e-3 / args.steps) / 1e12
-    kname = ("sf_kernel (fused persistent sparse kernel, one launch per integrate)" if b.fused
-             else "integrate (sparse engine, 4 launches per RK4 stage)")
+    team = b.team
+    split = b.fused and team == 1 and T > torch.cuda.get_device_properties(dev).multi_processor_count \
+        and os.environ.get("LR_SPARSE_SPLIT", "1") != "0"
+    kname = (("sf_kernel (fused persistent sparse kernel, one launch per integrate; %s)"
+              % ("equal spans of trajectory-steps per CTA" if split else "%d CTA(s) per trajectory" % team))
+             if b.fused else "integrate (sparse engine, 4 launches per RK4 stage)")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": kname,
                 "peak_source": "%s FMA pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
@@ -731,6 +736,8 @@ def run_paper(args):
                                       "x".join(map(str, wl.dims)), wl.M, dt, wl.tau, prec),
                        "trajectories": T, "N": model["N"], "M": wl.M, "nnz": int(model["nnz"]),
                        "engine": "sparse (fused persistent kernel)" if b.fused else "sparse (four launches per stage)",
+                       "schedule": (("equal spans of the batch's trajectory-steps, one per CTA" if split else
+                                     "teams of %d CTA(s), one trajectory at a time" % team) if b.fused else None),
                        "chunk_rk4_steps": chunk,
                        "parallelism": "dp%d (independent replicas)" % world,
                        "l2": "flushed (256 MiB write) between timed steps"},

@@ -109,7 +109,9 @@ typedef enum { LR_PREC_FP64 = 0, LR_PREC_FP32_G64 = 1, LR_PREC_FP32 = 2, LR_PREC
 
 /* PLAIN: straightforward HBM-resident kernels, several launches per RK4
  * stage (the reference GPU path). FUSED: one persistent launch per
- * integrate call, state resident on chip. AUTO picks FUSED when supported. */
+ * integrate call, state resident on chip. AUTO picks FUSED when supported,
+ * except for FP64 contexts whose fused plan needs teams of more than two CTAs
+ * per trajectory (batches far smaller than the GPU), which run PLAIN. */
 typedef enum { LR_ENGINE_AUTO = 0, LR_ENGINE_PLAIN = 1, LR_ENGINE_FUSED = 2 } lr_engine;
 
 typedef struct {

@@ -202,6 +202,13 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   }
   c->engine = opt->engine == LR_ENGINE_PLAIN ? LR_ENGINE_PLAIN
               : (fused_ok ? LR_ENGINE_FUSED : LR_ENGINE_PLAIN);
+  // AUTO in FP64 with teams of more than two CTAs per trajectory (a batch far
+  // smaller than the GPU): every CTA of a team repeats the FP64 M x M phase, a
+  // chain of ~M dependent eliminations on the FP64 pipe, so the plain kernels,
+  // which spread that phase over the batch, are faster (GB300, N = 2000, M = 20,
+  // 2 trajectories: plain 1471, fused on teams of 10 853 traj*steps/s)
+  if (opt->engine == LR_ENGINE_AUTO && fused_ok && opt->precision == LR_PREC_FP64 && c->fused.C > 2)
+    c->engine = LR_ENGINE_PLAIN;
   if (c->engine == LR_ENGINE_PLAIN && opt->precision != LR_PREC_FP64) {
     delete c;
     return LR_ERR_UNSUPPORTED;

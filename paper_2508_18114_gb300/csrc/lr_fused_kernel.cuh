@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
   static_assert(TC == 0 || (ZSM == 0 && sizeof(T2) == 8), "tensor-core projection: FP32 state in L2 only");
   using T = typename Real<T2>::t;
   constexpr int TP = sizeof(T) == 4 ? 4 : 2;     // phase-P tile edge
-  constexpr int TR = sizeof(T) == 4 ? 4 : 2;     // phase-F rows per thread tile
+  constexpr int TR = sizeof(T) == 4 ? 5 : 2;     // phase-F rows per thread tile
   // first step of this launch: the device step counter (so that a replayed
   // capture of the launch continues the pulse run), else the argument
   const long step0 = a.p.dstep ? (long)*a.p.dstep : a.step0;

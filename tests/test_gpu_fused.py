@@ -199,3 +199,12 @@ def test_fused_not_positive_definite_is_reported():
         b.observables()
     assert ei.value.status == 5
     b.close()
+
+
+def test_auto_engine_choice():
+    """AUTO runs the fused kernel, except in FP64 when its plan would spread one
+    trajectory over teams of more than two CTAs (the single pulse at N = 2000),
+    where the plain kernels are faster."""
+    assert runner.make_batch(li.c2(n_steps=10), precision="fp64", max_steps=10).engine == "plain"
+    assert runner.make_batch(li.c2(n_steps=10), precision="fp32_g64", max_steps=10).engine == "fused"
+    assert runner.make_batch(li.c1(n_steps=10), precision="fp64", max_steps=10).engine == "fused"
