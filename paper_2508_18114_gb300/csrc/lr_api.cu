@@ -596,6 +596,7 @@ lr_status lr_query(const lr_ctx* c, lr_info* info) {
   info->team_size = c->engine == LR_ENGINE_FUSED ? c->fused.C : 0;
   info->stage_in_smem = c->engine == LR_ENGINE_FUSED ? c->fused.zs_smem : 0;
   info->tensor_passes = c->engine == LR_ENGINE_FUSED ? c->fused.tc : 0;
+  info->gram_tc = c->engine == LR_ENGINE_FUSED && c->fused.gram_mode == 2 ? 1 : 0;
   return LR_OK;
 }
 

@@ -17,13 +17,14 @@ namespace {
 
 struct SmemLayout {
   int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop, o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
-  int o_ta, o_tb, npad, total;
+  int o_ta, o_tb, npad, o_gs, total;
 };
 
 int al16(int x) { return (x + 15) / 16 * 16; }
 int al128(int x) { return (x + 127) / 128 * 128; }
 
-SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
+// gs: the two bf16 slice buffers of the tensor-core Gram
+SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc, int gs) {
   SmemLayout L{};
   int o = 0;
   L.o_zs = o;
@@ -45,7 +46,7 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
   L.o_xs = o;
   o += al16(2 * Mp * Mp * (int)es);
   L.o_misc = o;
-  o += al16(144 * (int)sizeof(double));
+  o += al16(168 * (int)sizeof(double));
   L.o_tab = o;
   o += al16(fz::TAB * 7 * (int)(es / 2));
   L.o_ta = L.o_tb = o;
@@ -59,14 +60,21 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc) {
     L.o_tb = o;
     o += al128(nbuf * L.npad * K * 4);
   }
+  L.o_gs = o;
+  if (gs) {
+    o = al128(o);
+    L.o_gs = o;
+    o += 2 * fz::GS_BUF;
+  }
   L.total = o;
   return L;
 }
 
 // tc: tensor-core passes of the projection (0: CUDA cores; 3 or 1: tcgen05,
 // L2-resident stage state and FP32 state with the double-word Gram only)
-const void* kernel_ptr(lr_precision prec, int zs_smem, int tc, int frame) {
+const void* kernel_ptr(lr_precision prec, int zs_smem, int tc, int frame, int gram_mode) {
   if (frame) return fz::rwa_kernel_ptr(prec, zs_smem);
+  if (gram_mode == 2) return (const void*)fz::fused_kernel<float2, 2, 0, 0, 0>;
   if (tc == 3) return (const void*)fz::fused_kernel<float2, 1, 0, 3, 0>;
   if (tc == 1) return (const void*)fz::fused_kernel<float2, 1, 0, 1, 0>;
   if (zs_smem) {
@@ -128,28 +136,35 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
   // Overrides for tuning and tests: LR_FUSED_C = cluster size, LR_FUSED_ZS =
   // "global" keeps the stage state in L2, LR_FUSED_TC = 0 keeps the FP32_G64
   // projection on the CUDA cores (3: only the tensor-core variant).
-  int force_c = 0, force_global = 0, force_tc = -1;
+  int force_c = 0, force_global = 0, force_tc = -1, gram_dw = 0;
   if (const char* e = getenv("LR_FUSED_C")) force_c = atoi(e);
+  if (const char* e = getenv("LR_FUSED_GRAM")) gram_dw = strcmp(e, "dw") == 0;
   if (const char* e = getenv("LR_FUSED_ZS")) force_global = strcmp(e, "global") == 0;
   if (const char* e = getenv("LR_FUSED_TC")) force_tc = atoi(e);
   struct Variant {
-    int zs_smem, tc;
+    int zs_smem, tc, gs;
   };
   std::vector<Variant> vars;
   if (prec == LR_PREC_TF32_G64) {
     if (frame) return false;   // the tensor-core variants are built for the lab frame only
-    vars.push_back({0, 1});
+    vars.push_back({0, 1, 0});
   } else {
     if (force_tc != 3) {
-      if (!force_global) vars.push_back({1, 0});
-      vars.push_back({0, 0});
+      if (!force_global) vars.push_back({1, 0, 0});
+      // FP32_G64 in the lab frame at Mp = 20: the Gram matrix on the tensor cores
+      // (LR_FUSED_GRAM=dw keeps the double-word CUDA-core sums)
+      if (prec == LR_PREC_FP32_G64 && !frame && Mp == 20 && !gram_dw)
+        vars.push_back({0, 0, 1});
+      else
+        vars.push_back({0, 0, 0});
     }
-    if (prec == LR_PREC_FP32_G64 && force_tc != 0 && !frame) vars.push_back({0, 3});
+    if (prec == LR_PREC_FP32_G64 && force_tc != 0 && !frame) vars.push_back({0, 3, 0});
   }
   double best = 1e300;
   for (const Variant& v : vars) {
-    const int zs_smem = v.zs_smem, tc = v.tc;
-    const void* kern = kernel_ptr(prec, zs_smem, tc, frame);
+    const int zs_smem = v.zs_smem, tc = v.tc, gs = v.gs;
+    const int gmode = gs ? 2 : (prec == LR_PREC_FP32_G64 || prec == LR_PREC_TF32_G64 ? 1 : 0);
+    const void* kern = kernel_ptr(prec, zs_smem, tc, frame, gmode);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
       cudaGetLastError();
@@ -163,7 +178,8 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
       if (force_c > 0 && C != force_c) continue;
       int R = 0;
       for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
-      const SmemLayout L = layout(R, Mp, zs_smem, es, tc);
+      if (gs && R > fz::GS_MAXR) continue;   // the slice sums stay exact for <= GS_MAXR rows
+      const SmemLayout L = layout(R, Mp, zs_smem, es, tc, gs);
       if (L.total > smem_max) continue;
       if (raise_smem_limit(kern, L.total) != cudaSuccess) {
         cudaGetLastError();
@@ -198,7 +214,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
       // fixed ~60 us per team (the M x M phase and the cluster barrier, ~M
       // sequential elimination steps) that does not shrink with C; teams run
       // trajectories in waves.
-      const double row_cost = zs_smem ? 1.0 : (tc == 3 ? 1.7 : tc == 1 ? 1.55 : 1.3);
+      const double row_cost = zs_smem ? 1.0 : (tc == 3 ? 1.7 : tc == 1 ? 1.55 : gs ? 1.0 : 1.3);
       const double waves = std::ceil((double)n_traj / used);
       double t = 0.0;
       for (const TrajDev& d : traj) {
@@ -220,7 +236,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
         plan->Mp = Mp;
         plan->R = R;
         plan->Nmax = Nmax;
-        plan->gram_mode = prec == LR_PREC_FP32_G64 || prec == LR_PREC_TF32_G64 ? 1 : 0;
+        plan->gram_mode = gmode;
         plan->es = (int)es;
       }
     }
@@ -249,8 +265,8 @@ cudaError_t fused_prepare(const FusedPlan& plan, lr_precision prec, void* scratc
   cudaError_t e = cudaMemcpy(scratch, plan.order.data(), sizeof(int) * n_traj, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
-  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es, plan.tc);
-  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame);
+  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es, plan.tc, plan.gram_mode == 2);
+  const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame, plan.gram_mode);
   e = raise_smem_limit(kern, L.total);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -259,7 +275,7 @@ cudaError_t fused_prepare(const FusedPlan& plan, lr_precision prec, void* scratc
 cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunParams& rp, lr_precision prec,
                             long step0, long n_steps, cudaStream_t s) {
   const size_t es = prec == LR_PREC_FP64 ? sizeof(double2) : sizeof(float2);
-  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es, plan.tc);
+  const SmemLayout L = layout(plan.R, plan.Mp, plan.zs_smem, es, plan.tc, plan.gram_mode == 2);
   fz::Args a{};
   a.p = p;
   a.rp = rp;
@@ -287,6 +303,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   a.o_ta = L.o_ta;
   a.o_tb = L.o_tb;
   a.npad = L.npad;
+  a.o_gs = L.o_gs;
   char* sc = static_cast<char*>(p.scratch);
   size_t off = ((sizeof(int) * rp.n_traj + 255) / 256) * 256;
   a.order = reinterpret_cast<const int*>(sc);
@@ -303,7 +320,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   cudaError_t e = cudaStreamIsCapturing(s, &cap);
   if (e != cudaSuccess) return e;
   if (cap == cudaStreamCaptureStatusNone) {
-    const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame);
+    const void* kern = kernel_ptr(prec, plan.zs_smem, plan.tc, plan.frame, plan.gram_mode);
     e = raise_smem_limit(kern, L.total);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -322,6 +339,7 @@ cudaError_t fused_integrate(const FusedPlan& plan, const DevPtrs& p, const RunPa
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (plan.frame) return fz::rwa_launch(cfg, prec, plan.zs_smem, a);
+  if (plan.gram_mode == 2) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 2, 0, 0, 0>, a);
   if (plan.tc == 3) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 3, 0>, a);
   if (plan.tc == 1) return cudaLaunchKernelEx(&cfg, fz::fused_kernel<float2, 1, 0, 1, 0>, a);
   if (plan.zs_smem) {

@@ -28,7 +28,7 @@ struct FusedPlan {
   int Mp;          // padded rank (multiple of 4)
   int R;           // largest rows per CTA
   int Nmax;        // largest N in the batch
-  int gram_mode;   // 0 native (bulk type), 1 double-word FP32 (FP64-class)
+  int gram_mode;   // 0 native (bulk type), 1 double-word FP32 (FP64-class), 2 on the tensor cores (FP64-class)
   int es;          // bytes per complex state element
   std::vector<int> order;   // trajectories, largest work first
 };

@@ -58,6 +58,7 @@ struct Args {
   int o_zs, o_slot, slot_bytes, s_gp, s_tp, s_pop;   // s_*: offsets inside one slot
   int o_gd, o_w, o_tred, o_trd, o_xs, o_misc, o_tab;
   int o_ta, o_tb, npad;   // tensor-core operand tiles (TC > 0), B rows (2 Mp padded to 16)
+  int o_gs;               // Gram on the tensor cores (GRAM_DW == 2): two slice buffers
   const int* order;
   void* zs_glob;      // global stage buffers, per cluster [C][2][R][Mp+1]
   void* acc_glob;     // RK4 accumulator, per cluster [Nmax*Mp]
@@ -116,6 +117,12 @@ __device__ __forceinline__ void dw_add(DW& s, const DW& o) {
   s.lo += err + o.lo;
 }
 __device__ __forceinline__ double dw_value(const DW& s) { return (double)s.hi + (double)s.lo; }
+__device__ __forceinline__ void dw_add_f(DW& s, float x) {   // s += x (Knuth's two-sum into hi)
+  const float t = s.hi + x;
+  const float bp = t - s.hi;
+  s.lo += (s.hi - (t - bp)) + (x - bp);
+  s.hi = t;
+}
 
 // Double-word arithmetic for the M x M phase (Dekker's product via FMA,
 // Knuth's two-sum; results normalised, ~2^-48 relative).
@@ -300,6 +307,44 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Gram matrix on the tensor cores (GRAM_DW == 2; Mp = 20, at most 1024 rows
+// per CTA). G = A^T A for A = [Re Z | Im Z] (rows x 40 reals) is formed
+// exactly enough to be FP64-class from bf16 MMAs, by slicing (the error-free
+// splitting of the Ozaki scheme): every column a is scaled by a power of two
+// 2^-e_a with 2^e_a above its largest entry and cut into GS_N integer slices
+// of 7 bits, x = sum_s k_s 2^(-7(s+1)), |k_0| <= 128, |k_s| <= 64 (round to
+// nearest at each cut, the remainders exact in FP32). A k is exact in bf16,
+// a product k_s k_t (< 2^14) exact in FP32, and a sum of at most 1024 of them
+// stays below 2^24 units, so the FP32 accumulation of an MMA chain is exact.
+// The slice pairs (s, t) with s + t <= 8 are added in double-word with their
+// weights 2^(-7(s+t)); the dropped pairs and the cut after GS_N slices leave
+// an error below ~2^-50 of |z_a| |z_b| over 1000 rows.
+// Slice tile of a 128-row chunk: K-major bf16 core matrices (8 m-rows x 16
+// bytes), m = 40 s + a (320 rows), m-groups 128 bytes apart, k-groups (8 Z
+// rows) 320 x 16 bytes apart.
+constexpr int GS_N = 8;                              // slices per value
+constexpr int GS_CH = 128;                           // Z rows per chunk (one MMA K chain of 8 x 16)
+constexpr int GS_MR = 40 * GS_N;                     // m-rows of a slice tile
+constexpr int GS_LBO = GS_MR * 16;                   // bytes between k-groups
+constexpr int GS_BUF = (GS_CH / 8) * GS_LBO;         // bytes of one chunk buffer (81920)
+constexpr int GS_MAXR = 1024;                        // rows per CTA whose sums stay exact
+constexpr int GS_NPAIR = 24;                         // pairs s <= t, s + t <= 8
+// TMEM columns of the three accumulators: D0 = slices 0-2 x 0-5 (N 240),
+// D1 = slices 0-2 x 6-7 (N 80), D2 = slices 3-5 x 3-5 (N 128; 120 used)
+constexpr int GS_D0 = 0, GS_D1 = 256, GS_D2 = 384;
+__device__ __forceinline__ int gs_pair(int s, int t) {   // s <= t, s + t <= 8
+  return (s == 0 ? 0 : s == 1 ? 8 : s == 2 ? 15 : s == 3 ? 20 : 23) + (t - s);
+}
+__device__ __forceinline__ uint32_t gs_idesc(int n) {   // kind::f16, bf16 x bf16 -> f32, M = 128, K-major
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void gs_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
 // wait (at most `budget` SM cycles; ~1 s at the default) for the phase with
 // the given parity; false on timeout
 constexpr long long WAIT_BUDGET = 2000000000LL;
@@ -333,6 +378,12 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.p.err, DEV_CAPACITY);
     return;
   }
+  if (GRAM_DW == 2 && (a.Mp != 20 || a.R > GS_MAXR)) {
+    // the tensor-core Gram is laid out for 20 complex columns and exact for at
+    // most GS_MAXR rows per CTA; the whole grid leaves before any barrier
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.p.err, DEV_CAPACITY);
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int C = a.C;
@@ -354,8 +405,9 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
   // misc (FP64 scalars): [0] pulse coefficient, [1] not-PD flag, [8..24) photon
   // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
   // photons, [96..128) 1/L[k][k], [128..131) bulk-precision coefficient and
-  // steps, [140] phase-P task counter, [141] tensor-core timeout flag, [142]
-  // tensor-core mbarrier, [143] TMEM base address
+  // steps, [138..140) mbarriers of the tensor-core Gram, [140] phase-P task
+  // counter, [141] tensor-core timeout flag, [142] tensor-core mbarrier, [143]
+  // TMEM base address, [144..164) column maxima of the tensor-core Gram
   double* misc = reinterpret_cast<double*>(smem + a.o_misc);
   if (a.debug_wait > 0) {
     // Test hook for the timeout path: thread 0 waits on an mbarrier that
@@ -397,16 +449,30 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
   const uint32_t mbar = smem_u32(misc + 142);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 143);
   uint32_t tmem = 0, tc_phase = 0;
-  if constexpr (TC > 0) {
+  // Gram on the tensor cores: one mbarrier per slice buffer, and the number
+  // of completed phases of each
+  const uint32_t gs_bar[2] = {smem_u32(misc + 138), smem_u32(misc + 139)};
+  uint32_t gs_ph[2] = {0u, 0u};
+  // column maxima max(|Re|, |Im|) of the own rows of the stage input, as float
+  // bits: [2][20] at misc[144..164), by stage parity; phase F of a stage forms
+  // the next one's from the rows it writes
+  uint32_t* gs_cmax = reinterpret_cast<uint32_t*>(misc + 144);
+  int gs_par = 0;
+  if constexpr (TC > 0 || GRAM_DW == 2) {
     // B rows beyond 2 Mp stay zero for the whole launch
-    for (int e = tid; e < (a.npad - 2 * Mp) * 4 * Mp; e += NT) {
-      const int n = 2 * Mp + e / (4 * Mp), k = e % (4 * Mp);
-      tb_big[kmaj_off(n, k, a.npad) / 4] = 0.0f;
-      if (TC == 3) tb_small[kmaj_off(n, k, a.npad) / 4] = 0.0f;
-    }
+    if constexpr (TC > 0)
+      for (int e = tid; e < (a.npad - 2 * Mp) * 4 * Mp; e += NT) {
+        const int n = 2 * Mp + e / (4 * Mp), k = e % (4 * Mp);
+        tb_big[kmaj_off(n, k, a.npad) / 4] = 0.0f;
+        if (TC == 3) tb_small[kmaj_off(n, k, a.npad) / 4] = 0.0f;
+      }
     if (tid == 0) {
       *reinterpret_cast<int*>(misc + 141) = 0;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1));
+      if (GRAM_DW == 2) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gs_bar[0]), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gs_bar[1]), "r"(1));
+      }
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -490,6 +556,19 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
       const int l = e / Mp, m = e - l * Mp;
       own(0, l)[m] = m < M ? Zn[(size_t)grow(l) * M + m] : cm<T2>(0, 0);
     }
+    if constexpr (GRAM_DW == 2) {   // column maxima of the loaded rows
+      if (tid < 20) gs_cmax[gs_par * 20 + tid] = 0u;
+      __syncthreads();
+      if (tid < 500) {
+        const int j = tid % 20;
+        float mx = 0.f;
+        for (int l = tid / 20; l < P.R; l += 25) {
+          const T2 v = own(0, l)[j];
+          mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        atomicMax(gs_cmax + gs_par * 20 + j, __float_as_uint(mx));
+      }
+    }
     __syncthreads();
 
     int cur = 0;
@@ -507,7 +586,7 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
         // ================= P: partial sums over own rows of Z_s[cur]
         {
           const int nt_ = Mq / TP;
-          const int n_g = nt_ * (nt_ + 1) / 2, n_t = nt_ * nt_;
+          const int n_g = GRAM_DW == 2 ? 0 : nt_ * (nt_ + 1) / 2, n_t = nt_ * nt_;
           // warps take tasks dynamically (heavier Gram tiles first); every task's
           // arithmetic is independent of which warp runs it, so results stay bitwise
           // reproducible
@@ -529,6 +608,95 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
             tb[0] = (T)misc[0];
             tb[5] = (T)misc[2];
           }
+          if constexpr (GRAM_DW == 2) {
+            // ---- Gram on the tensor cores: the column exponents, then per chunk
+            // of GS_CH rows the slices into a buffer and one thread's MMAs,
+            // which run while the next chunk is sliced and the T tiles below
+            // are summed
+            const uint32_t* cmax = gs_cmax + gs_par * 20;
+            if (tid < 20) gs_cmax[(gs_par ^ 1) * 20 + tid] = 0u;   // phase F fills it for the next stage
+            volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
+            const int n_ch = (P.R + GS_CH - 1) / GS_CH;
+            // warp task: rows rg*8 .. +7 of a chunk x real columns ag*8 .. +7,
+            // task = warp + NWARP t; lane = (column ag*8 + lane/4, rows 2 (lane%4)
+            // and +1), so that each slice is one 128-byte core-matrix store per warp.
+            // The values of the next chunk are loaded while this one is sliced.
+            constexpr int GT = (GS_CH / 8) * 5 / NWARP;   // tasks per warp and chunk
+            static_assert((GS_CH / 8) * 5 % NWARP == 0, "slicing tasks per warp");
+            float gsc[GT];
+            int gcol[GT];
+#pragma unroll
+            for (int t = 0; t < GT; ++t) {
+              const int task = warp + NWARP * t, ag = task % 5, ar = ag * 8 + (lane >> 2);
+              gcol[t] = ar;
+              int ex = 0;
+              frexpf(__uint_as_float(cmax[ar < 20 ? ar : ar - 20]), &ex);
+              gsc[t] = ldexpf(1.0f, -ex);   // |value| scale < 1, exact
+            }
+            auto gload = [&](int ch, float (&v)[GT][2]) {
+#pragma unroll
+              for (int t = 0; t < GT; ++t) {
+                const int task = warp + NWARP * t, rg = task / 5, ar = gcol[t];
+                const int j = ar < 20 ? ar : ar - 20, r0 = ch * GS_CH + rg * 8 + 2 * (lane & 3);
+                const float* z0 = reinterpret_cast<const float*>(own(cur, r0 < P.R ? r0 : 0) + j) + (ar < 20 ? 0 : 1);
+                const float* z1 = reinterpret_cast<const float*>(own(cur, r0 + 1 < P.R ? r0 + 1 : 0) + j) + (ar < 20 ? 0 : 1);
+                v[t][0] = r0 < P.R ? *z0 : 0.f;
+                v[t][1] = r0 + 1 < P.R ? *z1 : 0.f;
+              }
+            };
+            float gnext[GT][2];
+            gload(0, gnext);
+            for (int ch = 0; ch < n_ch; ++ch) {
+              const int b = ch & 1;
+              float gv[GT][2];
+#pragma unroll
+              for (int t = 0; t < GT; ++t) {
+                gv[t][0] = gnext[t][0] * gsc[t];
+                gv[t][1] = gnext[t][1] * gsc[t];
+              }
+              if (ch + 1 < n_ch) gload(ch + 1, gnext);
+              if (ch >= 2) {   // the MMAs of chunk ch - 2 are done with buffer b
+                if (*tc_abort == 0 && !mbar_wait(gs_bar[b], gs_ph[b] & 1u)) {
+                  *tc_abort = 1;
+                  set_error(a.p.err, DEV_TIMEOUT);
+                }
+                ++gs_ph[b];
+                tc_fence_after();
+              }
+              unsigned char* buf = smem + a.o_gs + b * GS_BUF;
+#pragma unroll
+              for (int sl = 0; sl < GS_N; ++sl)
+#pragma unroll
+                for (int t = 0; t < GT; ++t) {
+                  const int task = warp + NWARP * t, rg = task / 5, ag = task % 5;
+                  const float y0 = gv[t][0] * 128.f, y1 = gv[t][1] * 128.f;
+                  const float k0 = rintf(y0), k1 = rintf(y1);
+                  gv[t][0] = y0 - k0;
+                  gv[t][1] = y1 - k1;
+                  // the integers are exact in bf16: the upper halves of their floats
+                  reinterpret_cast<uint32_t*>(buf + rg * GS_LBO + (sl * 5 + ag) * 128)[lane] =
+                      __byte_perm(__float_as_uint(k0), __float_as_uint(k1), 0x7632);
+                }
+              async_proxy_fence();
+              __syncthreads();
+              if (tid == 0 && *tc_abort == 0) {
+                tc_fence_after();
+                const uint32_t bb = smem_u32(buf);
+                for (int ks = 0; ks < GS_CH / 16; ++ks) {
+                  const uint32_t ko = bb + (uint32_t)(ks * 2 * GS_LBO);
+                  const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
+                  const uint64_t d0 = tc_desc(ko, GS_LBO, 128);              // m-rows 0..127
+                  const uint64_t d2 = tc_desc(ko + 15 * 128, GS_LBO, 128);   // m-rows 120..247
+                  gs_mma(tmem + GS_D0, d0, d0, gs_idesc(240), acc);
+                  gs_mma(tmem + GS_D1, d0, tc_desc(ko + 30 * 128, GS_LBO, 128), gs_idesc(80), acc);
+                  gs_mma(tmem + GS_D2, d2, d2, gs_idesc(128), acc);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 gs_bar[b])
+                             : "memory");
+              }
+            }
+          }
           for (;;) {
             int task = 0;
             if (lane == 0) task = atomicAdd(task_ctr, 1);
@@ -540,7 +708,7 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
               while (rem >= nt_ - ti) { rem -= nt_ - ti; ++ti; }
               const int tj2 = ti + rem;
               const int i0 = ti * TP, j0 = tj2 * TP;
-              if constexpr (GRAM_DW) {
+              if constexpr (GRAM_DW != 0) {
                 DW acc[TP][TP][2];
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
@@ -780,6 +948,82 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
               double ph = 0.0;
               for (int lv = 0; lv < Nt; ++lv) ph += misc[8 + lv];
               popp[LR_MAX_NT] = ph;
+            }
+          }
+          if constexpr (GRAM_DW == 2) {
+            // ---- Gram on the tensor cores: wait for the last MMAs, stage the
+            // slice-pair sums D(s,t) (s <= t, s + t <= 8) in the slice buffers,
+            // then add them in double-word with their weights
+            volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
+            const int n_ch = (P.R + GS_CH - 1) / GS_CH;
+            for (int q2 = 0; q2 < (n_ch >= 2 ? 2 : 1); ++q2) {   // one commit pending per used buffer
+              if (*tc_abort == 0 && !mbar_wait(gs_bar[q2], gs_ph[q2] & 1u)) {
+                *tc_abort = 1;
+                set_error(a.p.err, DEV_TIMEOUT);
+              }
+              ++gs_ph[q2];
+            }
+            tc_fence_after();
+            float* pb = reinterpret_cast<float*>(smem + a.o_gs);   // [GS_NPAIR][40 b][40 a]
+            const int qd = warp & 3, part = warp >> 2, m = qd * 32 + lane;
+            for (int blk = part; blk < 55; blk += NWARP / 4) {   // column blocks of 8: D0 30, D1 10, D2 15
+              const int dsel = blk < 30 ? 0 : (blk < 40 ? 1 : 2);
+              const int nb = (blk - (dsel == 0 ? 0 : dsel == 1 ? 30 : 40)) * 8;
+              const int col = (dsel == 0 ? GS_D0 : dsel == 1 ? GS_D1 : GS_D2) + nb;
+              uint32_t v[8];
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                  : "r"(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)col));
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+              if (m < 120) {
+                const int s0 = (dsel == 2 ? 3 : 0) + m / 40, aa = m % 40;
+                const int t0 = dsel == 0 ? 0 : (dsel == 1 ? 6 : 3);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const int n = nb + u, t = t0 + n / 40, bc = n % 40;
+                  if (t >= s0 && s0 + t <= 8) pb[gs_pair(s0, t) * 1600 + bc * 40 + aa] = __uint_as_float(v[u]);
+                }
+              }
+            }
+            tc_fence_before();
+            __syncthreads();
+            // S[a][b] = sum_{s<t} w_st (D_st[a][b] + D_st[b][a]) + sum_s w_ss D_ss[a][b],
+            // w_st = 2^-7(s+t), for the 820 entries G needs: [0, 210) (i, j) and
+            // [210, 420) (20+i, 20+j), i <= j; [420, 820) (i, 20+j), all i, j
+            DW* Sb = reinterpret_cast<DW*>(W);
+            for (int e = tid; e < 820; e += NT) {
+              int aa, bc;
+              if (e < 420) {
+                const int e2 = e < 210 ? e : e - 210, off = e < 210 ? 0 : 20;
+                aa = tri[e2].y + off;
+                bc = tri[e2].x + off;
+              } else {
+                aa = (e - 420) / 20;
+                bc = 20 + (e - 420) % 20;
+              }
+              DW acc{0.f, 0.f};
+              for (int s0 = 0; s0 <= 4; ++s0)
+                for (int t = s0; t <= (8 - s0 < 7 ? 8 - s0 : 7); ++t) {
+                  const float w = ldexpf(1.0f, -7 * (s0 + t));
+                  const float* D = pb + gs_pair(s0, t) * 1600;
+                  dw_add_f(acc, w * D[bc * 40 + aa]);
+                  if (s0 != t) dw_add_f(acc, w * D[aa * 40 + bc]);
+                }
+              Sb[e] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < 210; e += NT) {
+              const int i = tri[e].y, j = tri[e].x;   // i <= j
+              int ei = 0, ej = 0;
+              frexpf(__uint_as_float(gs_cmax[gs_par * 20 + i]), &ei);
+              frexpf(__uint_as_float(gs_cmax[gs_par * 20 + j]), &ej);
+              const double sc = ldexp(1.0, ei + ej - 14);
+              DW re = Sb[e], im = Sb[420 + i * 20 + j];
+              dw_add(re, Sb[210 + e]);
+              const DW n2 = Sb[420 + j * 20 + i];
+              dw_add(im, DW{-n2.hi, -n2.lo});
+              gp[i * Mp + j] = mk(dw_value(re) * sc, dw_value(im) * sc);
             }
           }
         }
@@ -1373,6 +1617,7 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
           const int row_lo = 0;
           for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4;
+            float cmx[4] = {0.f, 0.f, 0.f, 0.f};   // column maxima of the rows written (tensor-core Gram)
             T fr[TR][4], fi[TR][4];
             T sr[TR], sb[TR];
             const T2* yrp[TR];
@@ -1635,6 +1880,9 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
                   }
                 }
                 store4<ZSM>(own(nxt, l0 + r) + m0, zo);
+                if constexpr (GRAM_DW == 2)   // column maxima of the next stage input
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) cmx[u] = fmaxf(cmx[u], fmaxf(fabsf(zo[u].x), fabsf(zo[u].y)));
                 continue;
               }
 #pragma unroll
@@ -1665,9 +1913,14 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
               }
               store4<ZSM>(own(nxt, l0 + r) + m0, zo);
             }
+            if constexpr (GRAM_DW == 2)
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (m0 + u < 20) atomicMax(gs_cmax + (gs_par ^ 1) * 20 + m0 + u, __float_as_uint(cmx[u]));
           }
           }
           cur = nxt;
+          gs_par ^= 1;
           __syncthreads();
         }
       }
@@ -1676,7 +1929,7 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
     // every CTA is done reading its peers' shared memory before it is reused
     cluster.sync();
   }
-  if constexpr (TC > 0) {
+  if constexpr (TC > 0 || GRAM_DW == 2) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

@@ -611,7 +611,7 @@ void layout(lr_sparse* s) {
   s->o_trace = take((size_t)s->T * s->n_rec * sizeof(double));
   if (s->fused) {
     const size_t Mp = (size_t)(s->M + 3) / 4 * 4;
-    s->o_fsc = take((size_t)s->n_team * (3 + s->K + 1) * s->N * Mp * sizeof(float2));
+    s->o_fsc = take((size_t)s->n_team * (3 + s->K) * s->N * Mp * sizeof(float2));
     s->o_fvala = take((size_t)s->nnz * sizeof(float2));
     s->o_fdiag = take((size_t)s->N * sizeof(float4));
     s->o_fflag = take((size_t)s->T * sizeof(int));

@@ -11,9 +11,10 @@
 // batch's trajectory-steps instead: a trajectory cut between two CTAs passes
 // its state Z_n from one to the other through global memory (release /
 // acquire on a per-trajectory flag).
-// The stage input Z_s, the operator images Y_k = L_k(t) Z_s (and r(t) Z_s at
-// the first stage of a step) and the RK4 accumulator live in a per-team
-// global region that stays L2-resident. Per stage, each CTA works on its own
+// The stage input Z_s, the operator images Y_k = L_k(t) Z_s and the RK4
+// accumulator live in a per-team global region ((3 + K) N Mp complex64) that
+// stays L2-resident when the batch in flight is small; r(t) Z_s, needed only
+// for the signal, is summed where it is formed. Per stage, each CTA works on its own
 // rows (the operator gathers read any row), with two team barriers: B1 after
 // the partial sums of G, T_k and the signal over its rows (every CTA then adds
 // the team's partials in rank order from distributed shared memory and runs
@@ -64,7 +65,7 @@ struct Args {
   float2* Z;               // state [T][N][M]
   int* flag;               // [T] split schedule: 1 once the head of trajectory t is written
   int split;               // 1: equal spans of trajectory-steps per CTA (cooperative launch)
-  float2* scratch;         // per team: Z_s [2][N][Mp], Y [K + 1][N][Mp], accumulator [N][Mp]
+  float2* scratch;         // per team: Z_s [2][N][Mp], Y [K][N][Mp], accumulator [N][Mp]
   double2* beta;           // [T][max_steps + 1]
   double *pops, *nphot, *trace;
   int N, M, Mp, K, T, n_levels;
@@ -312,9 +313,9 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   // rank r's copy of a shared-memory object of this CTA
   auto at_rank = [&](auto* p, int r) { return r == q ? p : cluster.map_shared_rank(p, r); };
   const size_t zsb = (size_t)N * Mp;
-  float2* zs0 = a.scratch + (size_t)team * (size_t)(3 + K + 1) * zsb;
-  float2* ybuf = zs0 + 2 * zsb;              // Y_1 .. Y_K, then r Z_s
-  float2* accg = zs0 + (2 + K + 1) * zsb;
+  float2* zs0 = a.scratch + (size_t)team * (size_t)(3 + K) * zsb;
+  float2* ybuf = zs0 + 2 * zsb;              // Y_1 .. Y_K (r Z_s is only summed, never stored)
+  float2* accg = zs0 + (2 + K) * zsb;
   const double dt = a.dt;
   const int pe = a.pop_every;
 
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             float2 y[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
                            make_float2(0.f, 0.f)};
             row_gather4(a, 1 + k, n, m0, zc, chi, y);
-            store4(ybuf + (size_t)k * zsb + (size_t)n * Mp + m0, y);
+            if (k < K) store4(ybuf + (size_t)k * zsb + (size_t)n * Mp + m0, y);
             if (k == K) {
               float2 z[4];
               load4(zc + (size_t)n * Mp + m0, z);

@@ -74,7 +74,7 @@ class lr_info(C.Structure):
     _fields_ = [("n_cand", C.c_int), ("n_traj", C.c_int), ("nt_max", C.c_int),
                 ("n_rec", C.c_long), ("max_steps", C.c_long), ("step", C.c_long),
                 ("engine", C.c_int), ("team_size", C.c_int),
-                ("stage_in_smem", C.c_int), ("tensor_passes", C.c_int)]
+                ("stage_in_smem", C.c_int), ("tensor_passes", C.c_int), ("gram_tc", C.c_int)]
 
 
 _lib = None
