@@ -48,6 +48,11 @@ DTYPE_LABEL = {
     "fp32": "f32 bulk and Gram; double-word f32 (~2^-48) LDL^dag, G^-1 and X_k; f64 signal",
     "tf32_g64": "f32 bulk, tf32 projection; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 and X_k; f64 signal",
 }
+# DRAM bytes per trajectory-step of the tensor-core-Gram kernel (None: not captured since its last change)
+TRAFFIC_GRAM_TC = None
+# FP32_G64 with the Gram matrix on the tensor cores (the default plan of the N=2000, M=20 batch)
+DTYPE_GRAM_TC = ("f32 bulk; FP64-class (~2^-48) Gram from exact bf16-slice tcgen05 MMAs (f32 accumulation, "
+                 "exact) and double-word sums; double-word f32 LDL^dag, G^-1 and X_k; f64 signal")
 
 
 def parse():
@@ -237,9 +242,9 @@ def full_pulse_error(wl, info, dev):
     gold = full_pulse.load("c4")
     cands = sorted(gold["cands"])
     sub = [wl.candidates[c] for c in cands]
-    saved = {k: os.environ.get(k) for k in ("LR_FUSED_C", "LR_FUSED_ZS", "LR_FUSED_TC")}
+    saved = {k: os.environ.get(k) for k in ("LR_FUSED_C", "LR_FUSED_ZS", "LR_FUSED_TC", "LR_FUSED_GRAM")}
     os.environ.update({"LR_FUSED_C": str(info.team_size), "LR_FUSED_ZS": "smem" if info.stage_in_smem else "global",
-                       "LR_FUSED_TC": str(info.tensor_passes)})
+                       "LR_FUSED_TC": str(info.tensor_passes), "LR_FUSED_GRAM": "tc" if info.gram_tc else "dw"})
     try:
         b = LowRankBatch([c.model for c in sub], [c.M for c in sub], precision="fp32_g64", engine="fused",
                          max_steps=wl.n_steps, pop_every=gold["rec_every"], eta=wl.eta, device=dev)
@@ -415,13 +420,15 @@ def run_ours(args):
         pipe = "FP32 FMA"
     achieved = fl / (ms * 1e-3 / args.steps) / 1e12
     # DRAM bytes per launch from one ncu capture of this kernel on a 76-trajectory, 10-step case
-    # of the same workload (0.338 GB read + 1.586 GB written for 760 trajectory-steps: 2.532 MB
-    # per trajectory-step at the same number of resident teams), scaled by the trajectory-steps
-    # of one launch; only for the kernel that capture measured
+    # of the same workload, per trajectory-step at the same number of resident teams, scaled by
+    # the trajectory-steps of one launch; only for the kernels those captures measured:
+    # double-word Gram 0.338 GB read + 1.586 GB written for 760 trajectory-steps (2.532 MB),
+    # tensor-core Gram TRAFFIC_GRAM_TC
     traffic = None
     if (wl.name == "c4" and prec == "fp32_g64" and engine == "fused" and info.team_size == 2
             and not info.stage_in_smem and info.tensor_passes == 0):
-        traffic = 2.532e6 * ntraj * chunk
+        per = TRAFFIC_GRAM_TC if info.gram_tc else 2.532e6
+        traffic = per * ntraj * chunk if per else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "kernel": "integrate (%s engine)" % engine,
@@ -508,8 +515,8 @@ def run_ours(args):
         qinfo = bq.query()
         bq.close()
         bo = ora["beta"]
-        err = {"sample": "candidate 0, g and e, %d RK4 steps (team %d, tensor passes %d)"
-                         % (ns, qinfo.team_size, qinfo.tensor_passes),
+        err = {"sample": "candidate 0, g and e, %d RK4 steps (team %d, tensor passes %d, gram on tensor cores %d)"
+                         % (ns, qinfo.team_size, qinfo.tensor_passes, qinfo.gram_tc),
                "beta_rel": float(np.abs(og["beta"] - bo).max() / np.abs(bo).max()),
                "pops_abs": float(max(np.abs(og["pops"][j][:, :ora["pops"][j].shape[1]] - ora["pops"][j]).max()
                                      for j in range(2))),
@@ -520,6 +527,8 @@ def run_ours(args):
         desc.update({"parallelism": "dp%d (independent replicas)" % world, "engine": engine,
                      "team_size": info.team_size, "stage_state": "shared memory" if info.stage_in_smem else "L2",
                      "projection": ("tcgen05 TF32 x%d" % info.tensor_passes) if info.tensor_passes else "CUDA cores",
+                     "gram": ("tcgen05 bf16 slices (exact), double-word sums" if info.gram_tc else
+                              "double-word FP32 on the CUDA cores" if prec in ("fp32_g64", "tf32_g64") else prec),
                      "chunk_rk4_steps": chunk,
                      "launch": "CUDA graph replay" if graph is not None else "direct lr_integrate",
                      "l2": "flushed (256 MiB write) between timed steps"})
@@ -527,7 +536,7 @@ def run_ours(args):
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE_LABEL[prec],
+            "dtype": DTYPE_GRAM_TC if info.gram_tc else DTYPE_LABEL[prec],
             "data": "synthetic (seeded pulses and initial states)", "config": desc,
             "pulse_evals_per_s": value / (2 * spp),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

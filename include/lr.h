@@ -169,8 +169,9 @@ typedef struct {
   int stage_in_smem;  /* FUSED: 1 stage state in shared memory, 0 in L2 */
   int tensor_passes;  /* FUSED: TF32 tensor-core passes of the projection term (0: CUDA cores) */
   int gram_tc;        /* FUSED, FP32_G64: 1 when the Gram matrix is formed on the tensor cores
-                         (exact bf16 slices, double-word sums; set LR_FUSED_GRAM=dw at lr_create
-                         for the double-word CUDA-core sums), 0 otherwise */
+                         (exact bf16 slices, double-word sums; the default in the lab frame
+                         with the rank padded to 20 and <= 1024 rows per CTA), 0 for the
+                         double-word CUDA-core sums (LR_FUSED_GRAM=dw at lr_create) */
 } lr_info;
 
 /* Create a context for n_cand candidates (2 n_cand trajectories).

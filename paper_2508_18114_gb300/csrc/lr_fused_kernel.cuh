@@ -324,18 +324,16 @@ __device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.
 // bytes), m = 40 s + a (320 rows), m-groups 128 bytes apart, k-groups (8 Z
 // rows) 320 x 16 bytes apart.
 constexpr int GS_N = 8;                              // slices per value
-constexpr int GS_CH = 128;                           // Z rows per chunk (one MMA K chain of 8 x 16)
+constexpr int GS_CH = 32;                            // Z rows per chunk (two MMA K steps of 16)
 constexpr int GS_MR = 40 * GS_N;                     // m-rows of a slice tile
 constexpr int GS_LBO = GS_MR * 16;                   // bytes between k-groups
-constexpr int GS_BUF = (GS_CH / 8) * GS_LBO;         // bytes of one chunk buffer (81920)
+constexpr int GS_BUF = (GS_CH / 8) * GS_LBO;         // bytes of one chunk buffer (20480; two of them:
+                                                     // the kernel keeps most of L1 for the stage rows)
 constexpr int GS_MAXR = 1024;                        // rows per CTA whose sums stay exact
-constexpr int GS_NPAIR = 24;                         // pairs s <= t, s + t <= 8
+constexpr int GS_W = 10;                             // slicing warps (warp GS_W issues the MMAs)
 // TMEM columns of the three accumulators: D0 = slices 0-2 x 0-5 (N 240),
 // D1 = slices 0-2 x 6-7 (N 80), D2 = slices 3-5 x 3-5 (N 128; 120 used)
 constexpr int GS_D0 = 0, GS_D1 = 256, GS_D2 = 384;
-__device__ __forceinline__ int gs_pair(int s, int t) {   // s <= t, s + t <= 8
-  return (s == 0 ? 0 : s == 1 ? 8 : s == 2 ? 15 : s == 3 ? 20 : 23) + (t - s);
-}
 __device__ __forceinline__ uint32_t gs_idesc(int n) {   // kind::f16, bf16 x bf16 -> f32, M = 128, K-major
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
@@ -405,7 +403,7 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
   // misc (FP64 scalars): [0] pulse coefficient, [1] not-PD flag, [8..24) photon
   // partials per level, [32..64) Im diag T_r, [64..81) reduced populations and
   // photons, [96..128) 1/L[k][k], [128..131) bulk-precision coefficient and
-  // steps, [138..140) mbarriers of the tensor-core Gram, [140] phase-P task
+  // steps, [136..140) mbarriers of the tensor-core Gram, [140] phase-P task
   // counter, [141] tensor-core timeout flag, [142] tensor-core mbarrier, [143]
   // TMEM base address, [144..164) column maxima of the tensor-core Gram
   double* misc = reinterpret_cast<double*>(smem + a.o_misc);
@@ -453,6 +451,10 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
   // of completed phases of each
   const uint32_t gs_bar[2] = {smem_u32(misc + 138), smem_u32(misc + 139)};
   uint32_t gs_ph[2] = {0u, 0u};
+  // ... and one per buffer on which the slicing warps arrive when a chunk is in
+  // place (the issuing warp's phase counts)
+  const uint32_t gs_fill[2] = {smem_u32(misc + 136), smem_u32(misc + 137)};
+  uint32_t gs_fph[2] = {0u, 0u};
   // column maxima max(|Re|, |Im|) of the own rows of the stage input, as float
   // bits: [2][20] at misc[144..164), by stage parity; phase F of a stage forms
   // the next one's from the rows it writes
@@ -472,6 +474,8 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
       if (GRAM_DW == 2) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gs_bar[0]), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gs_bar[1]), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gs_fill[0]), "r"(GS_W * 32));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gs_fill[1]), "r"(GS_W * 32));
       }
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -609,91 +613,127 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
             tb[5] = (T)misc[2];
           }
           if constexpr (GRAM_DW == 2) {
-            // ---- Gram on the tensor cores: the column exponents, then per chunk
-            // of GS_CH rows the slices into a buffer and one thread's MMAs,
-            // which run while the next chunk is sliced and the T tiles below
-            // are summed
-            const uint32_t* cmax = gs_cmax + gs_par * 20;
+            // ---- Gram on the tensor cores. GS_W warps slice the chunks of GS_CH
+            // rows into the two buffers and arrive on the buffer's fill mbarrier;
+            // warp GS_W waits on it and one of its threads issues the chunk's MMAs,
+            // committed to the buffer's MMA mbarrier, on which the slicing warps
+            // wait before they refill it. The other warps start on the T tiles
+            // below, and the slicing and issuing warps join them when done.
             if (tid < 20) gs_cmax[(gs_par ^ 1) * 20 + tid] = 0u;   // phase F fills it for the next stage
-            volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
-            const int n_ch = (P.R + GS_CH - 1) / GS_CH;
-            // warp task: rows rg*8 .. +7 of a chunk x real columns ag*8 .. +7,
-            // task = warp + NWARP t; lane = (column ag*8 + lane/4, rows 2 (lane%4)
-            // and +1), so that each slice is one 128-byte core-matrix store per warp.
-            // The values of the next chunk are loaded while this one is sliced.
-            constexpr int GT = (GS_CH / 8) * 5 / NWARP;   // tasks per warp and chunk
-            static_assert((GS_CH / 8) * 5 % NWARP == 0, "slicing tasks per warp");
-            float gsc[GT];
-            int gcol[GT];
-#pragma unroll
-            for (int t = 0; t < GT; ++t) {
-              const int task = warp + NWARP * t, ag = task % 5, ar = ag * 8 + (lane >> 2);
-              gcol[t] = ar;
-              int ex = 0;
-              frexpf(__uint_as_float(cmax[ar < 20 ? ar : ar - 20]), &ex);
-              gsc[t] = ldexpf(1.0f, -ex);   // |value| scale < 1, exact
-            }
-            auto gload = [&](int ch, float (&v)[GT][2]) {
+            if (warp < GS_W) {
+              const uint32_t* cmax = gs_cmax + gs_par * 20;
+              volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
+              const int n_ch = (P.R + GS_CH - 1) / GS_CH;
+              // warp task: rows rg*8 .. +7 of a chunk x real columns ag*8 .. +7,
+              // task = warp + GS_W t; lane = (column ag*8 + lane/4, rows 2 (lane%4)
+              // and +1), so that each slice is one 128-byte core-matrix store per
+              // warp. The values of the next chunk are loaded while this one is
+              // sliced.
+              constexpr int GTASK = (GS_CH / 8) * 5;   // warp tasks per chunk
+              constexpr int GT = GTASK / GS_W;         // per slicing warp
+              static_assert(GTASK % GS_W == 0, "slicing tasks per warp");
+              float gsc[GT];
+              int gcol[GT];
 #pragma unroll
               for (int t = 0; t < GT; ++t) {
-                const int task = warp + NWARP * t, rg = task / 5, ar = gcol[t];
-                const int j = ar < 20 ? ar : ar - 20, r0 = ch * GS_CH + rg * 8 + 2 * (lane & 3);
-                const float* z0 = reinterpret_cast<const float*>(own(cur, r0 < P.R ? r0 : 0) + j) + (ar < 20 ? 0 : 1);
-                const float* z1 = reinterpret_cast<const float*>(own(cur, r0 + 1 < P.R ? r0 + 1 : 0) + j) + (ar < 20 ? 0 : 1);
-                v[t][0] = r0 < P.R ? *z0 : 0.f;
-                v[t][1] = r0 + 1 < P.R ? *z1 : 0.f;
+                const int task = warp + GS_W * t, ag = task % 5, ar = ag * 8 + (lane >> 2);
+                gcol[t] = ar;
+                int ex = 0;
+                frexpf(__uint_as_float(cmax[ar < 20 ? ar : ar - 20]), &ex);
+                gsc[t] = ldexpf(1.0f, -ex);   // |value| scale < 1, exact
               }
-            };
-            float gnext[GT][2];
-            gload(0, gnext);
-            for (int ch = 0; ch < n_ch; ++ch) {
-              const int b = ch & 1;
-              float gv[GT][2];
-#pragma unroll
-              for (int t = 0; t < GT; ++t) {
-                gv[t][0] = gnext[t][0] * gsc[t];
-                gv[t][1] = gnext[t][1] * gsc[t];
-              }
-              if (ch + 1 < n_ch) gload(ch + 1, gnext);
-              if (ch >= 2) {   // the MMAs of chunk ch - 2 are done with buffer b
-                if (*tc_abort == 0 && !mbar_wait(gs_bar[b], gs_ph[b] & 1u)) {
-                  *tc_abort = 1;
-                  set_error(a.p.err, DEV_TIMEOUT);
-                }
-                ++gs_ph[b];
-                tc_fence_after();
-              }
-              unsigned char* buf = smem + a.o_gs + b * GS_BUF;
-#pragma unroll
-              for (int sl = 0; sl < GS_N; ++sl)
+              auto gload = [&](int ch, float (&v)[GT][2]) {
 #pragma unroll
                 for (int t = 0; t < GT; ++t) {
-                  const int task = warp + NWARP * t, rg = task / 5, ag = task % 5;
-                  const float y0 = gv[t][0] * 128.f, y1 = gv[t][1] * 128.f;
-                  const float k0 = rintf(y0), k1 = rintf(y1);
-                  gv[t][0] = y0 - k0;
-                  gv[t][1] = y1 - k1;
-                  // the integers are exact in bf16: the upper halves of their floats
-                  reinterpret_cast<uint32_t*>(buf + rg * GS_LBO + (sl * 5 + ag) * 128)[lane] =
-                      __byte_perm(__float_as_uint(k0), __float_as_uint(k1), 0x7632);
+                  const int task = warp + GS_W * t, rg = task / 5, ar = gcol[t];
+                  const int j = ar < 20 ? ar : ar - 20, r0 = ch * GS_CH + rg * 8 + 2 * (lane & 3);
+                  const float* z0 =
+                      reinterpret_cast<const float*>(own(cur, r0 < P.R ? r0 : 0) + j) + (ar < 20 ? 0 : 1);
+                  const float* z1 =
+                      reinterpret_cast<const float*>(own(cur, r0 + 1 < P.R ? r0 + 1 : 0) + j) + (ar < 20 ? 0 : 1);
+                  v[t][0] = r0 < P.R ? *z0 : 0.f;
+                  v[t][1] = r0 + 1 < P.R ? *z1 : 0.f;
                 }
-              async_proxy_fence();
-              __syncthreads();
-              if (tid == 0 && *tc_abort == 0) {
-                tc_fence_after();
-                const uint32_t bb = smem_u32(buf);
-                for (int ks = 0; ks < GS_CH / 16; ++ks) {
-                  const uint32_t ko = bb + (uint32_t)(ks * 2 * GS_LBO);
-                  const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
-                  const uint64_t d0 = tc_desc(ko, GS_LBO, 128);              // m-rows 0..127
-                  const uint64_t d2 = tc_desc(ko + 15 * 128, GS_LBO, 128);   // m-rows 120..247
-                  gs_mma(tmem + GS_D0, d0, d0, gs_idesc(240), acc);
-                  gs_mma(tmem + GS_D1, d0, tc_desc(ko + 30 * 128, GS_LBO, 128), gs_idesc(80), acc);
-                  gs_mma(tmem + GS_D2, d2, d2, gs_idesc(128), acc);
+              };
+              float gnext[GT][2];
+              gload(0, gnext);
+              for (int ch = 0; ch < n_ch; ++ch) {
+                const int b = ch & 1;
+                float gv[GT][2];
+#pragma unroll
+                for (int t = 0; t < GT; ++t) {
+                  gv[t][0] = gnext[t][0] * gsc[t];
+                  gv[t][1] = gnext[t][1] * gsc[t];
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 gs_bar[b])
-                             : "memory");
+                if (ch + 1 < n_ch) gload(ch + 1, gnext);
+                if (ch >= 2) {   // the MMAs of chunk ch - 2 are done with buffer b
+                  if (*tc_abort == 0 && !mbar_wait(gs_bar[b], gs_ph[b] & 1u)) {
+                    *tc_abort = 1;
+                    set_error(a.p.err, DEV_TIMEOUT);
+                  }
+                  ++gs_ph[b];
+                  tc_fence_after();
+                }
+                unsigned char* buf = smem + a.o_gs + b * GS_BUF;
+#pragma unroll
+                for (int sl = 0; sl < GS_N; ++sl)
+#pragma unroll
+                  for (int t = 0; t < GT; ++t) {
+                    const int task = warp + GS_W * t, rg = task / 5, ag = task % 5;
+                    const float y0 = gv[t][0] * 128.f, y1 = gv[t][1] * 128.f;
+                    // round to the nearest integer by adding and subtracting 1.5 2^23
+                    // (exact for |y| < 2^22; ties to even, as rintf)
+                    const float k0 = __fsub_rn(__fadd_rn(y0, 12582912.f), 12582912.f);
+                    const float k1 = __fsub_rn(__fadd_rn(y1, 12582912.f), 12582912.f);
+                    gv[t][0] = y0 - k0;
+                    gv[t][1] = y1 - k1;
+                    // the integers are exact in bf16: the upper halves of their floats
+                    reinterpret_cast<uint32_t*>(buf + rg * GS_LBO + (sl * 5 + ag) * 128)[lane] =
+                        __byte_perm(__float_as_uint(k0), __float_as_uint(k1), 0x7632);
+                  }
+                // the chunk is in place: visible to the tensor cores, then announced
+                async_proxy_fence();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gs_fill[b]) : "memory");
+              }
+            } else {
+              const int n_ch = (P.R + GS_CH - 1) / GS_CH;
+              if (warp == GS_W) {
+                // the issuing warp: per chunk, wait until it is sliced, then one
+                // thread issues its MMAs and commits them to the buffer's mbarrier
+                volatile int* tc_abort = reinterpret_cast<volatile int*>(misc + 141);
+                for (int ch = 0; ch < n_ch; ++ch) {
+                  const int b = ch & 1;
+                  if (*tc_abort == 0 && !mbar_wait(gs_fill[b], gs_fph[b] & 1u)) {
+                    *tc_abort = 1;
+                    set_error(a.p.err, DEV_TIMEOUT);
+                  }
+                  ++gs_fph[b];
+                  if (lane == 0 && *tc_abort == 0) {
+                    tc_fence_after();
+                    const uint32_t bb = smem_u32(smem + a.o_gs + b * GS_BUF);
+                    for (int ks = 0; ks < GS_CH / 16; ++ks) {
+                      const uint32_t ko = bb + (uint32_t)(ks * 2 * GS_LBO);
+                      const uint32_t acc = (ch > 0 || ks > 0) ? 1u : 0u;
+                      const uint64_t d0 = tc_desc(ko, GS_LBO, 128);              // m-rows 0..127
+                      const uint64_t d2 = tc_desc(ko + 15 * 128, GS_LBO, 128);   // m-rows 120..247
+                      gs_mma(tmem + GS_D0, d0, d0, gs_idesc(240), acc);
+                      gs_mma(tmem + GS_D1, d0, tc_desc(ko + 30 * 128, GS_LBO, 128), gs_idesc(80), acc);
+                      gs_mma(tmem + GS_D2, d2, d2, gs_idesc(128), acc);
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(gs_bar[b])
+                        : "memory");
+                  }
+                  __syncwarp();
+                }
+              }
+              // the slicing warps waited on every commit of buffer b but its last
+              // (chunks b, b + 2, ...): the other warps count those phases too, so
+              // that every thread waits on the same phase in the readout
+#pragma unroll
+              for (int b = 0; b < 2; ++b) {
+                const int cb = (n_ch + 1 - b) / 2;
+                if (cb > 1) gs_ph[b] += (uint32_t)(cb - 1);
               }
             }
           }
@@ -951,6 +991,12 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
             }
           }
           if constexpr (GRAM_DW == 2) {
+            // every chunk is sliced and issued before any thread waits here: a
+            // parity wait tells a phase from the next one only, and the warps that
+            // do not slice would otherwise arrive several commits early
+            __syncthreads();
+          }
+          if constexpr (GRAM_DW == 2) {
             // ---- Gram on the tensor cores: wait for the last MMAs, stage the
             // slice-pair sums D(s,t) (s <= t, s + t <= 8) in the slice buffers,
             // then add them in double-word with their weights
@@ -964,52 +1010,101 @@ __global__ void __launch_bounds__(NTH, 1) fused_kernel(const Args a) {
               ++gs_ph[q2];
             }
             tc_fence_after();
-            float* pb = reinterpret_cast<float*>(smem + a.o_gs);   // [GS_NPAIR][40 b][40 a]
+            // V[a][b] = sum over pairs s <= t, s + t <= 8 of c_st 2^-7(s+t) D_st[a][b]
+            // with c_st = 1/2 for s = t, else 1, so that S = A^T A = V + V^T (D_ss is
+            // symmetric). TMEM lane m holds row a = m % 40 of slice s = m / 40 (D0,
+            // D1) and of slice 3 + m / 40 (D2); each warp of a lane quarter takes
+            // blocks of 8 columns b and sums its slices' pairs over t in double-word
+            // into V (double-word, in the slice buffers).
+            DW* V = reinterpret_cast<DW*>(smem + a.o_gs);   // [40][40]
             const int qd = warp & 3, part = warp >> 2, m = qd * 32 + lane;
-            for (int blk = part; blk < 55; blk += NWARP / 4) {   // column blocks of 8: D0 30, D1 10, D2 15
-              const int dsel = blk < 30 ? 0 : (blk < 40 ? 1 : 2);
-              const int nb = (blk - (dsel == 0 ? 0 : dsel == 1 ? 30 : 40)) * 8;
-              const int col = (dsel == 0 ? GS_D0 : dsel == 1 ? GS_D1 : GS_D2) + nb;
-              uint32_t v[8];
-              asm volatile(
-                  "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                  : "r"(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)col));
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-              if (m < 120) {
-                const int s0 = (dsel == 2 ? 3 : 0) + m / 40, aa = m % 40;
-                const int t0 = dsel == 0 ? 0 : (dsel == 1 ? 6 : 3);
+            const int sA = m / 40, aa = m % 40, sB = 3 + m / 40;
+            static_assert(NWARP == 16, "four warps per TMEM lane quarter");
+            for (int it2 = 0; it2 < 2; ++it2) {   // b-blocks part and part + 4 (< 5)
+              const int bk = part + 4 * it2, b0 = bk * 8;
+              const bool has = bk < 5;   // uniform within the warp
+              DW cA[8], cB[8];           // slice sA (D0, D1) and slice sB (D2)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  const int n = nb + u, t = t0 + n / 40, bc = n % 40;
-                  if (t >= s0 && s0 + t <= 8) pb[gs_pair(s0, t) * 1600 + bc * 40 + aa] = __uint_as_float(v[u]);
+              for (int u = 0; u < 8; ++u) cA[u] = cB[u] = DW{0.f, 0.f};
+              if (has) {
+                // columns t = 0..10: D0 t = 0..5 and D1 t = 6, 7 (slice sA), D2 t = 3..5
+                // (slice sB); loaded four blocks of 8 at a time, one wait per group
+                auto tcol = [&](int t) {
+                  return t < 6 ? GS_D0 + t * 40 + b0 : (t < 8 ? GS_D1 + (t - 6) * 40 + b0 : GS_D2 + (t - 8) * 40 + b0);
+                };
+                const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16);
+#pragma unroll
+                for (int g = 0; g < 3; ++g) {
+                  uint32_t v[4][8];
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {
+                    const int t = 4 * g + q;
+                    if (t < 11)
+                      asm volatile(
+                          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                          : "=r"(v[q][0]), "=r"(v[q][1]), "=r"(v[q][2]), "=r"(v[q][3]), "=r"(v[q][4]), "=r"(v[q][5]),
+                            "=r"(v[q][6]), "=r"(v[q][7])
+                          : "r"(lane_base + (uint32_t)tcol(t)));
+                  }
+                  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {
+                    const int t = 4 * g + q;
+                    if (t >= 11) continue;
+                    const int s0 = t < 8 ? sA : sB, tt = t < 8 ? t : t - 5;
+                    if (m < 120 && tt >= s0 && s0 + tt <= 8) {
+                      // 2^-7(s+t), halved on the diagonal pairs: an exact power of two
+                      const float w = __int_as_float((127 - 7 * (s0 + tt) - (s0 == tt ? 1 : 0)) << 23);
+#pragma unroll
+                      for (int u = 0; u < 8; ++u) {
+                        if (t < 8)
+                          dw_add_f(cA[u], w * __uint_as_float(v[q][u]));
+                        else
+                          dw_add_f(cB[u], w * __uint_as_float(v[q][u]));
+                      }
+                    }
+                  }
                 }
+              }
+              // every thread has seen the last MMA complete: the slice buffers are free.
+              // Lane m < 40 holds slices 0 and 3 of row a, 40 <= m < 80 slices 1 and 4,
+              // 80 <= m < 120 slice 2: each adds its two, and the three lane groups add
+              // their rows into V in that order, one barrier apart.
+              if (has && m < 120)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) dw_add(cA[u], cB[u]);
+              for (int round = 0; round < 3; ++round) {
+                if (has && m < 120 && sA == round)
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) {
+                    DW& dst = V[aa * 40 + b0 + u];
+                    if (round == 0) {
+                      dst = cA[u];
+                    } else {
+                      DW x = dst;
+                      dw_add(x, cA[u]);
+                      dst = x;
+                    }
+                  }
+                __syncthreads();
               }
             }
             tc_fence_before();
             __syncthreads();
-            // S[a][b] = sum_{s<t} w_st (D_st[a][b] + D_st[b][a]) + sum_s w_ss D_ss[a][b],
-            // w_st = 2^-7(s+t), for the 820 entries G needs: [0, 210) (i, j) and
-            // [210, 420) (20+i, 20+j), i <= j; [420, 820) (i, 20+j), all i, j
+            // S entries for G: S[a][b] = V[a][b] + V[b][a]
             DW* Sb = reinterpret_cast<DW*>(W);
             for (int e = tid; e < 820; e += NT) {
-              int aa, bc;
+              int ia, ib;
               if (e < 420) {
                 const int e2 = e < 210 ? e : e - 210, off = e < 210 ? 0 : 20;
-                aa = tri[e2].y + off;
-                bc = tri[e2].x + off;
+                ia = tri[e2].y + off;
+                ib = tri[e2].x + off;
               } else {
-                aa = (e - 420) / 20;
-                bc = 20 + (e - 420) % 20;
+                ia = (e - 420) / 20;
+                ib = 20 + (e - 420) % 20;
               }
-              DW acc{0.f, 0.f};
-              for (int s0 = 0; s0 <= 4; ++s0)
-                for (int t = s0; t <= (8 - s0 < 7 ? 8 - s0 : 7); ++t) {
-                  const float w = ldexpf(1.0f, -7 * (s0 + t));
-                  const float* D = pb + gs_pair(s0, t) * 1600;
-                  dw_add_f(acc, w * D[bc * 40 + aa]);
-                  if (s0 != t) dw_add_f(acc, w * D[aa * 40 + bc]);
-                }
+              DW acc = V[ia * 40 + ib];
+              dw_add(acc, V[ib * 40 + ia]);
               Sb[e] = acc;
             }
             __syncthreads();

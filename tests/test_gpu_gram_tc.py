@@ -5,8 +5,8 @@ FP64-class like the double-word CUDA-core sums it replaces: on the same FP32
 state, the spectrum of rho = Z Z^dag (from the recorded FP64 Gram matrix)
 agrees with the double-word Gram's to ~1e-10 relative even for the eigenvalues
 eps = 1e-5, which an FP32-accurate Gram matrix (2^-24 of the largest entry)
-would miss by ~1e-2. Parity of whole runs with the oracle is covered by the
-fused tests at N = 2000 (the default plan of that batch uses this Gram)."""
+would miss by ~1e-2. Whole runs against the oracle: the fused and full-pulse
+tests at N = 2000, whose plan uses this Gram by default, and the test below."""
 import numpy as np
 import pytest
 
@@ -22,7 +22,7 @@ def _spectrum(monkeypatch, gram, n_steps):
     for k, v in PLAN.items():
         monkeypatch.setenv(k, v)
     if gram:
-        monkeypatch.delenv("LR_FUSED_GRAM", raising=False)
+        monkeypatch.delenv("LR_FUSED_GRAM", raising=False)   # the default of this plan
     else:
         monkeypatch.setenv("LR_FUSED_GRAM", "dw")
     wl = li.c4(n_candidates=3)
@@ -60,3 +60,24 @@ def test_gram_tc_spectrum_after_steps(monkeypatch):
     print("spectrum after 40 steps: max relative difference", rel.max())
     assert rel.max() < 1e-3
     assert np.abs(zt - zd).max() < 1e-5 * np.abs(zd).max()
+
+
+def test_gram_tc_parity_with_oracle(monkeypatch):
+    """Three candidates of the N = 2000, M = 20 batch, 120 steps, against the
+    FP64 oracle at the FP32_G64 bounds, with the Gram on the tensor cores."""
+    from oracle import parallel
+    from _compare import compare_observables
+    for k, v in PLAN.items():
+        monkeypatch.setenv(k, v)
+    monkeypatch.delenv("LR_FUSED_GRAM", raising=False)
+    wl = li.c4(n_candidates=3, n_steps=120)
+    job = parallel.OracleJob(wl, None, 40)
+    b = runner.make_batch(wl, precision="fp32_g64", engine="fused", pop_every=40)
+    assert b.query().gram_tc == 1
+    b.set_initial(wl.init_seed, wl.eps)
+    b.integrate(wl.dt, wl.n_steps)
+    got = b.observables()
+    b.close()
+    ora = job.result()
+    nts = [c.model.dims[0] for c in wl.candidates for _ in (0, 1)]
+    print(compare_observables(got, ora, 6, nts, 5e-5, 5e-5, "gram on tensor cores"))
