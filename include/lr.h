@@ -266,6 +266,31 @@ lr_status lr_observables(lr_ctx* ctx, double* beta, double* pops, double* nphot,
  * Synchronises the stream and returns the device error word's status. */
 lr_status lr_loss(lr_ctx* ctx, double* ionization, double* loss, void* stream);
 
+/* Assignment error from simulated single-shot readout records with seeded
+ * Gaussian measurement noise (Sec. S3.A, measurement efficiency eta): the
+ * Monte Carlo counterpart of eps_a, over the steps integrated so far.
+ * For candidate c (trajectories 2c = |g>, 2c+1 = |e>, readout fields
+ * beta_g, beta_e on the step grid, trapezoid weights w_k over steps 0..n) the
+ * record is integrated in bins of bin_steps steps: q_b = sum_{k in b} w_k
+ * (beta_e - beta_g)_k dt, W_b = sum_{k in b} w_k dt, and a shot of state j has
+ * the increments dY_b = sqrt(2 eta kappa) sum_{k in b} w_k beta_j,k dt +
+ * sqrt(W_b) xi_b, xi_b complex Gaussian with E|xi|^2 = 1. The matched filter
+ * Re sum_b conj(q_b / W_b) dY_b against the midpoint of its two means gives
+ * T_j = +-D/2 + N, D = sqrt(2 eta kappa) sum_b |q_b|^2 / W_b,
+ * N = sum_b Re(conj(q_b) xi_b) / sqrt(W_b); shot j is misassigned when
+ * T_e <= 0 or T_g > 0. Noise: xi_b = (n1 + i n2) / sqrt 2 from Box-Muller on
+ * the uniforms u = ((x >> 11) + 1) 2^-53 of outputs 2b and 2b + 1 of the
+ * SplitMix64 stream whose seed is output (2c + j) n_shots + s of the stream
+ * of `seed` (shot s; the initial-state draws use the same generator).
+ * Outputs (host, any may be NULL): eps_shots[c] = (misassigned g + e) /
+ * (2 n_shots) + tau gamma / 2; eps_bin[c] = erfc(SNR_b / 2) / 2 + tau gamma / 2,
+ * SNR_b^2 = 2 eta kappa sum_b |q_b|^2 / W_b, the value eps_shots converges to
+ * (with bin_steps = 1 it is eps_a); errors[c][2] = misassigned g and e shots.
+ * LR_ERR_ARG for n_shots outside 1 .. 65535 x 256, bin_steps < 1 or more than 2048 bins;
+ * LR_ERR_STATE before the first step. Synchronises the stream. */
+lr_status lr_assignment_shots(lr_ctx* ctx, double eta, long n_shots, int bin_steps, unsigned long long seed,
+                              double* eps_shots, double* eps_bin, long long* errors, void* stream);
+
 /* Validity diagnostics of the low-rank ansatz (Sec. S1.B, Fig. S1): at every
  * recorded step, the spectrum of rho = Z Z^dag and its purity tr(rho^2).
  * The nonzero eigenvalues of rho are those of the Gram matrix G = Z^dag Z

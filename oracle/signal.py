@@ -14,6 +14,12 @@ every step t_n = n dt).
 
 Parity: pinned by the constant-difference closed form
 SNR = sqrt(2 eta kappa tau) |Delta| and by erfc(1) (tests).
+
+assignment_shots simulates the measurement behind that formula: seeded
+single-shot heterodyne records of the readout mode, a matched filter and a
+midpoint threshold; its misassignment rate converges to the formula's eps_sep
+(binomial bound) and its binned SNR reduces to the trapezoid SNR for bins of
+one step (tests).
 """
 from __future__ import annotations
 
@@ -57,3 +63,72 @@ def ionization(pops_g, pops_e, dt_rec: float, tau: float) -> float:
 def loss(eps_a: float, T: float) -> float:
     """Loss of Sec. S3.B: Lambda = log10(eps_a + T)."""
     return math.log10(eps_a + T)
+
+
+def assignment_shots(beta_g, beta_e, dt: float, kappa: float, gamma: float, eta: float, n_shots: int,
+                     bin_steps: int, seed: int, cand: int) -> dict:
+    """Seeded single-shot readout of candidate `cand` (Sec. S3.A's measurement).
+
+    Steps 0..n with trapezoid weights w_k (dt, halved at both ends), bins of
+    bin_steps steps: q_b = sum_{k in b} w_k (beta_e - beta_g)_k, W_b = sum w_k.
+    A shot of state j has record increments dY_b = sqrt(2 eta kappa) sum w_k
+    beta_j,k + sqrt(W_b) xi_b (xi_b complex Gaussian, E|xi|^2 = 1); the matched
+    filter Re sum_b conj(q_b / W_b) dY_b minus the midpoint of its two means is
+    T_j = +-D/2 + N, D = sqrt(2 eta kappa) sum_b |q_b|^2 / W_b,
+    N = sum_b Re(conj(q_b) xi_b) / sqrt(W_b). State e is misassigned when
+    T_e <= 0, state g when T_g > 0.
+
+    Noise: xi_b = (n1 + i n2) / sqrt(2), Box-Muller on the uniforms of outputs
+    2b, 2b + 1 of the SplitMix64 stream seeded with output (2 cand + j) n_shots
+    + s of the stream of `seed` (shot s), the generator of the initial states.
+    Sums over steps and over bins are sequential, in FP64.
+    Returns eps_shots, eps_bin = erfc(SNR_b / 2) / 2 + tau gamma / 2 with
+    SNR_b^2 = 2 eta kappa sum_b |q_b|^2 / W_b, errors (g, e), D and the
+    statistics T_g, T_e of every shot."""
+    from .init_state import GOLDEN, mix64, splitmix64
+    bg = np.asarray(beta_g, dtype=np.complex128)
+    be = np.asarray(beta_e, dtype=np.complex128)
+    n = len(bg) - 1
+    if n < 1:
+        raise ValueError("need at least one step")
+    w = np.full(n + 1, float(dt))
+    w[0] = w[n] = 0.5 * dt
+    nb = (n + bin_steps) // bin_steps
+    q = np.zeros(nb, np.complex128)
+    W = np.zeros(nb)
+    diff = be - bg
+    for b in range(nb):
+        k0, k1 = b * bin_steps, min((b + 1) * bin_steps, n + 1)
+        qr = qi = wt = 0.0
+        for k in range(k0, k1):                       # sequential, as the definition reads
+            qr += w[k] * diff[k].real
+            qi += w[k] * diff[k].imag
+            wt += w[k]
+        q[b] = complex(qr, qi)
+        W[b] = wt
+    s2 = float(np.sum(np.abs(q) ** 2 / W))
+    D = math.sqrt(2.0 * eta * kappa) * s2
+    snr_b = math.sqrt(2.0 * eta * kappa * s2)
+    a = np.conj(q) / np.sqrt(W)
+    k = np.arange(nb, dtype=np.uint64)
+    out_T = []
+    errors = []
+    for j in (0, 1):
+        keys = splitmix64(seed, np.uint64((2 * cand + j) * n_shots) + np.arange(n_shots, dtype=np.uint64))
+        with np.errstate(over="ignore"):
+            x1 = mix64(keys[:, None] + (2 * k[None, :] + np.uint64(1)) * GOLDEN)
+            x2 = mix64(keys[:, None] + (2 * k[None, :] + np.uint64(2)) * GOLDEN)
+        u1 = ((x1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        u2 = ((x2 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        r = np.sqrt(-2.0 * np.log(u1))
+        n1, n2 = r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)
+        terms = (a.real[None, :] * n1 - a.imag[None, :] * n2) / math.sqrt(2.0)
+        N = np.cumsum(terms, axis=1)[:, -1]           # sequential over the bins
+        T = (0.5 * D if j == 1 else -0.5 * D) + N
+        out_T.append(T)
+        errors.append(int(np.sum(T <= 0.0)) if j == 1 else int(np.sum(T > 0.0)))
+    tau = n * dt
+    dec = 0.5 * tau * gamma
+    return {"eps_shots": (errors[0] + errors[1]) / (2.0 * n_shots) + dec,
+            "eps_bin": 0.5 * math.erfc(0.5 * snr_b) + dec, "snr_bin": snr_b, "errors": tuple(errors), "D": D,
+            "T_g": out_T[0], "T_e": out_T[1]}

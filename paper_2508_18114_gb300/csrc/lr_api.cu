@@ -28,7 +28,7 @@ struct lr_ctx {
   // workspace layout (byte offsets)
   size_t o_traj = 0, o_pulse = 0, o_err = 0, o_zn = 0, o_za = 0, o_zb = 0, o_acc = 0, o_x = 0, o_part = 0,
          o_beta = 0, o_pops = 0, o_nphot = 0, o_trace = 0, o_eps = 0, o_ion = 0, o_loss = 0, o_scratch = 0,
-         o_gsnap = 0, o_dpur = 0, o_deig = 0, o_dstep = 0, total = 0;
+         o_gsnap = 0, o_dpur = 0, o_deig = 0, o_dstep = 0, o_shots = 0, total = 0;
   size_t scratch_bytes = 0;
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -242,6 +242,8 @@ lr_status lr_create(int n_cand, const lr_model* models, const int* ranks, const 
   c->o_eps = take(sizeof(double) * n_cand);
   c->o_ion = take(sizeof(double) * n_cand);
   c->o_loss = take(sizeof(double) * n_cand);
+  // lr_assignment_shots: counts [n_cand][2] (u64), SNR, eps_shots, eps_bin [n_cand]
+  c->o_shots = take(sizeof(double) * 5 * n_cand);
   if (opt->record_gram) {
     const size_t nr = (size_t)c->n_traj * c->n_rec;
     c->o_gsnap = take(sizeof(double2) * nr * c->max_M * c->max_M);
@@ -506,6 +508,38 @@ lr_status lr_loss(lr_ctx* c, double* ionization, double* loss, void* stream) {
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, c->ws + c->o_loss, sizeof(double) * c->n_cand, cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "copying the loss");
+  return check_device_error(c);
+}
+
+lr_status lr_assignment_shots(lr_ctx* c, double eta, long n_shots, int bin_steps, unsigned long long seed,
+                              double* eps_shots, double* eps_bin, long long* errors, void* stream) {
+  if (!c) return LR_ERR_ARG;
+  if (!ready(c)) return fail(c, LR_ERR_WORKSPACE, "no workspace bound");
+  if (n_shots < 1 || n_shots > 65535L * 256 || bin_steps < 1 || !(eta > 0.0))
+    return fail(c, LR_ERR_ARG, "bad n_shots (1 .. 65535 x 256), bin_steps or eta");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = refresh_step(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronising");
+  if (c->step < 1) return fail(c, LR_ERR_STATE, "lr_assignment_shots before the first step");
+  if ((c->step + bin_steps) / bin_steps > lr::shots_max_bins())
+    return fail(c, LR_ERR_ARG, "more than 2048 bins: raise bin_steps");
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(c->ws + c->o_shots);
+  double* snr = reinterpret_cast<double*>(c->ws + c->o_shots) + 2 * c->n_cand;
+  double* es = snr + c->n_cand;
+  double* eb = es + c->n_cand;
+  e = lr::launch_shots(dev_ptrs(c), run_params(c), c->step, eta, n_shots, bin_steps, seed, counts, snr, es, eb, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "launching the shot simulation");
+  std::vector<unsigned long long> cnt(2 * (size_t)c->n_cand);
+  if ((e = cudaMemcpyAsync(cnt.data(), counts, sizeof(unsigned long long) * cnt.size(), cudaMemcpyDeviceToHost, s)) ==
+          cudaSuccess &&
+      eps_shots)
+    e = cudaMemcpyAsync(eps_shots, es, sizeof(double) * c->n_cand, cudaMemcpyDefault, s);
+  if (e == cudaSuccess && eps_bin) e = cudaMemcpyAsync(eps_bin, eb, sizeof(double) * c->n_cand, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copying the shot results");
+  if (errors)
+    for (size_t i = 0; i < cnt.size(); ++i) errors[i] = (long long)cnt[i];
   return check_device_error(c);
 }
 

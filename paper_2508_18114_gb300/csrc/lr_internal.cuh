@@ -231,6 +231,11 @@ cudaError_t launch_grow(const DevPtrs& dst, const DevPtrs& src, int n_traj, int 
 // eps_a, T(tau) and Lambda at step *p.dstep + n_added (the integrate that
 // precedes it in the stream took n_added steps), then *p.dstep += n_added.
 cudaError_t launch_eps_a(const DevPtrs& p, const RunParams& rp, long n_added, cudaStream_t s);
+// seeded single-shot readout (lr_shots.cu)
+int shots_max_bins();
+cudaError_t launch_shots(const DevPtrs& p, const RunParams& rp, long step, double eta, long n_shots, int bin,
+                         unsigned long long seed, unsigned long long* counts, double* snr, double* eps_shots,
+                         double* eps_bin, cudaStream_t s);
 // Elementwise complex128 <-> complex64 conversion of n elements.
 cudaError_t launch_convert(const void* src, void* dst, long long n, int to_fp32, cudaStream_t s);
 

@@ -42,7 +42,7 @@ EXPORTS = (
     "lr_sparse_destroy", "lr_grow_rank", "lr_measure_peak", "lr_sparse_query",
     "lr_full_create", "lr_full_workspace_size", "lr_full_bind_workspace", "lr_full_set_initial",
     "lr_full_set_state", "lr_full_set_state_lowrank", "lr_full_get_state", "lr_full_integrate", "lr_full_observables", "lr_full_last_error",
-    "lr_full_destroy",
+    "lr_full_destroy", "lr_assignment_shots",
 )
 
 
@@ -111,6 +111,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_backward_workspace_size.argtypes = [vp, i, C.POINTER(C.c_size_t)]
     lib.lr_backward.argtypes = [vp, vp, C.c_size_t, vp, vp, i, vp]
     lib.lr_loss.argtypes = [vp, vp, vp, vp]
+    lib.lr_assignment_shots.argtypes = [vp, d, l, i, C.c_uint64, vp, vp, vp, vp]
     lib.lr_diagnostics.argtypes = [vp, vp, vp, vp]
     lib.lr_paper_model_size.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_long)]
     lib.lr_paper_model_build.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -348,6 +349,19 @@ class LowRankBatch:
         self._check(self._lib.lr_loss(self._h, ion.ctypes.data_as(C.c_void_p), loss.ctypes.data_as(C.c_void_p),
                                       C.c_void_p(_stream_ptr(stream))))
         return ion, loss
+
+    def assignment_shots(self, n_shots: int, seed: int, bin_steps: int = 1, eta: float = None, stream=None) -> dict:
+        """Seeded single-shot readout (lr_assignment_shots): per candidate the
+        empirical assignment error eps_shots, the binned closed form eps_bin it
+        converges to, and the misassigned g and e shots."""
+        n = len(self.models)
+        es, eb = np.empty(n), np.empty(n)
+        err = np.empty((n, 2), dtype=np.int64)
+        self._check(self._lib.lr_assignment_shots(self._h, float(self.options["eta"] if eta is None else eta), int(n_shots),
+                                                  int(bin_steps), C.c_uint64(seed), es.ctypes.data_as(C.c_void_p),
+                                                  eb.ctypes.data_as(C.c_void_p), err.ctypes.data_as(C.c_void_p),
+                                                  C.c_void_p(_stream_ptr(stream))))
+        return {"eps_shots": es, "eps_bin": eb, "errors": err}
 
     def grown(self, ranks, seed: int, eps: float = 1e-5, stream=None) -> "LowRankBatch":
         """A new batch with ranks >= the current ones that continues this pulse

@@ -601,3 +601,53 @@ def test_rwa_tracks_lab_frame_for_a_weak_near_resonant_drive():
     t = np.arange(n + 1) * dt
     diff = np.abs(a["beta"] * np.exp(1j * wd * t) - b["beta"]).max()
     assert diff < 3 * om / wd * np.abs(b["beta"]).max()
+
+
+def _shot_signals(n=1500, dt=0.01):
+    """A readout pair with a closed form: beta_g = 0, beta_e = A (1 - e^{-t/t0}) e^{i phi}."""
+    t = np.arange(n + 1) * dt
+    be = 0.8 * (1.0 - np.exp(-t / 2.0)) * np.exp(0.7j)
+    return np.zeros(n + 1, np.complex128), be, dt
+
+
+def test_assignment_shots_bins_of_one_step_are_the_trapezoid_snr():
+    bg, be, dt = _shot_signals()
+    kappa, gamma, eta = 0.9, 2e-4, 0.6
+    r = signal.assignment_shots(bg, be, dt, kappa, gamma, eta, 16, 1, 7, 0)
+    assert r["eps_bin"] == pytest.approx(signal.assignment_error(bg, be, dt, kappa, gamma, eta), rel=1e-13)
+    assert r["snr_bin"] == pytest.approx(signal.snr(bg, be, dt, kappa, eta), rel=1e-13)
+
+
+def test_assignment_shots_binning_loses_snr_except_for_a_constant_difference():
+    """Cauchy-Schwarz: |q_b|^2 / W_b <= sum_b w |Delta|^2, equality for a constant
+    difference Delta, where SNR_b = sqrt(2 eta kappa tau) |Delta| (the closed form)."""
+    bg, be, dt = _shot_signals()
+    r1 = signal.assignment_shots(bg, be, dt, 0.9, 0.0, 0.6, 4, 1, 1, 0)
+    r50 = signal.assignment_shots(bg, be, dt, 0.9, 0.0, 0.6, 4, 50, 1, 0)
+    assert r50["snr_bin"] < r1["snr_bin"]
+    n, delta = 1500, 0.3 - 0.4j
+    const = np.full(n + 1, delta)
+    rc = signal.assignment_shots(np.zeros(n + 1), const, dt, 0.9, 0.0, 0.6, 4, 37, 1, 0)
+    assert rc["snr_bin"] == pytest.approx(math.sqrt(2 * 0.6 * 0.9 * n * dt) * abs(delta), rel=1e-12)
+
+
+def test_assignment_shots_converge_to_the_closed_form():
+    """The misassignment rate of 40,000 seeded shots per state lies within four
+    binomial standard deviations of erfc(SNR_b / 2) / 2; the noise statistic N
+    has the variance D / (2 sqrt(2 eta kappa)) of the definition; the decay
+    term tau gamma / 2 is added to both."""
+    bg, be, dt = _shot_signals()
+    kappa, gamma, eta, ns = 0.25, 1e-3, 0.6, 40000
+    r = signal.assignment_shots(bg, be, dt, kappa, gamma, eta, ns, 25, 20250818, 3)
+    dec = 0.5 * 1500 * dt * gamma
+    p = r["eps_bin"] - dec
+    assert 0.02 < p < 0.3                      # a regime where the rate is measurable
+    got = r["eps_shots"] - dec
+    assert abs(got - p) <= 4.0 * math.sqrt(p * (1 - p) / (2 * ns)), (got, p)
+    var = np.var(np.concatenate([r["T_g"] + 0.5 * r["D"], r["T_e"] - 0.5 * r["D"]]))
+    assert var == pytest.approx(r["D"] / (2 * math.sqrt(2 * eta * kappa)), rel=0.03)
+    # the two states use different noise, the same seed gives the same shots
+    assert not np.array_equal(r["T_g"] + 0.5 * r["D"], r["T_e"] - 0.5 * r["D"])
+    r2 = signal.assignment_shots(bg, be, dt, kappa, gamma, eta, 64, 25, 20250818, 3)
+    r3 = signal.assignment_shots(bg, be, dt, kappa, gamma, eta, 64, 25, 20250818, 3)
+    assert np.array_equal(r2["T_g"], r3["T_g"]) and np.array_equal(r2["T_e"], r3["T_e"])
