@@ -48,8 +48,9 @@ DTYPE_LABEL = {
     "fp32": "f32 bulk and Gram; double-word f32 (~2^-48) LDL^dag, G^-1 and X_k; f64 signal",
     "tf32_g64": "f32 bulk, tf32 projection; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 and X_k; f64 signal",
 }
-# DRAM bytes per trajectory-step of the tensor-core-Gram kernel (None: not captured since its last change)
-TRAFFIC_GRAM_TC = None
+# DRAM bytes per trajectory-step of the tensor-core-Gram kernel, from its ncu capture on the
+# 76-trajectory, 10-step case (0.578 GB read + 1.713 GB written for 760 trajectory-steps)
+TRAFFIC_GRAM_TC = 3.015e6
 # FP32_G64 with the Gram matrix on the tensor cores (the default plan of the N=2000, M=20 batch)
 DTYPE_GRAM_TC = ("f32 bulk; FP64-class (~2^-48) Gram from exact bf16-slice tcgen05 MMAs (f32 accumulation, "
                  "exact) and double-word sums; double-word f32 LDL^dag, G^-1 and X_k; f64 signal")
@@ -423,7 +424,7 @@ def run_ours(args):
     # of the same workload, per trajectory-step at the same number of resident teams, scaled by
     # the trajectory-steps of one launch; only for the kernels those captures measured:
     # double-word Gram 0.338 GB read + 1.586 GB written for 760 trajectory-steps (2.532 MB),
-    # tensor-core Gram TRAFFIC_GRAM_TC
+    # tensor-core Gram 3.015 MB (TRAFFIC_GRAM_TC)
     traffic = None
     if (wl.name == "c4" and prec == "fp32_g64" and engine == "fused" and info.team_size == 2
             and not info.stage_in_smem and info.tensor_passes == 0):
