@@ -49,6 +49,7 @@ def test_graph_replays_continue_the_pulse_run():
     b.close()
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")   # the refused capture records nothing
 def test_plain_engine_refuses_capture():
     wl = li.c1(n_steps=10)
     b = runner.make_batch(wl, precision="fp64", engine="plain", pop_every=5, max_steps=10)
