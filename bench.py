@@ -737,7 +737,8 @@ def run_paper(args):
             "metric": "traj_steps_per_s", "value": value, "unit": "traj*steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == "fp64" else (("f32 bulk; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 "
+            "dtype": "f64" if prec == "fp64" else (DTYPE_GRAM_TC if b.fused and b.gram_tc else
+                                                   ("f32 bulk; double-word f32 (~2^-48) Gram, LDL^dag, G^-1 "
                                                     "and X_k; f64 signal") if b.fused else
                                                    "f32 bulk; double-word f32 (~2^-48) Gram; f64 Cholesky, "
                                                    "solves and signal"),
@@ -749,6 +750,8 @@ def run_paper(args):
                                       "x".join(map(str, wl.dims)), wl.M, dt, wl.tau, prec),
                        "trajectories": T, "N": model["N"], "M": wl.M, "nnz": int(model["nnz"]),
                        "engine": "sparse (fused persistent kernel)" if b.fused else "sparse (four launches per stage)",
+                       "gram": ("tcgen05 bf16 slices (exact), double-word sums" if b.fused and b.gram_tc else
+                                "double-word FP32 on the CUDA cores" if prec != "fp64" else "f64"),
                        "schedule": (("equal spans of the batch's trajectory-steps, one per CTA" if split else
                                      "teams of %d CTA(s), one trajectory at a time" % team) if b.fused else None),
                        "chunk_rk4_steps": chunk,

@@ -555,8 +555,12 @@ lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, double gamma, d
  * batch has at least as many trajectories as the GPU has SMs (each CTA then
  * takes an equal span of the batch's trajectory-steps, unless
  * LR_SPARSE_SPLIT=0 at lr_sparse_integrate), else up to 16 (LR_SPARSE_C at
- * lr_sparse_create forces it); 0 for the four-launch path. */
-lr_status lr_sparse_query(const lr_sparse* s, int* fused, int* team);
+ * lr_sparse_create forces it); 0 for the four-launch path. *gram_tc (may be
+ * NULL) = 1 when the fused kernel forms the Gram matrix on the tensor cores
+ * (exact bf16 slices, double-word sums, FP64-class; LR_SPARSE_GRAM=tc at
+ * lr_sparse_create, rank padded to 20), 0 for the double-word CUDA-core
+ * sums (the default). */
+lr_status lr_sparse_query(const lr_sparse* s, int* fused, int* team, int* gram_tc);
 const char* lr_sparse_last_error(const lr_sparse* s);
 void lr_sparse_destroy(lr_sparse* s);
 

@@ -64,7 +64,7 @@ SmemLayout layout(int R, int Mp, int zs_smem, size_t es, int tc, int gs) {
   if (gs) {
     o = al128(o);
     L.o_gs = o;
-    o += 2 * fz::GS_BUF;
+    o += 2 * GS_BUF;
   }
   L.total = o;
   return L;
@@ -179,7 +179,7 @@ bool fused_plan(const std::vector<TrajDev>& traj, lr_precision prec, int frame, 
       if (force_c > 0 && C != force_c) continue;
       int R = 0;
       for (const TrajDev& d : traj) R = std::max(R, rows_per_cta(d, C));
-      if (gs && R > fz::GS_MAXR) continue;   // the slice sums stay exact for <= GS_MAXR rows
+      if (gs && R > GS_MAXR) continue;   // the slice sums stay exact for <= GS_MAXR rows
       const SmemLayout L = layout(R, Mp, zs_smem, es, tc, gs);
       if (L.total > smem_max) continue;
       if (raise_smem_limit(kern, L.total) != cudaSuccess) {

@@ -542,6 +542,7 @@ struct lr_sparse {
   int N, M, K, T, n_levels, nblk, ntile;
   int fp32;   // 1: FP32_G64 state arithmetic
   int fused;  // 1: the fused persistent kernel (FP32_G64), 0: four launches per RK4 stage
+  int gram_tc;   // fused: 1 when the Gram matrix is formed on the tensor cores (rank padded to 20)
   int n_cta;   // fused: persistent CTAs (n_team teams of team_c)
   int n_team, team_c;   // fused: teams (one trajectory at a time each), CTAs per team
   size_t o_fsc;   // fused: per-CTA stage buffers
@@ -623,9 +624,10 @@ void layout(lr_sparse* s) {
 // [Mp][Mp+1]), T_k and XT_k (FP32 complex [K][Mp][Mp]), scalars, and the
 // partials of G (FP64 complex [Mp][Mp]) and the team's T_k ([K][Mp][Mp]).
 struct SfSmem {
-  int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum, total;
+  int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum, o_gs, o_gv, total;
 };
-SfSmem sf_smem(int M, int K) {
+// gtc: the slice buffers and V of the Gram matrix on the tensor cores
+SfSmem sf_smem(int M, int K, int gtc) {
   const int Mp = (M + 3) / 4 * 4;
   SfSmem L;
   int o = 0;
@@ -643,6 +645,14 @@ SfSmem sf_smem(int M, int K) {
   o += Mp * Mp * (int)sizeof(double2);
   L.o_tsum = o;
   o += K * Mp * Mp * (int)sizeof(float2);
+  L.o_gs = L.o_gv = o;
+  if (gtc) {
+    o = (o + 127) / 128 * 128;
+    L.o_gs = o;
+    o += 2 * GS_BUF;
+    L.o_gv = o;
+    o += 40 * 40 * 8;
+  }
   L.total = o;
   return L;
 }
@@ -650,7 +660,8 @@ SfSmem sf_smem(int M, int K) {
 cudaError_t raise_fused_smem(int bytes) {
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  for (const void* k : {(const void*)sfz::sf_kernel<false>, (const void*)sfz::sf_kernel<true>}) {
+  for (const void* k : {(const void*)sfz::sf_kernel<false, false>, (const void*)sfz::sf_kernel<true, false>,
+                        (const void*)sfz::sf_kernel<false, true>, (const void*)sfz::sf_kernel<true, true>}) {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, k);
     if (e != cudaSuccess) return e;
@@ -672,7 +683,7 @@ void fused_teams(lr_sparse* s, int sms) {
   if (s->T < sms) C = std::max(1, std::min({16, sms / s->T, s->N / 64}));
   if (const char* e = getenv("LR_SPARSE_C")) C = std::max(1, std::min(16, atoi(e)));
   C = std::min(C, s->N);
-  const SfSmem L = sf_smem(s->M, s->K);
+  const SfSmem L = sf_smem(s->M, s->K, s->gram_tc);
   for (; C > 1; --C) {   // the largest team that fits as a cluster
     if (raise_fused_smem(L.total) != cudaSuccess) break;
     cudaLaunchConfig_t cfg{};
@@ -687,7 +698,8 @@ void fused_teams(lr_sparse* s, int sms) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, sfz::sf_kernel<true>, &cfg) == cudaSuccess && ncl > 0) {
+    const void* kt = s->gram_tc ? (const void*)sfz::sf_kernel<true, true> : (const void*)sfz::sf_kernel<true, false>;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kt, &cfg) == cudaSuccess && ncl > 0) {
       s->team_c = C;
       s->n_team = std::min(s->T, ncl);
       s->n_cta = C * s->n_team;
@@ -899,12 +911,19 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   // one persistent CTA per SM (fewer when the batch is smaller)
   s->fused = 0;
   s->n_cta = s->n_team = s->team_c = 0;
+  s->gram_tc = 0;
   const char* fz_env = getenv("LR_SPARSE_FUSED");
   if (s->fp32 && !(fz_env && strcmp(fz_env, "0") == 0)) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
                                                    cudaSuccess && sms > 0) {
       s->fused = 1;
+      // LR_SPARSE_GRAM=tc: the Gram matrix on the tensor cores (rank padded to 20,
+      // its slice layout); the default keeps the double-word CUDA-core sums, which
+      // measured 1.8% faster on the 512-trajectory batch (this kernel waits on its
+      // operator gathers, not on the Gram's FMAs)
+      const char* gram_env = getenv("LR_SPARSE_GRAM");
+      s->gram_tc = (s->M + 3) / 4 * 4 == 20 && gram_env && strcmp(gram_env, "tc") == 0;
       fused_teams(s, sms);
     } else {
       cudaGetLastError();
@@ -1061,7 +1080,7 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
   const SpDev d = dev(s);
   const SpParams p = params(s);
   if (s->fused) {
-    const SfSmem L = sf_smem(s->M, s->K);
+    const SfSmem L = sf_smem(s->M, s->K, s->gram_tc);
     cudaError_t e0 = raise_fused_smem(L.total);
     if (e0 != cudaSuccess) return cuda_fail(s, e0);
     sfz::Args a{};
@@ -1107,11 +1126,14 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
     a.o_misc = L.o_misc;
     a.o_gpart = L.o_gpart;
     a.o_tsum = L.o_tsum;
+    a.o_gs = L.o_gs;
+    a.o_gv = L.o_gv;
     if (a.split) {
       // the hand-over waits need every CTA resident: a cooperative launch
       // (refused, rather than run, when the grid does not fit)
       int per_sm = 0, dev = 0, sms = 0;
-      cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sfz::sf_kernel<false>, sfz::NT, L.total);
+      const void* k1 = s->gram_tc ? (const void*)sfz::sf_kernel<false, true> : (const void*)sfz::sf_kernel<false, false>;
+      cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, sfz::NT, L.total);
       if (e1 == cudaSuccess) e1 = cudaGetDevice(&dev);
       if (e1 == cudaSuccess) e1 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e1 != cudaSuccess) return cuda_fail(s, e1);
@@ -1128,7 +1150,8 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
       at[0].val.cooperative = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      e1 = cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false>, a);
+      e1 = s->gram_tc ? cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false, true>, a)
+                      : cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false, false>, a);
       if (e1 != cudaSuccess) return cuda_fail(s, e1);
     } else {
       cudaLaunchConfig_t cfg{};
@@ -1144,7 +1167,10 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
       cfg.attrs = at;
       cfg.numAttrs = 1;
       const cudaError_t e1 =
-          a.C > 1 ? cudaLaunchKernelEx(&cfg, sfz::sf_kernel<true>, a) : cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false>, a);
+          a.C > 1 ? (s->gram_tc ? cudaLaunchKernelEx(&cfg, sfz::sf_kernel<true, true>, a)
+                                : cudaLaunchKernelEx(&cfg, sfz::sf_kernel<true, false>, a))
+                  : (s->gram_tc ? cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false, true>, a)
+                                : cudaLaunchKernelEx(&cfg, sfz::sf_kernel<false, false>, a));
       if (e1 != cudaSuccess) return cuda_fail(s, e1);
     }
   } else if (s->fp32) {
@@ -1210,10 +1236,11 @@ extern "C" lr_status lr_sparse_loss(lr_sparse* s, double eta, double kappa, doub
   return LR_OK;
 }
 
-extern "C" lr_status lr_sparse_query(const lr_sparse* s, int* fused, int* team) {
+extern "C" lr_status lr_sparse_query(const lr_sparse* s, int* fused, int* team, int* gram_tc) {
   if (!s || !fused) return LR_ERR_ARG;
   *fused = s->fused;
   if (team) *team = s->fused ? s->team_c : 0;
+  if (gram_tc) *gram_tc = s->fused ? s->gram_tc : 0;
   return LR_OK;
 }
 

@@ -37,6 +37,7 @@
 #include <cooperative_groups.h>
 
 #include "lr_internal.cuh"
+#include "lr_tc.cuh"
 
 namespace lr {
 namespace sfz {
@@ -76,7 +77,10 @@ struct Args {
   long step0, n_steps;
   // byte offsets in dynamic shared memory
   int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum;
+  int o_gs, o_gv;   // Gram on the tensor cores: two slice buffers, V [40][40] double-word
 };
+
+constexpr int SG_W = 10;   // slicing warps of the tensor-core Gram (warp SG_W issues the MMAs)
 
 struct DW {
   float hi, lo;
@@ -96,6 +100,12 @@ __device__ __forceinline__ void dw_add(DW& s, const DW& o) {
   const float err = (s.hi - (t - bp)) + (o.hi - bp);
   s.hi = t;
   s.lo += err + o.lo;
+}
+__device__ __forceinline__ void dw_add_f(DW& s, float x) {   // s += x (Knuth's two-sum into hi)
+  const float t = s.hi + x;
+  const float bp = t - s.hi;
+  s.lo += (s.hi - (t - bp)) + (x - bp);
+  s.hi = t;
 }
 __device__ __forceinline__ DW dw_make(double x) {
   DW r;
@@ -277,9 +287,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int tid)
 
 // TEAM = false: teams of one CTA (C = 1 known at compile time; the equal-span
 // schedule); TEAM = true: clusters of a.C CTAs.
-template <bool TEAM>
+template <bool TEAM, bool GTC>
 __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // tensor-core Gram (GTC): TMEM base, mbarriers (MMA commits and chunk fills per
+  // buffer, TMEM free after a readout) and column maxima [2][20] by stage parity
+  __shared__ __align__(8) unsigned long long gbar_s[5];
+  __shared__ uint32_t gslot;
+  __shared__ uint32_t gcmax[2][20];
   __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
   __shared__ float2 chi[NCH];
   __shared__ double red[NWARP * 4];
@@ -290,6 +305,33 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   const int ldg = Mp + 1;
   for (int i = tid; i < LR_MAX_RANK; i += NT)
     for (int j = 0; j <= i; ++j) tri[i * (i + 1) / 2 + j] = make_short2((short)i, (short)j);
+  const uint32_t gbar[2] = {smem_u32(&gbar_s[0]), smem_u32(&gbar_s[1])};
+  const uint32_t gfill[2] = {smem_u32(&gbar_s[2]), smem_u32(&gbar_s[3])};
+  const uint32_t gfree = smem_u32(&gbar_s[4]);
+  uint32_t tmem = 0;
+  // phases waited: commits (slicing warps), fills (issuing warp), TMEM frees (issuing warp)
+  uint32_t gph[2] = {0u, 0u}, gfph[2] = {0u, 0u}, gtf = 0u;
+  bool gused = false;   // the issuing warp: TMEM held a readout before
+  int gpar = 0;         // stage parity of the column maxima
+  if constexpr (GTC) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gbar[0]), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gbar[1]), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gfill[0]), "r"(SG_W * 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gfill[1]), "r"(SG_W * 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gfree), "r"(SG_W * 32));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&gslot)),
+                   "r"(512));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = gslot;
+  }
   double2* Gd = reinterpret_cast<double2*>(smem + a.o_gd);   // [Mp][Mp+1]  G -> L -> G^-1
   double2* W = reinterpret_cast<double2*>(smem + a.o_w);     // [Mp][Mp+1]  L^-1
   float2* Tred = reinterpret_cast<float2*>(smem + a.o_tred);  // [K][Mp*Mp]  T_k over this CTA's rows
@@ -319,6 +361,230 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   const double dt = a.dt;
   const int pe = a.pop_every;
 
+  // ---- Gram matrix of the own rows on the tensor cores (GTC; Mp = 20): exact
+  // bf16 slices of the scaled columns (see lr_tc.cuh), chunks of GS_CH rows,
+  // accumulation windows of GS_MAXR rows (the FP32 sums stay exact). Warps
+  // 0 .. SG_W-1 slice into the two buffers, arrive on the buffer's fill
+  // mbarrier and, at the end of each window, read the window's slice-pair sums
+  // out of tensor memory into V (double-word) and free it; warp SG_W waits on
+  // the fills (and, before a window, on the free) and issues the MMAs; the
+  // other warps go on to the T tiles. The slicing warps then form G over the
+  // own rows into gpart.
+  auto gram_tc = [&](int cur_buf) {
+    if (tid < 20) gcmax[gpar ^ 1][tid] = 0u;   // phase F fills it for the next stage
+    const int n_ch = (NR + GS_CH - 1) / GS_CH;
+    const int chw = GS_MAXR / GS_CH;            // chunks per window
+    const float2* zc = zs0 + (size_t)cur_buf * zsb;
+    if (warp < SG_W) {
+      constexpr int GTASK = (GS_CH / 8) * 5;
+      constexpr int GT = (GTASK + SG_W - 1) / SG_W;
+      float gsc[GT];
+      int gcol[GT];
+#pragma unroll
+      for (int t = 0; t < GT; ++t) {
+        const int task = (warp + SG_W * t) % GTASK, ag = task % 5, ar = ag * 8 + (lane >> 2);
+        gcol[t] = ar;
+        int ex = 0;
+        frexpf(__uint_as_float(gcmax[gpar][ar < 20 ? ar : ar - 20]), &ex);
+        gsc[t] = ldexpf(1.0f, -ex);   // |value| scale < 1, exact
+      }
+      auto gload = [&](int ch, float (&v)[GT][2]) {
+#pragma unroll
+        for (int t = 0; t < GT; ++t) {
+          const int task = (warp + SG_W * t) % GTASK, rg = task / 5, ar = gcol[t];
+          const int j = ar < 20 ? ar : ar - 20, r0 = ch * GS_CH + rg * 8 + 2 * (lane & 3);
+          const float* z0 = reinterpret_cast<const float*>(zc + (size_t)(r_lo + (r0 < NR ? r0 : 0)) * Mp + j) +
+                            (ar < 20 ? 0 : 1);
+          const float* z1 = reinterpret_cast<const float*>(zc + (size_t)(r_lo + (r0 + 1 < NR ? r0 + 1 : 0)) * Mp + j) +
+                            (ar < 20 ? 0 : 1);
+          v[t][0] = r0 < NR ? *z0 : 0.f;
+          v[t][1] = r0 + 1 < NR ? *z1 : 0.f;
+        }
+      };
+      // every commit is waited on once, in chunk order (a parity wait tells
+      // adjacent phases apart only)
+      int waited = -1;
+      auto wait_chunk = [&](int c) {
+        while (waited < c) {
+          ++waited;
+          const int b = waited & 1;
+          if (!mbar_wait(gbar[b], gph[b] & 1u)) set_error(a.err, DEV_TIMEOUT);
+          ++gph[b];
+        }
+      };
+      DW* V = reinterpret_cast<DW*>(smem + a.o_gv);   // [40][40]
+      const int qd = warp & 3, nq = (SG_W - qd + 3) / 4, rw = warp >> 2, m = qd * 32 + lane;
+      const int sA = m / 40, aa = m % 40, sB = 3 + m / 40;
+      float gnext[GT][2];
+      gload(0, gnext);
+      for (int ch = 0; ch < n_ch; ++ch) {
+        const int b = ch & 1;
+        float gv[GT][2];
+#pragma unroll
+        for (int t = 0; t < GT; ++t) {
+          gv[t][0] = gnext[t][0] * gsc[t];
+          gv[t][1] = gnext[t][1] * gsc[t];
+        }
+        if (ch + 1 < n_ch) gload(ch + 1, gnext);
+        if (ch >= 2) wait_chunk(ch - 2);   // the MMAs of chunk ch - 2 are done with buffer b
+        tc_fence_after();
+        unsigned char* buf = smem + a.o_gs + b * GS_BUF;
+#pragma unroll
+        for (int sl = 0; sl < GS_N; ++sl)
+#pragma unroll
+          for (int t = 0; t < GT; ++t) {
+            if (warp + SG_W * t >= GTASK) continue;   // uniform across the warp
+            const int task = warp + SG_W * t, rg = task / 5, ag = task % 5;
+            const float y0 = gv[t][0] * 128.f, y1 = gv[t][1] * 128.f;
+            // round to the nearest integer by adding and subtracting 1.5 2^23
+            const float k0 = __fsub_rn(__fadd_rn(y0, 12582912.f), 12582912.f);
+            const float k1 = __fsub_rn(__fadd_rn(y1, 12582912.f), 12582912.f);
+            gv[t][0] = y0 - k0;
+            gv[t][1] = y1 - k1;
+            reinterpret_cast<uint32_t*>(buf + rg * GS_LBO + (sl * 5 + ag) * 128)[lane] =
+                __byte_perm(__float_as_uint(k0), __float_as_uint(k1), 0x7632);
+          }
+        async_proxy_fence();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gfill[b]) : "memory");
+        if ((ch + 1) % chw == 0 || ch + 1 == n_ch) {
+          // end of a window: its slice-pair sums D_st, s <= t, s + t <= 8, from TMEM
+          // lane m (row a = m % 40 of slices s = m / 40 and s + 3) into V, V[a][b]
+          // += sum c_st 2^-7(s+t) D_st[a][b] (c_st = 1/2 for s = t, else 1), so that
+          // G's real form is V + V^T; lanes m < 40, < 80, < 120 add in that order
+          const int win = ch / chw;
+          wait_chunk(ch);
+          tc_fence_after();
+          for (int it2 = 0; it2 < 3; ++it2) {
+            const int bk = rw + nq * it2, b0 = bk * 8;
+            const bool has = bk < 5;   // uniform within the warp
+            DW cA[8], cB[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) cA[u] = cB[u] = DW{0.f, 0.f};
+            if (has) {
+              const uint32_t lane_base = tmem + ((uint32_t)(qd * 32) << 16);
+#pragma unroll
+              for (int g = 0; g < 3; ++g) {
+                uint32_t v[4][8];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                  const int t = 4 * g + qq;
+                  const int col = t < 6 ? GS_D0 + t * 40 + b0
+                                        : (t < 8 ? GS_D1 + (t - 6) * 40 + b0 : GS_D2 + (t - 8) * 40 + b0);
+                  if (t < 11)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                        : "=r"(v[qq][0]), "=r"(v[qq][1]), "=r"(v[qq][2]), "=r"(v[qq][3]), "=r"(v[qq][4]),
+                          "=r"(v[qq][5]), "=r"(v[qq][6]), "=r"(v[qq][7])
+                        : "r"(lane_base + (uint32_t)col));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                  const int t = 4 * g + qq;
+                  if (t >= 11) continue;
+                  const int s0 = t < 8 ? sA : sB, tt = t < 8 ? t : t - 5;
+                  if (m < 120 && tt >= s0 && s0 + tt <= 8) {
+                    const float w = __int_as_float((127 - 7 * (s0 + tt) - (s0 == tt ? 1 : 0)) << 23);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                      if (t < 8)
+                        dw_add_f(cA[u], w * __uint_as_float(v[qq][u]));
+                      else
+                        dw_add_f(cB[u], w * __uint_as_float(v[qq][u]));
+                    }
+                  }
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) dw_add(cA[u], cB[u]);
+            }
+            for (int round = 0; round < 3; ++round) {
+              if (has && m < 120 && sA == round)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  DW& dst = V[aa * 40 + b0 + u];
+                  if (win == 0 && round == 0) {
+                    dst = cA[u];
+                  } else {
+                    DW x = dst;
+                    dw_add(x, cA[u]);
+                    dst = x;
+                  }
+                }
+              asm volatile("bar.sync 1, %0;" ::"r"(SG_W * 32) : "memory");
+            }
+          }
+          tc_fence_before();
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gfree) : "memory");
+        }
+      }
+      // G over the own rows from V: S[a][b] = V[a][b] + V[b][a] for the 820
+      // entries G needs ([0, 210) (i, j), [210, 420) (20+i, 20+j), i <= j;
+      // [420, 820) (i, 20+j)), then G_ij = 2^(e_i + e_j - 14) (S[i][j] +
+      // S[20+i][20+j] + i (S[i][20+j] - S[j][20+i])) into gpart, both triangles
+      DW* Sb = reinterpret_cast<DW*>(W);
+      const int gt = tid;   // 0 .. SG_W * 32 - 1
+      for (int e = gt; e < 820; e += SG_W * 32) {
+        int ia, ib;
+        if (e < 420) {
+          const int e2 = e < 210 ? e : e - 210, off = e < 210 ? 0 : 20;
+          ia = tri[e2].y + off;
+          ib = tri[e2].x + off;
+        } else {
+          ia = (e - 420) / 20;
+          ib = 20 + (e - 420) % 20;
+        }
+        DW acc = V[ia * 40 + ib];
+        dw_add(acc, V[ib * 40 + ia]);
+        Sb[e] = acc;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(SG_W * 32) : "memory");
+      for (int e = gt; e < 210; e += SG_W * 32) {
+        const int i = tri[e].y, j = tri[e].x;   // i <= j
+        int ei = 0, ej = 0;
+        frexpf(__uint_as_float(gcmax[gpar][i]), &ei);
+        frexpf(__uint_as_float(gcmax[gpar][j]), &ej);
+        const double sc = ldexp(1.0, ei + ej - 14);
+        DW re = Sb[e], im = Sb[420 + i * 20 + j];
+        dw_add(re, Sb[210 + e]);
+        const DW n2 = Sb[420 + j * 20 + i];
+        dw_add(im, DW{-n2.hi, -n2.lo});
+        const double gr = ((double)re.hi + (double)re.lo) * sc, gi = ((double)im.hi + (double)im.lo) * sc;
+        gpart[i * Mp + j] = make_double2(gr, gi);
+        gpart[j * Mp + i] = make_double2(gr, -gi);
+      }
+    } else if (warp == SG_W) {
+      // the issuing warp
+      for (int ch = 0; ch < n_ch; ++ch) {
+        const int b = ch & 1;
+        if (ch % chw == 0) {   // a window starts: the previous readout has left TMEM
+          if (gused) {
+            if (!mbar_wait(gfree, gtf & 1u)) set_error(a.err, DEV_TIMEOUT);
+            ++gtf;
+          }
+          gused = true;
+        }
+        if (!mbar_wait(gfill[b], gfph[b] & 1u)) set_error(a.err, DEV_TIMEOUT);
+        ++gfph[b];
+        if (lane == 0) {
+          tc_fence_after();
+          const uint32_t bb = smem_u32(smem + a.o_gs + b * GS_BUF);
+          for (int ks = 0; ks < GS_CH / 16; ++ks) {
+            const uint32_t ko = bb + (uint32_t)(ks * 2 * GS_LBO);
+            const uint32_t acc = (ch % chw != 0 || ks > 0) ? 1u : 0u;
+            const uint64_t d0 = tc_desc(ko, GS_LBO, 128);              // m-rows 0..127
+            const uint64_t d2 = tc_desc(ko + 15 * 128, GS_LBO, 128);   // m-rows 120..247
+            gs_mma(tmem + GS_D0, d0, d0, gs_idesc(240), acc);
+            gs_mma(tmem + GS_D1, d0, tc_desc(ko + 30 * 128, GS_LBO, 128), gs_idesc(80), acc);
+            gs_mma(tmem + GS_D2, d2, d2, gs_idesc(128), acc);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(gbar[b])
+                       : "memory");
+        }
+        __syncwarp();
+      }
+    }
+  };
   // Steps [s_a, s_b) (relative to step0) of trajectory tj, and the signal at
   // s_b unless the piece is a head (its continuation evaluates it). A tail
   // piece first waits for the head's state; a head piece publishes it.
@@ -344,6 +610,19 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
     for (long long e = (long long)r_lo * Mp + tid; e < (long long)r_hi * Mp; e += NT) {
       const int n = (int)(e / Mp), m = (int)(e - (long long)n * Mp);
       zs0[e] = m < M ? __ldcg(Zn + (size_t)n * M + m) : make_float2(0.f, 0.f);
+    }
+    if constexpr (GTC) {   // column maxima of the own rows just loaded
+      if (tid < 20) gcmax[gpar][tid] = 0u;
+      __syncthreads();
+      if (tid < 500) {
+        const int j = tid % 20;
+        float mx = 0.f;
+        for (int n = r_lo + tid / 20; n < r_hi; n += 25) {
+          const float2 v = zs0[(size_t)n * Mp + j];
+          mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        atomicMax(&gcmax[gpar][j], __float_as_uint(mx));
+      }
     }
     team_sync();
     int cur = 0;
@@ -440,7 +719,8 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
         // ================= P: Gram and T_k tiles over all rows
         {
           const int nt_ = Mq / TP;
-          const int n_g = nt_ * (nt_ + 1) / 2, n_t = K * nt_ * nt_;
+          const int n_g = GTC ? 0 : nt_ * (nt_ + 1) / 2, n_t = K * nt_ * nt_;
+          if constexpr (GTC) gram_tc(cur);
           for (;;) {
             int task = 0;
             if (lane == 0) task = atomicAdd(&task_ctr, 1);
@@ -650,6 +930,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           const int mq = Mq / 4, nrt = (NR + TR - 1) / TR;
           for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = r_lo + rt * TR;
+            float cmx[4] = {0.f, 0.f, 0.f, 0.f};   // column maxima of the rows written (tensor-core Gram)
             float2 f[TR][4];
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
@@ -751,9 +1032,17 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 }
               }
               store4(zo_buf + (size_t)n * Mp + m0, zo);
+              if constexpr (GTC)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cmx[u] = fmaxf(cmx[u], fmaxf(fabsf(zo[u].x), fabsf(zo[u].y)));
             }
+            if constexpr (GTC)
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (m0 + u < 20) atomicMax(&gcmax[gpar ^ 1][m0 + u], __float_as_uint(cmx[u]));
           }
           cur ^= 1;
+          gpar ^= 1;
           team_sync();   // B2: the next stage input is visible to the team
         }
       }
@@ -765,9 +1054,18 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
     }
   };
 
+  auto release_tmem = [&]() {
+    if constexpr (GTC) {
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+  };
   if (!a.split) {
     for (int tj = team; tj < a.T; tj += n_teams) piece(tj, 0, a.n_steps, false, false);
     if (C > 1) cluster.sync();   // no CTA leaves while the team may read its shared memory
+    release_tmem();
     return;
   }
   // Equal spans of the T x n_steps trajectory-steps, in trajectory-major
@@ -783,6 +1081,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   if (sb < a.n_steps) piece(tb, 0, sb, true, false);
   for (int tj = sa > 0 ? ta + 1 : ta; tj <= (sb < a.n_steps ? tb - 1 : tb); ++tj) piece(tj, 0, a.n_steps, false, false);
   if (sa > 0) piece(ta, sa, a.n_steps, false, true);
+  release_tmem();
 }
 
 }  // namespace sfz

@@ -126,7 +126,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     lib.lr_sparse_loss.argtypes = [vp, d, d, d, vp, vp, vp, vp]
     lib.lr_grow_rank.argtypes = [vp, vp, C.c_uint64, d, vp]
     lib.lr_measure_peak.argtypes = [i, C.POINTER(d), C.POINTER(d), vp]
-    lib.lr_sparse_query.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.lr_sparse_query.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.lr_full_create.argtypes = [vp, C.POINTER(lr_pulse), d, l, i, C.POINTER(vp)]
     lib.lr_full_workspace_size.argtypes = [vp, C.POINTER(C.c_size_t)]
     lib.lr_full_bind_workspace.argtypes = [vp, vp, C.c_size_t, vp]

@@ -107,14 +107,21 @@ class SparseBatch:
     def fused(self) -> bool:
         """True when the context runs the fused persistent kernel."""
         f = C.c_int()
-        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), None))
+        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), None, None))
         return bool(f.value)
+
+    @property
+    def gram_tc(self) -> bool:
+        """True when the fused kernel forms the Gram matrix on the tensor cores."""
+        f, g = C.c_int(), C.c_int()
+        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), None, C.byref(g)))
+        return bool(g.value)
 
     @property
     def team(self) -> int:
         """CTAs per trajectory of the fused kernel (0: the four-launch path)."""
         f, t = C.c_int(), C.c_int()
-        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), C.byref(t)))
+        self._check(self._lib.lr_sparse_query(self._h, C.byref(f), C.byref(t), None))
         return t.value
 
     def _check(self, st: int):

@@ -373,3 +373,38 @@ def test_fused_team_default_for_small_batches():
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     b = sparse.SparseBatch(model, 20, [p] * n_sm, 40.0, 10, precision="fp32_g64")
     assert b.team == 1
+
+
+@pytest.mark.parametrize("dims,n_steps", [((10, 3, 5), 400), ((100, 4, 5), 120)])
+def test_fused_gram_on_tensor_cores(monkeypatch, dims, n_steps):
+    """LR_SPARSE_GRAM=tc at M = 20 runs the Gram matrix on the tensor cores
+    (exact bf16 slices, accumulation windows of at most 1024 rows: two per
+    stage at N = 2000, one at N = 150). Against the oracle at the FP32_G64
+    bounds, and against the default double-word CUDA-core Gram within FP32
+    rounding."""
+    from paper_2508_18114_gb300 import sparse
+    P = _params(kappa=2.0, gamma=0.1) if dims[0] == 10 else _params()
+    wd = P["wd"]
+    amp = TP * (0.8 if dims[0] == 10 else 0.15)
+    pulses = [(0, [amp, wd, 0.05, 0.0])] * 2 + [(0, [0.6 * amp, wd, 0.05, 0.0])] * 2
+    got = {}
+    for mode in ("tc", "dw"):
+        if mode == "tc":
+            monkeypatch.setenv("LR_SPARSE_GRAM", "tc")
+        else:
+            monkeypatch.delenv("LR_SPARSE_GRAM", raising=False)
+        model = sparse.paper_model(*dims, **P)
+        b = sparse.SparseBatch(model, 20, pulses, 0.4, n_steps, pop_every=40, precision="fp32_g64")
+        assert b.fused and b.gram_tc == (mode == "tc")
+        b.set_initial([j % 2 for j in range(4)], SEED, EPS)
+        b.integrate(5e-4, n_steps // 3)
+        b.integrate(5e-4, n_steps - n_steps // 3)
+        got[mode] = b.observables()
+        del b
+    t, d = got["tc"], got["dw"]
+    scale = np.abs(d["beta"][:, :n_steps + 1]).max()
+    assert np.abs(t["beta"][:, :n_steps + 1] - d["beta"][:, :n_steps + 1]).max() <= 2e-6 * max(scale, 1e-3)
+    assert np.abs(t["pops"] - d["pops"]).max() <= 2e-6
+    if dims[0] == 10:   # the oracle at the small size, tensor-core Gram
+        monkeypatch.setenv("LR_SPARSE_GRAM", "tc")
+        _run(dims, 20, pulses, 0.4, 5e-4, n_steps, 40, [0, 3], P, precision="fp32_g64")
