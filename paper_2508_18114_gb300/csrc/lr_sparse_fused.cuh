@@ -78,6 +78,10 @@ struct Args {
   // byte offsets in dynamic shared memory
   int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum;
   int o_gs, o_gv;   // Gram on the tensor cores: two slice buffers, V [40][40] double-word
+  // phase F stages, per round of NT tiles, the band of Z_s rows its gathers read
+  // (its rows +- halo, the operators' largest |col - row|) in shared memory;
+  // band_rows = 0: the gathers read the L2-resident Z_s directly
+  int o_band, band_rows, halo;
 };
 
 constexpr int SG_W = 10;   // slicing warps of the tensor-core Gram (warp SG_W issues the MMAs)
@@ -928,7 +932,23 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           const bool zn_vec = (M % 2) == 0;
           float2* zo_buf = zs0 + (size_t)(cur ^ 1) * zsb;
           const int mq = Mq / 4, nrt = (NR + TR - 1) / TR;
-          for (int tile = tid; tile < nrt * mq; tile += NT) {
+          float2* band = reinterpret_cast<float2*>(smem + a.o_band);
+          for (int base = 0; base < nrt * mq; base += NT) {
+          // rows of this round's tiles, and the band of Z_s rows their gathers read
+          const float2* zg = zc;
+          if (a.band_rows > 0) {
+            const int rt0 = base / mq, rt1 = min(nrt, (base + NT - 1) / mq + 1);
+            const int blo = max(0, r_lo + rt0 * TR - a.halo), bhi = min(N, min(r_hi, r_lo + rt1 * TR) + a.halo);
+            if (bhi - blo <= a.band_rows) {   // the host sized the band for every round
+              const float4* src = reinterpret_cast<const float4*>(zc + (size_t)blo * Mp);
+              float4* dst = reinterpret_cast<float4*>(band);
+              for (int i = tid; i < (bhi - blo) * Mp / 2; i += NT) dst[i] = src[i];
+              zg = band - (size_t)blo * Mp;   // row n of Z_s at zg + n Mp, for blo <= n < bhi
+            }
+            __syncthreads();
+          }
+          const int tile = base + tid;
+          if (tile < nrt * mq) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = r_lo + rt * TR;
             float cmx[4] = {0.f, 0.f, 0.f, 0.f};   // column maxima of the rows written (tensor-core Gram)
             float2 f[TR][4];
@@ -941,13 +961,13 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 // detunings), then the other entries of the row
                 const float4 dg = a.diag_a[l0 + r];
                 float2 z[4];
-                load4(zc + (size_t)(l0 + r) * Mp + m0, z);
+                load4(zg + (size_t)(l0 + r) * Mp + m0, z);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                   f[r][u].x = fmaf(dg.x, z[u].x, fmaf(-dg.y, z[u].y, fmaf(dg.z, z[u].x, -dg.w * z[u].y)));
                   f[r][u].y = fmaf(dg.x, z[u].y, fmaf(dg.y, z[u].x, fmaf(dg.z, z[u].y, dg.w * z[u].x)));
                 }
-                row_gather4(a, 0, l0 + r, m0, zc, chi, f[r]);
+                row_gather4(a, 0, l0 + r, m0, zg, chi, f[r]);
               }
             }
             // + sum_k Y_k XT_k: l in pairs, 16-byte loads of the Y rows
@@ -1040,6 +1060,8 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
 #pragma unroll
               for (int u = 0; u < 4; ++u)
                 if (m0 + u < 20) atomicMax(&gcmax[gpar ^ 1][m0 + u], __float_as_uint(cmx[u]));
+          }
+          if (a.band_rows > 0) __syncthreads();   // the next round refills the band
           }
           cur ^= 1;
           gpar ^= 1;
