@@ -226,16 +226,14 @@ __device__ __forceinline__ void reduce_scatter32(V (&v)[32], int lane, Add add) 
   }
 }
 
-// acc[u] += sum over the CSR row n of operator `op` of chi[ch] val * Z[col][m0 + u].
-// Entries go in groups of four: their indices and weights first, then the four
-// row loads, then the products, so that four gathers are in flight at once
-// (the order of the additions is the entry order either way).
-__device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0, const float2* __restrict__ zs,
-                                            const float2* chi, float2 (&acc)[4]) {
-  const int* rp = a.rowptr + (size_t)op * (a.N + 1);
-  const float2* __restrict__ vals = op == 0 ? a.valf_a : a.valf;
-  int e = rp[n];
-  const int e1 = rp[n + 1];
+// acc[u] += sum over the entries [e, e1) of one CSR row of chi[ch] val * Z[col][m0 + u]
+// (vals: the operator's values). Entries go in groups of four: their indices and
+// weights first, then the four row loads, then the products, so that four
+// gathers are in flight at once (the order of the additions is the entry order
+// either way). The caller loads the row extents, several rows' at once.
+__device__ __forceinline__ void row_gather4(const Args& a, const float2* __restrict__ vals, int e, const int e1,
+                                            int m0, const float2* __restrict__ zs, const float2* chi,
+                                            float2 (&acc)[4]) {
   for (; e + 4 <= e1; e += 4) {
     int c[4];
     float2 w[4], z[4][4];
@@ -268,25 +266,85 @@ __device__ __forceinline__ void row_gather4(const Args& a, int op, int n, int m0
   }
 }
 
-// Fixed-order block sum of NV doubles per thread; the totals are returned to
-// every thread. red: NWARP * NV doubles of shared memory.
+// y[k][u] = sum over the row n of operator 1 + k0 + k (k < nk <= KM; operators
+// 1 .. K are the jumps, K + 1 the readout) of chi[ch] val * Z[col][m0 + u].
+// The operators' rows go in lockstep (entry j
+// of every operator, then entry j + 1), so that their extents, indices,
+// weights and row loads are in flight together; within an operator the
+// additions keep the entry order.
+template <int KM>
+__device__ __forceinline__ void gather_ops(const Args& a, int k0, int nk, int n, int m0,
+                                           const float2* __restrict__ zs, const float2* chi, float2 (&y)[KM][4]) {
+  int e[KM], e1[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    e[k] = e1[k] = 0;
+    if (k < nk) {
+      const int* rp = a.rowptr + (size_t)(1 + k0 + k) * (a.N + 1);
+      e[k] = rp[n];
+      e1[k] = rp[n + 1];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[k][u] = make_float2(0.f, 0.f);
+  }
+  int len = 0;
+#pragma unroll
+  for (int k = 0; k < KM; ++k) len = max(len, e1[k] - e[k]);
+  for (int j = 0; j < len; ++j) {
+    int c[KM];
+    float2 w[KM], z[KM][4];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      c[k] = -1;
+      if (e[k] + j < e1[k]) {
+        const int ei = e[k] + j;
+        c[k] = a.col[ei];
+        const float2 ch = chi[a.chan[ei]], v = a.valf[ei];
+        w[k] = make_float2(ch.x * v.x - ch.y * v.y, ch.x * v.y + ch.y * v.x);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+      if (c[k] >= 0) load4(zs + (size_t)c[k] * a.Mp + m0, z[k]);
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+      if (c[k] >= 0)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          y[k][u].x = fmaf(w[k].x, z[k][u].x, fmaf(-w[k].y, z[k][u].y, y[k][u].x));
+          y[k][u].y = fmaf(w[k].x, z[k][u].y, fmaf(w[k].y, z[k][u].x, y[k][u].y));
+        }
+  }
+}
+
+// Fixed-order block sum of NV double-word values (warp shuffles, then the warp
+// partials in warp order); thread 0 returns the totals as doubles. red: NWARP
+// * NV float2 of shared memory.
 template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int tid) {
+__device__ __forceinline__ void block_sum_dw(DW (&v)[NV], float2* red, int tid, double (&out)[NV]) {
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int c = 0; c < NV; ++c)
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      DW t;
+      t.hi = __shfl_down_sync(0xffffffffu, v[c].hi, o);
+      t.lo = __shfl_down_sync(0xffffffffu, v[c].lo, o);
+      dw_add(v[c], t);
+    }
   if (lane == 0)
 #pragma unroll
-    for (int c = 0; c < NV; ++c) red[warp * NV + c] = v[c];
+    for (int c = 0; c < NV; ++c) red[warp * NV + c] = make_float2(v[c].hi, v[c].lo);
   __syncthreads();
+  if (tid == 0)
 #pragma unroll
-  for (int c = 0; c < NV; ++c) {
-    double s = 0.0;
-    for (int w = 0; w < NWARP; ++w) s += red[w * NV + c];
-    v[c] = s;
-  }
-  __syncthreads();
+    for (int c = 0; c < NV; ++c) {
+      DW s{0.f, 0.f};
+      for (int w = 0; w < NWARP; ++w) {
+        const float2 p = red[w * NV + c];
+        dw_add(s, DW{p.x, p.y});
+      }
+      out[c] = (double)s.hi + (double)s.lo;
+    }
 }
 
 // TEAM = false: teams of one CTA (C = 1 known at compile time; the equal-span
@@ -675,30 +733,33 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
         {
           const int nk = stage == 0 ? K + 1 : K;
           const int mq = Mq / 4;
-          double acc3[3] = {0.0, 0.0, 0.0};   // Re, Im tr(Z^dag r Z), |r Z|^2
-          for (long long t = tid; t < (long long)NR * mq * nk; t += NT) {
-            const int k = (int)(t / ((long long)NR * mq));
-            const int rem = (int)(t - (long long)k * NR * mq), nl = rem / mq, m0 = (rem - nl * mq) * 4, n = r_lo + nl;
-            float2 y[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                           make_float2(0.f, 0.f)};
-            row_gather4(a, 1 + k, n, m0, zc, chi, y);
-            if (k < K) store4(ybuf + (size_t)k * zsb + (size_t)n * Mp + m0, y);
+          // Re, Im tr(Z^dag r Z), |r Z|^2: exact FP32 products in double-word sums
+          DW s3[3] = {DW{0.f, 0.f}, DW{0.f, 0.f}, DW{0.f, 0.f}};
+          for (int t = tid; t < NR * mq * nk; t += NT) {
+            const int k = t / (NR * mq);
+            const int rem = t - k * NR * mq, nl = rem / mq, m0 = (rem - nl * mq) * 4, n = r_lo + nl;
+            float2 y[1][4];
+            gather_ops<1>(a, k, 1, n, m0, zc, chi, y);
+            if (k < K) store4(ybuf + (size_t)k * zsb + (size_t)n * Mp + m0, y[0]);
             if (k == K) {
               float2 z[4];
               load4(zc + (size_t)n * Mp + m0, z);
 #pragma unroll
               for (int u = 0; u < 4; ++u) {   // padding columns are zero
-                const double zx = z[u].x, zy = z[u].y, yx = y[u].x, yy = y[u].y;
-                acc3[0] += zx * yx + zy * yy;
-                acc3[1] += zx * yy - zy * yx;
-                acc3[2] += yx * yx + yy * yy;
+                dw_add_prod(s3[0], z[u].x, y[0][u].x);
+                dw_add_prod(s3[0], z[u].y, y[0][u].y);
+                dw_add_prod(s3[1], z[u].x, y[0][u].y);
+                dw_add_prod(s3[1], -z[u].y, y[0][u].x);
+                dw_add_prod(s3[2], y[0][u].x, y[0][u].x);
+                dw_add_prod(s3[2], y[0][u].y, y[0][u].y);
               }
             }
           }
           if (stage == 0) {
-            block_sum<3>(acc3, red, tid);
+            double tot[3];
+            block_sum_dw<3>(s3, reinterpret_cast<float2*>(red), tid, tot);
             if (tid == 0)
-              for (int c = 0; c < 3; ++c) misc[8 + c] = acc3[c];
+              for (int c = 0; c < 3; ++c) misc[8 + c] = tot[c];
           }
           if (record) {
             // level populations: warp per level, fixed order over the rows
@@ -952,6 +1013,9 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = r_lo + rt * TR;
             float cmx[4] = {0.f, 0.f, 0.f, 0.f};   // column maxima of the rows written (tensor-core Gram)
             float2 f[TR][4];
+            int ext[TR + 1];   // CSR extents of the tile's rows of A, loaded together
+#pragma unroll
+            for (int r = 0; r <= TR; ++r) ext[r] = a.rowptr[min(l0 + r, r_hi)];
 #pragma unroll
             for (int r = 0; r < TR; ++r) {
 #pragma unroll
@@ -967,7 +1031,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                   f[r][u].x = fmaf(dg.x, z[u].x, fmaf(-dg.y, z[u].y, fmaf(dg.z, z[u].x, -dg.w * z[u].y)));
                   f[r][u].y = fmaf(dg.x, z[u].y, fmaf(dg.y, z[u].x, fmaf(dg.z, z[u].y, dg.w * z[u].x)));
                 }
-                row_gather4(a, 0, l0 + r, m0, zg, chi, f[r]);
+                row_gather4(a, a.valf_a, ext[r], ext[r + 1], m0, zg, chi, f[r]);
               }
             }
             // + sum_k Y_k XT_k: l in pairs, 16-byte loads of the Y rows
