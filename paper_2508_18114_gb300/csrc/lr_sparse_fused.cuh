@@ -20,8 +20,8 @@
 // the team's partials in rank order from distributed shared memory and runs
 // the M x M phase itself), B2 after the RK4 update (the new Z_s is visible).
 // The phases:
-//   C  channel factors Omega(t)^a e^{i q w_d t} of the stage time (FP64,
-//      rounded once to FP32);
+//   C  channel factors Omega(t)^a e^{i q w_d t} of the stage time in FP32
+//      (the stage time and the phase reduced to one cycle in FP64);
 //   Y  Y_k = L_k(t) Z_s by CSR gathers; at the first stage of every step also
 //      r(t) Z_s, the readout signal beta = tr(Z_s^dag r Z_s) and, at recording
 //      steps, the photon number |r Z_s|^2 (FP64 sums in a fixed order);
@@ -49,9 +49,28 @@ constexpr int NWARP = NT / 32;
 constexpr int NCH = 10;   // time channels
 constexpr int TP = 4;     // phase-P tile edge
 constexpr int TR = 4;     // phase-F rows per thread tile
+constexpr int PB = 4;     // phase-P row blocks (at most)
 // bound of the wait for a head piece (~10 s at 2 GHz); the wait normally ends
 // at once, since the previous CTA runs that head first
 constexpr long long SPLIT_WAIT_BUDGET = 20000000000LL;
+
+constexpr double INV_2PI = 0.15915494309189533577;
+// logistic((t - t0) / s) with t - t0 formed in FP64 and the rest in FP32
+__device__ __forceinline__ float logistic_f(double t, double t0, float s) {
+  return 1.0f / (1.0f + __expf(-(float)(t - t0) / s));
+}
+// The envelope Omega(t) of Sec. S2.C in FP32 (the channel factors it enters are
+// rounded to FP32)
+__device__ __forceinline__ float envelope_f(const PulseDev& P, double tau, double t) {
+  if (P.kind == 0) {
+    const double s = 0.2 * P.p[2], t0 = 6.0 * s;
+    return (float)P.p[0] * logistic_f(t, t0, (float)s) * (1.0f - logistic_f(t, tau - t0, (float)s));
+  }
+  const double sr = 0.2 * P.p[3], sf = 0.2 * P.p[4], sm = 0.2 * P.p[5];
+  return (float)P.p[0] * logistic_f(t, 6.0 * sr, (float)sr) +
+         (float)(P.p[1] - P.p[0]) * logistic_f(t, P.p[2], (float)sm) -
+         (float)P.p[1] * logistic_f(t, tau - 6.0 * sf, (float)sf);
+}
 
 struct Args {
   const int* rowptr;   // [(K + 2) (N + 1)]
@@ -360,7 +379,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   __shared__ short2 tri[LR_MAX_RANK * (LR_MAX_RANK + 1) / 2];
   __shared__ float2 chi[NCH];
   __shared__ double red[NWARP * 4];
-  __shared__ int task_ctr;
+  __shared__ int task_ctr[2];   // phase-P task counters of alternate row blocks
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = a.N, M = a.M, Mp = a.Mp, K = a.K, MM = Mp * Mp;
   const int Mq = (M + 3) / 4 * 4;
@@ -722,12 +741,17 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
         if (tid < NCH) {
           const double ts = (double)step * dt + (stage == 0 ? 0.0 : (stage == 3 ? dt : 0.5 * dt));
           const int ach = tid / 5, q = tid % 5 - 2;
-          const double om = ach ? pulse_envelope(pulse, a.tau, ts) : 1.0;
-          double sn, cs;
-          sincos((double)q * a.wd * ts, &sn, &cs);
-          chi[tid] = make_float2((float)(om * cs), (float)(om * sn));
+          const float om = ach ? envelope_f(pulse, a.tau, ts) : 1.0f;
+          // e^{i q w_d t}: the phase in cycles, reduced to [-1/2, 1/2] in FP64, then
+          // sine and cosine of the reduced phase in FP32 (FP64 transcendentals hold
+          // the FP64 pipe for tens of cycles per warp instruction on this GPU)
+          const double cyc = (double)q * a.wd * ts * INV_2PI;
+          const float x = (float)(cyc - rint(cyc));
+          float sn, cs;
+          sincospif(2.0f * x, &sn, &cs);
+          chi[tid] = make_float2(om * cs, om * sn);
         }
-        if (tid == 0) task_ctr = 0;
+        if (tid == 0) task_ctr[0] = task_ctr[1] = 0;
         __syncthreads();
         // ================= Y: operator images, readout signal
         {
@@ -786,9 +810,18 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           const int nt_ = Mq / TP;
           const int n_g = GTC ? 0 : nt_ * (nt_ + 1) / 2, n_t = K * nt_ * nt_;
           if constexpr (GTC) gram_tc(cur);
+          // The rows go in PB blocks, each swept by all tasks before the next, so
+          // that a block's columns of Z_s and Y_k stay in L2 while the tasks re-read
+          // them (the whole of a trajectory's Z_s and Y_k, 0.96 MB at N = 2000, M =
+          // 20, times the CTAs in flight exceeds L2); the blocks' sums are added in
+          // block order, a barrier apart. (The tensor-core Gram's slicing warps keep
+          // to their own schedule: one block.)
+          const int nb = GTC ? 1 : max(1, min(PB, NR / 256));   // blocks of at least 256 rows
+          for (int blk = 0; blk < nb; ++blk) {
+          const int b_lo = r_lo + (int)((long long)NR * blk / nb), b_hi = r_lo + (int)((long long)NR * (blk + 1) / nb);
           for (;;) {
             int task = 0;
-            if (lane == 0) task = atomicAdd(&task_ctr, 1);
+            if (lane == 0) task = atomicAdd(&task_ctr[blk & 1], 1);
             task = __shfl_sync(0xffffffffu, task, 0);
             if (task >= n_g + n_t) break;
             if (task < n_g) {
@@ -803,7 +836,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               for (int i = 0; i < TP; ++i)
 #pragma unroll
                 for (int j = 0; j < TP; ++j) acc[i][j][0] = acc[i][j][1] = DW{0.f, 0.f};
-              for (int n = r_lo + lane; n < r_hi; n += 32) {
+              for (int n = b_lo + lane; n < b_hi; n += 32) {
                 float2 zi[4], zj[4];
                 load4(zc + (size_t)n * Mp + i0, zi);
                 load4(zc + (size_t)n * Mp + j0, zj);
@@ -833,9 +866,16 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               });
               const int i = i0 + (lane >> 3), j = j0 + ((lane >> 1) & 3), c = lane & 1;
               const double val = (double)v[0].hi + (double)v[0].lo;
-              if (i <= j) {   // G[i][j] and its conjugate G[j][i] over this CTA's rows
-                reinterpret_cast<double*>(gpart)[2 * (i * Mp + j) + c] = val;
-                reinterpret_cast<double*>(gpart)[2 * (j * Mp + i) + c] = c ? -val : val;
+              // G[i][j] and its conjugate G[j][i] over this CTA's rows (the diagonal's
+              // imaginary part is zero), summed over the row blocks in order
+              double* gp = reinterpret_cast<double*>(gpart);
+              if (i < j) {
+                const double lower = c ? -val : val;
+                gp[2 * (i * Mp + j) + c] = blk ? gp[2 * (i * Mp + j) + c] + val : val;
+                gp[2 * (j * Mp + i) + c] = blk ? gp[2 * (j * Mp + i) + c] + lower : lower;
+              } else if (i == j) {
+                const double d = c ? 0.0 : val;
+                gp[2 * (i * Mp + i) + c] = blk ? gp[2 * (i * Mp + i) + c] + d : d;
               }
             } else {
               const int t2 = task - n_g, k = t2 / (nt_ * nt_), r2 = t2 - k * nt_ * nt_, ti = r2 / nt_,
@@ -847,7 +887,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               for (int i = 0; i < TP; ++i)
 #pragma unroll
                 for (int j = 0; j < TP; ++j) tr_[i][j] = ti_[i][j] = 0.f;
-              for (int n = r_lo + lane; n < r_hi; n += 32) {
+              for (int n = b_lo + lane; n < b_hi; n += 32) {
                 float2 z[4], y[4];
                 load4(zc + (size_t)n * Mp + i0, z);
                 load4(yk + (size_t)n * Mp + j0, y);
@@ -871,8 +911,14 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 keep += __shfl_xor_sync(0xffffffffu, send, o);
               });
               const int i = i0 + (lane >> 3), j = j0 + ((lane >> 1) & 3), c = lane & 1;
-              reinterpret_cast<float*>(Tred)[2 * (k * MM + i * Mp + j) + c] = v[0];
+              float* tp = reinterpret_cast<float*>(Tred) + 2 * (k * MM + i * Mp + j) + c;
+              *tp = blk ? *tp + v[0] : v[0];
             }
+          }
+          if (blk + 1 < nb) {
+            __syncthreads();   // block blk's sums are in place; its counter is free
+            if (tid == 0) task_ctr[blk & 1] = 0;   // next used by block blk + 2, a barrier later
+          }
           }
         }
         // ================= B1: the team's partials are visible
