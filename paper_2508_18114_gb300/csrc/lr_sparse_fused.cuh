@@ -437,7 +437,11 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
   auto at_rank = [&](auto* p, int r) { return r == q ? p : cluster.map_shared_rank(p, r); };
   const size_t zsb = (size_t)N * Mp;
   float2* zs0 = a.scratch + (size_t)team * (size_t)(3 + K) * zsb;
-  float2* ybuf = zs0 + 2 * zsb;              // Y_1 .. Y_K (r Z_s is only summed, never stored)
+  // Y_1 .. Y_K (r Z_s is only summed, never stored), each in column quads: entry
+  // (n, m) at yq(n, m), so that a warp's loads of one quad over 32 consecutive
+  // rows (phase P) cover 1 KB of contiguous memory instead of 32 cache lines
+  float2* ybuf = zs0 + 2 * zsb;
+  auto yq = [N](int n, int m) { return (size_t)(m >> 2) * N * 4 + (size_t)n * 4 + (m & 3); };
   float2* accg = zs0 + (2 + K) * zsb;
   const double dt = a.dt;
   const int pe = a.pop_every;
@@ -764,7 +768,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
             const int rem = t - k * NR * mq, nl = rem / mq, m0 = (rem - nl * mq) * 4, n = r_lo + nl;
             float2 y[1][4];
             gather_ops<1>(a, k, 1, n, m0, zc, chi, y);
-            if (k < K) store4(ybuf + (size_t)k * zsb + (size_t)n * Mp + m0, y[0]);
+            if (k < K) store4(ybuf + (size_t)k * zsb + yq(n, m0), y[0]);
             if (k == K) {
               float2 z[4];
               load4(zc + (size_t)n * Mp + m0, z);
@@ -890,7 +894,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
               for (int n = b_lo + lane; n < b_hi; n += 32) {
                 float2 z[4], y[4];
                 load4(zc + (size_t)n * Mp + i0, z);
-                load4(yk + (size_t)n * Mp + j0, y);
+                load4(yk + yq(n, j0), y);
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
@@ -1080,7 +1084,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 row_gather4(a, a.valf_a, ext[r], ext[r + 1], m0, zg, chi, f[r]);
               }
             }
-            // + sum_k Y_k XT_k: l in pairs, 16-byte loads of the Y rows
+            // + sum_k Y_k XT_k: l in pairs, 16-byte loads of the Y entries
             for (int k = 0; k < K; ++k) {
               const float2* yk = ybuf + (size_t)k * zsb;
               const float2* xk = XT + k * MM;
@@ -1088,7 +1092,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 float4 y2[TR];
 #pragma unroll
                 for (int r = 0; r < TR; ++r)
-                  y2[r] = l0 + r < r_hi ? *reinterpret_cast<const float4*>(yk + (size_t)(l0 + r) * Mp + l)
+                  y2[r] = l0 + r < r_hi ? *reinterpret_cast<const float4*>(yk + yq(l0 + r, l))
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int ll = 0; ll < 2; ++ll) {
