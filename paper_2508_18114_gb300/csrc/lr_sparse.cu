@@ -543,7 +543,6 @@ struct lr_sparse {
   int fp32;   // 1: FP32_G64 state arithmetic
   int fused;  // 1: the fused persistent kernel (FP32_G64), 0: four launches per RK4 stage
   int gram_tc;   // fused: 1 when the Gram matrix is formed on the tensor cores (rank padded to 20)
-  int halo;      // largest |col - row| of A (the band of Z_s rows phase F stages)
   int n_cta;   // fused: persistent CTAs (n_team teams of team_c)
   int n_team, team_c;   // fused: teams (one trajectory at a time each), CTAs per team
   size_t o_fsc;   // fused: per-CTA stage buffers
@@ -625,15 +624,10 @@ void layout(lr_sparse* s) {
 // [Mp][Mp+1]), T_k and XT_k (FP32 complex [K][Mp][Mp]), scalars, and the
 // partials of G (FP64 complex [Mp][Mp]) and the team's T_k ([K][Mp][Mp]).
 struct SfSmem {
-  int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum, o_gs, o_gv, o_band, band_rows, total;
+  int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum, o_gs, o_gv, total;
 };
-// gtc: the slice buffers and V of the Gram matrix on the tensor cores; halo:
-// the largest |col - row| of A, which sizes phase F's band of Z_s rows (one
-// round of NT tiles of TR rows x 4 columns, +- halo; only with LR_SPARSE_BAND=1
-// and at most 100 KB: on the 512-trajectory batch of the paper's model the
-// staging cost more than the gathers it served, 68.4k against 70.7k
-// traj*steps/s, results bitwise equal)
-SfSmem sf_smem(int M, int K, int gtc, int halo) {
+// gtc: the slice buffers and V of the Gram matrix on the tensor cores
+SfSmem sf_smem(int M, int K, int gtc) {
   const int Mp = (M + 3) / 4 * 4;
   SfSmem L;
   int o = 0;
@@ -658,19 +652,6 @@ SfSmem sf_smem(int M, int K, int gtc, int halo) {
     o += 2 * GS_BUF;
     L.o_gv = o;
     o += 40 * 40 * 8;
-  }
-  L.o_band = o;
-  L.band_rows = 0;
-  {
-    const int mq = Mp / 4;
-    const int rows = ((sfz::NT + mq - 1) / mq + 1) * sfz::TR + 2 * halo;
-    const char* env = getenv("LR_SPARSE_BAND");
-    if (halo >= 0 && rows * Mp * (int)sizeof(float2) <= 100 * 1024 && env && strcmp(env, "1") == 0) {
-      o = (o + 15) / 16 * 16;
-      L.o_band = o;
-      L.band_rows = rows;
-      o += rows * Mp * (int)sizeof(float2);
-    }
   }
   L.total = o;
   return L;
@@ -702,7 +683,7 @@ void fused_teams(lr_sparse* s, int sms) {
   if (s->T < sms) C = std::max(1, std::min({16, sms / s->T, s->N / 64}));
   if (const char* e = getenv("LR_SPARSE_C")) C = std::max(1, std::min(16, atoi(e)));
   C = std::min(C, s->N);
-  const SfSmem L = sf_smem(s->M, s->K, s->gram_tc, s->halo);
+  const SfSmem L = sf_smem(s->M, s->K, s->gram_tc);
   for (; C > 1; --C) {   // the largest team that fits as a cluster
     if (raise_fused_smem(L.total) != cudaSuccess) break;
     cudaLaunchConfig_t cfg{};
@@ -919,10 +900,6 @@ extern "C" lr_status lr_sparse_create(const lr_sparse_model* m, int n_traj, int 
   s->val.assign(m->val, m->val + 2 * m->nnz);
   s->chan.assign(m->chan, m->chan + m->nnz);
   s->level.assign(m->level, m->level + N);
-  // bandwidth of A (operator 0): the rows phase F of the fused kernel gathers
-  s->halo = 0;
-  for (int n = 0; n < N; ++n)
-    for (int e = s->rowptr[n]; e < s->rowptr[n + 1]; ++e) s->halo = std::max(s->halo, std::abs(s->col[e] - n));
   s->pulses.resize(n_traj);
   for (int i = 0; i < n_traj; ++i) {
     s->pulses[i].kind = pulses[i].kind;
@@ -1103,7 +1080,7 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
   const SpDev d = dev(s);
   const SpParams p = params(s);
   if (s->fused) {
-    const SfSmem L = sf_smem(s->M, s->K, s->gram_tc, s->halo);
+    const SfSmem L = sf_smem(s->M, s->K, s->gram_tc);
     cudaError_t e0 = raise_fused_smem(L.total);
     if (e0 != cudaSuccess) return cuda_fail(s, e0);
     sfz::Args a{};
@@ -1151,9 +1128,6 @@ extern "C" lr_status lr_sparse_integrate(lr_sparse* s, double dt, long n_steps, 
     a.o_tsum = L.o_tsum;
     a.o_gs = L.o_gs;
     a.o_gv = L.o_gv;
-    a.o_band = L.o_band;
-    a.band_rows = L.band_rows;
-    a.halo = s->halo;
     if (a.split) {
       // the hand-over waits need every CTA resident: a cooperative launch
       // (refused, rather than run, when the grid does not fit)

@@ -97,10 +97,6 @@ struct Args {
   // byte offsets in dynamic shared memory
   int o_gd, o_w, o_tred, o_xt, o_misc, o_gpart, o_tsum;
   int o_gs, o_gv;   // Gram on the tensor cores: two slice buffers, V [40][40] double-word
-  // phase F stages, per round of NT tiles, the band of Z_s rows its gathers read
-  // (its rows +- halo, the operators' largest |col - row|) in shared memory;
-  // band_rows = 0: the gathers read the L2-resident Z_s directly
-  int o_band, band_rows, halo;
 };
 
 constexpr int SG_W = 10;   // slicing warps of the tensor-core Gram (warp SG_W issues the MMAs)
@@ -227,6 +223,23 @@ __device__ __forceinline__ void store4(float2* p, const float2 (&v)[4]) {
   reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
 }
 
+// The same as one 32-byte access per thread (global memory only; p 32-byte
+// aligned: rows of Mp = 4j complex64 entries, or column quads of Y_k, in a
+// 256-byte aligned region, at column quads m0 = 4i). Half the load and store
+// instructions, and half the cache-line lookups, of the 16-byte pairs.
+__device__ __forceinline__ void load4w(const float2* p, float2 (&v)[4]) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x), "=f"(v[2].y), "=f"(v[3].x),
+                 "=f"(v[3].y)
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void store4w(float2* p, const float2 (&v)[4]) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0].x), "f"(v[0].y),
+               "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y)
+               : "memory");
+}
+
 // Reduce-scatter of 32 values over the warp (recursive halving, fixed order):
 // lane L ends with the total of value L in v[0].
 template <typename V, typename Add>
@@ -249,7 +262,8 @@ __device__ __forceinline__ void reduce_scatter32(V (&v)[32], int lane, Add add) 
 // (vals: the operator's values). Entries go in groups of four: their indices and
 // weights first, then the four row loads, then the products, so that four
 // gathers are in flight at once (the order of the additions is the entry order
-// either way). The caller loads the row extents, several rows' at once.
+// either way). The caller loads the row extents, several rows' at once. zs:
+// Z_s in global memory (32-byte row quads).
 __device__ __forceinline__ void row_gather4(const Args& a, const float2* __restrict__ vals, int e, const int e1,
                                             int m0, const float2* __restrict__ zs, const float2* chi,
                                             float2 (&acc)[4]) {
@@ -263,7 +277,7 @@ __device__ __forceinline__ void row_gather4(const Args& a, const float2* __restr
       w[q] = make_float2(ch.x * v.x - ch.y * v.y, ch.x * v.y + ch.y * v.x);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) load4(zs + (size_t)c[q] * a.Mp + m0, z[q]);
+    for (int q = 0; q < 4; ++q) load4w(zs + (size_t)c[q] * a.Mp + m0, z[q]);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -276,7 +290,7 @@ __device__ __forceinline__ void row_gather4(const Args& a, const float2* __restr
     const float2 ch = chi[a.chan[e]], v = vals[e];
     const float wr = ch.x * v.x - ch.y * v.y, wi = ch.x * v.y + ch.y * v.x;
     float2 z[4];
-    load4(zs + (size_t)a.col[e] * a.Mp + m0, z);
+    load4w(zs + (size_t)a.col[e] * a.Mp + m0, z);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       acc[u].x = fmaf(wr, z[u].x, fmaf(-wi, z[u].y, acc[u].x));
@@ -842,8 +856,8 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 for (int j = 0; j < TP; ++j) acc[i][j][0] = acc[i][j][1] = DW{0.f, 0.f};
               for (int n = b_lo + lane; n < b_hi; n += 32) {
                 float2 zi[4], zj[4];
-                load4(zc + (size_t)n * Mp + i0, zi);
-                load4(zc + (size_t)n * Mp + j0, zj);
+                load4w(zc + (size_t)n * Mp + i0, zi);
+                load4w(zc + (size_t)n * Mp + j0, zj);
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
@@ -893,8 +907,8 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 for (int j = 0; j < TP; ++j) tr_[i][j] = ti_[i][j] = 0.f;
               for (int n = b_lo + lane; n < b_hi; n += 32) {
                 float2 z[4], y[4];
-                load4(zc + (size_t)n * Mp + i0, z);
-                load4(yk + yq(n, j0), y);
+                load4w(zc + (size_t)n * Mp + i0, z);
+                load4w(yk + yq(n, j0), y);
 #pragma unroll
                 for (int i = 0; i < TP; ++i)
 #pragma unroll
@@ -1043,23 +1057,8 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
           const bool zn_vec = (M % 2) == 0;
           float2* zo_buf = zs0 + (size_t)(cur ^ 1) * zsb;
           const int mq = Mq / 4, nrt = (NR + TR - 1) / TR;
-          float2* band = reinterpret_cast<float2*>(smem + a.o_band);
-          for (int base = 0; base < nrt * mq; base += NT) {
-          // rows of this round's tiles, and the band of Z_s rows their gathers read
           const float2* zg = zc;
-          if (a.band_rows > 0) {
-            const int rt0 = base / mq, rt1 = min(nrt, (base + NT - 1) / mq + 1);
-            const int blo = max(0, r_lo + rt0 * TR - a.halo), bhi = min(N, min(r_hi, r_lo + rt1 * TR) + a.halo);
-            if (bhi - blo <= a.band_rows) {   // the host sized the band for every round
-              const float4* src = reinterpret_cast<const float4*>(zc + (size_t)blo * Mp);
-              float4* dst = reinterpret_cast<float4*>(band);
-              for (int i = tid; i < (bhi - blo) * Mp / 2; i += NT) dst[i] = src[i];
-              zg = band - (size_t)blo * Mp;   // row n of Z_s at zg + n Mp, for blo <= n < bhi
-            }
-            __syncthreads();
-          }
-          const int tile = base + tid;
-          if (tile < nrt * mq) {
+          for (int tile = tid; tile < nrt * mq; tile += NT) {
             const int rt = tile / mq, m0 = (tile - rt * mq) * 4, l0 = r_lo + rt * TR;
             float cmx[4] = {0.f, 0.f, 0.f, 0.f};   // column maxima of the rows written (tensor-core Gram)
             float2 f[TR][4];
@@ -1075,7 +1074,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                 // detunings), then the other entries of the row
                 const float4 dg = a.diag_a[l0 + r];
                 float2 z[4];
-                load4(zg + (size_t)(l0 + r) * Mp + m0, z);
+                load4w(zg + (size_t)(l0 + r) * Mp + m0, z);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                   f[r][u].x = fmaf(dg.x, z[u].x, fmaf(-dg.y, z[u].y, fmaf(dg.z, z[u].x, -dg.w * z[u].y)));
@@ -1165,7 +1164,7 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
                   }
                 }
               }
-              store4(zo_buf + (size_t)n * Mp + m0, zo);
+              store4w(zo_buf + (size_t)n * Mp + m0, zo);
               if constexpr (GTC)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) cmx[u] = fmaxf(cmx[u], fmaxf(fabsf(zo[u].x), fabsf(zo[u].y)));
@@ -1174,8 +1173,6 @@ __global__ void __launch_bounds__(NT, 1) sf_kernel(const Args a) {
 #pragma unroll
               for (int u = 0; u < 4; ++u)
                 if (m0 + u < 20) atomicMax(&gcmax[gpar ^ 1][m0 + u], __float_as_uint(cmx[u]));
-          }
-          if (a.band_rows > 0) __syncthreads();   // the next round refills the band
           }
           cur ^= 1;
           gpar ^= 1;

@@ -408,32 +408,3 @@ def test_fused_gram_on_tensor_cores(monkeypatch, dims, n_steps):
     if dims[0] == 10:   # the oracle at the small size, tensor-core Gram
         monkeypatch.setenv("LR_SPARSE_GRAM", "tc")
         _run(dims, 20, pulses, 0.4, 5e-4, n_steps, 40, [0, 3], P, precision="fp32_g64")
-
-
-@pytest.mark.parametrize("n_traj", [4, "grid"])
-def test_fused_band_staging_is_bitwise(monkeypatch, n_traj):
-    """Phase F can stage the band of Z_s rows its operator gathers read (the
-    round's rows +- the bandwidth of A, 40 rows for the paper's model) in
-    shared memory (LR_SPARSE_BAND=1): the same values from another memory, so
-    the results equal bitwise those of gathers from L2 (the default), on teams
-    of CTAs (4 trajectories) and on the equal-span schedule (more trajectories
-    than SMs)."""
-    import torch
-    from paper_2508_18114_gb300 import sparse
-    P = _params()
-    model = sparse.paper_model(100, 4, 5, **P)
-    T = 4 if n_traj == 4 else torch.cuda.get_device_properties(0).multi_processor_count + 8
-    pulses = [(0, [TP * (0.05 + 0.2 * ((5 * j) % 7) / 6.0), P["wd"], 0.05, 0.0]) for j in range(T)]
-    out = {}
-    for mode in ("1", "0"):
-        monkeypatch.setenv("LR_SPARSE_BAND", mode)
-        b = sparse.SparseBatch(model, 20, pulses, 0.2, 40, pop_every=10, precision="fp32_g64")
-        b.set_initial([j % 2 for j in range(T)], SEED, EPS)
-        b.integrate(5e-4, 17)
-        b.integrate(5e-4, 13)
-        out[mode] = (b.observables(), b.get_state())
-        del b
-    (o1, z1), (o0, z0) = out["1"], out["0"]
-    assert np.array_equal(o1["beta"][:, :31], o0["beta"][:, :31])
-    assert np.array_equal(o1["pops"][:, :4], o0["pops"][:, :4])
-    assert np.array_equal(z1, z0)
