@@ -425,13 +425,15 @@ def run_ours(args):
     # the trajectory-steps of one launch; only for the kernels those captures measured:
     # double-word Gram 0.338 GB read + 1.586 GB written for 760 trajectory-steps (2.532 MB),
     # tensor-core Gram 3.015 MB (TRAFFIC_GRAM_TC)
-    traffic = None
+    # Those captures predate the 32-byte stage-state accesses of the current kernel, so the
+    # line's traffic is null and the last capture's figure is reported beside it.
+    traffic, traffic_last = None, None
     if (wl.name == "c4" and prec == "fp32_g64" and engine == "fused" and info.team_size == 2
             and not info.stage_in_smem and info.tensor_passes == 0):
         per = TRAFFIC_GRAM_TC if info.gram_tc else 2.532e6
-        traffic = per * ntraj * chunk if per else None
+        traffic_last = per * ntraj * chunk if per else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic,
+                "traffic": traffic, "traffic_last_capture": traffic_last,
                 "kernel": "integrate (%s engine)" % engine,
                 "peak_source": "%s pipe: 152 SMs x %d FMA/clk x 2 x %.0f MHz sampled SM clock (unit counts)"
                                % (pipe, FP64_FMA_PER_CLK if prec == "fp64" else FP32_FMA_PER_CLK, mhz),

@@ -255,11 +255,15 @@ __device__ __forceinline__ void warp_reduce_scatter(V (&v)[NV], int lane) {
 template <int ZSM, typename T2>
 __device__ __forceinline__ void load4(const T2* p, T2 (&v)[4]) {
   if constexpr (ZSM == 0 && sizeof(T2) == 8) {
-    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
-    v[0] = cm<T2>(x.x, x.y);
-    v[1] = cm<T2>(x.z, x.w);
-    v[2] = cm<T2>(y.x, y.y);
-    v[3] = cm<T2>(y.z, y.w);
+    // FP32 stage state in global memory: one 32-byte access (rows of Mp = 4j
+    // complex64 entries from a 256-byte aligned region, column quads m0 = 4i)
+    float x[8];
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
+                 : "l"(p)
+                 : "memory");
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = cm<T2>(x[2 * u], x[2 * u + 1]);
   } else {
 #pragma unroll
     for (int u = 0; u < 4; ++u) v[u] = p[u];
@@ -268,8 +272,9 @@ __device__ __forceinline__ void load4(const T2* p, T2 (&v)[4]) {
 template <int ZSM, typename T2>
 __device__ __forceinline__ void store4(T2* p, const T2 (&v)[4]) {
   if constexpr (ZSM == 0 && sizeof(T2) == 8) {
-    reinterpret_cast<float4*>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-    reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0].x), "f"(v[0].y),
+                 "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y)
+                 : "memory");
   } else {
 #pragma unroll
     for (int u = 0; u < 4; ++u) p[u] = v[u];
